@@ -1,0 +1,368 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself.
+
+Each test checks the oracle against a closed form, a textbook/library solution, an
+exhaustive enumeration, an inequality of the paper, or a hand-derived value, chosen so
+that a dropped term, a wrong sign, a wrong index or a transposed operand fails.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+from scipy.optimize import minimize
+
+import oracle as O
+from inputs import nesterov_lasso, random_lasso, ncquad_problem
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _prob(A, b, lam, **kw):
+    return O.Problem(A=np.asarray(A, float), b=np.asarray(b, float), lam=lam, **kw)
+
+
+# ---------------------------------------------------------------- soft threshold
+
+def test_soft_threshold_hand_values():
+    # Hand-computed values of sign(v) max(|v| - t, 0), including the tie |v| = t.
+    with open(os.path.join(GOLDEN, "soft_threshold.json")) as f:
+        cases = json.load(f)["cases"]
+    for v, t, want in cases:
+        assert O.soft(v, t) == want
+
+
+# ---------------------------------------------------------------- orthogonal designs
+
+def test_diagonal_design_closed_form():
+    """A = diag(s): min 0.5 (s_j x_j - b_j)^2 + lam |x_j| has x_j = soft(s_j b_j, lam) / s_j^2."""
+    rng = np.random.default_rng(1)
+    n = 9
+    s = rng.uniform(0.5, 3.0, n) * rng.choice([-1, 1], n)
+    b = rng.standard_normal(n) * 2
+    lam = 0.7
+    want = np.sign(s * b) * np.maximum(np.abs(s * b) - lam, 0) / s ** 2
+    p = _prob(np.diag(s), b, lam)
+    d = O.surrogate_weights(p)
+    # One Jacobi sweep with gamma = 1 from any start is exact for a diagonal Gram matrix.
+    x0 = rng.standard_normal(n)
+    x, _ = O.jacobi_sweep(p, x0, O.residual(p, x0), d, 1.0)
+    np.testing.assert_allclose(x, want, rtol=0, atol=1e-14)
+    # Same for Gauss-Seidel with blocks of 4.
+    x2, _ = O.gauss_seidel_sweep(p, x0, O.residual(p, x0), d, 1.0, w=4)
+    np.testing.assert_allclose(x2, want, rtol=0, atol=1e-14)
+
+
+def test_identity_design_with_box_closed_form():
+    """A = I with box [lo, hi]: the separable minimiser is clip(soft(b, lam), lo, hi)."""
+    rng = np.random.default_rng(2)
+    n = 12
+    b = rng.standard_normal(n) * 3
+    lo = -rng.uniform(0.1, 2, n)
+    hi = rng.uniform(0.1, 2, n)
+    lo[0], hi[0] = 0.5, 1.5       # box excluding 0
+    lo[1], hi[1] = -1.5, -0.25
+    lam = 0.8
+    want = np.clip(np.sign(b) * np.maximum(np.abs(b) - lam, 0), lo, hi)
+    p = _prob(np.eye(n), b, lam, lo=lo, hi=hi)
+    x, _ = O.jacobi_sweep(p, np.zeros(n), O.residual(p, np.zeros(n)), O.surrogate_weights(p), 1.0)
+    np.testing.assert_allclose(x, want, atol=1e-15)
+
+
+# ---------------------------------------------------------------- best response
+
+@pytest.mark.parametrize("seed", range(6))
+def test_best_response_matches_grid_minimisation(seed):
+    rng = np.random.default_rng(seed)
+    for _ in range(20):
+        x = rng.standard_normal() * 2
+        g = rng.standard_normal() * 3
+        d = rng.uniform(0.1, 4)
+        lam = rng.uniform(0, 2)
+        lo, hi = sorted(rng.uniform(-3, 3, 2))
+        if rng.random() < 0.3:
+            lo, hi = -np.inf, np.inf
+        phi = lambda y: g * (y - x) + 0.5 * d * (y - x) ** 2 + lam * np.abs(y)  # noqa: E731
+        a = max(lo, -20.0)
+        b = min(hi, 20.0)
+        grid = np.linspace(a, b, 400001)
+        ybest = grid[np.argmin(phi(grid))]
+        got = float(O.best_response(x, g, d, lam, lo, hi))
+        assert abs(got - ybest) <= 2 * (b - a) / 400000
+        assert phi(got) <= phi(ybest) + 1e-12
+
+
+def test_best_response_zero_weight_rule():
+    # d = 0 (a zero column without proximal term) -> clip(0, lo, hi)
+    assert O.best_response(1.0, 0.0, 0.0, 1.0, -1, 1) == 0.0
+    assert O.best_response(1.0, 0.0, 0.0, 1.0, 0.5, 1) == 0.5
+
+
+# ---------------------------------------------------------------- whole-solver pins
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_gs_limit_equals_brute_force_lasso(seed):
+    d = random_lasso(30, 7, seed=seed, lam=0.9)
+    p = O.Problem.from_data(d)
+    sols = O.brute_force_lasso(p.A, p.b, p.lam)
+    assert len(sols) == 1
+    x, F, _ = O.solve_gs(p, gamma=1.0, w=1, max_sweeps=5000, tol=1e-15)
+    np.testing.assert_allclose(x, sols[0], atol=1e-8)
+    assert O.kkt_violation(p, sols[0]) < 1e-10
+
+
+def test_gs_limit_matches_scipy_bound_constrained_qp():
+    """LASSO as a smooth bound-constrained problem in (u, v) >= 0, x = u - v (L-BFGS-B)."""
+    d = random_lasso(40, 12, seed=5, lam=0.5)
+    p = O.Problem.from_data(d)
+    A, b, lam = p.A, p.b, p.lam
+    n = p.n
+
+    def fun(z):
+        x = z[:n] - z[n:]
+        r = A @ x - b
+        g = A.T @ r
+        return 0.5 * r @ r + lam * z.sum(), np.concatenate([g + lam, -g + lam])
+
+    res = minimize(fun, np.zeros(2 * n), jac=True, method="L-BFGS-B",
+                   bounds=[(0, None)] * (2 * n), options=dict(ftol=1e-15, gtol=1e-12, maxiter=20000))
+    x_ref = res.x[:n] - res.x[n:]
+    x, F, _ = O.solve_gs(p, gamma=0.9, w=3, max_sweeps=20000, tol=1e-15)
+    np.testing.assert_allclose(x, x_ref, atol=1e-6)
+    assert abs(F - res.fun) <= 1e-9 * abs(res.fun)
+
+
+def test_least_squares_special_case():
+    """lam = 0, no box, full column rank: the limit is the least-squares solution."""
+    d = random_lasso(50, 10, seed=3, lam=0.0)
+    p = O.Problem.from_data(d)
+    x_ls = np.linalg.lstsq(p.A, p.b, rcond=None)[0]
+    x, _, _ = O.solve_gs(p, gamma=1.0, w=2, max_sweeps=20000, tol=1e-16)
+    np.testing.assert_allclose(x, x_ls, atol=1e-9)
+
+
+def test_planted_nesterov_optimum():
+    d = nesterov_lasso(60, 200, 10, lam=1.0, seed=0)
+    p = O.Problem.from_data(d)
+    xs = d["x_star"]
+    # generator: residual at x* is -y*, so F(x*) equals the closed form
+    np.testing.assert_allclose(O.residual(p, xs), -d["y_star"], atol=1e-12)
+    assert abs(O.objective(p, xs) - d["f_star"]) <= 1e-12 * d["f_star"]
+    assert O.kkt_violation(p, xs) < 1e-11
+    # GS from 0 reaches the planted optimum
+    x, F, _ = O.solve_gs(p, gamma=0.9, w=1, max_sweeps=20000, tol=1e-16)
+    assert (F - d["f_star"]) / d["f_star"] < 1e-12
+    np.testing.assert_allclose(x, xs, atol=1e-7)
+
+
+def test_planted_optimum_fp32_storage_gap_is_tiny():
+    """With FP32 storage the planted x* stays optimal up to ~1e-10 relative in F."""
+    d = nesterov_lasso(80, 300, 12, lam=1.0, seed=4, store_dtype=np.float32)
+    p = O.Problem.from_data(d)
+    x, F, _ = O.solve_gs(p, x0=d["x_star"], gamma=1.0, w=1, max_sweeps=2000, tol=1e-16)
+    F_xs = O.objective(p, d["x_star"])
+    assert F <= F_xs + 1e-12 * F_xs
+    assert (F_xs - F) / F < 1e-9
+    assert abs(F_xs - d["f_star"]) / d["f_star"] < 1e-6
+
+
+# ---------------------------------------------------------------- paper inequalities
+
+@pytest.mark.parametrize("loss", ["lasso", "ncquad"])
+def test_proposition1_descent_inequality(loss):
+    """(x^_i - y_i)^T grad_i f(y) + g_i(x^_i) - g_i(y_i) <= -c ||x^_i - y_i||^2 (Prop. 1)."""
+    rng = np.random.default_rng(7)
+    if loss == "lasso":
+        d = random_lasso(25, 16, seed=7, lam=0.4, box=1.0)
+        p = O.Problem.from_data(d)
+    else:
+        d = ncquad_problem(40, 16, seed=7)
+        p = O.Problem.from_data(d, loss="ncquad")
+    dw = O.surrogate_weights(p, tau=0.3)
+    lo, hi = p.lo_or_inf(), p.hi_or_inf()
+    for _ in range(50):
+        y = np.clip(rng.standard_normal(p.n), lo, hi)
+        g = O.gradient(p, y)
+        for cols in O.block_ranges(p.n, 4):
+            xh = O.best_response(y[cols], g[cols], dw[cols], p.lam, lo[cols], hi[cols])
+            lhs = (xh - y[cols]) @ g[cols] + p.lam * (np.abs(xh).sum() - np.abs(y[cols]).sum())
+            c = dw[cols].min()
+            assert lhs <= -c * np.sum((xh - y[cols]) ** 2) + 1e-10
+
+
+def test_sequential_descent_bound():
+    """Delay 0: F(x+) <= F(x) - gamma (d_j - gamma kappa_j / 2) |x^_j - x_j|^2 per update."""
+    d = random_lasso(30, 20, seed=8, lam=0.3)
+    p = O.Problem.from_data(d)
+    kap = O.coord_curvature(p)
+    dw = O.surrogate_weights(p, tau=0.1)
+    x = np.zeros(p.n)
+    r = O.residual(p, x)
+    gamma = 0.9
+    for sweep in range(5):
+        for j in range(p.n):
+            F0 = O.objective(p, x)
+            xn, r = O.gauss_seidel_sweep(p, x, r, dw, gamma, w=1, order=[j])
+            step = (xn[j] - x[j]) / gamma
+            F1 = O.objective(p, xn)
+            assert F1 <= F0 - gamma * (dw[j] - gamma * kap[j] / 2) * step ** 2 + 1e-10
+            x = xn
+
+
+def test_jacobi_descends_with_safe_tau():
+    d = random_lasso(40, 60, seed=9, lam=0.2)
+    p = O.Problem.from_data(d)
+    gamma = 0.9
+    tr = O.jacobi_tau_rel(p, gamma)
+    dw = O.surrogate_weights(p, tau_rel=tr)
+    x = np.zeros(p.n)
+    r = O.residual(p, x)
+    F = O.objective(p, x)
+    for _ in range(40):
+        x, r = O.jacobi_sweep(p, x, r, dw, gamma)
+        Fn = O.objective(p, x)
+        assert Fn <= F + 1e-12
+        F = Fn
+
+
+def test_coordinate_descent_is_exact_coordinate_minimisation():
+    """w = 1, tau = 0, gamma = 1: after the update the coordinate satisfies its 1-D optimality."""
+    d = random_lasso(20, 15, seed=10, lam=0.5)
+    p = O.Problem.from_data(d)
+    dw = O.surrogate_weights(p)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(p.n)
+    r = O.residual(p, x)
+    for j in range(p.n):
+        x, r = O.gauss_seidel_sweep(p, x, r, dw, 1.0, w=1, order=[j])
+        gj = p.A[:, j] @ (p.A @ x - p.b)
+        if x[j] == 0:
+            assert abs(gj) <= p.lam + 1e-12
+        else:
+            assert abs(gj + p.lam * np.sign(x[j])) < 1e-12
+
+
+@pytest.mark.parametrize("loss", ["lasso", "ncquad"])
+def test_scalar_update_minimises_objective_along_coordinate(loss):
+    """tau = 0, gamma = 1, w = 1: the surrogate is f restricted to x_j, so the update is
+    the exact minimiser of F along coordinate j within the box (grid search of F)."""
+    d = ncquad_problem(20, 8, seed=21, lam_frac=0.2)
+    p = O.Problem.from_data(d, loss=loss)
+    dw = O.surrogate_weights(p)
+    assert np.all(dw > 0)
+    rng = np.random.default_rng(4)
+    x = rng.uniform(-1, 1, p.n)
+    r = O.residual(p, x)
+    for j in range(p.n):
+        x, r = O.gauss_seidel_sweep(p, x, r, dw, 1.0, w=1, order=[j])
+        grid = np.linspace(-1, 1, 200001)
+        vals = []
+        for t in grid[::50]:
+            z = x.copy()
+            z[j] = t
+            vals.append(O.objective(p, z))
+        t0 = grid[::50][int(np.argmin(vals))]
+        fine = np.linspace(max(-1, t0 - 1e-3), min(1, t0 + 1e-3), 2001)
+        best = np.inf
+        for t in fine:
+            z = x.copy()
+            z[j] = t
+            best = min(best, O.objective(p, z))
+        assert O.objective(p, x) <= best + 1e-10
+
+
+def test_delay_zero_equals_gauss_seidel():
+    d = random_lasso(25, 30, seed=11, lam=0.3)
+    p = O.Problem.from_data(d)
+    dw = O.surrogate_weights(p, tau=0.5)
+    x0 = np.zeros(p.n)
+    r0 = O.residual(p, x0)
+    xa, _ = O.delayed_sweeps(p, x0, r0, dw, 0.8, 4, 0, 3, np.random.default_rng(0))
+    xb, rb = x0, r0
+    for _ in range(3):
+        xb, rb = O.gauss_seidel_sweep(p, xb, rb, dw, 0.8, w=4)
+    np.testing.assert_allclose(xa, xb, atol=1e-14)
+
+
+def test_delayed_sweeps_use_stale_residual():
+    """With a fixed delay of one update the result differs from GS but still converges."""
+    d = random_lasso(30, 24, seed=12, lam=0.3)
+    p = O.Problem.from_data(d)
+    dw = O.surrogate_weights(p, tau=1.0)
+    x_ref = O.brute_force_lasso(p.A[:, :8], p.b, p.lam)  # smoke of enumeration size
+    assert len(x_ref) == 1
+    x0 = np.zeros(p.n)
+    xg, _ = O.gauss_seidel_sweep(p, x0, O.residual(p, x0), dw, 0.9, w=2)
+    xd, _ = O.delayed_sweeps(p, x0, O.residual(p, x0), dw, 0.9, 2, 3, 1, np.random.default_rng(1))
+    assert np.abs(xg - xd).max() > 1e-6
+    xd, _ = O.delayed_sweeps(p, x0, O.residual(p, x0), dw, 0.9, 2, 3, 400, np.random.default_rng(1))
+    xs, Fs, _ = O.solve_gs(p, gamma=1.0, max_sweeps=20000, tol=1e-16)
+    assert abs(O.objective(p, xd) - Fs) <= 1e-9 * abs(Fs)
+
+
+# ---------------------------------------------------------------- optimality measures
+
+def test_gradient_matches_finite_differences():
+    for loss in ("lasso", "ncquad"):
+        d = ncquad_problem(30, 12, seed=13)
+        p = O.Problem.from_data(d, loss=loss)
+        x = np.random.default_rng(1).standard_normal(p.n)
+
+        def fsmooth(z):
+            r = p.A @ z - p.b
+            return 0.5 * r @ r if loss == "lasso" else r @ r - p.c * z @ z
+
+        h = 1e-6
+        fd = np.array([(fsmooth(x + h * e) - fsmooth(x - h * e)) / (2 * h) for e in np.eye(p.n)])
+        np.testing.assert_allclose(O.gradient(p, x), fd, rtol=1e-6, atol=1e-6)
+
+
+def test_mf_zero_exactly_at_stationary_points_box():
+    d = random_lasso(12, 5, seed=14, lam=0.3, box=0.6)
+    p = O.Problem.from_data(d)
+    pts = O.stationary_points_box(p)
+    assert len(pts) == 1            # convex: unique
+    assert O.stationarity(O.mf_measure(p, pts[0]), pts[0]) < 1e-10
+    x, _, _ = O.solve_gs(p, gamma=1.0, max_sweeps=20000, tol=1e-16)
+    np.testing.assert_allclose(x, pts[0], atol=1e-8)
+    rng = np.random.default_rng(0)
+    for _ in range(10):
+        y = np.clip(rng.standard_normal(p.n), -0.6, 0.6)
+        if np.abs(y - pts[0]).max() > 1e-3:
+            assert O.stationarity(O.mf_measure(p, y), y) > 1e-6
+
+
+def test_ncquad_limits_are_enumerated_stationary_points():
+    d = ncquad_problem(6, 5, seed=15, lam_frac=0.05)
+    p = O.Problem.from_data(d, loss="ncquad")
+    kap = O.coord_curvature(p)
+    assert np.all(kap > 0)
+    pts = O.stationary_points_box(p)
+    assert len(pts) >= 1
+    for pt in pts:
+        assert O.stationarity(O.mf_measure(p, pt), pt) < 1e-9
+        assert O.stationarity(O.xhat_merit(p, pt, O.surrogate_weights(p)), pt) < 1e-9
+    rng = np.random.default_rng(3)
+    for trial in range(6):
+        x0 = rng.uniform(-1, 1, p.n)
+        x, F, _ = O.solve_gs(p, x0=x0, gamma=0.9, w=1, max_sweeps=50000, tol=1e-16)
+        dist = min(np.abs(x - pt).max() for pt in pts)
+        assert dist < 1e-6, (trial, x, pts)
+
+
+def test_lambda_max_gram_matches_eigvalsh():
+    d = random_lasso(30, 20, seed=16)
+    p = O.Problem.from_data(d)
+    kap = O.coord_curvature(p)
+    M = (p.A / np.sqrt(kap)).T @ (p.A / np.sqrt(kap))
+    want = np.linalg.eigvalsh(M).max()
+    assert abs(O.lambda_max_gram(p.A, kap, iters=2000) - want) < 1e-8 * want
+
+
+def test_kkt_violation_detects_perturbation():
+    d = nesterov_lasso(40, 100, 5, seed=17)
+    p = O.Problem.from_data(d)
+    xs = d["x_star"].copy()
+    assert O.kkt_violation(p, xs) < 1e-11
+    xs[d["support"][0]] *= 1.01
+    assert O.kkt_violation(p, xs) > 1e-4
