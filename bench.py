@@ -1,0 +1,439 @@
+"""Benchmark: AsyFLEXA on the 20000 x 100000 FP32 planted LASSO (blocks of 32 columns).
+
+One step = one solve from x = 0 with the asynchronous persistent-CTA mode until the
+relative objective gap is <= 1e-6 and the stationarity merit ||xhat(x) - x||_inf /
+max(1, ||x||_inf) is <= 1e-6 (every row of the hot path: block pick, stale residual read,
+panel gradient, best response, fixed step, atomic scatter, counters, exact refresh and
+checks).  Inputs are resident in HBM before the timed region (A is 8 GB, larger than L2,
+so no L2 flush is needed).
+
+Printed JSON line (rank 0): value = block-updates/s of the whole job, ms_per_step = time
+to the 1e-6 gap, plus roofline (the async sweep kernel, timed live with CUDA events on its
+stream), e2e (host buffers through the public API), the synchronous Jacobi mode on the
+same instance, the oracle CPU baseline on a bounded sample, clocks sampled during the
+timed region and the kernel-launch count.
+
+--impl reference times the FP64 CPU oracle (the reference arm of this tier) on a bounded
+sample of the same workload and prints the same kind of line with "impl": "reference".
+Under torchrun with N > 1 each rank solves its own instance (independent replicas: the
+path is not sharded), reported as weak scaling.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-6 rel. gap & block-updates/s, async vs sync vs oracle, % HBM peak"
+M, N, K_PLANT, LAM, W_BLOCK, GAMMA = 20000, 100000, 1000, 1.0, 32, 0.9
+WORKLOAD = "lasso_nesterov_20000x100000_fp32_w32"
+SWEEP_SOURCES = ["sweep.cuh", "ptx.cuh", "types.cuh"]
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def sweep_kernel_digest() -> str:
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, "paper_1701_04900_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic():
+    """DRAM bytes per sweep of the async sweep kernel from a committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "sweep_async_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_digest") != sweep_kernel_digest():
+        return None
+    return d
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sms.append(float(parts[0]))
+                maxs.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sms:
+            return None
+        sms.sort()
+        return {"sm_mhz": sms[len(sms) // 2], "sm_max_mhz": max(maxs), "samples": len(sms),
+                "reasons": sorted(reasons)}
+
+
+def cpu_oracle_sample(At_sample, b_sample, lam, seconds: float, cores: int):
+    """Time the FP64 oracle's cyclic Gauss-Seidel sweeps (w = 32) on a column sample, in a
+    fresh interpreter with the BLAS thread count set to ``cores``."""
+    import numpy as np
+    with tempfile.TemporaryDirectory() as d:
+        np.save(os.path.join(d, "At.npy"), At_sample)
+        np.save(os.path.join(d, "b.npy"), b_sample)
+        code = f"""
+import sys, time, json
+sys.path.insert(0, {ROOT!r})
+import numpy as np
+import oracle as O
+At = np.load({os.path.join(d, 'At.npy')!r}); b = np.load({os.path.join(d, 'b.npy')!r})
+m = b.shape[0]
+p = O.Problem(A=At[:, :m].astype(np.float64).T, b=b.astype(np.float64), lam={lam})
+dw = O.surrogate_weights(p)
+x = np.zeros(p.n); r = O.residual(p, x)
+nb = len(O.block_ranges(p.n, {W_BLOCK}))
+t0 = time.perf_counter(); sweeps = 0
+while True:
+    x, r = O.gauss_seidel_sweep(p, x, r, dw, {GAMMA}, w={W_BLOCK})
+    sweeps += 1
+    el = time.perf_counter() - t0
+    if el >= {seconds}:
+        break
+print(json.dumps({{"block_updates": sweeps * nb, "seconds": el, "sweeps": sweeps, "blocks": nb}}))
+"""
+        env = dict(os.environ)
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[v] = str(cores)
+        res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+        if res.returncode != 0:
+            raise RuntimeError(res.stderr)
+        return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def planted_f_ref(gen):
+    """F(x*) on the stored (FP32) data, in FP64 on the host from the support columns."""
+    import numpy as np
+    sup = gen["support"].cpu().numpy()
+    As = gen["At"][gen["support"], :M].double().cpu().numpy()
+    xs = gen["x_star"].cpu().numpy()[sup]
+    r = As.T @ xs - gen["b"].double().cpu().numpy()
+    return 0.5 * float(r @ r) + LAM * float(np.abs(xs).sum())
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import torch
+    cores = os.cpu_count() or 1
+    ncols = 3200
+    gen = nesterov_lasso_cpu_sample(ncols)
+    At = gen["At"].numpy()
+    b = gen["b"].numpy()
+    per_step = max(2.0, min(20.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(At, b, LAM, min(per_step, 2.0), cores)
+    tot_bu, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(At, b, LAM, per_step, cores)
+        tot_bu += r["block_updates"]
+        tot_s += r["seconds"]
+    val = tot_bu / tot_s
+    sample = (f"cyclic Gauss-Seidel sweeps (w={W_BLOCK}, FP64 numpy) over the first {ncols} of {N} columns "
+              f"({ncols // W_BLOCK} blocks) of the {M}x{N} instance, ~{per_step:.0f} s per step")
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "block-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": bench_config(world),
+            "cpu_baseline": {"value": val, "unit": "block-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": "block-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    del torch
+    print(json.dumps(line), flush=True)
+
+
+def nesterov_lasso_cpu_sample(ncols):
+    from inputs import nesterov_lasso_torch
+    return nesterov_lasso_torch(M, N, K_PLANT, lam=LAM, seed=0, device="cpu", n_generate=ncols)
+
+
+def bench_config(world):
+    return {"workload": WORKLOAD, "m": M, "n": N, "planted_nonzeros": K_PLANT, "lambda": LAM,
+            "block_w": W_BLOCK, "blocks": math.ceil(N / W_BLOCK), "gamma": GAMMA, "mode": "async",
+            "tol_gap": 1e-6, "tol_stat": 1e-6, "x0": "zeros", "generator": "Nesterov-style planted LASSO, seed=rank",
+            "l2": "no flush: A (8 GB) is larger than L2 and streamed every sweep",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_1701_04900_gb300.build import build_library
+    build_library()
+    from paper_1701_04900_gb300 import Solver
+    from inputs import nesterov_lasso_torch
+
+    gen = nesterov_lasso_torch(M, N, K_PLANT, lam=LAM, seed=rank, device="cuda")
+    f_ref = planted_f_ref(gen)
+    At, b = gen["At"], gen["b"]
+    refresh_every, check_every = args.refresh_every, args.check_every
+    s = Solver(At, b, LAM, m=M, block_w=W_BLOCK, mode="async", gamma=GAMMA, refresh_every=refresh_every,
+               check_every=check_every, max_sweeps=args.max_sweeps, f_star=f_ref, profile=True)
+    x = torch.zeros(N, dtype=torch.float32, device="cuda")
+
+    def one_step():
+        x.zero_()
+        return s.solve(x)
+
+    for _ in range(args.warmup):
+        one_step()
+    s.reset_counters()
+    launches0 = s.read_counters()["kernel_launches"]
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    stats = [one_step() for _ in range(args.steps)]
+    ev1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    ctr = s.read_counters()
+    launches = ctr["kernel_launches"] - launches0
+    bu = sum(st["block_updates"] for st in stats)
+    if world > 1:
+        t = torch.tensor([elapsed, float(bu)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
+        elapsed_all, bu_all = float(tmax[0]), float(t[1])
+    else:
+        elapsed_all, bu_all = elapsed, float(bu)
+
+    # roofline of the dominant kernel: the async sweep kernel, timed live with CUDA events
+    # recorded on its own stream by the library (profile=True)
+    peak, peak_kind = measured_peaks()
+    alg_bytes_per_sweep = N * M * 4 + N * (4 + 4 + 8)
+    sk_launches = max(1, ctr["sweep_kernel_launches"])
+    avg_launch_s = ctr["sweep_kernel_seconds"] / sk_launches
+    sweeps_per_launch = ctr["sweep_kernel_sweeps"] / sk_launches
+    achieved = alg_bytes_per_sweep * sweeps_per_launch / avg_launch_s / 1e9
+    tr = profile_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": (tr["dram_bytes_per_sweep"] * sweeps_per_launch if tr else None),
+                "kernel": "sweep_kernel<float, async>", "peak_kind": peak_kind,
+                "avg_launch_ms": avg_launch_s * 1e3, "sweeps_per_launch": sweeps_per_launch,
+                "algorithmic_bytes_per_sweep": alg_bytes_per_sweep,
+                "share_of_step_time": ctr["sweep_kernel_seconds"] / elapsed}
+
+    last = stats[-1]
+    result = {"metric": METRIC, "value": bu_all / elapsed_all, "unit": "block-updates/s", "n_gpus": world,
+              "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed_all / args.steps,
+              "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+              "data": "synthetic (Nesterov-style planted LASSO generated on the device)",
+              "config": bench_config(world),
+              "time_to_gap_s": elapsed / args.steps, "sweeps_to_gap": last["sweeps"],
+              "rel_gap": last["rel_gap"], "stat_xhat": last["stat_xhat"], "stat_mf": last["stat_mf"],
+              "kkt_viol": last["kkt_viol"], "nnz": last["nnz"], "status": last["status"],
+              "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
+              "staleness_hist": ctr["staleness_hist"]}
+
+    if rank == 0 and not args.no_sync:
+        result["sync"] = run_sync(gen, f_ref, args)
+    if rank == 0 and not args.no_e2e:
+        result["e2e"] = run_e2e(gen, f_ref, args, refresh_every, check_every)
+    if rank == 0 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        ncols = 3200
+        At_s = At[:ncols].cpu().numpy()
+        b_s = b.cpu().numpy()
+        r = cpu_oracle_sample(At_s, b_s, LAM, args.cpu_seconds, cores)
+        result["cpu_baseline"] = {
+            "value": r["block_updates"] / r["seconds"], "unit": "block-updates/s", "cores": cores, "kind": "oracle",
+            "sample": f"FP64 numpy cyclic Gauss-Seidel sweeps (w={W_BLOCK}) over the first {ncols} columns "
+                      f"({ncols // W_BLOCK} blocks) of this {M}x{N} instance for {r['seconds']:.1f} s "
+                      f"({r['sweeps']} sweeps)"}
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    s.close()
+    del np
+
+
+def run_sync(gen, f_ref, args):
+    """Deterministic Jacobi mode on the same instance, with the descent-safe relative
+    proximal weight 1 + tau_rel = (gamma/2) * lambda_max(K^-1/2 A^T A K^-1/2) * 1.01."""
+    import torch
+    from paper_1701_04900_gb300 import Solver
+    At = gen["At"]
+    kap = torch.empty(N, dtype=torch.float64, device="cuda")
+    for j0 in range(0, N, 8192):
+        kap[j0:j0 + 8192] = (At[j0:j0 + 8192, :M].double() ** 2).sum(dim=1)
+    sc = (1.0 / kap.sqrt()).float()
+    v = torch.randn(N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    v /= v.norm()
+    lmax = 0.0
+    for _ in range(40):
+        u = At[:, :M].T @ (sc * v)
+        wv = sc * (At[:, :M] @ u)
+        lmax = float(wv.norm())
+        v = wv / lmax
+    tau_rel = max(0.0, 0.5 * GAMMA * lmax * 1.01 - 1.0)
+    s = Solver(At, gen["b"], LAM, m=M, block_w=W_BLOCK, mode="sync", gamma=GAMMA, tau_rel=tau_rel,
+               refresh_every=args.refresh_every, check_every=args.check_every, max_sweeps=args.sync_sweeps,
+               f_star=f_ref, profile=True)
+    x = torch.zeros(N, dtype=torch.float32, device="cuda")
+    s.step(x, 2)  # warm-up
+    x.zero_()
+    s.refresh(x)
+    s.reset_counters()
+    st = s.solve(x)
+    ctr = s.read_counters()
+    s.close()
+    return {"mode": "sync (Jacobi)", "tau_rel": tau_rel, "lambda_max_normalized_gram": lmax,
+            "seconds": st["seconds"], "sweeps": st["sweeps"], "rel_gap": st["rel_gap"],
+            "stat_xhat": st["stat_xhat"], "status": st["status"],
+            "block_updates_per_s": st["block_updates"] / st["seconds"] if st["seconds"] else None,
+            "sweep_kernel_ms": 1e3 * ctr["sweep_kernel_seconds"] / max(1, ctr["sweep_kernel_launches"]),
+            "reached_1e-6": bool(st["status"] == 0)}
+
+
+def run_e2e(gen, f_ref, args, refresh_every, check_every):
+    """Same metric through the public API from pinned host buffers: every step copies A, b
+    and x0 host->device, creates the solver (weights), solves, and copies x back."""
+    import torch
+    from paper_1701_04900_gb300 import Solver
+    At_h = gen["At"].cpu().pin_memory()
+    b_h = gen["b"].cpu().pin_memory()
+    x0_h = torch.zeros(N, dtype=torch.float32).pin_memory()
+    x_h = torch.empty(N, dtype=torch.float32).pin_memory()
+    At_d = gen["At"]          # same contents: the copy overwrites with identical data
+    b_d = torch.empty_like(gen["b"])
+    x_d = torch.empty(N, dtype=torch.float32, device="cuda")
+    h2d = At_h.numel() * 4 + b_h.numel() * 4 + x0_h.numel() * 4
+    d2h = x_h.numel() * 4
+    steps = max(1, min(args.steps, 3))
+
+    def step():
+        At_d.copy_(At_h, non_blocking=True)
+        b_d.copy_(b_h, non_blocking=True)
+        x_d.copy_(x0_h, non_blocking=True)
+        s = Solver(At_d, b_d, LAM, m=M, block_w=W_BLOCK, mode="async", gamma=GAMMA, refresh_every=refresh_every,
+                   check_every=check_every, max_sweeps=args.max_sweeps, f_star=f_ref)
+        st = s.solve(x_d)
+        x_h.copy_(x_d, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        s.close()
+        return st
+
+    step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bu = 0
+    for _ in range(steps):
+        bu += step()["block_updates"]
+    el = time.perf_counter() - t0
+    return {"value": bu / el, "unit": "block-updates/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "steps": steps, "seconds_per_step": el / steps}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--refresh-every", type=int, default=10)
+    ap.add_argument("--check-every", type=int, default=10)
+    ap.add_argument("--max-sweeps", type=int, default=2000)
+    ap.add_argument("--sync-sweeps", type=int, default=400)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-sync", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * asyflexa.h -- C ABI of the GB300 (sm_103a) AsyFLEXA block-update library.
+ *
+ * The library solves
+ *
+ *     minimise  F(x) = f(x) + lambda * ||x||_1   subject to  lo <= x <= hi      (eq. 1)
+ *
+ * with f one of
+ *     ASYFLEXA_LOSS_LASSO :  f(x) = 0.5 * ||A x - b||^2          (Section 4.2)
+ *     ASYFLEXA_LOSS_NCQUAD:  f(x) = ||A x - b||^2 - c * ||x||^2  (Section 4.3, nonconvex)
+ * by the fixed-stepsize AsyFLEXA iteration (Algorithm 1): a block of w columns reads a
+ * possibly stale residual r = A x - b, forms its gradient, takes the closed-form best
+ * response of the proximal-linear surrogate (eq. 2; soft-threshold then clip to the
+ * box) and steps  x_i <- x_i + gamma * (xhat_i - x_i)  (step S.4), after which
+ * r += A_i * Delta_i.
+ *
+ * Data layout: A is m x n column-major with leading dimension lda (elements); lda must
+ * be >= m and lda * sizeof(element) a multiple of 16 bytes, A itself 16-byte aligned.
+ * Vectors are dense and contiguous.
+ *
+ * Ownership: every pointer in asyflexa_problem and the x passed to solve/step/check are
+ * caller-owned DEVICE memory, borrowed (never freed) for the lifetime of the handle;
+ * the caller must keep them alive and unmodified (except x through this API) until
+ * asyflexa_destroy.  The handle owns its residual, weights and scratch.
+ *
+ * Streams: every call enqueues work on the stream given to asyflexa_create.
+ * asyflexa_step is asynchronous with respect to the host; asyflexa_solve,
+ * asyflexa_check and the getters synchronise that stream.
+ *
+ * Errors: every function returns an asyflexa_status.  Nothing throws across the ABI.
+ * A CUDA error or a device-side timeout is latched in the handle; asyflexa_last_error
+ * gives a message (per handle, or thread-local for a NULL handle).
+ */
+#ifndef ASYFLEXA_H
+#define ASYFLEXA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ASYFLEXA_ABI_VERSION 1
+
+typedef struct asyflexa_s* asyflexa_t;
+
+typedef enum {
+    ASYFLEXA_OK = 0,
+    ASYFLEXA_ENOTCONV = 1,      /* solve stopped at max_sweeps before meeting the tolerances */
+    ASYFLEXA_EINVAL = -1,       /* bad argument (null, misaligned, out of range, wrong dtype) */
+    ASYFLEXA_ECUDA = -2,        /* a CUDA runtime error (message in asyflexa_last_error) */
+    ASYFLEXA_ENOMEM = -3,       /* device allocation failed */
+    ASYFLEXA_ETIMEOUT = -4,     /* a bounded device-side wait expired; results invalid */
+    ASYFLEXA_ENONFINITE = -5,   /* NaN/Inf found in the objective or residual */
+    ASYFLEXA_EUNSUPPORTED = -6  /* valid request this build does not implement */
+} asyflexa_status;
+
+typedef enum { ASYFLEXA_LOSS_LASSO = 0, ASYFLEXA_LOSS_NCQUAD = 1 } asyflexa_loss;
+
+/* SYNC: deterministic Jacobi sweeps (every block from the same x; bit-reproducible).
+ * ASYNC: persistent CTAs, each owning a fixed set of blocks (Assumption D4), reading the
+ *        shared residual without locks and updating it with atomics (Algorithm 1 with
+ *        delays bounded by the number of updates in flight, Assumption D1). */
+typedef enum { ASYFLEXA_SYNC = 0, ASYFLEXA_ASYNC = 1 } asyflexa_mode;
+
+typedef enum {
+    ASYFLEXA_F64 = 0,
+    ASYFLEXA_F32 = 1,
+    ASYFLEXA_BF16 = 2,          /* A only, with per-column FP32 scales */
+    ASYFLEXA_FP8E4M3 = 3        /* A only, with per-column FP32 scales */
+} asyflexa_dtype;
+
+/* Problem data (eq. 1).  All pointers are device pointers owned by the caller. */
+typedef struct {
+    int64_t m;                  /* rows of A (>= 1) */
+    int64_t n;                  /* columns of A = number of variables (>= 1) */
+    int64_t lda;                /* leading dimension of A in elements (see layout above) */
+    int32_t a_dtype;            /* asyflexa_dtype of A */
+    int32_t x_dtype;            /* ASYFLEXA_F64 or ASYFLEXA_F32: type of x, b, lo, hi */
+    const void* A;              /* m x n column-major */
+    const float* col_scale;     /* length n: a_j = col_scale[j] * stored_j; BF16/FP8 only, else NULL */
+    const void* b;              /* length m */
+    const void* lo;             /* length n lower bounds, or NULL for -inf */
+    const void* hi;             /* length n upper bounds, or NULL for +inf */
+    double lambda;              /* weight of ||x||_1, >= 0 */
+    double c;                   /* NCQUAD concavity weight (ignored for LASSO) */
+    int32_t loss;               /* asyflexa_loss */
+    int32_t reserved0;
+} asyflexa_problem;
+
+/* Method parameters.  Fill with asyflexa_opts_default, then override. */
+typedef struct {
+    int32_t block_w;            /* columns per block, 1..128 (last block may be shorter) */
+    int32_t mode;               /* asyflexa_mode */
+    double gamma;               /* fixed step (Algorithm 1, S.4), > 0 */
+    double tau;                 /* proximal weight: surrogate curvature d_j = (1+tau_rel)*kappa_j + tau */
+    double tau_rel;             /* relative proximal weight (see tau); both >= 0 */
+    int32_t refresh_every;      /* recompute r = A x - b exactly every this many sweeps (>= 1) */
+    int32_t check_every;        /* solve: evaluate F every this many sweeps (>= 1) */
+    int32_t max_sweeps;         /* solve: sweep budget (>= 1) */
+    int32_t num_ctas;           /* CTAs of the sweep kernels; 0 = one per SM */
+    double tol_gap;             /* solve: stop when (F - f_star)/|f_star| <= tol_gap ... */
+    double tol_stat;            /* ... and ||xhat(x) - x||_inf / max(1,||x||_inf) <= tol_stat */
+    double f_star;              /* optimal value if known, else NaN (then only tol_stat is used) */
+    uint64_t seed;              /* reserved */
+    int32_t profile;            /* 1: time every sweep-kernel launch with CUDA events (see
+                                   asyflexa_read_counters); 0: off */
+    int32_t reserved1;
+} asyflexa_opts;
+
+/* Results and counters.  Optimality fields are FP64 and computed from an exact
+ * residual (FP64 accumulation) and a compensated gradient (see asyflexa_check). */
+typedef struct {
+    int64_t sweeps;             /* sweeps performed by the last solve (or since create for check) */
+    int64_t block_updates;      /* block updates performed (each sweep updates every block once) */
+    double F;                   /* objective at x */
+    double rel_gap;             /* (F - f_star)/|f_star|, NaN if f_star unknown */
+    double stat_xhat;           /* ||xhat(x) - x||_inf / max(1, ||x||_inf)   (Section 4.3 merit) */
+    double stat_mf;             /* ||M_F(x)||_inf / max(1, ||x||_inf)        (Section 3 measure) */
+    double kkt_viol;            /* LASSO without box: max KKT residual; NaN otherwise */
+    int64_t nnz;                /* nonzeros of x */
+    double seconds;             /* device time of the last solve (CUDA events) */
+    double hbm_bytes;           /* algorithmic bytes of A streamed by the sweeps of the last solve */
+    uint64_t staleness_hist[32];/* async: histogram of updates completed between a block's read
+                                   of r and its own update; bucket k holds delays in [2^k-1, 2^(k+1)-1) */
+    int64_t kernel_launches;    /* kernels launched by this handle so far */
+    double sweep_kernel_seconds;/* profile=1: summed device time of the sweep-kernel launches */
+    int64_t sweep_kernel_launches; /* profile=1: number of sweep-kernel launches timed */
+    int64_t sweep_kernel_sweeps;   /* profile=1: sweeps performed by those launches */
+    int32_t status;             /* asyflexa_status of the last solve/check */
+    int32_t checked;            /* 1 if the stat_* / kkt fields were evaluated */
+} asyflexa_stats;
+
+/* Library version (ASYFLEXA_ABI_VERSION).  Never fails. */
+int asyflexa_version(void);
+
+/* Human-readable name of a status code.  Never fails. */
+const char* asyflexa_status_string(int status);
+
+/* Default options: block_w 32, SYNC, gamma 0.9, tau 0, tau_rel 0, refresh_every 10,
+ * check_every 10, max_sweeps 1000, num_ctas 0, tol_gap 1e-6, tol_stat 1e-6, f_star NaN. */
+void asyflexa_opts_default(asyflexa_opts* opts);
+
+/* Validate the problem and options, compute the surrogate weights
+ * d_j = (1+tau_rel)*kappa_j + tau (kappa_j the curvature of f along coordinate j:
+ * ||a_j||^2 for LASSO, 2||a_j||^2 - 2c for NCQUAD; Section 4 surrogates) and allocate
+ * the handle's state on the current device.  cuda_stream is a cudaStream_t (NULL =
+ * legacy default stream).  EINVAL if any d_j < 0 (nonconvex curvature not compensated
+ * by tau).  On success *h is a new handle; on failure *h is NULL. */
+int asyflexa_create(asyflexa_t* h, const asyflexa_problem* prob, const asyflexa_opts* opts,
+                    void* cuda_stream);
+
+/* Release the handle's device memory (after synchronising its stream).  NULL is a no-op. */
+int asyflexa_destroy(asyflexa_t h);
+
+/* r = A x - b with FP64 accumulation over the nonzero columns of x (x: length n device
+ * vector of x_dtype).  The residual is the handle's internal FP64 vector. */
+int asyflexa_residual_refresh(asyflexa_t h, const void* x);
+
+/* n_sweeps sweeps of the configured mode on x (in place).  Each sweep updates every
+ * block once.  The residual must describe x: it does after create+refresh, solve, step
+ * or check on the same x; a first step after create refreshes it automatically.  If x is
+ * changed outside this API, call asyflexa_residual_refresh first.  The residual is
+ * recomputed exactly every refresh_every sweeps and at the end of the call.
+ * Asynchronous: returns after enqueueing. */
+int asyflexa_step(asyflexa_t h, void* x, int32_t n_sweeps);
+
+/* Run sweeps from the given x (in place) until the stopping rule of the options holds
+ * or max_sweeps is reached (ENOTCONV).  Fills *out (may be NULL).  Synchronises. */
+int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out);
+
+/* Evaluate F, rel_gap, the stationarity measures, KKT and nnz at x, after an exact
+ * residual refresh.  Fills *out.  Synchronises. */
+int asyflexa_check(asyflexa_t h, const void* x, asyflexa_stats* out);
+
+/* Counters accumulated since create or the last asyflexa_reset_counters: fills sweeps,
+ * block_updates, staleness_hist, kernel_launches and (profile=1) the sweep_kernel_* fields
+ * of *out (other fields untouched).  Synchronises. */
+int asyflexa_read_counters(asyflexa_t h, asyflexa_stats* out);
+
+/* Zero the update counters, the staleness histogram and the sweep-kernel timers. */
+int asyflexa_reset_counters(asyflexa_t h);
+
+/* Copy the handle's residual (FP64, length m) into a caller device buffer.  Synchronises. */
+int asyflexa_get_residual(asyflexa_t h, double* r_out);
+
+/* Copy the surrogate weights d_j (FP64, length n) into a caller device buffer.  Synchronises. */
+int asyflexa_get_weights(asyflexa_t h, double* d_out);
+
+/* Last error message of the handle (or of the calling thread for NULL).  Never NULL. */
+const char* asyflexa_last_error(asyflexa_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASYFLEXA_H */

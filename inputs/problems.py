@@ -99,7 +99,7 @@ def nesterov_lasso(m: int, n: int, k: int, lam: float = 1.0, seed: int = 0,
 
 
 def nesterov_lasso_torch(m: int, n: int, k: int, lam: float = 1.0, seed: int = 0,
-                         device="cuda", dtype=None, chunk: int = 4096) -> dict:
+                         device="cuda", dtype=None, chunk: int = 4096, n_generate: int | None = None) -> dict:
     """Same recipe as :func:`nesterov_lasso`, generated with torch on ``device``.
 
     Used for instances too large to build on the host (e.g. 20000 x 100000).  The
@@ -107,50 +107,62 @@ def nesterov_lasso_torch(m: int, n: int, k: int, lam: float = 1.0, seed: int = 0
     same distribution.  Construction is in FP64 column chunk by column chunk; the
     returned ``At`` is stored in ``dtype`` (default float32) with zero padding.
     Returns torch tensors on ``device`` (x_star, y_star in FP64).
+
+    ``n_generate`` < n builds only the first n_generate columns (a bounded sample of the
+    same draw): the support is restricted to those columns and b = y* + A x* uses them
+    only, so the sample is itself a planted instance with n_generate variables.
     """
     import torch
 
+    ncols = n if n_generate is None else min(n, int(n_generate))
     if dtype is None:
         dtype = torch.float32
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     f64 = torch.float64
+    # the draws below always cover the full instance, so a sample is a prefix of it
     y = torch.randn(m, generator=g, device=device, dtype=f64)
     perm = torch.randperm(n, generator=g, device=device)
-    support = torch.sort(perm[:k]).values
-    mag = 1.0 - torch.rand(k, generator=g, device=device, dtype=f64)
+    support_full = torch.sort(perm[:k]).values
+    mag_full = 1.0 - torch.rand(k, generator=g, device=device, dtype=f64)
     u = torch.randint(0, 2 ** 52, (n,), generator=g, device=device, dtype=torch.int64)
     xi = (u.to(f64) + 0.5) / float(2 ** 52)
-    on = torch.zeros(n, dtype=torch.bool, device=device)
+    keep = support_full < ncols
+    support = support_full[keep]
+    mag = mag_full[keep]
+    on = torch.zeros(ncols, dtype=torch.bool, device=device)
     on[support] = True
 
     elt = torch.tensor([], dtype=dtype).element_size()
     lda = pad_lda(m, elt)
-    At = torch.zeros((n, lda), dtype=dtype, device=device)
-    s_all = torch.empty(n, dtype=f64, device=device)
-    for j0 in range(0, n, chunk):
-        j1 = min(n, j0 + chunk)
-        Bt = torch.rand((j1 - j0, m), generator=g, device=device, dtype=f64) * 2.0 - 1.0
+    At = torch.zeros((ncols, lda), dtype=dtype, device=device)
+    s_all = torch.empty(ncols, dtype=f64, device=device)
+    for j0 in range(0, ncols, chunk):
+        j1 = min(ncols, j0 + chunk)
+        Bt = torch.rand((min(n, j0 + chunk) - j0, m), generator=g, device=device, dtype=f64)[: j1 - j0]
+        Bt = Bt * 2.0 - 1.0
         s = Bt @ y
         s_all[j0:j1] = s
         o = on[j0:j1]
-        scale = torch.ones(j1 - j0, dtype=f64, device=device)
         sa = s.abs()
+        scale = torch.ones(j1 - j0, dtype=f64, device=device)
         scale = torch.where(o, lam / sa, scale)
         big = (~o) & (sa > lam)
         scale = torch.where(big, lam * xi[j0:j1] / sa, scale)
         At[j0:j1, :m] = (Bt * scale[:, None]).to(dtype)
         del Bt
-    if k > 0 and bool((s_all[support] == 0).any()):
+    ks = int(support.numel())
+    if ks > 0 and bool((s_all[support] == 0).any()):
         raise RuntimeError("degenerate draw: a support column is orthogonal to y*")
-    x_star = torch.zeros(n, dtype=f64, device=device)
-    x_star[support] = mag * torch.sign(s_all[support])
+    x_star = torch.zeros(ncols, dtype=f64, device=device)
+    if ks:
+        x_star[support] = mag * torch.sign(s_all[support])
     stored = At[support, :m].to(f64)
-    b64 = y + stored.T @ x_star[support] if k > 0 else y.clone()
+    b64 = y + stored.T @ x_star[support] if ks > 0 else y.clone()
     b = b64.to(dtype)
     f_star = 0.5 * float(y @ y) + lam * float(x_star.abs().sum())
     return dict(At=At, b=b, x_star=x_star, y_star=y, f_star=f_star, lam=float(lam),
-                m=m, n=n, lda=lda, support=support)
+                m=m, n=ncols, lda=lda, support=support)
 
 
 def random_lasso(m: int, n: int, seed: int = 0, dist: str = "uniform", lam: float = 0.1,

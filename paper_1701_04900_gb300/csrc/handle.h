@@ -1,0 +1,84 @@
+// Internal state of an asyflexa handle (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/asyflexa.h"
+
+struct asyflexa_s {
+    asyflexa_problem prob{};
+    asyflexa_opts opts{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    size_t smem_optin = 0;
+
+    int elt_a = 0;          // bytes per stored element of A
+    int vec = 0;            // rows per 16-byte unit of A
+    int elt_c = 0;          // bytes of the compute type (double or float)
+    int64_t mcopy = 0;      // m rounded up to whole 16-byte units
+    int nblocks = 0;
+
+    // sweep kernel geometry
+    int sweep_ctas = 0;
+    int stages = 0, chunk_rows = 0, tile_rows = 0, ntiles = 0;
+    size_t sweep_smem = 0;
+
+    // gather-GEMV / compaction geometry
+    int nseg = 0, gemv_rowtiles = 0, compact_tiles = 0;
+    int check_ctas = 0;
+    size_t check_smem = 0;
+    bool check_use_smem = false;
+
+    // device buffers (owned)
+    double* r = nullptr;                    // mcopy
+    double* dw = nullptr;                   // n
+    void* delta = nullptr;                  // n of the compute type
+    int* list_idx = nullptr;                // n
+    void* list_val = nullptr;               // n of the x type
+    int* tilecnt = nullptr;                 // compact_tiles
+    int* count = nullptr;                   // 1
+    void* partial = nullptr;                // nseg * mcopy doubles
+    double* norms_part = nullptr;           // kNormsGrid * 4
+    double* norms_out = nullptr;            // 4
+    unsigned long long* counters = nullptr; // 4
+    unsigned long long* hist = nullptr;     // 32
+    unsigned long long* meas = nullptr;     // 8
+    int* err = nullptr;                     // 1
+    int* flag = nullptr;                    // 1
+
+    // profile=1: event pairs around sweep launches (start, stop, sweeps), drained on read
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;
+    std::vector<int> prof_sweeps;
+    double prof_seconds = 0.0;
+    long long prof_launches = 0, prof_sweep_total = 0;
+
+    // host-side bookkeeping
+    bool r_valid = false;
+    const void* r_x = nullptr;
+    long long launches = 0;
+    long long total_sweeps = 0;
+    int last_status = 0;
+    std::string msg;
+};
+
+namespace asyflexa {
+
+// Per-storage-type launchers (instantiated in one translation unit per type).
+template <typename TA>
+struct Launcher {
+    static cudaError_t colnorm(asyflexa_s& h);
+    static cudaError_t sweep(asyflexa_s& h, void* x, int mode, int sweeps);
+    static cudaError_t jacobi_apply(asyflexa_s& h);
+    static cudaError_t refresh(asyflexa_s& h, const void* x);
+    static cudaError_t norms(asyflexa_s& h, const void* x);
+    static cudaError_t check(asyflexa_s& h, const void* x);
+    static int set_smem_attrs(asyflexa_s& h);
+};
+
+}  // namespace asyflexa

@@ -1,0 +1,299 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (normwise relative, ||x_gpu - x_oracle||_inf / ||x_oracle||_inf):
+  FP64 storage: 1e-10;  FP32 / BF16 / FP8 storage (FP32 arithmetic): 1e-5.
+The oracle sees exactly the stored values (FP32 / dequantised codes widened to FP64).
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from inputs import nesterov_lasso, random_lasso, ncquad_problem
+from tests._gpu_helpers import quantize_columns, rel_inf, to_cuda
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import torch
+    from paper_1701_04900_gb300.build import build_library
+    assert torch.cuda.is_available()
+    build_library()
+
+
+def make_solver(d, **kw):
+    from paper_1701_04900_gb300 import Solver
+    t = to_cuda(d)
+    loss = kw.pop("loss", "lasso")
+    c = kw.pop("c", d.get("c", 0.0))
+    return Solver(t["At"], t["b"], d["lam"], m=d["m"], lo=t.get("lo"), hi=t.get("hi"), loss=loss, c=c, **kw)
+
+
+def xzeros(d, dtype):
+    import torch
+    return torch.zeros(d["n"], dtype=dtype, device="cuda")
+
+
+def oracle_jacobi(p, d_w, gamma, sweeps, x0=None):
+    x = np.zeros(p.n) if x0 is None else x0.copy()
+    r = O.residual(p, x)
+    out = []
+    for _ in range(sweeps):
+        x, r = O.jacobi_sweep(p, x, r, d_w, gamma)
+        out.append(x.copy())
+    return out
+
+
+# ----------------------------------------------------------------------------- create
+
+@pytest.mark.parametrize("store", [np.float64, np.float32])
+@pytest.mark.parametrize("loss", ["lasso", "ncquad"])
+def test_weights_match_oracle(store, loss):
+    if loss == "lasso":
+        d = random_lasso(301, 257, seed=1, store_dtype=store)
+        p = O.Problem.from_data(d)
+    else:
+        d = ncquad_problem(400, 300, seed=1, store_dtype=store)
+        p = O.Problem.from_data(d, loss="ncquad")
+    s = make_solver(d, loss=loss, tau=0.25, tau_rel=0.5)
+    got = s.weights().cpu().numpy()
+    want = O.surrogate_weights(p, tau=0.25, tau_rel=0.5)
+    assert rel_inf(got, want) < 1e-13
+
+
+@pytest.mark.parametrize("store", [np.float64, np.float32])
+def test_refresh_matches_oracle_residual(store):
+    import torch
+    d = random_lasso(1003, 777, seed=2, store_dtype=store)
+    p = O.Problem.from_data(d)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(777) * (rng.random(777) < 0.3)
+    x = x.astype(store)
+    s = make_solver(d)
+    xt = torch.from_numpy(x).cuda()
+    s.refresh(xt)
+    got = s.residual().cpu().numpy()
+    want = O.residual(p, x.astype(np.float64))
+    assert rel_inf(got, want) < 1e-14
+
+
+# ----------------------------------------------------------------------------- sync Jacobi
+
+def run_sync_parity(d, w, gamma, sweeps_list, tol, store, loss="lasso", tau=0.0, use_safe=True, num_ctas=0):
+    import torch
+    p = O.Problem.from_data(d, loss=loss)
+    tr = O.jacobi_tau_rel(p, gamma) if use_safe else 0.0
+    dw = O.surrogate_weights(p, tau=tau, tau_rel=tr)
+    ref = oracle_jacobi(p, dw, gamma, max(sweeps_list))
+    s = make_solver(d, loss=loss, block_w=w, mode="sync", gamma=gamma, tau=tau, tau_rel=tr, num_ctas=num_ctas)
+    x = xzeros(d, torch.float64 if store == np.float64 else torch.float32)
+    done = 0
+    worst = 0.0
+    for k in sweeps_list:
+        s.step(x, k - done)
+        done = k
+        e = rel_inf(x.cpu().numpy(), ref[k - 1])
+        worst = max(worst, e)
+        assert e < tol, (k, e)
+    return worst
+
+
+def test_sync_parity_config1_fp64():
+    """LASSO FP64 200 x 1000, Nesterov planted (50 nonzeros), scalar blocks, gamma = 0.9."""
+    d = nesterov_lasso(200, 1000, 50, lam=1.0, seed=0)
+    run_sync_parity(d, 1, 0.9, [1, 5, 20, 60], TOL64, np.float64)
+
+
+def test_sync_parity_fp32_slice():
+    d = nesterov_lasso(2000, 10000, 100, lam=1.0, seed=1, store_dtype=np.float32)
+    run_sync_parity(d, 32, 0.9, [1, 3, 10], TOL32, np.float32)
+
+
+@pytest.mark.parametrize("store,tol", [(np.float64, TOL64), (np.float32, TOL32)])
+def test_sync_parity_ragged_with_box(store, tol):
+    d = random_lasso(1003, 777, seed=3, lam=0.05, store_dtype=store, zero_cols=3, box=0.5)
+    run_sync_parity(d, 32, 0.9, [1, 4, 12], tol, store, tau=0.1)
+
+
+@pytest.mark.parametrize("store,tol", [(np.float64, TOL64), (np.float32, TOL32)])
+def test_sync_parity_ncquad(store, tol):
+    d = ncquad_problem(300, 500, seed=4, store_dtype=store)
+    run_sync_parity(d, 16, 0.9, [1, 5, 15], tol, store, loss="ncquad")
+
+
+def test_sync_parity_grid_independent():
+    """The Jacobi result does not depend on the number of CTAs (fixed reduction order)."""
+    import torch
+    d = nesterov_lasso(500, 3000, 30, seed=5, store_dtype=np.float32)
+    p = O.Problem.from_data(d)
+    tr = O.jacobi_tau_rel(p, 0.9)
+    xs = []
+    for ctas in (1, 7, 0):
+        s = make_solver(d, block_w=32, mode="sync", tau_rel=tr, num_ctas=ctas)
+        x = xzeros(d, torch.float32)
+        s.step(x, 6)
+        xs.append(x.cpu().numpy())
+    assert np.array_equal(xs[0], xs[1]) and np.array_equal(xs[0], xs[2])
+
+
+def test_sync_bitwise_reproducible():
+    import torch
+    d = nesterov_lasso(2000, 10000, 100, seed=6, store_dtype=np.float32)
+    p = O.Problem.from_data(d)
+    tr = O.jacobi_tau_rel(p, 0.9)
+    outs = []
+    for _ in range(2):
+        s = make_solver(d, block_w=32, mode="sync", tau_rel=tr)
+        x = xzeros(d, torch.float32)
+        s.step(x, 8)
+        outs.append((x.cpu().numpy(), s.residual().cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_sync_multitile_residual():
+    """m larger than one shared-memory residual tile (several tiles per panel)."""
+    d = random_lasso(60001, 96, seed=7, lam=0.5, dist="gauss", store_dtype=np.float32)
+    run_sync_parity(d, 8, 0.9, [1, 3], TOL32, np.float32)
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8"])
+def test_sync_parity_quantized_storage(kind):
+    import torch
+    from paper_1701_04900_gb300 import Solver
+    d = random_lasso(1000, 800, seed=8, lam=0.02, dist="gauss", store_dtype=np.float32)
+    q, scale, deq = quantize_columns(d["At"], d["m"], kind)
+    p = O.Problem(A=deq.T, b=d["b"].astype(np.float64), lam=d["lam"])
+    gamma = 0.9
+    tr = O.jacobi_tau_rel(p, gamma)
+    dw = O.surrogate_weights(p, tau_rel=tr)
+    ref = oracle_jacobi(p, dw, gamma, 6)
+    b = torch.from_numpy(d["b"]).cuda()
+    s = Solver(q, b, d["lam"], m=d["m"], col_scale=scale, block_w=32, mode="sync", tau_rel=tr)
+    assert rel_inf(s.weights().cpu().numpy(), dw) < 1e-12
+    x = torch.zeros(d["n"], dtype=torch.float32, device="cuda")
+    s.step(x, 6)
+    assert rel_inf(x.cpu().numpy(), ref[-1]) < TOL32
+
+
+# ----------------------------------------------------------------------------- async
+
+@pytest.mark.parametrize("store,tol", [(np.float64, TOL64), (np.float32, TOL32)])
+@pytest.mark.parametrize("w", [1, 4, 32])
+def test_async_single_cta_equals_gauss_seidel(store, tol, w):
+    """One CTA owns every block and runs them in order: exactly cyclic block Gauss-Seidel."""
+    import torch
+    d = random_lasso(301, 200, seed=9, lam=0.3, store_dtype=store, box=0.8)
+    p = O.Problem.from_data(d)
+    dw = O.surrogate_weights(p, tau=0.2)
+    x_ref = np.zeros(p.n)
+    r_ref = O.residual(p, x_ref)
+    s = make_solver(d, block_w=w, mode="async", tau=0.2, num_ctas=1, refresh_every=100)
+    x = xzeros(d, torch.float64 if store == np.float64 else torch.float32)
+    for sweep in range(3):
+        x_ref, r_ref = O.gauss_seidel_sweep(p, x_ref, r_ref, dw, 0.9, w=w)
+        s.step(x, 1)
+        assert rel_inf(x.cpu().numpy(), x_ref) < tol, sweep
+
+
+def test_async_single_cta_multitile_equals_gauss_seidel():
+    import torch
+    d = random_lasso(50001, 40, seed=10, lam=0.5, dist="gauss", store_dtype=np.float32)
+    p = O.Problem.from_data(d)
+    dw = O.surrogate_weights(p)
+    x_ref, r_ref = O.gauss_seidel_sweep(p, np.zeros(p.n), O.residual(p, np.zeros(p.n)), dw, 0.9, w=8)
+    x_ref, r_ref = O.gauss_seidel_sweep(p, x_ref, r_ref, dw, 0.9, w=8)
+    s = make_solver(d, block_w=8, mode="async", num_ctas=1)
+    x = xzeros(d, torch.float32)
+    s.step(x, 2)
+    assert rel_inf(x.cpu().numpy(), x_ref) < TOL32
+
+
+@pytest.mark.parametrize("store", [np.float64, np.float32])
+def test_async_reaches_planted_optimum(store):
+    """Many CTAs, stale reads: objective within 1e-6 of the optimum, stationarity <= 1e-6."""
+    import torch
+    d = nesterov_lasso(2000, 10000, 100, lam=1.0, seed=11, store_dtype=store)
+    p = O.Problem.from_data(d)
+    f_ref = O.objective(p, d["x_star"])   # optimal value on the stored data (up to ~1e-12)
+    s = make_solver(d, block_w=32, mode="async", gamma=0.9, f_star=f_ref, max_sweeps=3000,
+                    check_every=10, refresh_every=5)
+    x = xzeros(d, torch.float64 if store == np.float64 else torch.float32)
+    st = s.solve(x)
+    assert st["status"] == 0, st
+    assert st["rel_gap"] <= 1e-6 and st["stat_xhat"] <= 1e-6
+    xg = x.cpu().numpy().astype(np.float64)
+    F = O.objective(p, xg)
+    assert (F - f_ref) / f_ref <= 1.5e-6
+    assert abs(F - st["F"]) <= 1e-9 * abs(F)
+    dwt = O.surrogate_weights(p)
+    assert O.stationarity(O.xhat_merit(p, xg, dwt), xg) <= 1.5e-6
+    assert st["block_updates"] == st["sweeps"] * math.ceil(d["n"] / 32)
+    assert sum(st["staleness_hist"]) == st["block_updates"]
+
+
+def test_check_measures_match_oracle():
+    import torch
+    d = random_lasso(777, 501, seed=12, lam=0.4, store_dtype=np.float32)
+    p = O.Problem.from_data(d)
+    rng = np.random.default_rng(1)
+    x = (rng.standard_normal(p.n) * (rng.random(p.n) < 0.2)).astype(np.float32)
+    s = make_solver(d, tau=0.3)
+    st = s.check(torch.from_numpy(x).cuda())
+    x64 = x.astype(np.float64)
+    assert abs(st["F"] - O.objective(p, x64)) <= 1e-12 * abs(O.objective(p, x64))
+    assert abs(st["stat_mf"] - O.stationarity(O.mf_measure(p, x64), x64)) <= 1e-9
+    dwt = O.surrogate_weights(p, tau=0.3)
+    assert abs(st["stat_xhat"] - O.stationarity(O.xhat_merit(p, x64, dwt), x64)) <= 1e-9
+    assert abs(st["kkt_viol"] - O.kkt_violation(p, x64)) <= 1e-9
+    assert st["nnz"] == int(np.count_nonzero(x))
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+def test_degenerate_shapes_and_bounds():
+    import torch
+    # n = 1, m = 1
+    d = random_lasso(1, 1, seed=13, lam=0.1)
+    p = O.Problem.from_data(d)
+    s = make_solver(d, block_w=32, mode="async")
+    x = xzeros(d, torch.float64)
+    s.step(x, 3)
+    xr = np.zeros(1)
+    rr = O.residual(p, xr)
+    for _ in range(3):
+        xr, rr = O.gauss_seidel_sweep(p, xr, rr, O.surrogate_weights(p), 0.9, w=32)
+    assert rel_inf(x.cpu().numpy(), xr) < TOL64
+    # lo = hi pins the variable
+    d = random_lasso(40, 30, seed=14, lam=0.1, box=1.0)
+    d["lo"][:5] = 0.25
+    d["hi"][:5] = 0.25
+    s = make_solver(d, block_w=4, mode="sync")
+    x = xzeros(d, torch.float64)
+    s.step(x, 2)
+    assert np.all(x.cpu().numpy()[:5] == 0.25)
+
+
+def test_invalid_inputs_are_rejected():
+    import torch
+    from paper_1701_04900_gb300 import AsyflexaError
+    d = random_lasso(40, 30, seed=15, box=1.0)
+    d["lo"][3] = 2.0     # lo > hi
+    with pytest.raises(AsyflexaError) as ei:
+        make_solver(d)
+    assert ei.value.code == -1
+    d = ncquad_problem(40, 30, seed=15)
+    with pytest.raises(AsyflexaError) as ei:
+        make_solver(d, loss="ncquad", c=1e6)      # negative surrogate weights
+    assert ei.value.code == -1
+    d = random_lasso(40, 30, seed=15)
+    s = make_solver(d)
+    with pytest.raises(ValueError):
+        s.step(torch.zeros(30, dtype=torch.float32, device="cuda"), 1)
