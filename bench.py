@@ -412,8 +412,35 @@ def run_e2e(gen, f_ref, args, refresh_every, check_every):
             "steps": steps, "seconds_per_step": el / steps}
 
 
+def run_ncu_case(args):
+    """Small case for ncu captures: the same generator with n = 12800 (A = 1 GB, larger
+    than L2), one refresh, then `--ncu-launches` async sweep launches of 10 sweeps each
+    (or Jacobi sweeps with --ncu-mode sync).  Used by the commands in profiles/."""
+    import torch
+    from paper_1701_04900_gb300.build import build_library
+    build_library()
+    from paper_1701_04900_gb300 import Solver
+    from inputs import nesterov_lasso_torch
+    torch.cuda.set_device(0)
+    n = 12800
+    gen = nesterov_lasso_torch(M, n, K_PLANT * n // N, lam=LAM, seed=0, device="cuda")
+    s = Solver(gen["At"], gen["b"], LAM, m=M, block_w=W_BLOCK, mode=args.ncu_mode, gamma=GAMMA,
+               refresh_every=10, tau_rel=4.0 if args.ncu_mode == "sync" else 0.0)
+    x = torch.zeros(n, dtype=torch.float32, device="cuda")
+    s.refresh(x)
+    for _ in range(args.ncu_launches):
+        s.step(x, 10 if args.ncu_mode == "async" else 1)
+    torch.cuda.synchronize()
+    st = s.check(x)
+    print(json.dumps({"ncu_case": True, "n": n, "mode": args.ncu_mode, "F": st["F"], "nnz": st["nnz"]}))
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--ncu-case", action="store_true", help="small profiling case (see run_ncu_case)")
+    ap.add_argument("--ncu-mode", default="async", choices=["async", "sync"])
+    ap.add_argument("--ncu-launches", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
@@ -429,7 +456,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.ncu_case:
+        run_ncu_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -105,7 +105,9 @@ typedef struct {
     uint64_t seed;              /* reserved */
     int32_t profile;            /* 1: time every sweep-kernel launch with CUDA events (see
                                    asyflexa_read_counters); 0: off */
-    int32_t reserved1;
+    int32_t variant;            /* async kernel: 0 = automatic, 1 = staged residual tile (any m, any
+                                   dtype), 2 = register-resident residual (FP32/BF16/FP8, m up to
+                                   24576 rows; EUNSUPPORTED otherwise) */
 } asyflexa_opts;
 
 /* Results and counters.  Optimality fields are FP64 and computed from an exact

@@ -223,6 +223,7 @@ int validate_opts(const asyflexa_opts* o, std::string* why) {
     if (o->refresh_every < 1 || o->check_every < 1 || o->max_sweeps < 1)
         return *why = "refresh_every, check_every and max_sweeps must be >= 1", 1;
     if (o->num_ctas < 0) return *why = "num_ctas must be >= 0", 1;
+    if (o->variant < 0 || o->variant > 2) return *why = "variant must be 0, 1 or 2", 1;
     if (!(o->tol_gap >= 0.0) || !(o->tol_stat >= 0.0)) return *why = "tolerances must be >= 0", 1;
     return 0;
 }
@@ -392,6 +393,15 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
     {
         int rc = dispatch(*h, [&](auto L) { return decltype(L)::set_smem_attrs(*h); });
         if (rc) CKC(static_cast<cudaError_t>(rc), "set shared-memory attribute");
+        rc = dispatch(*h, [&](auto L) { return decltype(L)::choose_reg(*h); });
+        if (rc < 0) CKC(static_cast<cudaError_t>(-rc), "set shared-memory attribute (register kernel)");
+        if (O->variant == 1) {
+            h->reg_upt = 0;
+        } else if (O->variant == 2 && rc != 1) {
+            set_error(h, ASYFLEXA_EUNSUPPORTED,
+                      "variant 2 (register-resident residual) needs FP32/BF16/FP8 storage and m <= 24576");
+            return fail(ASYFLEXA_EUNSUPPORTED);
+        }
     }
     {
         cudaError_t e = dispatch(*h, [&](auto L) { return decltype(L)::colnorm(*h); });

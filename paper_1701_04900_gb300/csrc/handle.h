@@ -31,6 +31,10 @@ struct asyflexa_s {
 
     // gather-GEMV / compaction geometry
     int nseg = 0, gemv_rowtiles = 0, compact_tiles = 0;
+    // register-resident async kernel (0 = not used)
+    int reg_upt = 0, reg_cpc = 0, reg_stages = 0;
+    size_t reg_smem = 0;
+
     int check_ctas = 0;
     size_t check_smem = 0;
     bool check_use_smem = false;
@@ -79,6 +83,7 @@ struct Launcher {
     static cudaError_t norms(asyflexa_s& h, const void* x);
     static cudaError_t check(asyflexa_s& h, const void* x);
     static int set_smem_attrs(asyflexa_s& h);
+    static int choose_reg(asyflexa_s& h);
 };
 
 }  // namespace asyflexa

@@ -5,8 +5,72 @@
 #include "aux.cuh"
 #include "handle.h"
 #include "sweep.cuh"
+#include "sweep_async.cuh"
 
 namespace asyflexa {
+
+// Register-increment async kernel instances: CPC = 16 KB stages per column (1..6).
+template <typename TA, int CPC>
+constexpr bool reg_fits() {
+    return kRegKpc * CPC * ATraits<TA>::kVec <= kRegMaxRowsPerThread;
+}
+
+template <typename TA>
+const void* reg_kernel(int cpc) {
+    if constexpr (sizeof(typename ATraits<TA>::TC) != 4) {
+        return nullptr;  // FP64 problems use the staged kernel
+    } else {
+        switch (cpc) {
+            case 1:
+                if constexpr (reg_fits<TA, 1>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 1>);
+                break;
+            case 2:
+                if constexpr (reg_fits<TA, 2>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 2>);
+                break;
+            case 3:
+                if constexpr (reg_fits<TA, 3>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 3>);
+                break;
+            case 4:
+                if constexpr (reg_fits<TA, 4>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 4>);
+                break;
+            case 5:
+                if constexpr (reg_fits<TA, 5>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 5>);
+                break;
+            case 6:
+                if constexpr (reg_fits<TA, 6>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 6>);
+                break;
+            default: break;
+        }
+        return nullptr;
+    }
+}
+
+// Choose the register-increment kernel instance that covers the column (sets h.reg_*).
+// Returns 0 if none applies (the staged kernel is used), 1 if chosen, or a negative
+// cudaError_t if setting its shared-memory attribute failed.  The ring must hold one
+// column plus at least two 16 KB stages of prefetch.
+template <typename TA>
+int Launcher<TA>::choose_reg(asyflexa_s& h) {
+    h.reg_upt = h.reg_cpc = h.reg_stages = 0;
+    h.reg_smem = 0;
+    const int64_t units = h.mcopy / h.vec;
+    const int cpc = static_cast<int>((units + kRegStageUnits - 1) / kRegStageUnits);
+    if (cpc < 1 || cpc > 6) return 0;
+    const void* fn = reg_kernel<TA>(cpc);
+    if (!fn) return 0;
+    const int rt_rows = static_cast<int>(h.mcopy);
+    const RegLayout L0 = make_reg_layout(rt_rows, 0);
+    if (L0.total + 512 + static_cast<size_t>(cpc + 2) * L0.stage_bytes > h.smem_optin) return 0;
+    int stages = static_cast<int>((h.smem_optin - L0.total - 512) / L0.stage_bytes);
+    if (stages > 16) stages = 16;
+    h.reg_upt = kRegKpc * cpc;
+    h.reg_cpc = cpc;
+    h.reg_stages = stages;
+    h.reg_smem = make_reg_layout(rt_rows, stages).total;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.reg_smem));
+    if (e != cudaSuccess) return -static_cast<int>(e);
+    return 1;
+}
 
 template <typename TA>
 int Launcher<TA>::set_smem_attrs(asyflexa_s& h) {
@@ -17,7 +81,7 @@ int Launcher<TA>::set_smem_attrs(asyflexa_s& h) {
     e = cudaFuncSetAttribute(sweep_kernel<TA, kAsync>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(h.sweep_smem));
     if (e != cudaSuccess) return static_cast<int>(e);
-    if (h.check_smem > 48 * 1024) {
+    if (h.check_use_smem && h.check_smem > 48 * 1024) {
         e = cudaFuncSetAttribute(check_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(h.check_smem));
         if (e != cudaSuccess) return static_cast<int>(e);
@@ -68,6 +132,15 @@ cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
     p.counters = h.counters;
     p.hist = h.hist;
     p.err = h.err;
+    if (mode == ASYFLEXA_ASYNC && h.reg_upt > 0) {
+        p.stages = h.reg_stages;
+        p.tile_rows = static_cast<int>(h.mcopy);
+        void* args[] = {&p};
+        const cudaError_t e = cudaLaunchKernel(reg_kernel<TA>(h.reg_cpc), dim3(h.sweep_ctas), dim3(kRegThreads), args,
+                                               h.reg_smem, h.stream);
+        ++h.launches;
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     if (mode == ASYFLEXA_ASYNC)
         sweep_kernel<TA, kAsync><<<h.sweep_ctas, kSweepThreads, h.sweep_smem, h.stream>>>(p);
     else

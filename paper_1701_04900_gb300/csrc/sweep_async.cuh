@@ -1,0 +1,304 @@
+// Asynchronous sweep kernel with a register-resident block increment (FP32/BF16/FP8
+// storage; m up to 24576 rows for FP32/BF16 and 16384 for FP8).
+//
+// Same method step as sweep.cuh (Algorithm 1, S.1-S.5; eq. 2 best response; Section 4
+// surrogate), organised so that A is read from HBM exactly once per sweep even when many
+// coordinates move (the generic kernel re-reads every moving column for its scatter):
+//
+//   * at the start of a block the consumers stage the FP64 residual, converted to FP32, in
+//     shared memory: the stale read r~ of step S.2;
+//   * every consumer thread owns the same 16-byte units u = k*256 + tid (k < 4*CPC) of
+//     every column.  A column arrives in CPC ring stages of 1024 units (16 KB, 1-D bulk TMA
+//     copies).  Consumers form a_j^T r~ from shared memory, reduce across warps, and one
+//     thread takes the closed-form best response and fixed step in FP64 (the surrogate is
+//     diagonal, so Delta_j only needs a_j^T r~);
+//   * while the column is still in shared memory every thread adds a_j * Delta_j to its
+//     register copy of the block increment, then releases the column's stages;
+//   * after the block's w columns the increment is added to r with one FP64 atomic per row
+//     (lock-free).  All columns of the block used the same snapshot r~, so this is exactly
+//     the block update r += A_i Delta_i.
+#pragma once
+
+#include "ptx.cuh"
+#include "sweep.cuh"
+#include "types.cuh"
+
+namespace asyflexa {
+
+constexpr int kRegConsWarps = 8;
+constexpr int kRegConsThreads = kRegConsWarps * 32;
+constexpr int kRegThreads = kRegConsThreads + 32;
+constexpr int kRegKpc = 4;                                   // units per thread per stage
+constexpr int kRegStageUnits = kRegKpc * kRegConsThreads;    // 1024 units = 16 KB
+constexpr int kRegMaxRowsPerThread = 96;
+
+struct RegLayout {
+    int stages;
+    size_t stage_bytes;
+    size_t off_ring, off_rt, off_colpart, off_bars, off_misc, total;
+};
+
+__host__ __device__ inline RegLayout make_reg_layout(int rt_rows, int stages) {
+    RegLayout L;
+    L.stages = stages;
+    L.stage_bytes = static_cast<size_t>(kRegStageUnits) * 16;
+    size_t o = 0;
+    L.off_ring = o;
+    o += L.stage_bytes * stages;
+    L.off_rt = o;
+    o = align_up_sz(o + static_cast<size_t>(rt_rows) * sizeof(float), 16);
+    L.off_colpart = o;
+    o = align_up_sz(o + kRegConsWarps * sizeof(float), 16);
+    L.off_bars = o;
+    o = align_up_sz(o + 2 * stages * sizeof(uint64_t), 16);
+    L.off_misc = o;  // abort flag, any flag, delta
+    o += 32;
+    L.total = align_up_sz(o, 128);
+    return L;
+}
+
+template <typename TA, int CPC>
+__global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const SweepParams p) {
+    using TC = typename ATraits<TA>::TC;
+    static_assert(sizeof(TC) == 4, "register kernel computes in FP32");
+    using TX = typename XType<TA>::T;
+    constexpr int V = ATraits<TA>::kVec;
+    constexpr int UPT = kRegKpc * CPC;
+    static_assert(UPT * V <= kRegMaxRowsPerThread, "too many rows per thread");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    const RegLayout L = make_reg_layout(p.tile_rows, p.stages);
+    unsigned char* ring = smem + L.off_ring;
+    float* rt = reinterpret_cast<float*>(smem + L.off_rt);
+    float* colpart = reinterpret_cast<float*>(smem + L.off_colpart);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.off_bars);
+    uint64_t* empty = full + p.stages;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.off_misc);
+    volatile int* s_any = reinterpret_cast<volatile int*>(smem + L.off_misc + 4);
+    volatile float* s_delta = reinterpret_cast<volatile float*>(smem + L.off_misc + 8);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const TA* A = static_cast<const TA*>(p.A);
+    const int64_t lda = p.lda;
+    const int64_t units = p.mcopy / V;
+    const int64_t units_full = p.m / V;  // units whose rows are all < m
+
+    if (tid == 0) {
+        for (int s = 0; s < p.stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kRegConsWarps);
+        }
+        *abort_flag = 0;
+        *s_any = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    // ------------------------------------------------------------------ producer
+    if (warp == kRegConsWarps) {
+        if (lane != 0) return;
+        const uint64_t pol = l2_policy_evict_first();
+        uint32_t stage = 0, phase = 0;
+        long long issued = 0;
+        for (int s = 0; s < p.sweeps; ++s) {
+            for (int b = blockIdx.x; b < p.nblocks; b += gridDim.x) {
+                const int64_t c0 = static_cast<int64_t>(b) * p.w;
+                const int wb = static_cast<int>(min64(p.w, p.n - c0));
+                for (int jl = 0; jl < wb; ++jl) {
+                    const TA* col = A + (c0 + jl) * lda;
+                    for (int c = 0; c < CPC; ++c) {
+                        const int64_t u0 = static_cast<int64_t>(c) * kRegStageUnits;
+                        if (u0 >= units) break;
+                        const uint32_t nbytes = static_cast<uint32_t>(min64(kRegStageUnits, units - u0) * 16);
+                        if (!mbar_wait_bounded(&empty[stage], phase ^ 1u, abort_flag, p.err)) goto drain;
+                        mbar_arrive_expect_tx(&full[stage], nbytes);
+                        bulk_load(ring + stage * L.stage_bytes, col + u0 * V, nbytes, &full[stage], pol);
+                        ++issued;
+                        if (++stage == static_cast<uint32_t>(p.stages)) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    }
+                }
+            }
+        }
+        return;
+    drain: {
+        const long long first = issued > p.stages ? issued - p.stages : 0;
+        for (long long i = first; i < issued; ++i) {
+            const uint32_t st = static_cast<uint32_t>(i % p.stages);
+            const uint32_t ph = static_cast<uint32_t>((i / p.stages) & 1);
+            const uint64_t t0 = global_timer_ns();
+            while (!mbar_try_wait(&full[st], ph)) {
+                if (global_timer_ns() - t0 > kWaitLimitNs) break;
+            }
+        }
+    }
+        return;
+    }
+
+    // ------------------------------------------------------------------ consumers
+    uint32_t stage = 0, phase = 0;
+    unsigned long long u_read = 0, my_updates = 0, my_active = 0;
+    TX* x = static_cast<TX*>(p.x);
+    const TX* lo = static_cast<const TX*>(p.lo);
+    const TX* hi = static_cast<const TX*>(p.hi);
+    int nchunks = 0;  // stages per column actually present
+    for (int c = 0; c < CPC; ++c)
+        if (static_cast<int64_t>(c) * kRegStageUnits < units) ++nchunks;
+
+    float inc[UPT][V];
+
+    for (int s = 0; s < p.sweeps; ++s) {
+        for (int b = blockIdx.x; b < p.nblocks; b += gridDim.x) {
+            const int64_t c0 = static_cast<int64_t>(b) * p.w;
+            const int wb = static_cast<int>(min64(p.w, p.n - c0));
+            // S.2: stale read of the residual into shared memory (rows >= m hold 0).  The
+            // barrier at the end of the previous block guarantees nobody still reads rt.
+            if (tid == 0) u_read = ld_relaxed_u64(&p.counters[0]);
+            {
+                const double2* rsrc = reinterpret_cast<const double2*>(p.r);
+                const int64_t pairs = p.mcopy / 2;
+                for (int64_t i = tid; i < pairs; i += kRegConsThreads) {
+                    const double2 v = __ldcg(rsrc + i);
+                    reinterpret_cast<float2*>(rt)[i] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < UPT; ++k)
+#pragma unroll
+                for (int e = 0; e < V; ++e) inc[k][e] = 0.f;
+            named_bar_sync(1, kRegConsThreads);
+
+            for (int jl = 0; jl < wb; ++jl) {
+                // ---- dot a_j^T r~ over this thread's rows
+                float acc0 = 0.f, acc1 = 0.f;
+                uint32_t st_c = stage, ph_c = phase;
+                bool ok = !*abort_flag;
+#pragma unroll 1
+                for (int c = 0; c < CPC; ++c) {
+                    if (c < nchunks) {
+                        if (ok) ok = mbar_wait_bounded(&full[st_c], ph_c, abort_flag, p.err);
+                        if (ok) {
+                            const uint4* src = reinterpret_cast<const uint4*>(ring + st_c * L.stage_bytes);
+#pragma unroll
+                            for (int kk = 0; kk < kRegKpc; ++kk) {
+                                const int64_t u = static_cast<int64_t>(c * kRegKpc + kk) * kRegConsThreads + tid;
+                                if (u < units) {
+                                    float a[V];
+                                    ATraits<TA>::unpack(src[kk * kRegConsThreads + tid], a);
+                                    const float* rv = rt + u * V;
+                                    if (u < units_full) {
+#pragma unroll
+                                        for (int e = 0; e < V; e += 4) {
+                                            const float4 r4 = *reinterpret_cast<const float4*>(rv + e);
+                                            acc0 = fmaf(a[e], r4.x, acc0);
+                                            acc1 = fmaf(a[e + 1], r4.y, acc1);
+                                            acc0 = fmaf(a[e + 2], r4.z, acc0);
+                                            acc1 = fmaf(a[e + 3], r4.w, acc1);
+                                        }
+                                    } else {
+                                        const int valid = static_cast<int>(p.m - u * V);
+#pragma unroll
+                                        for (int e = 0; e < V; ++e)
+                                            if (e < valid) acc0 = fmaf(a[e], rv[e], acc0);
+                                    }
+                                }
+                            }
+                        }
+                        if (++st_c == static_cast<uint32_t>(p.stages)) {
+                            st_c = 0;
+                            ph_c ^= 1u;
+                        }
+                    }
+                }
+                const float v = warp_sum(acc0 + acc1);
+                if (lane == 0) colpart[warp] = v;
+                named_bar_sync(1, kRegConsThreads);
+                // ---- best response + fixed step (one thread, FP64)
+                if (tid == 0) {
+                    float dv = 0.f;
+                    if (!*abort_flag) {
+                        double g = 0.0;
+#pragma unroll
+                        for (int k = 0; k < kRegConsWarps; ++k) g += static_cast<double>(colpart[k]);
+                        const int64_t j = c0 + jl;
+                        const double sc = p.scale ? static_cast<double>(p.scale[j]) : 1.0;
+                        const double delta =
+                            coordinate_update<TX>(g * sc, x, lo, hi, j, p.dw[j], p.lam, p.gamma, p.s_loss, p.c2);
+                        dv = static_cast<float>(delta * sc);
+                        if (delta != 0.0) *s_any = 1;
+                    }
+                    *s_delta = dv;
+                }
+                named_bar_sync(1, kRegConsThreads);
+                // ---- fold a_j * Delta_j into the register increment, then release the stages
+                const float dj = *s_delta;
+                st_c = stage;
+                ph_c = phase;
+#pragma unroll
+                for (int c = 0; c < CPC; ++c) {
+                    if (c < nchunks) {
+                        if (dj != 0.f) {
+                            const uint4* src = reinterpret_cast<const uint4*>(ring + st_c * L.stage_bytes);
+#pragma unroll
+                            for (int kk = 0; kk < kRegKpc; ++kk) {
+                                const int k = c * kRegKpc + kk;
+                                const int64_t u = static_cast<int64_t>(k) * kRegConsThreads + tid;
+                                if (u < units) {
+                                    float a[V];
+                                    ATraits<TA>::unpack(src[kk * kRegConsThreads + tid], a);
+#pragma unroll
+                                    for (int e = 0; e < V; ++e) inc[k][e] = fmaf(a[e], dj, inc[k][e]);
+                                }
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&empty[st_c]);
+                        if (++st_c == static_cast<uint32_t>(p.stages)) {
+                            st_c = 0;
+                            ph_c ^= 1u;
+                        }
+                    }
+                }
+                stage = st_c;
+                phase = ph_c;
+            }
+            // ---- r += A_i Delta_i : one FP64 atomic per row (skipping exact zeros)
+            const bool any = *s_any != 0;
+            if (any && !*abort_flag) {
+#pragma unroll
+                for (int k = 0; k < UPT; ++k) {
+                    const int64_t u = static_cast<int64_t>(k) * kRegConsThreads + tid;
+                    if (u < units) {
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            const int64_t row = u * V + e;
+                            if (row < p.m && inc[k][e] != 0.f) red_add_f64(p.r + row, static_cast<double>(inc[k][e]));
+                        }
+                    }
+                }
+                __threadfence();
+            }
+            named_bar_sync(1, kRegConsThreads);  // scatter complete; rt free; s_any read by all
+            if (tid == 0) {
+                *s_any = 0;
+                ++my_updates;
+                if (any) ++my_active;
+                const unsigned long long u1 = atomicAdd(&p.counters[0], 1ull);
+                const unsigned long long dly = u1 - u_read;
+                int bucket = 63 - __clzll(static_cast<long long>(dly + 1ull));
+                bucket = bucket > 31 ? 31 : bucket;
+                atomicAdd(&p.hist[bucket], 1ull);
+            }
+        }
+    }
+    if (tid == 0) {
+        atomicAdd(&p.counters[1], my_updates);
+        atomicAdd(&p.counters[2], my_active);
+    }
+}
+
+}  // namespace asyflexa

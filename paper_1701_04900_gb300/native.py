@@ -40,7 +40,7 @@ class Opts(C.Structure):
         ("refresh_every", C.c_int32), ("check_every", C.c_int32), ("max_sweeps", C.c_int32),
         ("num_ctas", C.c_int32),
         ("tol_gap", C.c_double), ("tol_stat", C.c_double), ("f_star", C.c_double),
-        ("seed", C.c_uint64), ("profile", C.c_int32), ("reserved1", C.c_int32),
+        ("seed", C.c_uint64), ("profile", C.c_int32), ("variant", C.c_int32),
     ]
 
 
@@ -156,7 +156,7 @@ class Solver:
     def __init__(self, At, b, lam, m=None, *, loss="lasso", c=0.0, lo=None, hi=None, col_scale=None,
                  block_w=32, mode="sync", gamma=0.9, tau=0.0, tau_rel=0.0, refresh_every=10,
                  check_every=10, max_sweeps=1000, num_ctas=0, tol_gap=1e-6, tol_stat=1e-6,
-                 f_star=math.nan, profile=False, stream=None):
+                 f_star=math.nan, profile=False, variant=0, stream=None):
         import torch
         L = lib()
         if At.dim() != 2 or not At.is_contiguous() or not At.is_cuda:
@@ -180,6 +180,7 @@ class Solver:
         o.num_ctas = int(num_ctas)
         o.tol_gap, o.tol_stat, o.f_star = float(tol_gap), float(tol_stat), float(f_star)
         o.profile = 1 if profile else 0
+        o.variant = int(variant)
         self.problem, self.opts = p, o
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream

@@ -185,22 +185,62 @@ def test_sync_parity_quantized_storage(kind):
 
 # ----------------------------------------------------------------------------- async
 
-@pytest.mark.parametrize("store,tol", [(np.float64, TOL64), (np.float32, TOL32)])
+@pytest.mark.parametrize("store,tol,variant", [(np.float64, TOL64, 0), (np.float32, TOL32, 1),
+                                               (np.float32, TOL32, 2)])
 @pytest.mark.parametrize("w", [1, 4, 32])
-def test_async_single_cta_equals_gauss_seidel(store, tol, w):
-    """One CTA owns every block and runs them in order: exactly cyclic block Gauss-Seidel."""
+def test_async_single_cta_equals_gauss_seidel(store, tol, variant, w):
+    """One CTA owns every block and runs them in order: exactly cyclic block Gauss-Seidel.
+    variant 1 = staged-residual kernel, 2 = register-increment kernel."""
     import torch
     d = random_lasso(301, 200, seed=9, lam=0.3, store_dtype=store, box=0.8)
     p = O.Problem.from_data(d)
     dw = O.surrogate_weights(p, tau=0.2)
     x_ref = np.zeros(p.n)
     r_ref = O.residual(p, x_ref)
-    s = make_solver(d, block_w=w, mode="async", tau=0.2, num_ctas=1, refresh_every=100)
+    s = make_solver(d, block_w=w, mode="async", tau=0.2, num_ctas=1, refresh_every=100, variant=variant)
     x = xzeros(d, torch.float64 if store == np.float64 else torch.float32)
     for sweep in range(3):
         x_ref, r_ref = O.gauss_seidel_sweep(p, x_ref, r_ref, dw, 0.9, w=w)
         s.step(x, 1)
         assert rel_inf(x.cpu().numpy(), x_ref) < tol, sweep
+
+
+@pytest.mark.parametrize("m", [1021, 5003, 9001, 17001, 24571])
+@pytest.mark.parametrize("variant", [1, 2])
+def test_async_single_cta_shapes(m, variant):
+    """Column lengths spanning 1..6 shared-memory stages of the register-increment kernel
+    (ragged last unit included), against Gauss-Seidel."""
+    import torch
+    d = random_lasso(m, 48, seed=m, lam=0.2, dist="gauss", store_dtype=np.float32, box=2.0)
+    p = O.Problem.from_data(d)
+    dw = O.surrogate_weights(p, tau=0.05)
+    x_ref, r_ref = np.zeros(p.n), O.residual(p, np.zeros(p.n))
+    for _ in range(2):
+        x_ref, r_ref = O.gauss_seidel_sweep(p, x_ref, r_ref, dw, 0.9, w=8)
+    s = make_solver(d, block_w=8, mode="async", tau=0.05, num_ctas=1, variant=variant)
+    x = xzeros(d, torch.float32)
+    s.step(x, 2)
+    assert rel_inf(x.cpu().numpy(), x_ref) < TOL32
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8"])
+@pytest.mark.parametrize("variant", [1, 2])
+def test_async_single_cta_quantized(kind, variant):
+    import torch
+    from paper_1701_04900_gb300 import Solver
+    d = random_lasso(3001, 300, seed=17, lam=0.02, dist="gauss", store_dtype=np.float32)
+    q, scale, deq = quantize_columns(d["At"], d["m"], kind)
+    p = O.Problem(A=deq.T, b=d["b"].astype(np.float64), lam=d["lam"])
+    dw = O.surrogate_weights(p, tau=0.1)
+    x_ref, r_ref = np.zeros(p.n), O.residual(p, np.zeros(p.n))
+    for _ in range(3):
+        x_ref, r_ref = O.gauss_seidel_sweep(p, x_ref, r_ref, dw, 0.9, w=16)
+    b = torch.from_numpy(d["b"]).cuda()
+    s = Solver(q, b, d["lam"], m=d["m"], col_scale=scale, block_w=16, mode="async", tau=0.1, num_ctas=1,
+               variant=variant)
+    x = torch.zeros(d["n"], dtype=torch.float32, device="cuda")
+    s.step(x, 3)
+    assert rel_inf(x.cpu().numpy(), x_ref) < TOL32
 
 
 def test_async_single_cta_multitile_equals_gauss_seidel():
@@ -216,15 +256,18 @@ def test_async_single_cta_multitile_equals_gauss_seidel():
     assert rel_inf(x.cpu().numpy(), x_ref) < TOL32
 
 
-@pytest.mark.parametrize("store", [np.float64, np.float32])
-def test_async_reaches_planted_optimum(store):
-    """Many CTAs, stale reads: objective within 1e-6 of the optimum, stationarity <= 1e-6."""
+@pytest.mark.parametrize("store,variant", [(np.float64, 0), (np.float32, 1), (np.float32, 2)])
+def test_async_reaches_planted_optimum(store, variant):
+    """Many CTAs, stale reads: objective within 1e-6 of the optimum, stationarity <= 1e-6.
+
+    16 CTAs x 32 columns keep ~5% of the variables in flight, as in the 20000 x 100000
+    bench configuration (152 CTAs x 32 of 100000)."""
     import torch
     d = nesterov_lasso(2000, 10000, 100, lam=1.0, seed=11, store_dtype=store)
     p = O.Problem.from_data(d)
     f_ref = O.objective(p, d["x_star"])   # optimal value on the stored data (up to ~1e-12)
     s = make_solver(d, block_w=32, mode="async", gamma=0.9, f_star=f_ref, max_sweeps=3000,
-                    check_every=10, refresh_every=5)
+                    check_every=10, refresh_every=5, num_ctas=16, variant=variant)
     x = xzeros(d, torch.float64 if store == np.float64 else torch.float32)
     st = s.solve(x)
     assert st["status"] == 0, st
@@ -271,14 +314,41 @@ def test_degenerate_shapes_and_bounds():
     for _ in range(3):
         xr, rr = O.gauss_seidel_sweep(p, xr, rr, O.surrogate_weights(p), 0.9, w=32)
     assert rel_inf(x.cpu().numpy(), xr) < TOL64
-    # lo = hi pins the variable
+    # lo = hi: the best response is the bound; the fixed step moves a fraction gamma of
+    # the way each sweep (gamma = 1 lands on it, gamma = 0.9 leaves 0.1^k of the distance)
     d = random_lasso(40, 30, seed=14, lam=0.1, box=1.0)
     d["lo"][:5] = 0.25
     d["hi"][:5] = 0.25
-    s = make_solver(d, block_w=4, mode="sync")
+    for gamma, want in ((1.0, 0.25), (0.9, 0.25 * (1 - 0.1 ** 2))):
+        s = make_solver(d, block_w=4, mode="sync", gamma=gamma)
+        x = xzeros(d, torch.float64)
+        s.step(x, 2)
+        np.testing.assert_allclose(x.cpu().numpy()[:5], want, rtol=1e-15)
+    # more columns per block than columns in the problem
+    d = random_lasso(17, 5, seed=16, lam=0.05)
+    p = O.Problem.from_data(d)
+    s = make_solver(d, block_w=32, mode="sync")
     x = xzeros(d, torch.float64)
-    s.step(x, 2)
-    assert np.all(x.cpu().numpy()[:5] == 0.25)
+    s.step(x, 3)
+    ref = oracle_jacobi(p, O.surrogate_weights(p), 0.9, 3)
+    assert rel_inf(x.cpu().numpy(), ref[-1]) < TOL64
+
+
+def test_async_divergence_is_reported():
+    """Too many blocks in flight for the step (every block of a small problem at once, no
+    proximal weight) can make the asynchronous iteration diverge; the library must report
+    it (ENONFINITE) instead of returning garbage."""
+    import torch
+    from paper_1701_04900_gb300 import AsyflexaError
+    d = nesterov_lasso(2000, 10000, 100, lam=1.0, seed=11, store_dtype=np.float64)
+    s = make_solver(d, block_w=32, mode="async", gamma=0.9, max_sweeps=400, check_every=10)
+    x = xzeros(d, torch.float64)
+    try:
+        st = s.solve(x)
+    except AsyflexaError as e:
+        assert e.code == -5
+    else:
+        assert np.isfinite(st["F"])
 
 
 def test_invalid_inputs_are_rejected():
