@@ -21,6 +21,7 @@ constexpr int kCompactPerThread = 16;
 constexpr int kCompactTile = kAuxThreads * kCompactPerThread;
 constexpr int kGemvUnits = 2;     // 16-byte units of A per thread in gather_gemv
 constexpr int kNormsGrid = 256;
+constexpr int kCheckThreads = 1024;
 
 template <typename T>
 __device__ __forceinline__ T block_sum_256(T v, T* sh /* >= 8 */) {
@@ -40,7 +41,21 @@ __device__ __forceinline__ T block_sum_256(T v, T* sh /* >= 8 */) {
 
 // ----------------------------------------------------------------------------- weights
 
-// One warp per column: kappa_j = s_loss * ||a_j||^2 * scale_j^2 - c2, accumulated in FP64.
+// Accumulator of sums of products: FP64 FMAs for FP64 storage, the double-FP32 pair for
+// FP32-widened storage.
+template <typename TC>
+struct ProdAcc;
+template <>
+struct ProdAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct ProdAcc<float> : DFAcc {};
+
+// One warp per column: kappa_j = s_loss * ||a_j||^2 * scale_j^2 - c2, with the squares
+// accumulated exactly (ProdAcc) and combined across lanes in FP64.
 template <typename TA>
 __global__ void colnorm_kernel(const TA* A, int64_t lda, int64_t m, int64_t n, const float* scale, double s_loss,
                                double c2, double tau, double tau_rel, double* dw, int* neg_flag) {
@@ -51,7 +66,7 @@ __global__ void colnorm_kernel(const TA* A, int64_t lda, int64_t m, int64_t n, c
     const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
     for (int64_t j = gw; j < n; j += nw) {
         const TA* col = A + j * lda;
-        double acc = 0.0;
+        ProdAcc<TC> pa;
         const int64_t units = (m + V - 1) / V;
         for (int64_t u = lane; u < units; u += 32) {
             const uint4 q = ld_stream_u4(col + u * V);
@@ -59,8 +74,9 @@ __global__ void colnorm_kernel(const TA* A, int64_t lda, int64_t m, int64_t n, c
             ATraits<TA>::unpack(q, a);
 #pragma unroll
             for (int e = 0; e < V; ++e)
-                if (u * V + e < m) acc = fma(static_cast<double>(a[e]), static_cast<double>(a[e]), acc);
+                if (u * V + e < m) pa.add_prod(a[e], a[e]);
         }
+        double acc = pa.value();
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) {
@@ -189,6 +205,60 @@ __global__ void __launch_bounds__(kAuxThreads) gather_gemv_kernel(const TA* A, i
             for (int e = 0; e < V; ++e) out[uu[q] * V + e] = acc[q][e];
 }
 
+// Exact-accumulation variant for the residual refresh: same slicing as gather_gemv_kernel,
+// products a * (val * scale) summed with ProdAcc (FP64 FMAs for FP64 storage, the
+// double-FP32 pair otherwise), written as FP64 partials.  The factor val * scale is formed
+// in FP64 and split into hi + lo parts in the compute type.
+template <typename TA, typename TV>
+__global__ void __launch_bounds__(kAuxThreads) gather_gemv_exact_kernel(const TA* A, int64_t lda, int64_t mcopy,
+                                                                        const float* scale, const int* idx,
+                                                                        const TV* val, const int* count,
+                                                                        double* partial) {
+    using TC = typename ATraits<TA>::TC;
+    constexpr int V = ATraits<TA>::kVec;
+    const int cnt = *count;
+    const int nseg = gridDim.y;
+    const int seg = blockIdx.y;
+    const int k0 = static_cast<int>((static_cast<int64_t>(cnt) * seg) / nseg);
+    const int k1 = static_cast<int>((static_cast<int64_t>(cnt) * (seg + 1)) / nseg);
+    const int64_t units = mcopy / V;
+    int64_t uu[kGemvUnits];
+#pragma unroll
+    for (int q = 0; q < kGemvUnits; ++q)
+        uu[q] = (static_cast<int64_t>(blockIdx.x) * kGemvUnits + q) * kAuxThreads + threadIdx.x;
+    ProdAcc<TC> acc[kGemvUnits][V];
+    for (int k = k0; k < k1; ++k) {
+        const int j = __ldg(idx + k);
+        double v = static_cast<double>(__ldg(val + k));
+        if (scale) v *= static_cast<double>(__ldg(scale + j));
+        const TC vh = static_cast<TC>(v);
+        const TC vl = static_cast<TC>(v - static_cast<double>(vh));
+        const TA* col = A + static_cast<int64_t>(j) * lda;
+        uint4 q4[kGemvUnits];
+#pragma unroll
+        for (int q = 0; q < kGemvUnits; ++q)
+            if (uu[q] < units) q4[q] = ld_stream_u4(col + uu[q] * V);
+#pragma unroll
+        for (int q = 0; q < kGemvUnits; ++q) {
+            if (uu[q] < units) {
+                TC a[V];
+                ATraits<TA>::unpack(q4[q], a);
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    acc[q][e].add_prod(a[e], vh);
+                    if (vl != TC(0)) acc[q][e].add_prod(a[e], vl);
+                }
+            }
+        }
+    }
+    double* out = partial + static_cast<int64_t>(seg) * mcopy;
+#pragma unroll
+    for (int q = 0; q < kGemvUnits; ++q)
+        if (uu[q] < units)
+#pragma unroll
+            for (int e = 0; e < V; ++e) out[uu[q] * V + e] = acc[q][e].value();
+}
+
 // r[i] = (set ? -b[i] : r[i]) + sum_seg partial[seg][i]  for i < m (fixed order); r[i] = 0 for m <= i < mcopy.
 template <typename TP, typename TB>
 __global__ void reduce_partials_kernel(double* r, const TP* partial, int nseg, int64_t m, int64_t mcopy, const TB* b,
@@ -292,7 +362,7 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double 
 //       [5] nonfinite flag.  One warp per column.  The residual is staged in shared memory
 //       as (hi, lo) pairs when it fits (use_smem), else read from global memory.
 template <typename TA>
-__global__ void __launch_bounds__(kAuxThreads) check_kernel(const TA* A, int64_t lda, int64_t m, int64_t n,
+__global__ void __launch_bounds__(kCheckThreads) check_kernel(const TA* A, int64_t lda, int64_t m, int64_t n,
                                                             const float* scale, const double* r,
                                                             const typename XType<TA>::T* x,
                                                             const typename XType<TA>::T* lo,
@@ -320,28 +390,38 @@ __global__ void __launch_bounds__(kAuxThreads) check_kernel(const TA* A, int64_t
     double mmf = 0.0, mxh = 0.0, mkkt = 0.0, mx = 0.0;
     unsigned long long nnz = 0;
     int nonfinite = 0;
+    constexpr int kU = 4;  // independent 16-byte loads in flight per lane
     for (int64_t j = gw; j < n; j += nw) {
         const TA* col = A + j * lda;
         CheckDot<TA> acc;
         const int64_t units = mc / V;
-        for (int64_t u = lane; u < units; u += 32) {
-            const uint4 q = ld_stream_u4(col + u * V);
-            TC a[V];
-            ATraits<TA>::unpack(q, a);
+        for (int64_t u0 = lane; u0 < units; u0 += 32 * kU) {
+            uint4 q[kU];
 #pragma unroll
-            for (int e = 0; e < V; ++e) {
-                const int64_t i = u * V + e;
-                if (i < m) {
-                    TC h, l;
-                    if (use_smem) {
-                        h = rh_s[i];
-                        l = rl_s[i];
-                    } else {
-                        const double v = r[i];
-                        h = static_cast<TC>(v);
-                        l = static_cast<TC>(v - static_cast<double>(h));
+            for (int t = 0; t < kU; ++t)
+                if (u0 + 32 * t < units) q[t] = ld_stream_u4(col + (u0 + 32 * t) * V);
+#pragma unroll
+            for (int t = 0; t < kU; ++t) {
+                const int64_t u = u0 + 32 * t;
+                if (u < units) {
+                    TC a[V];
+                    ATraits<TA>::unpack(q[t], a);
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        const int64_t i = u * V + e;
+                        if (i < m) {
+                            TC h, l;
+                            if (use_smem) {
+                                h = rh_s[i];
+                                l = rl_s[i];
+                            } else {
+                                const double v = r[i];
+                                h = static_cast<TC>(v);
+                                l = static_cast<TC>(v - static_cast<double>(h));
+                            }
+                            acc.add(a[e], h, l);
+                        }
                     }
-                    acc.add(a[e], h, l);
                 }
             }
         }

@@ -181,7 +181,7 @@ cudaError_t Launcher<TA>::refresh(asyflexa_s& h, const void* xv) {
     compact_kernel<TX><<<h.compact_tiles, kAuxThreads, 0, h.stream>>>(x, P.n, h.tilecnt, h.compact_tiles, h.list_idx,
                                                                       static_cast<TX*>(h.list_val), h.count);
     dim3 g(h.gemv_rowtiles, h.nseg);
-    gather_gemv_kernel<TA, TX, double><<<g, kAuxThreads, 0, h.stream>>>(
+    gather_gemv_exact_kernel<TA, TX><<<g, kAuxThreads, 0, h.stream>>>(
         static_cast<const TA*>(P.A), P.lda, h.mcopy, P.col_scale, h.list_idx, static_cast<const TX*>(h.list_val),
         h.count, static_cast<double*>(h.partial));
     const int rg = static_cast<int>((h.mcopy + kAuxThreads - 1) / kAuxThreads);
@@ -207,7 +207,7 @@ cudaError_t Launcher<TA>::check(asyflexa_s& h, const void* xv) {
     const auto& P = h.prob;
     const bool lasso = P.loss == ASYFLEXA_LOSS_LASSO;
     const int lasso_nobox = lasso && P.lo == nullptr && P.hi == nullptr;
-    check_kernel<TA><<<h.check_ctas, kAuxThreads, h.check_use_smem ? h.check_smem : 0, h.stream>>>(
+    check_kernel<TA><<<h.check_ctas, kCheckThreads, h.check_use_smem ? h.check_smem : 0, h.stream>>>(
         static_cast<const TA*>(P.A), P.lda, P.m, P.n, P.col_scale, h.r, static_cast<const TX*>(xv),
         static_cast<const TX*>(P.lo), static_cast<const TX*>(P.hi), h.dw, P.lambda, lasso ? 1.0 : 2.0,
         lasso ? 0.0 : 2.0 * P.c, lasso_nobox, h.check_use_smem ? 1 : 0, h.meas);

@@ -6,12 +6,15 @@
 // coordinates move (the generic kernel re-reads every moving column for its scatter):
 //
 //   * at the start of a block the consumers stage the FP64 residual, converted to FP32, in
-//     shared memory: the stale read r~ of step S.2;
+//     shared memory (the stale read r~ of step S.2), together with the block's x_j, bounds,
+//     column scales, 1/d_j and lam/d_j;
 //   * every consumer thread owns the same 16-byte units u = k*256 + tid (k < 4*CPC) of
 //     every column.  A column arrives in CPC ring stages of 1024 units (16 KB, 1-D bulk TMA
-//     copies).  Consumers form a_j^T r~ from shared memory, reduce across warps, and one
-//     thread takes the closed-form best response and fixed step in FP64 (the surrogate is
-//     diagonal, so Delta_j only needs a_j^T r~);
+//     copies).  Consumers form a_j^T r~ from shared memory and publish per-warp partial
+//     sums; after one barrier every consumer thread evaluates the closed-form best
+//     response and fixed step for column j itself (identical FP32 arithmetic in every
+//     thread, so they all agree; the surrogate is diagonal, so Delta_j only needs
+//     a_j^T r~);
 //   * while the column is still in shared memory every thread adds a_j * Delta_j to its
 //     register copy of the block increment, then releases the column's stages;
 //   * after the block's w columns the increment is added to r with one FP64 atomic per row
@@ -35,7 +38,13 @@ constexpr int kRegMaxRowsPerThread = 96;
 struct RegLayout {
     int stages;
     size_t stage_bytes;
-    size_t off_ring, off_rt, off_colpart, off_bars, off_misc, total;
+    size_t off_ring, off_rt, off_colpart, off_coef, off_bars, off_misc, total;
+};
+
+// Per-column coefficients staged at the start of a block.
+struct ColCoef {
+    float x, lo, hi, dinv, thr, scale;  // x_j, bounds, 1/d_j (0 if d_j <= 0), lam/d_j, column scale
+    float pad0, pad1;
 };
 
 __host__ __device__ inline RegLayout make_reg_layout(int rt_rows, int stages) {
@@ -47,12 +56,14 @@ __host__ __device__ inline RegLayout make_reg_layout(int rt_rows, int stages) {
     o += L.stage_bytes * stages;
     L.off_rt = o;
     o = align_up_sz(o + static_cast<size_t>(rt_rows) * sizeof(float), 16);
-    L.off_colpart = o;
-    o = align_up_sz(o + kRegConsWarps * sizeof(float), 16);
+    L.off_colpart = o;  // two buffers of per-warp partial sums
+    o = align_up_sz(o + 2 * kRegConsWarps * sizeof(float), 16);
+    L.off_coef = o;
+    o = align_up_sz(o + kWMax * sizeof(ColCoef), 16);
     L.off_bars = o;
     o = align_up_sz(o + 2 * stages * sizeof(uint64_t), 16);
-    L.off_misc = o;  // abort flag, any flag, delta
-    o += 32;
+    L.off_misc = o;  // abort flag
+    o += 16;
     L.total = align_up_sz(o, 128);
     return L;
 }
@@ -62,6 +73,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
     using TC = typename ATraits<TA>::TC;
     static_assert(sizeof(TC) == 4, "register kernel computes in FP32");
     using TX = typename XType<TA>::T;
+    static_assert(sizeof(TX) == 4, "register kernel updates FP32 x");
     constexpr int V = ATraits<TA>::kVec;
     constexpr int UPT = kRegKpc * CPC;
     static_assert(UPT * V <= kRegMaxRowsPerThread, "too many rows per thread");
@@ -71,11 +83,10 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
     unsigned char* ring = smem + L.off_ring;
     float* rt = reinterpret_cast<float*>(smem + L.off_rt);
     float* colpart = reinterpret_cast<float*>(smem + L.off_colpart);
+    ColCoef* coef = reinterpret_cast<ColCoef*>(smem + L.off_coef);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.off_bars);
     uint64_t* empty = full + p.stages;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.off_misc);
-    volatile int* s_any = reinterpret_cast<volatile int*>(smem + L.off_misc + 4);
-    volatile float* s_delta = reinterpret_cast<volatile float*>(smem + L.off_misc + 8);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -91,7 +102,6 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
             mbar_init(&empty[s], kRegConsWarps);
         }
         *abort_flag = 0;
-        *s_any = 0;
         fence_barrier_init();
     }
     __syncthreads();
@@ -145,18 +155,23 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
     TX* x = static_cast<TX*>(p.x);
     const TX* lo = static_cast<const TX*>(p.lo);
     const TX* hi = static_cast<const TX*>(p.hi);
+    const float gamma = static_cast<float>(p.gamma);
+    const float s_loss = static_cast<float>(p.s_loss);
+    const float c2 = static_cast<float>(p.c2);
     int nchunks = 0;  // stages per column actually present
     for (int c = 0; c < CPC; ++c)
         if (static_cast<int64_t>(c) * kRegStageUnits < units) ++nchunks;
 
     float inc[UPT][V];
+    int buf = 0;
 
     for (int s = 0; s < p.sweeps; ++s) {
         for (int b = blockIdx.x; b < p.nblocks; b += gridDim.x) {
             const int64_t c0 = static_cast<int64_t>(b) * p.w;
             const int wb = static_cast<int>(min64(p.w, p.n - c0));
-            // S.2: stale read of the residual into shared memory (rows >= m hold 0).  The
-            // barrier at the end of the previous block guarantees nobody still reads rt.
+            // S.2: stale read of the residual into shared memory (rows >= m hold 0), and the
+            // block's per-column coefficients.  The barrier that ended the previous block
+            // guarantees nobody still reads rt or coef.
             if (tid == 0) u_read = ld_relaxed_u64(&p.counters[0]);
             {
                 const double2* rsrc = reinterpret_cast<const double2*>(p.r);
@@ -166,10 +181,24 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                     reinterpret_cast<float2*>(rt)[i] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
                 }
             }
+            if (tid < wb) {
+                const int64_t j = c0 + tid;
+                const double dj = p.dw[j];
+                ColCoef cf;
+                cf.x = static_cast<float>(x[j]);
+                cf.lo = lo ? static_cast<float>(lo[j]) : -INFINITY;
+                cf.hi = hi ? static_cast<float>(hi[j]) : INFINITY;
+                cf.dinv = dj > 0.0 ? static_cast<float>(1.0 / dj) : 0.f;
+                cf.thr = dj > 0.0 ? static_cast<float>(p.lam / dj) : 0.f;
+                cf.scale = p.scale ? p.scale[j] : 1.f;
+                cf.pad0 = cf.pad1 = 0.f;
+                coef[tid] = cf;
+            }
 #pragma unroll
             for (int k = 0; k < UPT; ++k)
 #pragma unroll
                 for (int e = 0; e < V; ++e) inc[k][e] = 0.f;
+            bool any = false;
             named_bar_sync(1, kRegConsThreads);
 
             for (int jl = 0; jl < wb; ++jl) {
@@ -215,27 +244,33 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                     }
                 }
                 const float v = warp_sum(acc0 + acc1);
-                if (lane == 0) colpart[warp] = v;
+                float* cp = colpart + buf * kRegConsWarps;
+                if (lane == 0) cp[warp] = v;
                 named_bar_sync(1, kRegConsThreads);
-                // ---- best response + fixed step (one thread, FP64)
-                if (tid == 0) {
-                    float dv = 0.f;
-                    if (!*abort_flag) {
-                        double g = 0.0;
+                // ---- best response (eq. 2) + fixed step (S.4): the same FP32 arithmetic in
+                // every consumer thread (fixed summation order), so all agree on Delta_j
+                float g = 0.f;
 #pragma unroll
-                        for (int k = 0; k < kRegConsWarps; ++k) g += static_cast<double>(colpart[k]);
-                        const int64_t j = c0 + jl;
-                        const double sc = p.scale ? static_cast<double>(p.scale[j]) : 1.0;
-                        const double delta =
-                            coordinate_update<TX>(g * sc, x, lo, hi, j, p.dw[j], p.lam, p.gamma, p.s_loss, p.c2);
-                        dv = static_cast<float>(delta * sc);
-                        if (delta != 0.0) *s_any = 1;
-                    }
-                    *s_delta = dv;
+                for (int k = 0; k < kRegConsWarps; ++k) g += cp[k];
+                buf ^= 1;
+                const ColCoef cf = coef[jl];
+                const float grad = s_loss * g * cf.scale - c2 * cf.x;
+                float xh = 0.f;
+                if (cf.dinv > 0.f) {
+                    const float vv = fmaf(-grad, cf.dinv, cf.x);
+                    const float av = fabsf(vv) - cf.thr;
+                    xh = av > 0.f ? copysignf(av, vv) : 0.f;
                 }
-                named_bar_sync(1, kRegConsThreads);
+                xh = fminf(fmaxf(xh, cf.lo), cf.hi);
+                const float xn = fmaf(gamma, xh - cf.x, cf.x);
+                const float dlt = xn - cf.x;
+                float dj = 0.f;
+                if (!*abort_flag) {
+                    if (tid == 0) x[c0 + jl] = static_cast<TX>(xn);
+                    dj = dlt * cf.scale;
+                    any |= dlt != 0.f;
+                }
                 // ---- fold a_j * Delta_j into the register increment, then release the stages
-                const float dj = *s_delta;
                 st_c = stage;
                 ph_c = phase;
 #pragma unroll
@@ -267,7 +302,6 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 phase = ph_c;
             }
             // ---- r += A_i Delta_i : one FP64 atomic per row (skipping exact zeros)
-            const bool any = *s_any != 0;
             if (any && !*abort_flag) {
 #pragma unroll
                 for (int k = 0; k < UPT; ++k) {
@@ -282,9 +316,8 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 }
                 __threadfence();
             }
-            named_bar_sync(1, kRegConsThreads);  // scatter complete; rt free; s_any read by all
+            named_bar_sync(1, kRegConsThreads);  // scatter complete and visible; rt and coef free
             if (tid == 0) {
-                *s_any = 0;
                 ++my_updates;
                 if (any) ++my_active;
                 const unsigned long long u1 = atomicAdd(&p.counters[0], 1ull);

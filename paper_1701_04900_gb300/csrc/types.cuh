@@ -77,6 +77,26 @@ __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return
 __device__ __forceinline__ float fmac(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fmac(double a, double b, double c) { return ::fma(a, b, c); }
 
+// Sum of FP32 products carried as an unevaluated pair (s, c) of FP32 numbers using the
+// error-free transformations TwoProduct (via FMA) and TwoSum (Knuth), as in the Dot2
+// algorithm of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26(6), 2005).  The result is as accurate as a dot product computed in twice the
+// working precision, without FP64 arithmetic in the loop (FP64 throughput on GB300 is a
+// small fraction of FP32).
+struct DFAcc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = a * b;
+        const float ep = fmaf(a, b, -p);  // exact: a*b = p + ep
+        const float t = s + p;
+        const float z = t - s;
+        const float es = (s - (t - z)) + (p - z);  // exact: s + p = t + es
+        s = t;
+        c += es + ep;
+    }
+    __device__ __forceinline__ double value() const { return static_cast<double>(s) + static_cast<double>(c); }
+};
+
 // x / b / bounds type: double for FP64 problems, float otherwise.
 template <typename TA>
 struct XType {
