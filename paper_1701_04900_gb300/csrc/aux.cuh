@@ -178,22 +178,35 @@ __global__ void __launch_bounds__(kAuxThreads) gather_gemv_kernel(const TA* A, i
     for (int q = 0; q < kGemvUnits; ++q)
 #pragma unroll
         for (int e = 0; e < V; ++e) acc[q][e] = TP(0);
-    for (int k = k0; k < k1; ++k) {
-        const int j = __ldg(idx + k);
-        TP vk = static_cast<TP>(__ldg(val + k));
-        if (scale) vk *= static_cast<TP>(__ldg(scale + j));
-        const TA* col = A + static_cast<int64_t>(j) * lda;
-        uint4 q4[kGemvUnits];
+    constexpr int KU = 4;  // list entries whose loads are in flight together
+    for (int k = k0; k < k1; k += KU) {
+        uint4 q4[KU][kGemvUnits];
+        TP vk[KU];
 #pragma unroll
-        for (int q = 0; q < kGemvUnits; ++q)
-            if (uu[q] < units) q4[q] = ld_stream_u4(col + uu[q] * V);
+        for (int t = 0; t < KU; ++t) {
+            vk[t] = TP(0);
+            if (k + t < k1) {
+                const int j = __ldg(idx + k + t);
+                vk[t] = static_cast<TP>(__ldg(val + k + t));
+                if (scale) vk[t] *= static_cast<TP>(__ldg(scale + j));
+                const TA* col = A + static_cast<int64_t>(j) * lda;
 #pragma unroll
-        for (int q = 0; q < kGemvUnits; ++q) {
-            if (uu[q] < units) {
-                TC a[V];
-                ATraits<TA>::unpack(q4[q], a);
+                for (int q = 0; q < kGemvUnits; ++q)
+                    if (uu[q] < units) q4[t][q] = ld_stream_u4(col + uu[q] * V);
+            }
+        }
 #pragma unroll
-                for (int e = 0; e < V; ++e) acc[q][e] = fmac(static_cast<TP>(a[e]), vk, acc[q][e]);
+        for (int t = 0; t < KU; ++t) {
+            if (k + t < k1) {
+#pragma unroll
+                for (int q = 0; q < kGemvUnits; ++q) {
+                    if (uu[q] < units) {
+                        TC a[V];
+                        ATraits<TA>::unpack(q4[t][q], a);
+#pragma unroll
+                        for (int e = 0; e < V; ++e) acc[q][e] = fmac(static_cast<TP>(a[e]), vk[t], acc[q][e]);
+                    }
+                }
             }
         }
     }
@@ -227,26 +240,39 @@ __global__ void __launch_bounds__(kAuxThreads) gather_gemv_exact_kernel(const TA
     for (int q = 0; q < kGemvUnits; ++q)
         uu[q] = (static_cast<int64_t>(blockIdx.x) * kGemvUnits + q) * kAuxThreads + threadIdx.x;
     ProdAcc<TC> acc[kGemvUnits][V];
-    for (int k = k0; k < k1; ++k) {
-        const int j = __ldg(idx + k);
-        double v = static_cast<double>(__ldg(val + k));
-        if (scale) v *= static_cast<double>(__ldg(scale + j));
-        const TC vh = static_cast<TC>(v);
-        const TC vl = static_cast<TC>(v - static_cast<double>(vh));
-        const TA* col = A + static_cast<int64_t>(j) * lda;
-        uint4 q4[kGemvUnits];
+    constexpr int KU = 4;  // list entries whose loads are in flight together
+    for (int k = k0; k < k1; k += KU) {
+        uint4 q4[KU][kGemvUnits];
+        TC vh[KU], vl[KU];
 #pragma unroll
-        for (int q = 0; q < kGemvUnits; ++q)
-            if (uu[q] < units) q4[q] = ld_stream_u4(col + uu[q] * V);
+        for (int t = 0; t < KU; ++t) {
+            vh[t] = vl[t] = TC(0);
+            if (k + t < k1) {
+                const int j = __ldg(idx + k + t);
+                double v = static_cast<double>(__ldg(val + k + t));
+                if (scale) v *= static_cast<double>(__ldg(scale + j));
+                vh[t] = static_cast<TC>(v);
+                vl[t] = static_cast<TC>(v - static_cast<double>(vh[t]));
+                const TA* col = A + static_cast<int64_t>(j) * lda;
 #pragma unroll
-        for (int q = 0; q < kGemvUnits; ++q) {
-            if (uu[q] < units) {
-                TC a[V];
-                ATraits<TA>::unpack(q4[q], a);
+                for (int q = 0; q < kGemvUnits; ++q)
+                    if (uu[q] < units) q4[t][q] = ld_stream_u4(col + uu[q] * V);
+            }
+        }
 #pragma unroll
-                for (int e = 0; e < V; ++e) {
-                    acc[q][e].add_prod(a[e], vh);
-                    if (vl != TC(0)) acc[q][e].add_prod(a[e], vl);
+        for (int t = 0; t < KU; ++t) {
+            if (k + t < k1) {
+#pragma unroll
+                for (int q = 0; q < kGemvUnits; ++q) {
+                    if (uu[q] < units) {
+                        TC a[V];
+                        ATraits<TA>::unpack(q4[t][q], a);
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            acc[q][e].add_prod(a[e], vh[t]);
+                            if (vl[t] != TC(0)) acc[q][e].add_prod(a[e], vl[t]);
+                        }
+                    }
                 }
             }
         }

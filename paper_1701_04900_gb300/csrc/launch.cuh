@@ -48,7 +48,7 @@ const void* reg_kernel(int cpc) {
 // Choose the register-increment kernel instance that covers the column (sets h.reg_*).
 // Returns 0 if none applies (the staged kernel is used), 1 if chosen, or a negative
 // cudaError_t if setting its shared-memory attribute failed.  The ring must hold one
-// column plus at least two 16 KB stages of prefetch.
+// column plus at least one 16 KB stage of prefetch (more stages when they fit).
 template <typename TA>
 int Launcher<TA>::choose_reg(asyflexa_s& h) {
     h.reg_upt = h.reg_cpc = h.reg_stages = 0;
@@ -60,7 +60,7 @@ int Launcher<TA>::choose_reg(asyflexa_s& h) {
     if (!fn) return 0;
     const int rt_rows = static_cast<int>(h.mcopy);
     const RegLayout L0 = make_reg_layout(rt_rows, 0);
-    if (L0.total + 512 + static_cast<size_t>(cpc + 2) * L0.stage_bytes > h.smem_optin) return 0;
+    if (L0.total + 512 + static_cast<size_t>(cpc + 1) * L0.stage_bytes > h.smem_optin) return 0;
     int stages = static_cast<int>((h.smem_optin - L0.total - 512) / L0.stage_bytes);
     if (stages > 16) stages = 16;
     h.reg_upt = kRegKpc * cpc;

@@ -174,11 +174,23 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
             // guarantees nobody still reads rt or coef.
             if (tid == 0) u_read = ld_relaxed_u64(&p.counters[0]);
             {
+                // 8 independent 16-byte L2 loads in flight per thread
+                constexpr int kB = 8;
                 const double2* rsrc = reinterpret_cast<const double2*>(p.r);
-                const int64_t pairs = p.mcopy / 2;
-                for (int64_t i = tid; i < pairs; i += kRegConsThreads) {
-                    const double2 v = __ldcg(rsrc + i);
-                    reinterpret_cast<float2*>(rt)[i] = make_float2(static_cast<float>(v.x), static_cast<float>(v.y));
+                float2* rdst = reinterpret_cast<float2*>(rt);
+                const int pairs = static_cast<int>(p.mcopy / 2);
+                for (int i0 = tid; i0 < pairs; i0 += kB * kRegConsThreads) {
+                    double2 v[kB];
+#pragma unroll
+                    for (int t = 0; t < kB; ++t) {
+                        const int i = i0 + t * kRegConsThreads;
+                        v[t] = i < pairs ? __ldcg(rsrc + i) : make_double2(0.0, 0.0);
+                    }
+#pragma unroll
+                    for (int t = 0; t < kB; ++t) {
+                        const int i = i0 + t * kRegConsThreads;
+                        if (i < pairs) rdst[i] = make_float2(static_cast<float>(v[t].x), static_cast<float>(v[t].y));
+                    }
                 }
             }
             if (tid < wb) {
@@ -203,7 +215,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
 
             for (int jl = 0; jl < wb; ++jl) {
                 // ---- dot a_j^T r~ over this thread's rows
-                float acc0 = 0.f, acc1 = 0.f;
+                float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
                 uint32_t st_c = stage, ph_c = phase;
                 bool ok = !*abort_flag;
 #pragma unroll 1
@@ -225,8 +237,8 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                                             const float4 r4 = *reinterpret_cast<const float4*>(rv + e);
                                             acc0 = fmaf(a[e], r4.x, acc0);
                                             acc1 = fmaf(a[e + 1], r4.y, acc1);
-                                            acc0 = fmaf(a[e + 2], r4.z, acc0);
-                                            acc1 = fmaf(a[e + 3], r4.w, acc1);
+                                            acc2 = fmaf(a[e + 2], r4.z, acc2);
+                                            acc3 = fmaf(a[e + 3], r4.w, acc3);
                                         }
                                     } else {
                                         const int valid = static_cast<int>(p.m - u * V);
@@ -243,7 +255,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                         }
                     }
                 }
-                const float v = warp_sum(acc0 + acc1);
+                const float v = warp_sum((acc0 + acc1) + (acc2 + acc3));
                 float* cp = colpart + buf * kRegConsWarps;
                 if (lane == 0) cp[warp] = v;
                 named_bar_sync(1, kRegConsThreads);
@@ -314,9 +326,13 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                         }
                     }
                 }
-                __threadfence();
+                // A single CTA runs its blocks strictly in order (cyclic Gauss-Seidel), so its
+                // next read of r must see this scatter.  With several CTAs the next read may
+                // miss it: that is one more update in flight, within the bounded-delay model
+                // (Assumption D1), so no fence is spent there.
+                if (gridDim.x == 1) __threadfence();
             }
-            named_bar_sync(1, kRegConsThreads);  // scatter complete and visible; rt and coef free
+            named_bar_sync(1, kRegConsThreads);  // scatter issued; rt and coef free
             if (tid == 0) {
                 ++my_updates;
                 if (any) ++my_active;
