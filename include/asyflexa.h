@@ -189,6 +189,34 @@ int asyflexa_get_residual(asyflexa_t h, double* r_out);
 /* Copy the surrogate weights d_j (FP64, length n) into a caller device buffer.  Synchronises. */
 int asyflexa_get_weights(asyflexa_t h, double* d_out);
 
+/* r_out = A x - b for the problem *prob at x, without a handle and without allocating
+ * any device memory.  (The paper has no counterpart; this is a service entry point.)
+ *
+ * For callers that cannot allocate device memory when they need the residual: code that
+ * runs while a CUDA stream is being captured into a graph, where cudaMalloc is not
+ * permitted, or a latency-sensitive loop in which cudaMalloc/cudaFree would synchronise
+ * the device and stall other streams.  The result equals asyflexa_residual_refresh on a
+ * handle for the same problem and x (same kernels: ordered compaction of the nonzeros of
+ * x, compensated products, fixed-order FP64 reduction), up to the number of partial sums.
+ *
+ * prob: as for asyflexa_create (device pointers A, b, col_scale; lo, hi, lambda, c, loss
+ * are ignored).  x: length n device vector of x_dtype.  r_out: caller-owned device buffer
+ * of m doubles.  cuda_stream: the stream the kernels are enqueued on (NULL = legacy
+ * default stream); the call does not synchronise.
+ *
+ * Limits: n <= 262144 and m <= 654848 (the row limit is what fits one FP64 partial sum per
+ * row in the scratch).
+ * Larger problems return ASYFLEXA_EINVAL with a message naming the limit; other argument
+ * errors also return ASYFLEXA_EINVAL.  Messages: asyflexa_last_error(NULL), per thread.
+ *
+ * Scratch: one file-scope 8 MiB device array, held by every GPU that loads the library
+ * until the process exits.  Its device address is looked up (cudaGetSymbolAddress) by the
+ * first call on each device, so make that first call before any stream capture.  Every
+ * call shares the array: calls that overlap on the GPU (e.g. on two streams) race and must
+ * be serialised by the caller.  The array keeps the last call's contents; every scratch
+ * value a call reads is written earlier in the same call, so nothing needs clearing. */
+int asyflexa_residual_noalloc(const asyflexa_problem* prob, const void* x, double* r_out, void* cuda_stream);
+
 /* Last error message of the handle (or of the calling thread for NULL).  Never NULL. */
 const char* asyflexa_last_error(asyflexa_t h);
 

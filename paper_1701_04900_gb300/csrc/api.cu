@@ -230,6 +230,12 @@ int validate_opts(const asyflexa_opts* o, std::string* why) {
 
 }  // namespace
 
+namespace asyflexa_internal {
+// Used by the handle-free entry point in noalloc.cu to report errors through
+// asyflexa_last_error(NULL).  Not exported.
+__attribute__((visibility("hidden"))) void set_thread_error(const std::string& msg) { g_thread_msg = msg; }
+}  // namespace asyflexa_internal
+
 extern "C" {
 
 int asyflexa_version(void) { return ASYFLEXA_ABI_VERSION; }

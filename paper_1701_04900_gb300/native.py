@@ -66,7 +66,7 @@ EXPORTS = [
     "asyflexa_version", "asyflexa_status_string", "asyflexa_opts_default", "asyflexa_create",
     "asyflexa_destroy", "asyflexa_residual_refresh", "asyflexa_step", "asyflexa_solve", "asyflexa_check",
     "asyflexa_read_counters", "asyflexa_reset_counters", "asyflexa_get_residual", "asyflexa_get_weights",
-    "asyflexa_last_error",
+    "asyflexa_last_error", "asyflexa_residual_noalloc",
 ]
 
 
@@ -108,6 +108,8 @@ def lib(path: str | None = None):
     L.asyflexa_get_weights.argtypes = [vp, vp]
     L.asyflexa_last_error.restype = C.c_char_p
     L.asyflexa_last_error.argtypes = [vp]
+    L.asyflexa_residual_noalloc.restype = C.c_int
+    L.asyflexa_residual_noalloc.argtypes = [C.POINTER(Problem), vp, vp, vp]
     del dbl
     if path is None:
         _lib = L
