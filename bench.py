@@ -326,12 +326,18 @@ def run_ours(args):
             "sample": f"FP64 numpy cyclic Gauss-Seidel sweeps (w={W_BLOCK}) over the first {ncols} columns "
                       f"({ncols // W_BLOCK} blocks) of this {M}x{N} instance for {r['seconds']:.1f} s "
                       f"({r['sweeps']} sweeps)"}
+    s.close()
+    if rank == 0 and not args.no_forms:
+        del gen, At, b
+        torch.cuda.empty_cache()
+        result["forms"] = {"mixed_precision": run_form_mixed_precision(args)}
+        torch.cuda.empty_cache()
+        result["forms"]["gradient"] = run_form_gradient(args)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(result), flush=True)
-    s.close()
     del np
 
 
@@ -412,6 +418,113 @@ def run_e2e(gen, f_ref, args, refresh_every, check_every):
             "steps": steps, "seconds_per_step": el / steps}
 
 
+def run_form_mixed_precision(args):
+    """System form (1): the nonconvex quadratic 10000 x 50000 with box |x| <= 1, A stored as
+    FP32, BF16 or FP8-e4m3 codes with per-column scales (library quantiser), solved from
+    x = 0 to ||xhat(x) - x||_inf / max(1, ||x||_inf) <= 1e-6 on the FP32 problem.  The
+    BF16/FP8 runs refresh and check on the FP32 master copy and finish with FP32 polish
+    sweeps.  Reports time, sweeps and speedup over the plain FP32 form at that accuracy."""
+    import torch
+    from paper_1701_04900_gb300 import Solver
+    from paper_1701_04900_gb300.native import quantize
+    from inputs import ncquad_problem_torch
+    m, n = 10000, 50000
+    gen = ncquad_problem_torch(m, n, seed=0, device="cuda")
+    At, b, lo, hi = gen["At"], gen["b"], gen["lo"], gen["hi"]
+    # Proximal weight for the asynchronous iteration: with P CTAs x w columns in flight the
+    # stale updates behave like a Jacobi step on that many columns, whose Hessian block
+    # 2 A_S^T A_S has norm about 2 (1 + sqrt(P w / m))^2 for unit-norm Gaussian columns; the
+    # surrogate curvature must exceed gamma/2 of it (the descent condition of Theorem 1's proof
+    # with the delay in place of the Jacobi coupling).  kappa_j = 2||a_j||^2 - 2c ~ 2 - 2c.
+    inflight = torch.cuda.get_device_properties(0).multi_processor_count * W_BLOCK
+    tau = max(0.0, 0.5 * GAMMA * 2.0 * (1.0 + math.sqrt(inflight / m)) ** 2 - (2.0 - 2.0 * gen["c"]))
+    common = dict(loss="ncquad", c=gen["c"], lo=lo, hi=hi, block_w=W_BLOCK, mode="async", gamma=GAMMA, tau=tau,
+                  max_sweeps=4000, check_every=10, refresh_every=10, tol_stat=1e-6)
+    out = {"workload": f"ncquad_{m}x{n}_box1", "c": gen["c"], "lambda": gen["lam"], "tau": tau}
+    runs = {"fp32": None, "bf16": "bf16", "fp8": "fp8"}
+    for name, kind in runs.items():
+        if kind is None:
+            s = Solver(At, b, gen["lam"], m=m, **common)
+        else:
+            Q, sc = quantize(At, m, kind)
+            s = Solver(Q, b, gen["lam"], m=m, col_scale=sc, A_master=At, **common)
+        x = torch.zeros(n, dtype=torch.float32, device="cuda")
+        s.solve(x)                      # warm-up (same work)
+        times = []
+        for _ in range(2):
+            x.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = s.solve(x)
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        out[name] = {"seconds": min(times), "sweeps": st["sweeps"], "polish_sweeps": st["polish_sweeps"],
+                     "stat_xhat": st["stat_xhat"], "F": st["F"], "nnz": st["nnz"], "status": st["status"],
+                     "bytes_per_sweep": n * m * {"fp32": 4, "bf16": 2, "fp8": 1}[name]}
+        s.close()
+    for name in ("bf16", "fp8"):
+        out[name]["speedup_vs_fp32"] = out["fp32"]["seconds"] / out[name]["seconds"]
+    return out
+
+
+def run_form_gradient(args):
+    """System form (3): L(lam, b) = ||A_val x*(lam, b) - b_val||^2 on the LASSO train split
+    5000 x 20000 (Nesterov planted at lam = 1) with a 2000-row validation split from the same
+    generator.  Times the forward solve, the backward (adjoint block update on the support,
+    through torch.autograd), and central differences (2 solves); then tunes lam by 20 steps of
+    gradient descent on log(lam) (first step normalised to 0.1 in log(lam))."""
+    import torch
+    from inputs import nesterov_lasso_torch, validation_rows_torch
+    from paper_1701_04900_gb300.autograd import lasso_solution
+    m, n, k = 5000, 20000, 200
+    gen = nesterov_lasso_torch(m, n, k, lam=1.0, seed=0, device="cuda")
+    val = validation_rows_torch(gen, 2000, seed=1)
+    At, b = gen["At"], gen["b"]
+    Av = val["At"][:, :2000].T.contiguous()
+    bv = val["b"]
+    solve_kw = dict(mode="async", block_w=W_BLOCK, gamma=GAMMA, max_sweeps=4000, check_every=10, tol_stat=1e-7,
+                    num_ctas=32)
+
+    def fwd_bwd(lam_v):
+        lam = torch.tensor(lam_v, dtype=torch.float64, device="cuda", requires_grad=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = lasso_solution(lam, b, At, m, solve_kw)
+        loss = ((Av @ x - bv) ** 2).sum()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        loss.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        return float(loss), float(lam.grad), t1 - t0, t2 - t1, int((x != 0).sum())
+
+    def loss_only(lam_v):
+        with torch.no_grad():
+            x = lasso_solution(torch.tensor(lam_v, dtype=torch.float64, device="cuda"), b, At, m, solve_kw)
+            return float(((Av @ x - bv) ** 2).sum())
+
+    fwd_bwd(1.0)                                       # warm-up
+    L0, g0, t_fwd, t_bwd, nnz = fwd_bwd(1.0)
+    h = 1e-4
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    fd = (loss_only(1.0 + h) - loss_only(1.0 - h)) / (2 * h)
+    t_fd = time.perf_counter() - t0
+    log_lam, lr = 0.0, 0.1 / max(abs(g0), 1e-30)      # gradient wrt log(lam) is lam * dL/dlam
+    traj = []
+    t0 = time.perf_counter()
+    for _ in range(20):
+        lam_v = math.exp(log_lam)
+        L, g, _, _, _ = fwd_bwd(lam_v)
+        traj.append((lam_v, L))
+        log_lam -= lr * lam_v * g
+    t_tune = time.perf_counter() - t0
+    return {"workload": f"lasso_train_{m}x{n}_val_2000", "loss_at_lam1": L0, "dL_dlam": g0, "fd_dL_dlam": fd,
+            "rel_diff_vs_fd": abs(g0 - fd) / max(abs(fd), 1e-30), "forward_s": t_fwd, "backward_s": t_bwd,
+            "fd_two_solves_s": t_fd, "backward_speedup_vs_fd": t_fd / max(t_bwd, 1e-12), "nnz": nnz,
+            "tune_20_steps_s": t_tune, "lambda_final": traj[-1][0], "loss_first": traj[0][1], "loss_last": traj[-1][1]}
+
+
 def run_ncu_case(args):
     """Small case for ncu captures: the same generator with n = 12800 (A = 1 GB, larger
     than L2), one refresh, then `--ncu-launches` async sweep launches of 10 sweeps each
@@ -453,6 +566,7 @@ def main():
     ap.add_argument("--no-sync", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

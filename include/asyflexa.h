@@ -86,6 +86,13 @@ typedef struct {
     double c;                   /* NCQUAD concavity weight (ignored for LASSO) */
     int32_t loss;               /* asyflexa_loss */
     int32_t reserved0;
+    const void* A_master;       /* optional FP32 copy of A (m x n, leading dimension lda_master), only
+                                   with BF16/FP8 storage: exact residual refreshes and checks use it, and
+                                   solve ends with FP32 "polish" sweeps on it (see asyflexa_solve) */
+    int64_t lda_master;
+    const void* lin;            /* optional linear term (length n, x_dtype): f(x) += lin^T x, so
+                                   grad_j f gains lin_j; NULL = 0.  With lambda = 0 and b = 0 the method
+                                   then solves A^T A x = -lin (used by the adjoint of the solution map) */
 } asyflexa_problem;
 
 /* Method parameters.  Fill with asyflexa_opts_default, then override. */
@@ -108,6 +115,8 @@ typedef struct {
     int32_t variant;            /* async kernel: 0 = automatic, 1 = staged residual tile (any m, any
                                    dtype), 2 = register-resident residual (FP32/BF16/FP8, m up to
                                    24576 rows; EUNSUPPORTED otherwise) */
+    double switch_tol;          /* with A_master: solve leaves the low-precision phase when a check
+                                   interval lowers F by less than switch_tol * |F| (default 1e-7) */
 } asyflexa_opts;
 
 /* Results and counters.  Optimality fields are FP64 and computed from an exact
@@ -131,6 +140,8 @@ typedef struct {
     int64_t sweep_kernel_sweeps;   /* profile=1: sweeps performed by those launches */
     int32_t status;             /* asyflexa_status of the last solve/check */
     int32_t checked;            /* 1 if the stat_* / kkt fields were evaluated */
+    int64_t polish_sweeps;      /* with A_master: sweeps of the last solve run on the FP32 copy */
+    double polish_seconds;      /* with A_master: device time of that FP32 phase */
 } asyflexa_stats;
 
 /* Library version (ASYFLEXA_ABI_VERSION).  Never fails. */
@@ -168,7 +179,14 @@ int asyflexa_residual_refresh(asyflexa_t h, const void* x);
 int asyflexa_step(asyflexa_t h, void* x, int32_t n_sweeps);
 
 /* Run sweeps from the given x (in place) until the stopping rule of the options holds
- * or max_sweeps is reached (ENOTCONV).  Fills *out (may be NULL).  Synchronises. */
+ * or max_sweeps is reached (ENOTCONV).  Every check_every sweeps F is evaluated from an
+ * exact residual; once (F - f_star)/|f_star| <= tol_gap (or always, if f_star is NaN) the
+ * stationarity ||xhat(x) - x||_inf / max(1, ||x||_inf) is evaluated and the solve stops when
+ * it is <= tol_stat.  With A_master set, these sweeps run on the BF16/FP8 matrix while
+ * F, the residual refreshes and the stationarity are those of the FP32 problem; when a check
+ * interval lowers F by less than switch_tol * |F| the solve continues with FP32 sweeps on
+ * A_master ("polish") until the same stopping rule holds.  Fills *out (may be NULL);
+ * out->block_updates counts this solve's updates.  Synchronises. */
 int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out);
 
 /* Evaluate F, rel_gap, the stationarity measures, KKT and nnz at x, after an exact
@@ -216,6 +234,25 @@ int asyflexa_get_weights(asyflexa_t h, double* d_out);
  * be serialised by the caller.  The array keeps the last call's contents; every scratch
  * value a call reads is written earlier in the same call, so nothing needs clearing. */
 int asyflexa_residual_noalloc(const asyflexa_problem* prob, const void* x, double* r_out, void* cuda_stream);
+
+/* Per-column scaled low-precision storage of an FP32 matrix, for the BF16/FP8 form of the
+ * method: Q[:, j] = round(A[:, j] / scale[j]) in `dtype` (ASYFLEXA_BF16 or ASYFLEXA_FP8E4M3,
+ * round-to-nearest, FP8 saturating to finite values), with scale[j] = max_i |A[i, j]| / qmax
+ * (qmax = 448 for FP8, 1 for BF16; 1 for a zero column), so that a_j ~= scale[j] * Q[:, j].
+ * A: m x n FP32 column-major (lda >= m).  Q: output, ldq >= m with ldq * element size a
+ * multiple of 16 bytes (rows m..ldq-1 are written as 0).  scale: output, n floats.  All
+ * device pointers, caller-owned.  Enqueued on cuda_stream; does not synchronise.
+ * EINVAL on bad arguments (message: asyflexa_last_error(NULL)). */
+int asyflexa_quantize(const float* A, int64_t m, int64_t n, int64_t lda, int32_t dtype, void* Q, int64_t ldq,
+                      float* scale, void* cuda_stream);
+
+/* out[:, c] = A[:, idx[c]] for c < k: the column submatrix A_S of an m x n column-major
+ * matrix of `dtype` (asyflexa_dtype), e.g. the columns on the support of a solution for the
+ * adjoint of the solution map.  Rows m..ldo-1 of out are written as 0.  A (lda), out (ldo):
+ * device, 16-byte aligned, column strides multiples of 16 bytes; idx: k device int32 indices
+ * in [0, n) (not checked).  Enqueued on cuda_stream.  EINVAL on bad arguments. */
+int asyflexa_gather_columns(const void* A, int64_t lda, int32_t dtype, int64_t m, const int32_t* idx, int64_t k,
+                            void* out, int64_t ldo, void* cuda_stream);
 
 /* Last error message of the handle (or of the calling thread for NULL).  Never NULL. */
 const char* asyflexa_last_error(asyflexa_t h);

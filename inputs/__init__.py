@@ -13,5 +13,8 @@ from .problems import (  # noqa: F401
     nesterov_lasso_torch,
     random_lasso,
     ncquad_problem,
+    ncquad_problem_torch,
     pad_lda,
+    validation_rows,
+    validation_rows_torch,
 )

@@ -95,7 +95,22 @@ def nesterov_lasso(m: int, n: int, k: int, lam: float = 1.0, seed: int = 0,
     b = b64.astype(store_dtype)
     f_star = 0.5 * float(y @ y) + lam * float(np.abs(x_star).sum())
     return dict(At=At, b=b, x_star=x_star, y_star=y, f_star=f_star, lam=float(lam),
-                m=m, n=n, lda=lda, support=support)
+                m=m, n=n, lda=lda, support=support, col_scale=scale)
+
+
+def validation_rows(gen: dict, m_val: int, seed: int = 1, noise: float = 0.01) -> dict:
+    """Validation split "from the same generator": m_val new rows with entries iid U[-1, 1]
+    times the training column scalings, and b_val = A_val x* + noise * N(0, 1).
+    Returns At_val (n, lda_val) in the training storage type and b_val."""
+    rng = np.random.default_rng(seed)
+    n = gen["n"]
+    B = rng.uniform(-1.0, 1.0, size=(n, m_val)) * gen["col_scale"][:, None]
+    dt = gen["At"].dtype
+    lda = pad_lda(m_val, np.dtype(dt).itemsize)
+    At_val = np.zeros((n, lda), dtype=dt)
+    At_val[:, :m_val] = B.astype(dt)
+    b_val = At_val[:, :m_val].astype(np.float64).T @ gen["x_star"] + noise * rng.standard_normal(m_val)
+    return dict(At=At_val, b=b_val.astype(dt), m=m_val, n=n, lda=lda)
 
 
 def nesterov_lasso_torch(m: int, n: int, k: int, lam: float = 1.0, seed: int = 0,
@@ -137,6 +152,7 @@ def nesterov_lasso_torch(m: int, n: int, k: int, lam: float = 1.0, seed: int = 0
     lda = pad_lda(m, elt)
     At = torch.zeros((ncols, lda), dtype=dtype, device=device)
     s_all = torch.empty(ncols, dtype=f64, device=device)
+    col_scale = torch.empty(ncols, dtype=f64, device=device)
     for j0 in range(0, ncols, chunk):
         j1 = min(ncols, j0 + chunk)
         Bt = torch.rand((min(n, j0 + chunk) - j0, m), generator=g, device=device, dtype=f64)[: j1 - j0]
@@ -149,6 +165,7 @@ def nesterov_lasso_torch(m: int, n: int, k: int, lam: float = 1.0, seed: int = 0
         scale = torch.where(o, lam / sa, scale)
         big = (~o) & (sa > lam)
         scale = torch.where(big, lam * xi[j0:j1] / sa, scale)
+        col_scale[j0:j1] = scale
         At[j0:j1, :m] = (Bt * scale[:, None]).to(dtype)
         del Bt
     ks = int(support.numel())
@@ -162,7 +179,28 @@ def nesterov_lasso_torch(m: int, n: int, k: int, lam: float = 1.0, seed: int = 0
     b = b64.to(dtype)
     f_star = 0.5 * float(y @ y) + lam * float(x_star.abs().sum())
     return dict(At=At, b=b, x_star=x_star, y_star=y, f_star=f_star, lam=float(lam),
-                m=m, n=ncols, lda=lda, support=support)
+                m=m, n=ncols, lda=lda, support=support, col_scale=col_scale)
+
+
+def validation_rows_torch(gen: dict, m_val: int, seed: int = 1, noise: float = 0.01) -> dict:
+    """:func:`validation_rows` for a torch instance (generated on its device)."""
+    import torch
+
+    dev = gen["At"].device
+    g = torch.Generator(device=dev)
+    g.manual_seed(int(seed))
+    n = gen["n"]
+    lda = pad_lda(m_val, gen["At"].element_size())
+    At_val = torch.zeros((n, lda), dtype=gen["At"].dtype, device=dev)
+    chunk = 8192
+    for j0 in range(0, n, chunk):
+        j1 = min(n, j0 + chunk)
+        B = torch.rand((j1 - j0, m_val), generator=g, device=dev, dtype=torch.float64) * 2.0 - 1.0
+        At_val[j0:j1, :m_val] = (B * gen["col_scale"][j0:j1, None]).to(gen["At"].dtype)
+    sup = gen["support"]
+    b_val = At_val[sup, :m_val].double().T @ gen["x_star"][sup] + noise * torch.randn(
+        m_val, generator=g, device=dev, dtype=torch.float64)
+    return dict(At=At_val, b=b_val.to(gen["At"].dtype), m=m_val, n=n, lda=lda)
 
 
 def random_lasso(m: int, n: int, seed: int = 0, dist: str = "uniform", lam: float = 0.1,
@@ -195,6 +233,37 @@ def random_lasso(m: int, n: int, seed: int = 0, dist: str = "uniform", lam: floa
         out["lo"] = np.full(n, -box, dtype=store_dtype)
         out["hi"] = np.full(n, box, dtype=store_dtype)
     return out
+
+
+def ncquad_problem_torch(m: int, n: int, seed: int = 0, frac: float = 0.05, noise: float = 0.01,
+                         box: float = 1.0, lam_frac: float = 0.1, device="cuda") -> dict:
+    """:func:`ncquad_problem` generated with torch on ``device`` in FP32 storage (for the
+    10000 x 50000 instance).  Same recipe; a different random stream."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    lda = pad_lda(m, 4)
+    At = torch.zeros((n, lda), dtype=torch.float32, device=device)
+    chunk = 8192
+    for j0 in range(0, n, chunk):
+        j1 = min(n, j0 + chunk)
+        At[j0:j1, :m] = torch.randn((j1 - j0, m), generator=g, device=device, dtype=torch.float32) / math.sqrt(m)
+    k = int(round(frac * n))
+    idx = torch.randperm(n, generator=g, device=device)[:k]
+    x0 = torch.zeros(n, dtype=torch.float64, device=device)
+    x0[idx] = torch.randn(k, generator=g, device=device, dtype=torch.float64)
+    e = noise * torch.randn(m, generator=g, device=device, dtype=torch.float64)
+    b64 = At[idx, :m].double().T @ x0[idx] + e
+    b = b64.to(torch.float32)
+    atb = torch.empty(n, dtype=torch.float64, device=device)
+    for j0 in range(0, n, chunk):
+        atb[j0:j0 + chunk] = At[j0:j0 + chunk, :m].double() @ b.double()
+    c = 0.5 * (1.0 - math.sqrt(n / m)) ** 2
+    lam = lam_frac * 2.0 * float(atb.abs().max())
+    return dict(At=At, b=b, x0=x0, c=float(c), lam=float(lam), m=m, n=n, lda=lda,
+                lo=torch.full((n,), -box, dtype=torch.float32, device=device),
+                hi=torch.full((n,), box, dtype=torch.float32, device=device))
 
 
 def ncquad_problem(m: int, n: int, seed: int = 0, frac: float = 0.05, noise: float = 0.01,

@@ -54,7 +54,7 @@ __all__ = [
     "gauss_seidel_sweep", "random_sequential", "delayed_sweeps", "mf_measure",
     "xhat_merit", "kkt_violation", "stationarity", "brute_force_lasso",
     "stationary_points_box", "lambda_max_gram", "jacobi_tau_rel", "solve_gs",
-    "solve_jacobi",
+    "solve_jacobi", "lasso_support", "lasso_adjoint_gradient",
 ]
 
 
@@ -69,6 +69,7 @@ class Problem:
     c: float = 0.0
     lo: np.ndarray | None = None
     hi: np.ndarray | None = None
+    lin: np.ndarray | None = None      # optional linear term of f: f(x) += lin^T x
     meta: dict = field(default_factory=dict)
 
     @property
@@ -125,6 +126,8 @@ def objective(p: Problem, x: np.ndarray) -> float:
         f = 0.5 * float(r @ r)
     else:
         f = float(r @ r) - p.c * float(x @ x)
+    if p.lin is not None:
+        f += float(p.lin @ x)
     return f + p.lam * float(np.abs(x).sum())
 
 
@@ -135,6 +138,8 @@ def gradient(p: Problem, x: np.ndarray, r: np.ndarray | None = None) -> np.ndarr
     g = p.s * (p.A.T @ r)
     if p.loss != "lasso":
         g = g - 2.0 * p.c * x
+    if p.lin is not None:
+        g = g + p.lin
     return g
 
 
@@ -178,6 +183,8 @@ def _block_step(p: Problem, x, r_tilde, d, gamma, cols, lo, hi):
     g = p.s * (p.A[:, cols].T @ r_tilde)
     if p.loss != "lasso":
         g = g - 2.0 * p.c * x[cols]
+    if p.lin is not None:
+        g = g + p.lin[cols]
     xh = best_response(x[cols], g, d[cols], p.lam, lo[cols], hi[cols])
     return gamma * (xh - x[cols])
 
@@ -410,6 +417,33 @@ def stationary_points_box(p: Problem, tol=1e-9):
         if good and not any(np.allclose(x, y, atol=1e-9, rtol=0) for y in pts):
             pts.append(x)
     return pts
+
+
+# ------------------------------------------------------------- adjoint (not in the paper)
+
+def lasso_support(x, rel_tol=1e-5):
+    """Support of a LASSO solution: |x_j| > rel_tol * max(1, ||x||_inf)."""
+    x = np.asarray(x, dtype=np.float64)
+    return np.nonzero(np.abs(x) > rel_tol * max(1.0, float(np.abs(x).max(initial=0.0))))[0]
+
+
+def lasso_adjoint_gradient(A, x, v, rel_tol=1e-5):
+    """Gradient of L(x*(lam, b)) for the LASSO minimiser x* of 0.5||Ax - b||^2 + lam||x||_1.
+
+    On the support S with signs s the optimality conditions A_S^T (A_S x_S - b) + lam s = 0
+    are smooth in (lam, b); differentiating them gives dx_S = (A_S^T A_S)^-1 (A_S^T db - s dlam).
+    With v = dL/dx* and w = (A_S^T A_S)^-1 v_S (FP64 Cholesky):
+        dL/dlam = -s^T w,   dL/db = A_S w.
+    Valid where the support and signs are locally constant.  Returns (dL/dlam, dL/db, w, S).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    S = lasso_support(x, rel_tol)
+    s = np.sign(np.asarray(x, dtype=np.float64)[S])
+    AS = A[:, S]
+    G = AS.T @ AS
+    L = np.linalg.cholesky(G)
+    w = np.linalg.solve(L.T, np.linalg.solve(L, np.asarray(v, dtype=np.float64)[S]))
+    return float(-(s @ w)), AS @ w, w, S
 
 
 # ------------------------------------------------------------- parameter helpers

@@ -79,8 +79,16 @@ void free_buffers(asyflexa_s* h) {
 }
 
 int do_refresh(asyflexa_s& h, const void* x) {
-    cudaError_t e = dispatch(h, [&](auto L) { return decltype(L)::refresh(h, x); });
-    if (e != cudaSuccess) return cuda_error(&h, e, "residual refresh");
+    if (h.master) {
+        // exact residual of the FP32 problem, shared with the low-precision sweeps
+        int rc = do_refresh(*h.master, x);
+        if (rc) return set_error(&h, rc, std::string("master refresh: ") + h.master->msg);
+        CK(&h, cudaMemcpyAsync(h.r, h.master->r, h.prob.m * sizeof(double), cudaMemcpyDeviceToDevice, h.stream),
+           "copy master residual");
+    } else {
+        cudaError_t e = dispatch(h, [&](auto L) { return decltype(L)::refresh(h, x); });
+        if (e != cudaSuccess) return cuda_error(&h, e, "residual refresh");
+    }
     h.r_valid = true;
     h.r_x = x;
     return ASYFLEXA_OK;
@@ -102,11 +110,11 @@ int device_error(asyflexa_s& h) {
 int objective(asyflexa_s& h, const void* x, double* F, double* nnz) {
     cudaError_t e = dispatch(h, [&](auto L) { return decltype(L)::norms(h, x); });
     if (e != cudaSuccess) return cuda_error(&h, e, "norms");
-    double v[4];
+    double v[5];
     CK(&h, cudaMemcpyAsync(v, h.norms_out, sizeof(v), cudaMemcpyDeviceToHost, h.stream), "read norms");
     CK(&h, cudaStreamSynchronize(h.stream), "synchronize");
     const bool lasso = h.prob.loss == ASYFLEXA_LOSS_LASSO;
-    *F = (lasso ? 0.5 * v[0] : v[0] - h.prob.c * v[2]) + h.prob.lambda * v[1];
+    *F = (lasso ? 0.5 * v[0] : v[0] - h.prob.c * v[2]) + v[4] + h.prob.lambda * v[1];
     if (nnz) *nnz = v[3];
     if (!std::isfinite(*F)) return set_error(&h, ASYFLEXA_ENONFINITE, "objective is not finite");
     return ASYFLEXA_OK;
@@ -225,6 +233,7 @@ int validate_opts(const asyflexa_opts* o, std::string* why) {
     if (o->num_ctas < 0) return *why = "num_ctas must be >= 0", 1;
     if (o->variant < 0 || o->variant > 2) return *why = "variant must be 0, 1 or 2", 1;
     if (!(o->tol_gap >= 0.0) || !(o->tol_stat >= 0.0)) return *why = "tolerances must be >= 0", 1;
+    if (!(o->switch_tol >= 0.0)) return *why = "switch_tol must be >= 0", 1;
     return 0;
 }
 
@@ -270,6 +279,7 @@ void asyflexa_opts_default(asyflexa_opts* o) {
     o->tol_stat = 1e-6;
     o->f_star = std::nan("");
     o->seed = 0;
+    o->switch_tol = 1e-7;
 }
 
 const char* asyflexa_last_error(asyflexa_t h) { return h ? h->msg.c_str() : g_thread_msg.c_str(); }
@@ -298,6 +308,12 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
     if (!(P->lambda >= 0.0) || !std::isfinite(P->lambda)) return set_error(nullptr, ASYFLEXA_EINVAL, "lambda must be finite and >= 0");
     if (P->loss != ASYFLEXA_LOSS_LASSO && P->loss != ASYFLEXA_LOSS_NCQUAD) return set_error(nullptr, ASYFLEXA_EINVAL, "unknown loss");
     if (!std::isfinite(P->c)) return set_error(nullptr, ASYFLEXA_EINVAL, "c must be finite");
+    if (P->A_master) {
+        if (!quant) return set_error(nullptr, ASYFLEXA_EINVAL, "A_master is only for BF16/FP8 storage");
+        if (P->lda_master < P->m || (P->lda_master * 4) % 16 != 0 || (reinterpret_cast<uintptr_t>(P->A_master) & 15u))
+            return set_error(nullptr, ASYFLEXA_EINVAL,
+                             "A_master must be 16-byte aligned with lda_master >= m and lda_master a multiple of 4");
+    }
 
     auto* h = new (std::nothrow) asyflexa_s();
     if (!h) return set_error(nullptr, ASYFLEXA_ENOMEM, "host allocation failed");
@@ -367,7 +383,7 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
         const int64_t units = h->mcopy / h->vec;
         const int64_t per_cta = 256 * kGemvUnitsHost;
         h->gemv_rowtiles = static_cast<int>((units + per_cta - 1) / per_cta);
-        int nseg = static_cast<int>((2 * h->sm_count + h->gemv_rowtiles - 1) / h->gemv_rowtiles);
+        int nseg = static_cast<int>((4 * h->sm_count + h->gemv_rowtiles - 1) / h->gemv_rowtiles);
         h->nseg = nseg < 1 ? 1 : (nseg > 64 ? 64 : nseg);
         h->compact_tiles = static_cast<int>((n + kCompactTileHost - 1) / kCompactTileHost);
         h->check_ctas = h->sm_count;
@@ -383,8 +399,8 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
     CKC(cudaMalloc(&h->tilecnt, h->compact_tiles * sizeof(int)), "alloc tiles");
     CKC(cudaMalloc(&h->count, sizeof(int)), "alloc count");
     CKC(cudaMalloc(&h->partial, static_cast<size_t>(h->nseg) * h->mcopy * sizeof(double)), "alloc partials");
-    CKC(cudaMalloc(&h->norms_part, kNormsGridHost * 4 * sizeof(double)), "alloc norms");
-    CKC(cudaMalloc(&h->norms_out, 4 * sizeof(double)), "alloc norms");
+    CKC(cudaMalloc(&h->norms_part, kNormsGridHost * 8 * sizeof(double)), "alloc norms");
+    CKC(cudaMalloc(&h->norms_out, 8 * sizeof(double)), "alloc norms");
     CKC(cudaMalloc(&h->counters, 4 * sizeof(unsigned long long)), "alloc counters");
     CKC(cudaMalloc(&h->hist, 32 * sizeof(unsigned long long)), "alloc hist");
     CKC(cudaMalloc(&h->meas, 8 * sizeof(unsigned long long)), "alloc measures");
@@ -445,6 +461,25 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
             }
         }
     }
+    if (P->A_master) {
+        asyflexa_problem mp = *P;
+        mp.A = P->A_master;
+        mp.lda = P->lda_master;
+        mp.a_dtype = ASYFLEXA_F32;
+        mp.x_dtype = ASYFLEXA_F32;
+        mp.col_scale = nullptr;
+        mp.A_master = nullptr;
+        mp.lda_master = 0;
+        asyflexa_opts mo = *O;
+        mo.variant = 0;
+        asyflexa_t mh = nullptr;
+        const int rc = asyflexa_create(&mh, &mp, &mo, stream);
+        if (rc) {
+            set_error(h, rc, std::string("FP32 master copy: ") + asyflexa_last_error(nullptr));
+            return fail(rc);
+        }
+        h->master = mh;
+    }
 #undef CKC
     h->msg = "no error";
     *out = h;
@@ -458,6 +493,7 @@ int asyflexa_destroy(asyflexa_t h) {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);
     }
+    if (h->master) asyflexa_destroy(h->master);
     free_buffers(h);
     delete h;
     return ASYFLEXA_OK;
@@ -480,6 +516,17 @@ int asyflexa_step(asyflexa_t h, void* x, int32_t n_sweeps) {
 int asyflexa_check(asyflexa_t h, const void* x, asyflexa_stats* out) {
     if (!h) return set_error(nullptr, ASYFLEXA_EINVAL, "h is NULL");
     if (!x || !out) return set_error(h, ASYFLEXA_EINVAL, "x or out is NULL");
+    if (h->master) {
+        // optimality of the FP32 problem, evaluated on the master copy
+        int rc = asyflexa_check(h->master, x, out);
+        if (rc) return set_error(h, rc, std::string("master check: ") + h->master->msg);
+        CK(h, cudaMemcpyAsync(h->r, h->master->r, h->prob.m * sizeof(double), cudaMemcpyDeviceToDevice, h->stream),
+           "copy master residual");
+        h->r_valid = true;
+        h->r_x = x;
+        out->kernel_launches = h->launches + h->master->launches;
+        return ASYFLEXA_OK;
+    }
     int rc = do_refresh(*h, x);
     if (rc) return rc;
     double F = 0.0, nnz = 0.0;
@@ -517,7 +564,11 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
     const bool known = std::isfinite(fs);
     long long sweeps = 0;
     int status = ASYFLEXA_ENOTCONV;
-    double F = NAN;
+    double F = NAN, F_prev = NAN;
+    bool polish = false;
+    // With an FP32 master copy the loop below is the low-precision phase: F and the
+    // stationarity are those of the FP32 problem (the refreshes use the master copy), and the
+    // phase ends early when a check interval no longer lowers F by switch_tol * |F|.
     while (!rc && sweeps < h->opts.max_sweeps) {
         const int k = static_cast<int>(std::min<long long>(h->opts.check_every, h->opts.max_sweeps - sweeps));
         rc = run_sweeps(*h, x, k);
@@ -528,13 +579,19 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
         rc = device_error(*h);
         if (rc) break;
         const double gap = known ? (F - fs) / std::fabs(fs) : NAN;
-        if (known && !(gap <= h->opts.tol_gap)) continue;
+        const bool stalled = h->master && std::isfinite(F_prev) && (F_prev - F) <= h->opts.switch_tol * std::fabs(F);
+        F_prev = F;
+        if (known && !(gap <= h->opts.tol_gap) && !stalled) continue;
         Measures M{};
-        rc = measure(*h, x, &M);
+        rc = h->master ? measure(*h->master, x, &M) : measure(*h, x, &M);
         if (rc) break;
         const double stat = M.xh / std::max(1.0, M.xmax);
-        if (stat <= h->opts.tol_stat) {
+        if (stat <= h->opts.tol_stat && (!known || gap <= h->opts.tol_gap)) {
             status = ASYFLEXA_OK;
+            break;
+        }
+        if (stalled) {
+            polish = true;
             break;
         }
     }
@@ -544,6 +601,23 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    long long polish_sweeps = 0;
+    double polish_seconds = 0.0;
+    if (!rc && polish && sweeps < h->opts.max_sweeps) {
+        // FP32 polish on the master copy, from the current x (its residual is current)
+        asyflexa_s& mh = *h->master;
+        const int saved = mh.opts.max_sweeps;
+        mh.opts.max_sweeps = static_cast<int>(h->opts.max_sweeps - sweeps);
+        asyflexa_stats ms_st;
+        std::memset(&ms_st, 0, sizeof ms_st);
+        const int prc = asyflexa_solve(&mh, x, &ms_st);
+        mh.opts.max_sweeps = saved;
+        if (prc < 0) return set_error(h, prc, std::string("FP32 polish: ") + mh.msg);
+        polish_sweeps = ms_st.sweeps;
+        polish_seconds = ms_st.seconds;
+        sweeps += polish_sweeps;
+        status = prc;
+    }
     if (rc) {
         if (out) {
             out->status = rc;
@@ -553,18 +627,20 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
     // final evaluation at the returned x
     rc = asyflexa_check(h, x, &st);
     st.sweeps = sweeps;
-    st.seconds = ms * 1e-3;
-    st.hbm_bytes = static_cast<double>(sweeps) * static_cast<double>(h->prob.n) * static_cast<double>(h->prob.m) *
-                   static_cast<double>(h->elt_a);
+    st.seconds = ms * 1e-3 + polish_seconds;
+    st.polish_sweeps = polish_sweeps;
+    st.polish_seconds = polish_seconds;
+    st.hbm_bytes = (static_cast<double>(sweeps - polish_sweeps) * h->elt_a + static_cast<double>(polish_sweeps) * 4.0) *
+                   static_cast<double>(h->prob.n) * static_cast<double>(h->prob.m);
     {
-        unsigned long long c[4], hist[32];
-        CK(h, cudaMemcpyAsync(c, h->counters, sizeof c, cudaMemcpyDeviceToHost, h->stream), "read counters");
+        unsigned long long hist[32];
         CK(h, cudaMemcpyAsync(hist, h->hist, sizeof hist, cudaMemcpyDeviceToHost, h->stream), "read hist");
         CK(h, cudaStreamSynchronize(h->stream), "synchronize");
-        st.block_updates = static_cast<int64_t>(c[1]);
+        // every sweep updates every block exactly once
+        st.block_updates = static_cast<int64_t>(sweeps) * h->nblocks;
         for (int k = 0; k < 32; ++k) st.staleness_hist[k] = hist[k];
     }
-    st.kernel_launches = h->launches;
+    st.kernel_launches = h->launches + (h->master ? h->master->launches : 0);
     if (!rc) rc = status;
     st.status = rc;
     if (out) *out = st;

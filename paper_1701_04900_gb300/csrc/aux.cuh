@@ -303,39 +303,46 @@ __global__ void reduce_partials_kernel(double* r, const TP* partial, int nseg, i
 
 // ----------------------------------------------------------------------------- norms
 
-// part[blk*4 + {0,1,2,3}] = {sum r_i^2, sum |x_j|, sum x_j^2, nnz(x)} over a fixed stride.
+constexpr int kNormsFields = 5;
+
+// part[blk*5 + {0..4}] = {sum r_i^2, sum |x_j|, sum x_j^2, nnz(x), sum lin_j x_j} over a
+// fixed stride (lin may be null).
 template <typename TX>
 __global__ void __launch_bounds__(kAuxThreads) norms_kernel(const double* r, int64_t m, const TX* x, int64_t n,
-                                                            double* part) {
+                                                            const TX* lin, double* part) {
     __shared__ double sh[kAuxThreads / 32];
     const int64_t stride = static_cast<int64_t>(gridDim.x) * kAuxThreads;
     const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kAuxThreads + threadIdx.x;
-    double rr = 0.0, a1 = 0.0, a2 = 0.0, nz = 0.0;
+    double rr = 0.0, a1 = 0.0, a2 = 0.0, nz = 0.0, lx = 0.0;
     for (int64_t i = i0; i < m; i += stride) rr = fma(r[i], r[i], rr);
     for (int64_t j = i0; j < n; j += stride) {
         const double v = static_cast<double>(x[j]);
         a1 += fabs(v);
         a2 = fma(v, v, a2);
         nz += (v != 0.0) ? 1.0 : 0.0;
+        if (lin) lx = fma(static_cast<double>(lin[j]), v, lx);
     }
     rr = block_sum_256<double>(rr, sh);
     a1 = block_sum_256<double>(a1, sh);
     a2 = block_sum_256<double>(a2, sh);
     nz = block_sum_256<double>(nz, sh);
+    lx = block_sum_256<double>(lx, sh);
     if (threadIdx.x == 0) {
-        part[blockIdx.x * 4 + 0] = rr;
-        part[blockIdx.x * 4 + 1] = a1;
-        part[blockIdx.x * 4 + 2] = a2;
-        part[blockIdx.x * 4 + 3] = nz;
+        double* o = part + blockIdx.x * kNormsFields;
+        o[0] = rr;
+        o[1] = a1;
+        o[2] = a2;
+        o[3] = nz;
+        o[4] = lx;
     }
 }
 
 template <typename T>
 __global__ void finalize_norms_kernel(const T* part, int nparts, T* out) {
     // templated only so that every translation unit may instantiate it
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < kNormsFields) {
         double s = 0.0;
-        for (int k = 0; k < nparts; ++k) s += part[k * 4 + threadIdx.x];
+        for (int k = 0; k < nparts; ++k) s += part[k * kNormsFields + threadIdx.x];
         out[threadIdx.x] = s;
     }
 }
@@ -393,8 +400,9 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(const TA* A, int64
                                                             const typename XType<TA>::T* x,
                                                             const typename XType<TA>::T* lo,
                                                             const typename XType<TA>::T* hi, const double* dw,
-                                                            double lam, double s_loss, double c2, int lasso_nobox,
-                                                            int use_smem, unsigned long long* meas) {
+                                                            const typename XType<TA>::T* lin, double lam,
+                                                            double s_loss, double c2, int lasso_nobox, int use_smem,
+                                                            unsigned long long* meas) {
     using TC = typename ATraits<TA>::TC;
     constexpr int V = ATraits<TA>::kVec;
     extern __shared__ __align__(16) unsigned char csm[];
@@ -457,7 +465,7 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(const TA* A, int64
         if (lane == 0) {
             const double sc = scale ? static_cast<double>(scale[j]) : 1.0;
             const double xj = static_cast<double>(x[j]);
-            const double grad = s_loss * g * sc - c2 * xj;
+            const double grad = s_loss * g * sc - c2 * xj + (lin ? static_cast<double>(lin[j]) : 0.0);
             const double l = lo ? static_cast<double>(lo[j]) : -INFINITY;
             const double h = hi ? static_cast<double>(hi[j]) : INFINITY;
             // M_F: unit-weight proximal step

@@ -62,6 +62,9 @@ struct asyflexa_s {
     double prof_seconds = 0.0;
     long long prof_launches = 0, prof_sweep_total = 0;
 
+    // FP32 master copy of a BF16/FP8 problem (an internal handle), or null
+    asyflexa_s* master = nullptr;
+
     // host-side bookkeeping
     bool r_valid = false;
     const void* r_x = nullptr;

@@ -117,6 +117,7 @@ cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
     p.lo = P.lo;
     p.hi = P.hi;
     p.dw = h.dw;
+    p.lin = P.lin;
     p.lam = P.lambda;
     p.gamma = h.opts.gamma;
     p.s_loss = lasso ? 1.0 : 2.0;
@@ -195,7 +196,7 @@ template <typename TA>
 cudaError_t Launcher<TA>::norms(asyflexa_s& h, const void* xv) {
     using TX = typename XType<TA>::T;
     norms_kernel<TX><<<kNormsGrid, kAuxThreads, 0, h.stream>>>(h.r, h.prob.m, static_cast<const TX*>(xv), h.prob.n,
-                                                                h.norms_part);
+                                                                static_cast<const TX*>(h.prob.lin), h.norms_part);
     finalize_norms_kernel<double><<<1, 32, 0, h.stream>>>(h.norms_part, kNormsGrid, h.norms_out);
     h.launches += 2;
     return cudaGetLastError();
@@ -209,7 +210,8 @@ cudaError_t Launcher<TA>::check(asyflexa_s& h, const void* xv) {
     const int lasso_nobox = lasso && P.lo == nullptr && P.hi == nullptr;
     check_kernel<TA><<<h.check_ctas, kCheckThreads, h.check_use_smem ? h.check_smem : 0, h.stream>>>(
         static_cast<const TA*>(P.A), P.lda, P.m, P.n, P.col_scale, h.r, static_cast<const TX*>(xv),
-        static_cast<const TX*>(P.lo), static_cast<const TX*>(P.hi), h.dw, P.lambda, lasso ? 1.0 : 2.0,
+        static_cast<const TX*>(P.lo), static_cast<const TX*>(P.hi), h.dw, static_cast<const TX*>(P.lin), P.lambda,
+        lasso ? 1.0 : 2.0,
         lasso ? 0.0 : 2.0 * P.c, lasso_nobox, h.check_use_smem ? 1 : 0, h.meas);
     ++h.launches;
     return cudaGetLastError();

@@ -81,6 +81,7 @@ struct SweepParams {
     const void* lo;          // TX[n] or nullptr
     const void* hi;          // TX[n] or nullptr
     const double* dw;        // surrogate weights d_j
+    const void* lin;         // TX[n] linear term of f, or nullptr
     double lam, gamma, s_loss, c2;
     int w, nblocks, sweeps;
     int tile_rows, ntiles, chunk_rows, stages;
@@ -102,9 +103,9 @@ __device__ __forceinline__ TC warp_sum(TC v) {
 template <typename TX>
 __device__ __forceinline__ double coordinate_update(double g_atr, TX* x, const TX* lo, const TX* hi, int64_t j,
                                                     double dj, double lam, double gamma, double s_loss,
-                                                    double c2) {
+                                                    double c2, double linj) {
     const double xj = static_cast<double>(x[j]);
-    const double grad = s_loss * g_atr - c2 * xj;
+    const double grad = s_loss * g_atr - c2 * xj + linj;
     double xh = 0.0;
     if (dj > 0.0) {
         const double v = xj - grad / dj;
@@ -316,8 +317,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(const SweepPara
                     for (int k = 0; k < kConsWarps; ++k) g += static_cast<double>(colsum[k * kWMax + tid]);
                     const int64_t j = c0 + tid;
                     const double sc = p.scale ? static_cast<double>(p.scale[j]) : 1.0;
-                    const double delta =
-                        coordinate_update<TX>(g * sc, x, lo, hi, j, p.dw[j], p.lam, p.gamma, p.s_loss, p.c2);
+                    const double linj = p.lin ? static_cast<double>(static_cast<const TX*>(p.lin)[j]) : 0.0;
+                    const double delta = coordinate_update<TX>(g * sc, x, lo, hi, j, p.dw[j], p.lam, p.gamma,
+                                                               p.s_loss, p.c2, linj);
                     flag = delta != 0.0;
                     if (MODE == kJacobi) {
                         static_cast<TC*>(p.delta)[j] = static_cast<TC>(delta);

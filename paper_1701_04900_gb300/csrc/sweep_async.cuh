@@ -8,7 +8,7 @@
 //   * at the start of a block the consumers stage the FP64 residual, converted to FP32, in
 //     shared memory (the stale read r~ of step S.2), together with the block's x_j, bounds,
 //     column scales, 1/d_j and lam/d_j;
-//   * every consumer thread owns the same 16-byte units u = k*256 + tid (k < 4*CPC) of
+//   * every consumer thread owns the same 16-byte units u = k*512 + tid (k < 2*CPC) of
 //     every column.  A column arrives in CPC ring stages of 1024 units (16 KB, 1-D bulk TMA
 //     copies).  Consumers form a_j^T r~ from shared memory and publish per-warp partial
 //     sums; after one barrier every consumer thread evaluates the closed-form best
@@ -28,12 +28,12 @@
 
 namespace asyflexa {
 
-constexpr int kRegConsWarps = 8;
+constexpr int kRegConsWarps = 16;
 constexpr int kRegConsThreads = kRegConsWarps * 32;
 constexpr int kRegThreads = kRegConsThreads + 32;
-constexpr int kRegKpc = 4;                                   // units per thread per stage
+constexpr int kRegKpc = 2;                                   // units per thread per stage
 constexpr int kRegStageUnits = kRegKpc * kRegConsThreads;    // 1024 units = 16 KB
-constexpr int kRegMaxRowsPerThread = 96;
+constexpr int kRegMaxRowsPerThread = 48;
 
 struct RegLayout {
     int stages;
@@ -44,7 +44,7 @@ struct RegLayout {
 // Per-column coefficients staged at the start of a block.
 struct ColCoef {
     float x, lo, hi, dinv, thr, scale;  // x_j, bounds, 1/d_j (0 if d_j <= 0), lam/d_j, column scale
-    float pad0, pad1;
+    float lin, pad0;                    // linear term of f (0 if none)
 };
 
 __host__ __device__ inline RegLayout make_reg_layout(int rt_rows, int stages) {
@@ -203,7 +203,8 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 cf.dinv = dj > 0.0 ? static_cast<float>(1.0 / dj) : 0.f;
                 cf.thr = dj > 0.0 ? static_cast<float>(p.lam / dj) : 0.f;
                 cf.scale = p.scale ? p.scale[j] : 1.f;
-                cf.pad0 = cf.pad1 = 0.f;
+                cf.lin = p.lin ? static_cast<float>(static_cast<const TX*>(p.lin)[j]) : 0.f;
+                cf.pad0 = 0.f;
                 coef[tid] = cf;
             }
 #pragma unroll
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 for (int k = 0; k < kRegConsWarps; ++k) g += cp[k];
                 buf ^= 1;
                 const ColCoef cf = coef[jl];
-                const float grad = s_loss * g * cf.scale - c2 * cf.x;
+                const float grad = s_loss * g * cf.scale - c2 * cf.x + cf.lin;
                 float xh = 0.f;
                 if (cf.dinv > 0.f) {
                     const float vv = fmaf(-grad, cf.dinv, cf.x);

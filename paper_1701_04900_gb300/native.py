@@ -30,6 +30,8 @@ class Problem(C.Structure):
         ("lo", C.c_void_p), ("hi", C.c_void_p),
         ("lam", C.c_double), ("c", C.c_double),
         ("loss", C.c_int32), ("reserved0", C.c_int32),
+        ("A_master", C.c_void_p), ("lda_master", C.c_int64),
+        ("lin", C.c_void_p),
     ]
 
 
@@ -41,6 +43,7 @@ class Opts(C.Structure):
         ("num_ctas", C.c_int32),
         ("tol_gap", C.c_double), ("tol_stat", C.c_double), ("f_star", C.c_double),
         ("seed", C.c_uint64), ("profile", C.c_int32), ("variant", C.c_int32),
+        ("switch_tol", C.c_double),
     ]
 
 
@@ -53,6 +56,7 @@ class Stats(C.Structure):
         ("sweep_kernel_seconds", C.c_double), ("sweep_kernel_launches", C.c_int64),
         ("sweep_kernel_sweeps", C.c_int64),
         ("status", C.c_int32), ("checked", C.c_int32),
+        ("polish_sweeps", C.c_int64), ("polish_seconds", C.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -66,7 +70,7 @@ EXPORTS = [
     "asyflexa_version", "asyflexa_status_string", "asyflexa_opts_default", "asyflexa_create",
     "asyflexa_destroy", "asyflexa_residual_refresh", "asyflexa_step", "asyflexa_solve", "asyflexa_check",
     "asyflexa_read_counters", "asyflexa_reset_counters", "asyflexa_get_residual", "asyflexa_get_weights",
-    "asyflexa_last_error", "asyflexa_residual_noalloc",
+    "asyflexa_last_error", "asyflexa_residual_noalloc", "asyflexa_quantize", "asyflexa_gather_columns",
 ]
 
 
@@ -110,6 +114,10 @@ def lib(path: str | None = None):
     L.asyflexa_last_error.argtypes = [vp]
     L.asyflexa_residual_noalloc.restype = C.c_int
     L.asyflexa_residual_noalloc.argtypes = [C.POINTER(Problem), vp, vp, vp]
+    L.asyflexa_quantize.restype = C.c_int
+    L.asyflexa_quantize.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, i32, vp, C.c_int64, vp, vp]
+    L.asyflexa_gather_columns.restype = C.c_int
+    L.asyflexa_gather_columns.argtypes = [vp, C.c_int64, i32, C.c_int64, vp, C.c_int64, vp, C.c_int64, vp]
     del dbl
     if path is None:
         _lib = L
@@ -158,14 +166,15 @@ class Solver:
     def __init__(self, At, b, lam, m=None, *, loss="lasso", c=0.0, lo=None, hi=None, col_scale=None,
                  block_w=32, mode="sync", gamma=0.9, tau=0.0, tau_rel=0.0, refresh_every=10,
                  check_every=10, max_sweeps=1000, num_ctas=0, tol_gap=1e-6, tol_stat=1e-6,
-                 f_star=math.nan, profile=False, variant=0, stream=None):
+                 f_star=math.nan, profile=False, variant=0, A_master=None, switch_tol=1e-7, lin=None,
+                 stream=None):
         import torch
         L = lib()
         if At.dim() != 2 or not At.is_contiguous() or not At.is_cuda:
             raise ValueError("At must be a contiguous (n, lda) CUDA tensor")
         n, lda = At.shape
         m = lda if m is None else int(m)
-        self._keep = [At, b, lo, hi, col_scale]
+        self._keep = [At, b, lo, hi, col_scale, A_master, lin]
         p = Problem()
         p.m, p.n, p.lda = m, n, lda
         p.a_dtype = _dtype_code(At)
@@ -175,6 +184,12 @@ class Solver:
         p.hi = hi.data_ptr() if hi is not None else None
         p.lam, p.c = float(lam), float(c)
         p.loss = LOSS_LASSO if loss == "lasso" else LOSS_NCQUAD
+        if lin is not None:
+            p.lin = lin.data_ptr()
+        if A_master is not None:
+            if A_master.dtype != torch.float32 or not A_master.is_contiguous() or A_master.shape[0] != n:
+                raise ValueError("A_master must be a contiguous float32 (n, lda_master) CUDA tensor")
+            p.A_master, p.lda_master = A_master.data_ptr(), A_master.shape[1]
         o = default_opts()
         o.block_w, o.mode = int(block_w), (ASYNC if mode == "async" else SYNC)
         o.gamma, o.tau, o.tau_rel = float(gamma), float(tau), float(tau_rel)
@@ -183,6 +198,7 @@ class Solver:
         o.tol_gap, o.tol_stat, o.f_star = float(tol_gap), float(tol_stat), float(f_star)
         o.profile = 1 if profile else 0
         o.variant = int(variant)
+        o.switch_tol = float(switch_tol)
         self.problem, self.opts = p, o
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
@@ -277,3 +293,28 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def quantize(At, m: int, kind: str, stream=None):
+    """Per-column scaled BF16 / FP8-e4m3 copy of a float32 (n, lda) CUDA matrix by the
+    library's kernel (asyflexa_quantize).  Returns (Q of shape (n, ldq), scale (n,))."""
+    import torch
+    if At.dtype != torch.float32 or not At.is_cuda or not At.is_contiguous():
+        raise ValueError("At must be a contiguous float32 CUDA tensor")
+    n, lda = At.shape
+    if kind == "bf16":
+        tdt, code, per = torch.bfloat16, BF16, 8
+    elif kind == "fp8":
+        tdt, code, per = torch.float8_e4m3fn, FP8E4M3, 16
+    else:
+        raise ValueError(kind)
+    ldq = (m + per - 1) // per * per
+    Q = torch.empty((n, ldq), dtype=tdt, device=At.device)
+    scale = torch.empty(n, dtype=torch.float32, device=At.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = lib().asyflexa_quantize(At.data_ptr(), m, n, lda, code, Q.data_ptr(), ldq, scale.data_ptr(),
+                                 C.c_void_p(stream))
+    if rc != OK:
+        raise AsyflexaError(rc, lib().asyflexa_last_error(None).decode())
+    return Q, scale

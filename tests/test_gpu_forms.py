@@ -1,0 +1,144 @@
+"""System forms on the GPU, checked against the FP64 oracle.
+
+Mixed precision: A stored as per-column scaled BF16 / FP8-e4m3 codes (library quantiser),
+sweeps on the codes, exact residual refreshes and checks on the FP32 master copy, and a
+final FP32 polish; the returned x is judged by the oracle on the FP32 (master) problem.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from inputs import nesterov_lasso, ncquad_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1701_04900_gb300.build import build_library
+    build_library()
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8"])
+def test_quantize_matches_definition(kind):
+    """Q = round(A / scale) per column, scale = max|a_j| / qmax; error within half a unit
+    in the last place of the format (relative 2^-9 for BF16, 2^-4 for e4m3) plus the FP8
+    subnormal spacing."""
+    import torch
+    from paper_1701_04900_gb300.native import quantize
+    g = torch.Generator(device="cuda").manual_seed(3)
+    m, n = 1003, 257
+    A = torch.zeros((n, 1004), dtype=torch.float32, device="cuda")
+    A[:, :m] = torch.randn((n, m), generator=g, device="cuda") * torch.rand((n, 1), generator=g, device="cuda") * 10
+    A[5, :m] = 0.0                                   # zero column -> scale 1, codes 0
+    Q, s = quantize(A, m, kind)
+    qmax = 448.0 if kind == "fp8" else 1.0
+    amax = A[:, :m].abs().amax(dim=1)
+    want_s = torch.where(amax > 0, amax / qmax, torch.ones_like(amax))
+    assert torch.allclose(s, want_s, rtol=3e-7, atol=0)   # 2 ulp: torch divides by a scalar via its reciprocal
+    deq = Q[:, :m].float() * s[:, None]
+    err = (deq - A[:, :m]).abs()
+    if kind == "bf16":
+        bound = A[:, :m].abs() * 2.0 ** -8 + 1e-30
+    else:
+        bound = A[:, :m].abs() * 2.0 ** -4 + s[:, None] * 2.0 ** -9
+    assert bool((err <= bound).all())
+    assert bool((Q[:, m:].float() == 0).all())
+    assert bool((Q[5].float() == 0).all()) and float(s[5]) == 1.0
+
+
+def _torch(d):
+    import torch
+    At = torch.from_numpy(np.ascontiguousarray(d["At"])).cuda()
+    b = torch.from_numpy(d["b"]).cuda()
+    lo = torch.from_numpy(d["lo"]).cuda() if "lo" in d else None
+    hi = torch.from_numpy(d["hi"]).cuda() if "hi" in d else None
+    return At, b, lo, hi
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8"])
+def test_mixed_precision_lasso_reaches_fp32_optimum(kind):
+    import torch
+    from paper_1701_04900_gb300 import Solver
+    from paper_1701_04900_gb300.native import quantize
+    d = nesterov_lasso(2000, 10000, 100, lam=1.0, seed=31, store_dtype=np.float32)
+    p = O.Problem.from_data(d)
+    f_ref = O.objective(p, d["x_star"])
+    At, b, _, _ = _torch(d)
+    Q, s = quantize(At, d["m"], kind)
+    solver = Solver(Q, b, d["lam"], m=d["m"], col_scale=s, A_master=At, block_w=32, mode="async",
+                    num_ctas=16, f_star=f_ref, max_sweeps=3000, check_every=10, refresh_every=5)
+    x = torch.zeros(d["n"], dtype=torch.float32, device="cuda")
+    st = solver.solve(x)
+    assert st["status"] == 0, st
+    xg = x.cpu().numpy().astype(np.float64)
+    F = O.objective(p, xg)
+    assert (F - f_ref) / f_ref <= 1.5e-6
+    assert abs(F - st["F"]) <= 1e-9 * F
+    assert O.stationarity(O.xhat_merit(p, xg, O.surrogate_weights(p)), xg) <= 1.5e-6
+    assert st["polish_sweeps"] <= st["sweeps"]
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8"])
+def test_mixed_precision_ncquad_box_is_stationary(kind):
+    import torch
+    from paper_1701_04900_gb300 import Solver
+    from paper_1701_04900_gb300.native import quantize
+    d = ncquad_problem(2000, 6000, seed=32, store_dtype=np.float32)
+    p = O.Problem.from_data(d, loss="ncquad")
+    At, b, lo, hi = _torch(d)
+    Q, s = quantize(At, d["m"], kind)
+    solver = Solver(Q, b, d["lam"], m=d["m"], loss="ncquad", c=d["c"], lo=lo, hi=hi, col_scale=s, A_master=At,
+                    block_w=32, mode="async", num_ctas=16, max_sweeps=4000, check_every=10, refresh_every=10)
+    x = torch.zeros(d["n"], dtype=torch.float32, device="cuda")
+    st = solver.solve(x)
+    assert st["status"] == 0, st
+    xg = x.cpu().numpy().astype(np.float64)
+    assert np.all(xg >= -1.0) and np.all(xg <= 1.0)
+    merit = O.stationarity(O.xhat_merit(p, xg, O.surrogate_weights(p)), xg)
+    assert merit <= 1.5e-6
+    assert abs(O.objective(p, xg) - st["F"]) <= 1e-9 * max(1.0, abs(st["F"]))
+    assert math.isnan(st["rel_gap"])
+
+
+def test_autograd_gradient_matches_oracle_adjoint_and_finite_differences():
+    """d(validation loss)/d(lam, b) through the solution map: library adjoint (block update on
+    the support) vs the FP64 oracle (its own optimum, Cholesky adjoint) and vs central
+    differences (h = 1e-4) of library solves."""
+    import torch
+    from inputs import validation_rows
+    from paper_1701_04900_gb300.autograd import lasso_solution
+    d = nesterov_lasso(800, 3000, 30, lam=1.0, seed=41, store_dtype=np.float32)
+    val = validation_rows(d, 300, seed=42)
+    p = O.Problem.from_data(d)
+    At, b, _, _ = _torch(d)
+    Av = torch.from_numpy(val["At"][:, :300].T.copy()).cuda()          # (300, n) row-major
+    bv = torch.from_numpy(val["b"]).cuda()
+    solve_kw = dict(mode="async", num_ctas=8, block_w=32, max_sweeps=4000, check_every=10, tol_stat=1e-7)
+
+    lam = torch.tensor(1.0, dtype=torch.float64, device="cuda", requires_grad=True)
+    bt = b.clone().requires_grad_(True)
+    x = lasso_solution(lam, bt, At, d["m"], solve_kw)
+    loss = ((Av @ x - bv) ** 2).sum()
+    loss.backward()
+
+    # oracle: own optimum, own v, Cholesky adjoint
+    xo, _, _ = O.solve_gs(p, gamma=1.0, w=32, max_sweeps=20000, tol=1e-16)
+    Avn = val["At"][:, :300].astype(np.float64).T
+    v = 2.0 * Avn.T @ (Avn @ xo - val["b"].astype(np.float64))
+    dlam_o, db_o, _, S = O.lasso_adjoint_gradient(p.A, xo, v)
+    assert abs(float(lam.grad) - dlam_o) <= 2e-3 * abs(dlam_o)
+    gb = bt.grad.double().cpu().numpy()
+    assert np.abs(gb - db_o).max() <= 2e-3 * np.abs(db_o).max()
+
+    def L(lam_v):
+        with torch.no_grad():
+            xx = lasso_solution(torch.tensor(lam_v, dtype=torch.float64, device="cuda"), b, At, d["m"], solve_kw)
+            return float(((Av.double() @ xx.double() - bv.double()) ** 2).sum())
+
+    h = 1e-4
+    fd = (L(1.0 + h) - L(1.0 - h)) / (2 * h)
+    assert abs(float(lam.grad) - fd) <= 2e-2 * abs(fd)

@@ -359,6 +359,64 @@ def test_lambda_max_gram_matches_eigvalsh():
     assert abs(O.lambda_max_gram(p.A, kap, iters=2000) - want) < 1e-8 * want
 
 
+def test_linear_term_gradient_and_objective_by_finite_differences():
+    d = ncquad_problem(25, 10, seed=18)
+    for loss in ("lasso", "ncquad"):
+        p = O.Problem.from_data(d, loss=loss)
+        p.lin = np.random.default_rng(2).standard_normal(p.n)
+        x = np.random.default_rng(3).standard_normal(p.n)
+        lam = p.lam
+        p.lam = 0.0                                  # smooth part only
+        h = 1e-6
+        fd = np.array([(O.objective(p, x + h * e) - O.objective(p, x - h * e)) / (2 * h) for e in np.eye(p.n)])
+        np.testing.assert_allclose(O.gradient(p, x), fd, rtol=1e-6, atol=1e-6)
+        p.lam = lam
+
+
+def test_linear_term_solves_normal_equations():
+    """lam = 0, b = 0, lin = -v: the minimiser of 0.5||Aw||^2 - v^T w solves A^T A w = v."""
+    d = random_lasso(40, 9, seed=19, lam=0.0)
+    p = O.Problem.from_data(d)
+    p.b = np.zeros(p.m)
+    v = np.random.default_rng(4).standard_normal(p.n)
+    p.lin = -v
+    w, _, _ = O.solve_gs(p, gamma=1.0, w=1, max_sweeps=50000, tol=1e-17)
+    np.testing.assert_allclose(w, np.linalg.solve(p.A.T @ p.A, v), rtol=1e-8, atol=1e-9)
+
+
+def test_adjoint_gradient_matches_finite_differences_of_exact_solutions():
+    """dL/dlam and dL/db from the Cholesky adjoint against central differences (h = 1e-6) of
+    exact LASSO minimisers (brute-force support enumeration), L = ||A_val x* - b_val||^2."""
+    rng = np.random.default_rng(20)
+    d = random_lasso(30, 8, seed=20, lam=0.4)
+    A, b, lam = d["At"][:, :30].T.astype(np.float64), d["b"].astype(np.float64), d["lam"]
+    Av = rng.standard_normal((12, 8))
+    bv = rng.standard_normal(12)
+
+    def solve(lam_, b_):
+        sols = O.brute_force_lasso(A, b_, lam_)
+        assert len(sols) == 1
+        return sols[0]
+
+    def loss(lam_, b_):
+        x = solve(lam_, b_)
+        r = Av @ x - bv
+        return float(r @ r)
+
+    x = solve(lam, b)
+    assert 0 < np.count_nonzero(x) < 8
+    v = 2.0 * Av.T @ (Av @ x - bv)
+    dlam, db, _, S = O.lasso_adjoint_gradient(A, x, v)
+    h = 1e-6
+    fd_lam = (loss(lam + h, b) - loss(lam - h, b)) / (2 * h)
+    assert abs(dlam - fd_lam) <= 1e-5 * max(1.0, abs(fd_lam))
+    for i in range(0, 30, 7):
+        e = np.zeros(30)
+        e[i] = h
+        fd_b = (loss(lam, b + e) - loss(lam, b - e)) / (2 * h)
+        assert abs(db[i] - fd_b) <= 1e-5 * max(1.0, abs(fd_b))
+
+
 def test_kkt_violation_detects_perturbation():
     d = nesterov_lasso(40, 100, 5, seed=17)
     p = O.Problem.from_data(d)
