@@ -77,7 +77,7 @@ class LassoSolution(torch.autograd.Function):
             lin = (-gx[S]).to(torch.float32).contiguous()
             zero_b = torch.zeros(m, dtype=torch.float32, device=x.device)
             kw = dict(mode="async", num_ctas=1, block_w=8, gamma=1.0, max_sweeps=2000, check_every=5,
-                      refresh_every=5, tol_stat=1e-7)
+                      refresh_every=5, tol_stat=1e-6)
             kw.update(ctx.adjoint_kwargs or {})
             adj = Solver(AS, zero_b, 0.0, m=m, lin=lin, **kw)
             w = torch.zeros(k, dtype=torch.float32, device=x.device)

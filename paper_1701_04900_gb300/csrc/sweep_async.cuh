@@ -262,9 +262,8 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 named_bar_sync(1, kRegConsThreads);
                 // ---- best response (eq. 2) + fixed step (S.4): the same FP32 arithmetic in
                 // every consumer thread (fixed summation order), so all agree on Delta_j
-                float g = 0.f;
-#pragma unroll
-                for (int k = 0; k < kRegConsWarps; ++k) g += cp[k];
+                static_assert(kRegConsWarps <= 32, "one partial per lane");
+                const float g = warp_sum(lane < kRegConsWarps ? cp[lane] : 0.f);  // same order in every warp
                 buf ^= 1;
                 const ColCoef cf = coef[jl];
                 const float grad = s_loss * g * cf.scale - c2 * cf.x + cf.lin;
