@@ -332,7 +332,8 @@ def run_ours(args):
         del gen, At, b
         torch.cuda.empty_cache()
         result["forms"] = {}
-        for name, fn in (("mixed_precision", run_form_mixed_precision), ("gradient", run_form_gradient)):
+        for name, fn in (("mixed_precision", run_form_mixed_precision), ("gradient", run_form_gradient),
+                         ("batched", run_form_batched)):
             try:
                 result["forms"][name] = fn(args)
             except Exception as exc:  # a failing form is reported, the headline line still prints
@@ -528,6 +529,107 @@ def run_form_gradient(args):
             "rel_diff_vs_fd": abs(g0 - fd) / max(abs(fd), 1e-30), "forward_s": t_fwd, "backward_s": t_bwd,
             "fd_two_solves_s": t_fd, "backward_speedup_vs_fd": t_fd / max(t_bwd, 1e-12), "nnz": nnz,
             "tune_20_steps_s": t_tune, "lambda_final": traj[-1][0], "loss_first": traj[0][1], "loss_last": traj[-1][1]}
+
+
+def run_form_batched(args):
+    """System form (2).  (a) 256 LASSO instances of uneven sizes (m ~ U[500, 4000],
+    n ~ U[2000, 20000], 2% planted, FP32) solved together: one sweep launch per round,
+    CUDA-graph rounds, autotuned block width; time until every instance has a 1e-6 relative
+    gap, against sequential single-problem solves of the first 32 instances (scaled to 256).
+    (b) A 64-point geometric lambda path on one 5000 x 20000 instance (lambda_max = ||A^T b||_inf
+    down to the planted lambda = 1): the 64 problems share A and run in one batch (blocks
+    interleaved for L2 reuse, stall criterion), against 64 sequential warm-started solves."""
+    import numpy as np
+    import torch
+    from paper_1701_04900_gb300 import Solver
+    from paper_1701_04900_gb300.batch import BatchSolver
+    from inputs import nesterov_lasso_torch
+    rng = np.random.default_rng(0)
+    probs, f_ref, gens = [], [], []
+    for i in range(256):
+        m = int(rng.integers(500, 4001))
+        n = int(rng.integers(2000, 20001))
+        g = nesterov_lasso_torch(m, n, max(1, int(0.02 * n)), lam=1.0, seed=1000 + i, device="cuda")
+        sup = g["support"]
+        r = g["At"][sup, :m].double().T @ g["x_star"][sup] - g["b"].double()
+        f_ref.append(0.5 * float(r @ r) + float(g["x_star"].abs().sum()))
+        probs.append(dict(At=g["At"], b=g["b"], lam=1.0, m=m))
+        gens.append((m, n))
+    total_bytes = sum(m * n * 4 for m, n in gens)
+    bs = BatchSolver(probs, block_w=0, refresh_every=10, max_sweeps=3000)
+    xs = [torch.zeros(p["At"].shape[0], dtype=torch.float32, device="cuda") for p in probs]
+    bs.solve(xs, f_star=f_ref)                       # warm-up (includes the autotuner)
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    per, tot = bs.solve(xs, f_star=f_ref)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    bs.close()
+    seq_n = 32
+    t_seq = 0.0
+    for i in range(seq_n):
+        p = probs[i]
+        s = Solver(p["At"], p["b"], 1.0, m=p["m"], block_w=tot["block_w"], mode="async", refresh_every=10,
+                   check_every=10, max_sweeps=3000, f_star=f_ref[i])
+        x = torch.zeros(p["At"].shape[0], dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        s.solve(x)
+        torch.cuda.synchronize()
+        t_seq += time.perf_counter() - t1
+        s.close()
+    batched = {"instances": 256, "A_bytes": total_bytes, "seconds_to_all_1e-6": t_batch, "status": tot["status"],
+               "sweeps": tot["sweeps"], "block_w_autotuned": tot["block_w"],
+               "block_updates_per_s": tot["block_updates"] / t_batch,
+               "max_rel_gap": max(s["rel_gap"] for s in per), "max_stat_xhat": max(s["stat_xhat"] for s in per),
+               "sequential_seconds_32": t_seq, "sequential_seconds_est_256": t_seq * 256 / seq_n,
+               "speedup_vs_sequential": t_seq * 256 / seq_n / t_batch}
+    del probs, xs, gens
+    torch.cuda.empty_cache()
+
+    m, n = 5000, 20000
+    g = nesterov_lasso_torch(m, n, 200, lam=1.0, seed=7, device="cuda")
+    At, b = g["At"], g["b"]
+    lam_max = float((At[:, :m].double() @ b.double()).abs().max())
+    lams = [lam_max * (1.0 / lam_max) ** (k / 63) for k in range(64)]
+    base = dict(At=At, b=b, m=m)
+    bs = BatchSolver([dict(base, lam=l) for l in lams], block_w=32, refresh_every=10, max_sweeps=3000,
+                     switch_tol=1e-9, shared_a=True)
+    xs = [torch.zeros(n, dtype=torch.float32, device="cuda") for _ in lams]
+    bs.solve(xs)
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    per, tot = bs.solve(xs)
+    torch.cuda.synchronize()
+    t_path = time.perf_counter() - t0
+    bs.close()
+    # sequential warm-started path (same stopping rule: stall of F between checks)
+    x = torch.zeros(n, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq_sweeps = 0
+    seq_last = None
+    for l in lams:
+        s = Solver(At, b, l, m=m, block_w=32, mode="async", refresh_every=10, check_every=10, max_sweeps=3000,
+                   tol_stat=1e-6)
+        seq_last = s.solve(x)
+        seq_sweeps += seq_last["sweeps"]
+        s.close()
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    path = {"lambdas": 64, "lambda_max": lam_max, "seconds_batched": t_path, "status": tot["status"],
+            "sweeps_batched": tot["sweeps"], "seconds_sequential_warm": t_seq, "sweeps_sequential": seq_sweeps,
+            "speedup_vs_sequential": t_seq / t_path, "last_lane_stat_xhat": per[-1]["stat_xhat"],
+            "last_lane_rel_gap_vs_planted": None, "sequential_last_stat_xhat": seq_last["stat_xhat"]}
+    sup = g["support"]
+    r = At[sup, :m].double().T @ g["x_star"][sup] - b.double()
+    f1 = 0.5 * float(r @ r) + float(g["x_star"].abs().sum())
+    path["last_lane_rel_gap_vs_planted"] = (per[-1]["F"] - f1) / f1
+    return {"batched": batched, "lambda_path": path}
 
 
 def run_ncu_case(args):

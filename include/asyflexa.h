@@ -142,6 +142,8 @@ typedef struct {
     int32_t checked;            /* 1 if the stat_* / kkt fields were evaluated */
     int64_t polish_sweeps;      /* with A_master: sweeps of the last solve run on the FP32 copy */
     double polish_seconds;      /* with A_master: device time of that FP32 phase */
+    int32_t block_w;            /* batched solve: block width used (given or autotuned) */
+    int32_t reserved2;
 } asyflexa_stats;
 
 /* Library version (ASYFLEXA_ABI_VERSION).  Never fails. */
@@ -253,6 +255,38 @@ int asyflexa_quantize(const float* A, int64_t m, int64_t n, int64_t lda, int32_t
  * in [0, n) (not checked).  Enqueued on cuda_stream.  EINVAL on bad arguments. */
 int asyflexa_gather_columns(const void* A, int64_t lda, int32_t dtype, int64_t m, const int32_t* idx, int64_t k,
                             void* out, int64_t ldo, void* cuda_stream);
+
+/* ---------------------------------------------------------------- batched problems
+ * Many independent problems (e.g. LASSO instances of uneven sizes, or one matrix with many
+ * lambda values) solved together: one persistent asynchronous sweep launch covers the blocks
+ * of every problem (each block still has a single owning CTA, Assumption D4), and every
+ * round of refresh_every sweeps, exact residual refreshes, objectives and a device-side
+ * convergence test is replayed as one captured CUDA graph. */
+typedef struct asyflexa_batch_s* asyflexa_batch_t;
+
+/* flags for asyflexa_batch_create */
+#define ASYFLEXA_BATCH_SHARED_A 1   /* problems share A: blocks are interleaved across problems so
+                                       that their reads of the same panel hit L2 */
+
+/* probs: count FP32 problems (as for asyflexa_create; m <= 24576 each).  opts: shared method
+ * parameters (mode is always ASYNC; block_w = 0 lets an autotuner pick the width from
+ * {16, 32, 64} by timing one sweep each at the first solve).  All problems and their device
+ * buffers must outlive the batch.  Errors: asyflexa_last_error(NULL). */
+int asyflexa_batch_create(asyflexa_batch_t* hb, const asyflexa_problem* probs, int32_t count,
+                          const asyflexa_opts* opts, int32_t flags, void* cuda_stream);
+
+/* Solve every problem from its iterate xs[k] (device, in place).  f_star: count optimal values
+ * or NULL; problem k stops when (F_k - f_star[k])/|f_star[k]| <= tol_gap, or, when f_star[k]
+ * is NaN (or f_star is NULL), when a round lowers F_k by no more than switch_tol * |F_k|.
+ * Converged problems are skipped by later rounds.  per (count entries, may be NULL): each
+ * problem's check at its returned x (F, gap, stationarity) with its sweeps and status;
+ * total: sweeps (rounds x refresh_every, plus autotuning sweeps), block_updates, seconds
+ * (CUDA events around the whole solve), block_w, status (OK if all converged). */
+int asyflexa_batch_solve(asyflexa_batch_t hb, void* const* xs, const double* f_star, asyflexa_stats* per,
+                         asyflexa_stats* total);
+
+/* Release the batch and its internal handles.  NULL is a no-op. */
+int asyflexa_batch_destroy(asyflexa_batch_t hb);
 
 /* Last error message of the handle (or of the calling thread for NULL).  Never NULL. */
 const char* asyflexa_last_error(asyflexa_t h);

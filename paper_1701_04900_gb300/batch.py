@@ -1,0 +1,75 @@
+"""ctypes wrapper of the batched C ABI (asyflexa_batch_*), argument marshalling only."""
+
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+from . import native
+from .native import AsyflexaError, Problem, Stats, default_opts, lib
+
+
+class BatchSolver:
+    """Many FP32 problems solved together (one sweep launch per round, CUDA-graph rounds).
+
+    ``problems``: list of dicts with keys At (n, lda) CUDA float32, b, lam, m and optional
+    lo, hi, lin, loss ("lasso"/"ncquad"), c.  ``block_w = 0`` autotunes the block width.
+    ``shared_a``: the problems share one matrix (blocks are interleaved for L2 reuse).
+    """
+
+    def __init__(self, problems, *, block_w=32, gamma=0.9, tau=0.0, tau_rel=0.0, refresh_every=10,
+                 max_sweeps=1000, num_ctas=0, tol_gap=1e-6, switch_tol=1e-9, shared_a=False, stream=None):
+        import torch
+        L = lib()
+        n = len(problems)
+        arr = (Problem * n)()
+        self._keep = []
+        for k, pr in enumerate(problems):
+            At = pr["At"]
+            p = arr[k]
+            p.m, p.n, p.lda = int(pr["m"]), At.shape[0], At.shape[1]
+            p.a_dtype = p.x_dtype = native.F32
+            p.A, p.b = At.data_ptr(), pr["b"].data_ptr()
+            for key in ("lo", "hi", "lin"):
+                if pr.get(key) is not None:
+                    setattr(p, key, pr[key].data_ptr())
+            p.lam, p.c = float(pr["lam"]), float(pr.get("c", 0.0))
+            p.loss = native.LOSS_LASSO if pr.get("loss", "lasso") == "lasso" else native.LOSS_NCQUAD
+            self._keep.append(pr)
+        o = default_opts()
+        o.block_w, o.mode, o.gamma, o.tau, o.tau_rel = int(block_w), native.ASYNC, float(gamma), float(tau), float(tau_rel)
+        o.refresh_every, o.max_sweeps, o.num_ctas = int(refresh_every), int(max_sweeps), int(num_ctas)
+        o.tol_gap, o.switch_tol = float(tol_gap), float(switch_tol)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        h = C.c_void_p()
+        rc = L.asyflexa_batch_create(C.byref(h), arr, n, C.byref(o), native.BATCH_SHARED_A if shared_a else 0,
+                                     C.c_void_p(stream))
+        if rc != native.OK:
+            raise AsyflexaError(rc, L.asyflexa_last_error(None).decode())
+        self.h, self.count, self.problems = h, n, arr
+
+    def solve(self, xs, f_star=None):
+        """Solve in place; returns (per-problem stats list, total stats dict)."""
+        L = lib()
+        ptrs = (C.c_void_p * self.count)(*[x.data_ptr() for x in xs])
+        fs = None
+        if f_star is not None:
+            fs = (C.c_double * self.count)(*[math.nan if v is None else float(v) for v in f_star])
+        per = (Stats * self.count)()
+        tot = Stats()
+        rc = L.asyflexa_batch_solve(self.h, ptrs, fs, per, C.byref(tot))
+        if rc < 0:
+            raise AsyflexaError(rc, L.asyflexa_last_error(None).decode())
+        return [s.as_dict() for s in per], tot.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().asyflexa_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -72,6 +72,21 @@ __host__ __device__ inline SweepLayout make_sweep_layout(int elt_a, int elt_c, i
     return L;
 }
 
+// One problem of a batched launch (see sweep_async.cuh).
+struct BatchInst {
+    const void* A;
+    int64_t lda, m, mcopy, n;
+    double* r;
+    void* x;
+    const void* lo;
+    const void* hi;
+    const void* lin;
+    const double* dw;
+    const float* scale;
+    double lam, s_loss, c2;
+    int w, nblocks, active, pad;
+};
+
 struct SweepParams {
     const void* A;
     int64_t lda, m, mcopy, n;
@@ -89,6 +104,12 @@ struct SweepParams {
     unsigned long long* counters;  // [0] global update counter, [1] block updates, [2] blocks with Delta != 0
     unsigned long long* hist;      // 32-bucket staleness histogram
     int* err;
+    // batched launches only
+    const BatchInst* batch;        // problem table
+    const int* blk_inst;           // global block -> problem
+    const int* blk_local;          // global block -> block index within its problem
+    int total_blocks;
+    int keep_a_in_l2;              // 1: load A with normal L2 priority (several problems share A)
 };
 
 template <typename TC>

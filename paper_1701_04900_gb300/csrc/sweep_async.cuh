@@ -20,6 +20,13 @@
 //   * after the block's w columns the increment is added to r with one FP64 atomic per row
 //     (lock-free).  All columns of the block used the same snapshot r~, so this is exactly
 //     the block update r += A_i Delta_i.
+//
+// BATCHED = true runs many independent problems in one launch: the blocks of every problem
+// form one global list (p.blk_inst / p.blk_local), each CTA owns the global blocks
+// blockIdx.x, blockIdx.x + gridDim.x, ... (so each problem's blocks still have a single
+// owner, Assumption D4), and each block reads its problem's matrix, residual, iterate and
+// weights from the table p.batch.  Problems whose `active` flag is 0 are skipped (the flag is
+// only changed between launches).
 #pragma once
 
 #include "ptx.cuh"
@@ -68,7 +75,71 @@ __host__ __device__ inline RegLayout make_reg_layout(int rt_rows, int stages) {
     return L;
 }
 
-template <typename TA, int CPC>
+// What one block update needs to know about its problem.
+template <typename TA>
+struct BlockView {
+    using TX = typename XType<TA>::T;
+    const TA* A;
+    int64_t lda, m, mcopy, c0;
+    double* r;
+    TX* x;
+    const TX* lo;
+    const TX* hi;
+    const TX* lin;
+    const double* dw;
+    const float* scale;
+    double lam;
+    float s_loss, c2;
+    int wb;
+    bool skip;
+};
+
+template <typename TA, bool BATCHED>
+__device__ __forceinline__ BlockView<TA> block_view(const SweepParams& p, int b) {
+    using TX = typename XType<TA>::T;
+    BlockView<TA> v;
+    if constexpr (BATCHED) {
+        const BatchInst& I = p.batch[p.blk_inst[b]];
+        v.A = static_cast<const TA*>(I.A);
+        v.lda = I.lda;
+        v.m = I.m;
+        v.mcopy = I.mcopy;
+        v.c0 = static_cast<int64_t>(p.blk_local[b]) * I.w;
+        v.wb = static_cast<int>(min64(I.w, I.n - v.c0));
+        v.r = I.r;
+        v.x = static_cast<TX*>(I.x);
+        v.lo = static_cast<const TX*>(I.lo);
+        v.hi = static_cast<const TX*>(I.hi);
+        v.lin = static_cast<const TX*>(I.lin);
+        v.dw = I.dw;
+        v.scale = I.scale;
+        v.lam = I.lam;
+        v.s_loss = static_cast<float>(I.s_loss);
+        v.c2 = static_cast<float>(I.c2);
+        v.skip = I.active == 0;
+    } else {
+        v.A = static_cast<const TA*>(p.A);
+        v.lda = p.lda;
+        v.m = p.m;
+        v.mcopy = p.mcopy;
+        v.c0 = static_cast<int64_t>(b) * p.w;
+        v.wb = static_cast<int>(min64(p.w, p.n - v.c0));
+        v.r = p.r;
+        v.x = static_cast<TX*>(p.x);
+        v.lo = static_cast<const TX*>(p.lo);
+        v.hi = static_cast<const TX*>(p.hi);
+        v.lin = static_cast<const TX*>(p.lin);
+        v.dw = p.dw;
+        v.scale = p.scale;
+        v.lam = p.lam;
+        v.s_loss = static_cast<float>(p.s_loss);
+        v.c2 = static_cast<float>(p.c2);
+        v.skip = false;
+    }
+    return v;
+}
+
+template <typename TA, int CPC, bool BATCHED = false>
 __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const SweepParams p) {
     using TC = typename ATraits<TA>::TC;
     static_assert(sizeof(TC) == 4, "register kernel computes in FP32");
@@ -91,10 +162,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    const TA* A = static_cast<const TA*>(p.A);
-    const int64_t lda = p.lda;
-    const int64_t units = p.mcopy / V;
-    const int64_t units_full = p.m / V;  // units whose rows are all < m
+    const int nblk = BATCHED ? p.total_blocks : p.nblocks;
 
     if (tid == 0) {
         for (int s = 0; s < p.stages; ++s) {
@@ -109,15 +177,17 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
     // ------------------------------------------------------------------ producer
     if (warp == kRegConsWarps) {
         if (lane != 0) return;
-        const uint64_t pol = l2_policy_evict_first();
+        // A is streamed once per sweep (evict first) unless several batched problems share it
+        const uint64_t pol = (BATCHED && p.keep_a_in_l2) ? l2_policy_evict_normal() : l2_policy_evict_first();
         uint32_t stage = 0, phase = 0;
         long long issued = 0;
         for (int s = 0; s < p.sweeps; ++s) {
-            for (int b = blockIdx.x; b < p.nblocks; b += gridDim.x) {
-                const int64_t c0 = static_cast<int64_t>(b) * p.w;
-                const int wb = static_cast<int>(min64(p.w, p.n - c0));
-                for (int jl = 0; jl < wb; ++jl) {
-                    const TA* col = A + (c0 + jl) * lda;
+            for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+                const BlockView<TA> bv = block_view<TA, BATCHED>(p, b);
+                if (bv.skip) continue;
+                const int64_t units = bv.mcopy / V;
+                for (int jl = 0; jl < bv.wb; ++jl) {
+                    const TA* col = bv.A + (bv.c0 + jl) * bv.lda;
                     for (int c = 0; c < CPC; ++c) {
                         const int64_t u0 = static_cast<int64_t>(c) * kRegStageUnits;
                         if (u0 >= units) break;
@@ -152,23 +222,20 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
     // ------------------------------------------------------------------ consumers
     uint32_t stage = 0, phase = 0;
     unsigned long long u_read = 0, my_updates = 0, my_active = 0;
-    TX* x = static_cast<TX*>(p.x);
-    const TX* lo = static_cast<const TX*>(p.lo);
-    const TX* hi = static_cast<const TX*>(p.hi);
     const float gamma = static_cast<float>(p.gamma);
-    const float s_loss = static_cast<float>(p.s_loss);
-    const float c2 = static_cast<float>(p.c2);
-    int nchunks = 0;  // stages per column actually present
-    for (int c = 0; c < CPC; ++c)
-        if (static_cast<int64_t>(c) * kRegStageUnits < units) ++nchunks;
 
     float inc[UPT][V];
     int buf = 0;
 
     for (int s = 0; s < p.sweeps; ++s) {
-        for (int b = blockIdx.x; b < p.nblocks; b += gridDim.x) {
-            const int64_t c0 = static_cast<int64_t>(b) * p.w;
-            const int wb = static_cast<int>(min64(p.w, p.n - c0));
+        for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+            const BlockView<TA> bv = block_view<TA, BATCHED>(p, b);
+            if (bv.skip) continue;  // uniform across the CTA and the producer
+            const int64_t units = bv.mcopy / V;
+            const int64_t units_full = bv.m / V;  // units whose rows are all < m
+            int nchunks = 0;                      // stages per column actually present
+            for (int c = 0; c < CPC; ++c)
+                if (static_cast<int64_t>(c) * kRegStageUnits < units) ++nchunks;
             // S.2: stale read of the residual into shared memory (rows >= m hold 0), and the
             // block's per-column coefficients.  The barrier that ended the previous block
             // guarantees nobody still reads rt or coef.
@@ -176,9 +243,9 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
             {
                 // 8 independent 16-byte L2 loads in flight per thread
                 constexpr int kB = 8;
-                const double2* rsrc = reinterpret_cast<const double2*>(p.r);
+                const double2* rsrc = reinterpret_cast<const double2*>(bv.r);
                 float2* rdst = reinterpret_cast<float2*>(rt);
-                const int pairs = static_cast<int>(p.mcopy / 2);
+                const int pairs = static_cast<int>(bv.mcopy / 2);
                 for (int i0 = tid; i0 < pairs; i0 += kB * kRegConsThreads) {
                     double2 v[kB];
 #pragma unroll
@@ -193,17 +260,17 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                     }
                 }
             }
-            if (tid < wb) {
-                const int64_t j = c0 + tid;
-                const double dj = p.dw[j];
+            if (tid < bv.wb) {
+                const int64_t j = bv.c0 + tid;
+                const double dj = bv.dw[j];
                 ColCoef cf;
-                cf.x = static_cast<float>(x[j]);
-                cf.lo = lo ? static_cast<float>(lo[j]) : -INFINITY;
-                cf.hi = hi ? static_cast<float>(hi[j]) : INFINITY;
+                cf.x = static_cast<float>(bv.x[j]);
+                cf.lo = bv.lo ? static_cast<float>(bv.lo[j]) : -INFINITY;
+                cf.hi = bv.hi ? static_cast<float>(bv.hi[j]) : INFINITY;
                 cf.dinv = dj > 0.0 ? static_cast<float>(1.0 / dj) : 0.f;
-                cf.thr = dj > 0.0 ? static_cast<float>(p.lam / dj) : 0.f;
-                cf.scale = p.scale ? p.scale[j] : 1.f;
-                cf.lin = p.lin ? static_cast<float>(static_cast<const TX*>(p.lin)[j]) : 0.f;
+                cf.thr = dj > 0.0 ? static_cast<float>(bv.lam / dj) : 0.f;
+                cf.scale = bv.scale ? bv.scale[j] : 1.f;
+                cf.lin = bv.lin ? static_cast<float>(bv.lin[j]) : 0.f;
                 cf.pad0 = 0.f;
                 coef[tid] = cf;
             }
@@ -214,7 +281,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
             bool any = false;
             named_bar_sync(1, kRegConsThreads);
 
-            for (int jl = 0; jl < wb; ++jl) {
+            for (int jl = 0; jl < bv.wb; ++jl) {
                 // ---- dot a_j^T r~ over this thread's rows
                 float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
                 uint32_t st_c = stage, ph_c = phase;
@@ -242,7 +309,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                                             acc3 = fmaf(a[e + 3], r4.w, acc3);
                                         }
                                     } else {
-                                        const int valid = static_cast<int>(p.m - u * V);
+                                        const int valid = static_cast<int>(bv.m - u * V);
 #pragma unroll
                                         for (int e = 0; e < V; ++e)
                                             if (e < valid) acc0 = fmaf(a[e], rv[e], acc0);
@@ -266,7 +333,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 const float g = warp_sum(lane < kRegConsWarps ? cp[lane] : 0.f);  // same order in every warp
                 buf ^= 1;
                 const ColCoef cf = coef[jl];
-                const float grad = s_loss * g * cf.scale - c2 * cf.x + cf.lin;
+                const float grad = bv.s_loss * g * cf.scale - bv.c2 * cf.x + cf.lin;
                 float xh = 0.f;
                 if (cf.dinv > 0.f) {
                     const float vv = fmaf(-grad, cf.dinv, cf.x);
@@ -278,7 +345,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 const float dlt = xn - cf.x;
                 float dj = 0.f;
                 if (!*abort_flag) {
-                    if (tid == 0) x[c0 + jl] = static_cast<TX>(xn);
+                    if (tid == 0) bv.x[bv.c0 + jl] = static_cast<TX>(xn);
                     dj = dlt * cf.scale;
                     any |= dlt != 0.f;
                 }
@@ -322,7 +389,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
 #pragma unroll
                         for (int e = 0; e < V; ++e) {
                             const int64_t row = u * V + e;
-                            if (row < p.m && inc[k][e] != 0.f) red_add_f64(p.r + row, static_cast<double>(inc[k][e]));
+                            if (row < bv.m && inc[k][e] != 0.f) red_add_f64(bv.r + row, static_cast<double>(inc[k][e]));
                         }
                     }
                 }

@@ -57,6 +57,7 @@ class Stats(C.Structure):
         ("sweep_kernel_sweeps", C.c_int64),
         ("status", C.c_int32), ("checked", C.c_int32),
         ("polish_sweeps", C.c_int64), ("polish_seconds", C.c_double),
+        ("block_w", C.c_int32), ("reserved2", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -71,7 +72,9 @@ EXPORTS = [
     "asyflexa_destroy", "asyflexa_residual_refresh", "asyflexa_step", "asyflexa_solve", "asyflexa_check",
     "asyflexa_read_counters", "asyflexa_reset_counters", "asyflexa_get_residual", "asyflexa_get_weights",
     "asyflexa_last_error", "asyflexa_residual_noalloc", "asyflexa_quantize", "asyflexa_gather_columns",
+    "asyflexa_batch_create", "asyflexa_batch_solve", "asyflexa_batch_destroy",
 ]
+BATCH_SHARED_A = 1
 
 
 def lib(path: str | None = None):
@@ -116,6 +119,12 @@ def lib(path: str | None = None):
     L.asyflexa_residual_noalloc.argtypes = [C.POINTER(Problem), vp, vp, vp]
     L.asyflexa_quantize.restype = C.c_int
     L.asyflexa_quantize.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, i32, vp, C.c_int64, vp, vp]
+    L.asyflexa_batch_create.restype = C.c_int
+    L.asyflexa_batch_create.argtypes = [C.POINTER(vp), C.POINTER(Problem), i32, C.POINTER(Opts), i32, vp]
+    L.asyflexa_batch_solve.restype = C.c_int
+    L.asyflexa_batch_solve.argtypes = [vp, C.POINTER(vp), vp, C.POINTER(Stats), C.POINTER(Stats)]
+    L.asyflexa_batch_destroy.restype = C.c_int
+    L.asyflexa_batch_destroy.argtypes = [vp]
     L.asyflexa_gather_columns.restype = C.c_int
     L.asyflexa_gather_columns.argtypes = [vp, C.c_int64, i32, C.c_int64, vp, C.c_int64, vp, C.c_int64, vp]
     del dbl
