@@ -41,6 +41,20 @@ WORKLOAD = "lasso_nesterov_20000x100000_fp32_w32"
 SWEEP_SOURCES = ["sweep_async.cuh", "sweep.cuh", "ptx.cuh", "types.cuh"]
 
 
+def aggregate_over_ranks(elapsed_s: float, units: float, device="cpu"):
+    """Whole-job numbers for independent replicas: the slowest rank's time and the units
+    all ranks processed (max / sum all-reduce; a no-op without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(elapsed_s), float(units)
+    t = torch.tensor([float(elapsed_s)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t[0]), float(u[0])
+
+
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
         os.environ.get("LOCAL_RANK", "0"))
@@ -274,14 +288,7 @@ def run_ours(args):
     ctr = s.read_counters()
     launches = ctr["kernel_launches"] - launches0
     bu = sum(st["block_updates"] for st in stats)
-    if world > 1:
-        t = torch.tensor([elapsed, float(bu)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax[0:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:2], op=dist.ReduceOp.SUM)
-        elapsed_all, bu_all = float(tmax[0]), float(t[1])
-    else:
-        elapsed_all, bu_all = elapsed, float(bu)
+    elapsed_all, bu_all = aggregate_over_ranks(elapsed, float(bu), device="cuda")
 
     # roofline of the dominant kernel: the async sweep kernel, timed live with CUDA events
     # recorded on its own stream by the library (profile=True)
