@@ -38,7 +38,13 @@ sys.path.insert(0, ROOT)
 METRIC = "time to 1e-6 rel. gap & block-updates/s, async vs sync vs oracle, % HBM peak"
 M, N, K_PLANT, LAM, W_BLOCK, GAMMA = 20000, 100000, 1000, 1.0, 32, 0.9
 WORKLOAD = "lasso_nesterov_20000x100000_fp32_w32"
-SWEEP_SOURCES = ["sweep_async.cuh", "sweep.cuh", "ptx.cuh", "types.cuh"]
+SWEEP_SOURCES = ["sweep_async_rr.cuh", "sweep_async.cuh", "sweep.cuh", "ptx.cuh", "types.cuh"]
+# the async sweep kernel behind each value of asyflexa_opts.variant / stats.kernel_variant
+ASYNC_KERNELS = {
+    1: "sweep_kernel<float, async> (staged residual tile)",
+    2: "sweep_async_reg_kernel<float, 5> (register increment, residual snapshot in shared memory)",
+    3: "sweep_async_rr_kernel<float, 5> (residual snapshot and increment in registers)",
+}
 
 
 def aggregate_over_ranks(elapsed_s: float, units: float, device="cpu"):
@@ -77,15 +83,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def profile_traffic():
+def profile_traffic(kernel: str):
     """DRAM bytes per sweep of the async sweep kernel from a committed ncu summary, if it
-    was taken on the current kernel source (else None)."""
+    was taken on the current kernel source and on the kernel in use (else None)."""
     p = os.path.join(ROOT, "profiles", "sweep_async_traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("kernel_digest") != sweep_kernel_digest():
+    if d.get("kernel_digest") != sweep_kernel_digest() or not kernel.startswith(d.get("kernel", "?")):
         return None
     return d
 
@@ -259,7 +265,8 @@ def run_ours(args):
     At, b = gen["At"], gen["b"]
     refresh_every, check_every = args.refresh_every, args.check_every
     s = Solver(At, b, LAM, m=M, block_w=W_BLOCK, mode="async", gamma=GAMMA, refresh_every=refresh_every,
-               check_every=check_every, max_sweeps=args.max_sweeps, f_star=f_ref, profile=True)
+               check_every=check_every, max_sweeps=args.max_sweeps, f_star=f_ref, profile=True,
+               variant=args.variant)
     x = torch.zeros(N, dtype=torch.float32, device="cuda")
 
     def one_step():
@@ -298,10 +305,11 @@ def run_ours(args):
     avg_launch_s = ctr["sweep_kernel_seconds"] / sk_launches
     sweeps_per_launch = ctr["sweep_kernel_sweeps"] / sk_launches
     achieved = alg_bytes_per_sweep * sweeps_per_launch / avg_launch_s / 1e9
-    tr = profile_traffic()
+    kernel = ASYNC_KERNELS[ctr["kernel_variant"]]
+    tr = profile_traffic(kernel)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": (tr["dram_bytes_per_sweep"] * sweeps_per_launch if tr else None),
-                "kernel": "sweep_async_reg_kernel<float, 5> (async sweep, register-resident block increment)",
+                "kernel": kernel,
                 "peak_kind": peak_kind,
                 "avg_launch_ms": avg_launch_s * 1e3, "sweeps_per_launch": sweeps_per_launch,
                 "algorithmic_bytes_per_sweep": alg_bytes_per_sweep,
@@ -336,15 +344,16 @@ def run_ours(args):
                       f"({r['sweeps']} sweeps)"}
     s.close()
     if rank == 0 and not args.no_forms:
+        ctx = {"gen": gen, "f_ref": f_ref}
         del gen, At, b
-        torch.cuda.empty_cache()
         result["forms"] = {}
         for name, fn in (("mixed_precision", run_form_mixed_precision), ("gradient", run_form_gradient),
                          ("batched", run_form_batched)):
             try:
-                result["forms"][name] = fn(args)
+                result["forms"][name] = fn(args, ctx)
             except Exception as exc:  # a failing form is reported, the headline line still prints
                 result["forms"][name] = {"error": f"{type(exc).__name__}: {exc}"[:400]}
+            ctx = {}
             torch.cuda.empty_cache()
     if world > 1:
         dist.barrier()
@@ -431,56 +440,75 @@ def run_e2e(gen, f_ref, args, refresh_every, check_every):
             "steps": steps, "seconds_per_step": el / steps}
 
 
-def run_form_mixed_precision(args):
-    """System form (1): the nonconvex quadratic 10000 x 50000 with box |x| <= 1, A stored as
-    FP32, BF16 or FP8-e4m3 codes with per-column scales (library quantiser), solved from
-    x = 0 to ||xhat(x) - x||_inf / max(1, ||x||_inf) <= 1e-6 on the FP32 problem.  The
-    BF16/FP8 runs refresh and check on the FP32 master copy and finish with FP32 polish
-    sweeps.  Reports time, sweeps and speedup over the plain FP32 form at that accuracy."""
+def _time_solves(make_solver, n, repeats=2):
+    """Warm-up solve, then the best of `repeats` timed solves from x = 0 (same work each)."""
+    import torch
+    s = make_solver()
+    x = torch.zeros(n, dtype=torch.float32, device="cuda")
+    s.solve(x)
+    times = []
+    st = None
+    for _ in range(repeats):
+        x.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = s.solve(x)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    s.close()
+    return min(times), st
+
+
+def run_form_mixed_precision(args, ctx):
+    """System form (1): A stored as FP32, BF16 or FP8-e4m3 codes with per-column scales (library
+    quantiser).  The BF16/FP8 runs refresh and check on the FP32 master copy and finish with
+    FP32 polish sweeps; each result is stated against the FP32 problem.
+    (a) The 20000 x 100000 LASSO of the headline, to a 1e-6 relative gap against the planted
+        optimum's objective (FP64) and ||xhat(x) - x||_inf / max(1, ||x||_inf) <= 1e-6.
+    (b) The nonconvex quadratic 10000 x 50000 with box |x| <= 1, to the same stationarity.
+    Reports time, sweeps and speedup over the plain FP32 form at that accuracy."""
     import torch
     from paper_1701_04900_gb300 import Solver
     from paper_1701_04900_gb300.native import quantize
     from inputs import ncquad_problem_torch
+    out = {}
+    kinds = {"fp32": None, "bf16": "bf16", "fp8": "fp8"}
+    elt = {"fp32": 4, "bf16": 2, "fp8": 1}
+
+    def run_all(At, b, lam, m, n, common):
+        res = {}
+        for name, kind in kinds.items():
+            if kind is None:
+                t, st = _time_solves(lambda: Solver(At, b, lam, m=m, **common), n)
+            else:
+                Q, sc = quantize(At, m, kind)
+                t, st = _time_solves(lambda: Solver(Q, b, lam, m=m, col_scale=sc, A_master=At, **common), n)
+                del Q, sc
+            res[name] = {"seconds": t, "sweeps": st["sweeps"], "polish_sweeps": st["polish_sweeps"],
+                         "rel_gap": st["rel_gap"], "stat_xhat": st["stat_xhat"], "F": st["F"], "nnz": st["nnz"],
+                         "status": st["status"], "A_bytes_per_sweep": n * m * elt[name]}
+        for name in ("bf16", "fp8"):
+            res[name]["speedup_vs_fp32"] = res["fp32"]["seconds"] / res[name]["seconds"]
+        return res
+
+    gen = ctx.get("gen")
+    if gen is not None:
+        common = dict(block_w=W_BLOCK, mode="async", gamma=GAMMA, max_sweeps=2000, check_every=10,
+                      refresh_every=10, tol_stat=1e-6, f_star=ctx["f_ref"])
+        out["lasso"] = dict(workload=f"lasso_nesterov_{M}x{N}", **run_all(gen["At"], gen["b"], LAM, M, N, common))
+        ctx.clear()
+        del gen
+        torch.cuda.empty_cache()
     m, n = 10000, 50000
-    gen = ncquad_problem_torch(m, n, seed=0, device="cuda")
-    At, b, lo, hi = gen["At"], gen["b"], gen["lo"], gen["hi"]
-    # Proximal weight for the asynchronous iteration: with P CTAs x w columns in flight the
-    # stale updates behave like a Jacobi step on that many columns, whose Hessian block
-    # 2 A_S^T A_S has norm about 2 (1 + sqrt(P w / m))^2 for unit-norm Gaussian columns; the
-    # surrogate curvature must exceed gamma/2 of it (the descent condition of Theorem 1's proof
-    # with the delay in place of the Jacobi coupling).  kappa_j = 2||a_j||^2 - 2c ~ 2 - 2c.
-    inflight = torch.cuda.get_device_properties(0).multi_processor_count * W_BLOCK
-    tau = max(0.0, 0.5 * GAMMA * 2.0 * (1.0 + math.sqrt(inflight / m)) ** 2 - (2.0 - 2.0 * gen["c"]))
-    common = dict(loss="ncquad", c=gen["c"], lo=lo, hi=hi, block_w=W_BLOCK, mode="async", gamma=GAMMA, tau=tau,
+    g = ncquad_problem_torch(m, n, seed=0, device="cuda")
+    common = dict(loss="ncquad", c=g["c"], lo=g["lo"], hi=g["hi"], block_w=W_BLOCK, mode="async", gamma=GAMMA,
                   max_sweeps=4000, check_every=10, refresh_every=10, tol_stat=1e-6)
-    out = {"workload": f"ncquad_{m}x{n}_box1", "c": gen["c"], "lambda": gen["lam"], "tau": tau}
-    runs = {"fp32": None, "bf16": "bf16", "fp8": "fp8"}
-    for name, kind in runs.items():
-        if kind is None:
-            s = Solver(At, b, gen["lam"], m=m, **common)
-        else:
-            Q, sc = quantize(At, m, kind)
-            s = Solver(Q, b, gen["lam"], m=m, col_scale=sc, A_master=At, **common)
-        x = torch.zeros(n, dtype=torch.float32, device="cuda")
-        s.solve(x)                      # warm-up (same work)
-        times = []
-        for _ in range(2):
-            x.zero_()
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st = s.solve(x)
-            torch.cuda.synchronize()
-            times.append(time.perf_counter() - t0)
-        out[name] = {"seconds": min(times), "sweeps": st["sweeps"], "polish_sweeps": st["polish_sweeps"],
-                     "stat_xhat": st["stat_xhat"], "F": st["F"], "nnz": st["nnz"], "status": st["status"],
-                     "bytes_per_sweep": n * m * {"fp32": 4, "bf16": 2, "fp8": 1}[name]}
-        s.close()
-    for name in ("bf16", "fp8"):
-        out[name]["speedup_vs_fp32"] = out["fp32"]["seconds"] / out[name]["seconds"]
+    out["ncquad"] = dict(workload=f"ncquad_{m}x{n}_box1", c=g["c"], lam=g["lam"],
+                         **run_all(g["At"], g["b"], g["lam"], m, n, common))
     return out
 
 
-def run_form_gradient(args):
+def run_form_gradient(args, ctx=None):
     """System form (3): L(lam, b) = ||A_val x*(lam, b) - b_val||^2 on the LASSO train split
     5000 x 20000 (Nesterov planted at lam = 1) with a 2000-row validation split from the same
     generator.  Times the forward solve, the backward (adjoint block update on the support,
@@ -538,7 +566,7 @@ def run_form_gradient(args):
             "tune_20_steps_s": t_tune, "lambda_final": traj[-1][0], "loss_first": traj[0][1], "loss_last": traj[-1][1]}
 
 
-def run_form_batched(args):
+def run_form_batched(args, ctx=None):
     """System form (2).  (a) 256 LASSO instances of uneven sizes (m ~ U[500, 4000],
     n ~ U[2000, 20000], 2% planted, FP32) solved together: one sweep launch per round,
     CUDA-graph rounds, autotuned block width; time until every instance has a 1e-6 relative
@@ -652,7 +680,7 @@ def run_ncu_case(args):
     n = 12800
     gen = nesterov_lasso_torch(M, n, K_PLANT * n // N, lam=LAM, seed=0, device="cuda")
     s = Solver(gen["At"], gen["b"], LAM, m=M, block_w=W_BLOCK, mode=args.ncu_mode, gamma=GAMMA,
-               refresh_every=10, tau_rel=4.0 if args.ncu_mode == "sync" else 0.0)
+               refresh_every=10, tau_rel=4.0 if args.ncu_mode == "sync" else 0.0, variant=args.variant)
     x = torch.zeros(n, dtype=torch.float32, device="cuda")
     s.refresh(x)
     for _ in range(args.ncu_launches):
@@ -668,6 +696,8 @@ def main():
     ap.add_argument("--ncu-case", action="store_true", help="small profiling case (see run_ncu_case)")
     ap.add_argument("--ncu-mode", default="async", choices=["async", "sync"])
     ap.add_argument("--ncu-launches", type=int, default=3)
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="async sweep kernel (asyflexa_opts.variant; 0 = automatic)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)

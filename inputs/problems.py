@@ -236,7 +236,7 @@ def random_lasso(m: int, n: int, seed: int = 0, dist: str = "uniform", lam: floa
 
 
 def ncquad_problem_torch(m: int, n: int, seed: int = 0, frac: float = 0.05, noise: float = 0.01,
-                         box: float = 1.0, lam_frac: float = 0.1, device="cuda") -> dict:
+                         box: float = 1.0, lam_frac: float = 0.3, device="cuda") -> dict:
     """:func:`ncquad_problem` generated with torch on ``device`` in FP32 storage (for the
     10000 x 50000 instance).  Same recipe; a different random stream."""
     import torch
@@ -267,7 +267,7 @@ def ncquad_problem_torch(m: int, n: int, seed: int = 0, frac: float = 0.05, nois
 
 
 def ncquad_problem(m: int, n: int, seed: int = 0, frac: float = 0.05, noise: float = 0.01,
-                   box: float = 1.0, lam_frac: float = 0.1, store_dtype=np.float64) -> dict:
+                   box: float = 1.0, lam_frac: float = 0.3, store_dtype=np.float64) -> dict:
     """Nonconvex quadratic instance  f = ||Ax - b||^2 - c||x||^2,  G = lam||x||_1, |x| <= box.
 
     A iid N(0, 1/m); x0 has round(frac * n) nonzeros drawn N(0, 1); b = A x0 + noise N(0,1).
@@ -275,7 +275,9 @@ def ncquad_problem(m: int, n: int, seed: int = 0, frac: float = 0.05, noise: flo
     nonzero spectrum of A^T A), which makes f nonconvex on the null space of A while
     every coordinate curvature 2||a_j||^2 - 2c stays positive for the usual draw.
     lam = lam_frac * 2 ||A^T b||_inf (lam_frac times the smallest weight for which
-    x = 0 is stationary).
+    x = 0 is stationary).  The default 0.3 puts lam above 2c on the usual shapes, so the
+    penalty lam|x| - c x^2 still increases on the box (a nonconvex, MCP-like penalty); with
+    lam < 2c the concave term drives most coordinates to the box over thousands of sweeps.
     """
     rng = np.random.default_rng(seed)
     At64 = rng.standard_normal((n, m)) / math.sqrt(m)

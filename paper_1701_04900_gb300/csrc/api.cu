@@ -41,9 +41,13 @@ int set_error(asyflexa_s* h, int code, const std::string& msg) {
 }
 
 int cuda_error(asyflexa_s* h, cudaError_t e, const char* where) {
+    (void)cudaGetLastError();  // consume a non-sticky error so that later launches do not report it
     std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return set_error(h, e == cudaErrorMemoryAllocation ? ASYFLEXA_ENOMEM : ASYFLEXA_ECUDA, m);
 }
+
+// The async sweep kernel a handle launches: 3 register residual, 2 register increment, 1 staged.
+int async_variant(const asyflexa_s& h) { return h.rr_cpc > 0 ? 3 : (h.reg_upt > 0 ? 2 : 1); }
 
 #define CK(h, call, where)                                   \
     do {                                                     \
@@ -231,7 +235,7 @@ int validate_opts(const asyflexa_opts* o, std::string* why) {
     if (o->refresh_every < 1 || o->check_every < 1 || o->max_sweeps < 1)
         return *why = "refresh_every, check_every and max_sweeps must be >= 1", 1;
     if (o->num_ctas < 0) return *why = "num_ctas must be >= 0", 1;
-    if (o->variant < 0 || o->variant > 2) return *why = "variant must be 0, 1 or 2", 1;
+    if (o->variant < 0 || o->variant > 3) return *why = "variant must be 0, 1, 2 or 3", 1;
     if (!(o->tol_gap >= 0.0) || !(o->tol_stat >= 0.0)) return *why = "tolerances must be >= 0", 1;
     if (!(o->switch_tol >= 0.0)) return *why = "switch_tol must be >= 0", 1;
     return 0;
@@ -417,11 +421,25 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
         if (rc) CKC(static_cast<cudaError_t>(rc), "set shared-memory attribute");
         rc = dispatch(*h, [&](auto L) { return decltype(L)::choose_reg(*h); });
         if (rc < 0) CKC(static_cast<cudaError_t>(-rc), "set shared-memory attribute (register kernel)");
+        int rrc = dispatch(*h, [&](auto L) { return decltype(L)::choose_rr(*h); });
+        if (rrc < 0) CKC(static_cast<cudaError_t>(-rrc), "set shared-memory attribute (register-residual kernel)");
+        // variant 0 takes the first kernel that applies: register increment, staged.  The
+        // register-residual kernel (3) is only used when asked for: it streams A more slowly
+        // on GB300 (one CTA of 16 warps refills its own ring).
+        if (O->variant == 0) h->rr_cpc = 0;
         if (O->variant == 1) {
             h->reg_upt = 0;
-        } else if (O->variant == 2 && rc != 1) {
+            h->rr_cpc = 0;
+        } else if (O->variant == 2) {
+            h->rr_cpc = 0;
+            if (rc != 1) {
+                set_error(h, ASYFLEXA_EUNSUPPORTED,
+                          "variant 2 (register increment) needs FP32/BF16/FP8 storage and m <= 24576");
+                return fail(ASYFLEXA_EUNSUPPORTED);
+            }
+        } else if (O->variant == 3 && rrc != 1) {
             set_error(h, ASYFLEXA_EUNSUPPORTED,
-                      "variant 2 (register-resident residual) needs FP32/BF16/FP8 storage and m <= 24576");
+                      "variant 3 (register residual) needs FP32 storage with m <= 20480, or BF16/FP8 with m <= 16384");
             return fail(ASYFLEXA_EUNSUPPORTED);
         }
     }
@@ -544,6 +562,7 @@ int asyflexa_check(asyflexa_t h, const void* x, asyflexa_stats* out) {
     out->kkt_viol = lasso_nobox ? M.kkt : std::nan("");
     out->nnz = M.nnz;
     out->checked = 1;
+    out->kernel_variant = async_variant(*h);
     out->status = rc;
     out->kernel_launches = h->launches;
     return rc;
@@ -641,6 +660,7 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
         for (int k = 0; k < 32; ++k) st.staleness_hist[k] = hist[k];
     }
     st.kernel_launches = h->launches + (h->master ? h->master->launches : 0);
+    st.kernel_variant = async_variant(*h);
     if (!rc) rc = status;
     st.status = rc;
     if (out) *out = st;
@@ -664,6 +684,7 @@ int asyflexa_read_counters(asyflexa_t h, asyflexa_stats* out) {
     out->sweep_kernel_seconds = h->prof_seconds;
     out->sweep_kernel_launches = h->prof_launches;
     out->sweep_kernel_sweeps = h->prof_sweep_total;
+    out->kernel_variant = async_variant(*h);
     return device_error(*h);
 }
 

@@ -79,7 +79,9 @@ struct asyflexa_batch_s {
     std::vector<asyflexa_t> h;
     int count = 0;
     asyflexa_opts opts{};
-    cudaStream_t stream = nullptr;
+    cudaStream_t user_stream = nullptr;  // the caller's stream (may be the legacy default stream)
+    cudaStream_t stream = nullptr;       // own non-blocking stream: all batch work and the graph capture
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int flags = 0;
     int sm_count = 0;
     size_t smem_optin = 0;
@@ -116,7 +118,10 @@ int bfail(const std::string& m, int code = ASYFLEXA_EINVAL) {
 #define BCK(call, where)                                                                              \
     do {                                                                                              \
         cudaError_t e_ = (call);                                                                      \
-        if (e_ != cudaSuccess) return bfail(std::string(where) + ": " + cudaGetErrorString(e_), ASYFLEXA_ECUDA); \
+        if (e_ != cudaSuccess) {                                                                      \
+            (void)cudaGetLastError(); /* consume a non-sticky error so later launches do not report it */ \
+            return bfail(std::string(where) + ": " + cudaGetErrorString(e_), ASYFLEXA_ECUDA);          \
+        }                                                                                             \
     } while (0)
 
 const void* batched_kernel(int cpc) {
@@ -172,7 +177,7 @@ int build_blocks(asyflexa_batch_s& B, int w) {
 }
 
 int launch_batched(asyflexa_batch_s& B, int sweeps) {
-    asyflexa::SweepParams p;
+    asyflexa::SweepParams p{};
     std::memset(&p, 0, sizeof p);
     p.gamma = B.opts.gamma;
     p.sweeps = sweeps;
@@ -238,11 +243,24 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
     B->count = count;
     B->opts = *opts;
     B->flags = flags;
-    B->stream = static_cast<cudaStream_t>(stream);
+    B->user_stream = static_cast<cudaStream_t>(stream);
     auto fail = [&](int rc) {
         asyflexa_batch_destroy(B);
         return rc;
     };
+    {
+        // Graph capture is not possible on the legacy default stream, so the batch runs on a
+        // stream of its own, ordered after the caller's stream by an event.
+        cudaError_t e = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_in, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->ev_out, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(B->ev_in, B->user_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(B->stream, B->ev_in, 0);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(bfail(std::string("batch stream: ") + cudaGetErrorString(e), ASYFLEXA_ECUDA));
+        }
+    }
     asyflexa_opts io = *opts;
     io.mode = ASYFLEXA_ASYNC;
     io.block_w = opts->block_w > 0 ? opts->block_w : 32;
@@ -251,7 +269,7 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
         if (probs[k].a_dtype != ASYFLEXA_F32 || probs[k].A_master)
             return fail(bfail("batched problems use FP32 storage (problem " + std::to_string(k) + ")"));
         asyflexa_t hk = nullptr;
-        const int rc = asyflexa_create(&hk, &probs[k], &io, stream);
+        const int rc = asyflexa_create(&hk, &probs[k], &io, B->stream);
         if (rc) return fail(bfail("problem " + std::to_string(k) + ": " + asyflexa_last_error(nullptr), rc));
         B->h.push_back(hk);
         if (hk->mcopy > B->max_mcopy) B->max_mcopy = hk->mcopy;
@@ -317,6 +335,13 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
     if (e != cudaSuccess) return fail(bfail(std::string("batch allocation: ") + cudaGetErrorString(e), ASYFLEXA_ENOMEM));
     const int rc = build_blocks(*B, opts->block_w > 0 ? opts->block_w : 32);
     if (rc) return fail(rc);
+    // the caller's stream continues after the set-up work
+    e = cudaEventRecord(B->ev_out, B->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(B->user_stream, B->ev_out, 0);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(bfail(std::string("batch stream: ") + cudaGetErrorString(e), ASYFLEXA_ECUDA));
+    }
     *out = B;
     return ASYFLEXA_OK;
 }
@@ -327,6 +352,9 @@ int asyflexa_batch_destroy(asyflexa_batch_t B) {
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
     for (auto hk : B->h) asyflexa_destroy(hk);
+    if (B->ev_in) cudaEventDestroy(B->ev_in);
+    if (B->ev_out) cudaEventDestroy(B->ev_out);
+    if (B->stream) cudaStreamDestroy(B->stream);
     void* ptrs[] = {B->d_inst, B->d_blk_inst, B->d_blk_local, B->d_conv, B->d_round, B->d_nactive,
                     B->counters, B->hist, B->err};
     for (void* p : ptrs)
@@ -339,6 +367,9 @@ int asyflexa_batch_solve(asyflexa_batch_t B, void* const* xs, const double* f_st
                          asyflexa_stats* total) {
     if (!B || !xs) return bfail("batch or xs is NULL");
     const int count = B->count;
+    // the batch's stream starts after the caller's prior work (the iterates may come from it)
+    BCK(cudaEventRecord(B->ev_in, B->user_stream), "event record");
+    BCK(cudaStreamWaitEvent(B->stream, B->ev_in, 0), "stream wait");
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0), "event");
     BCK(cudaEventCreate(&e1), "event");
@@ -454,6 +485,8 @@ int asyflexa_batch_solve(asyflexa_batch_t B, void* const* xs, const double* f_st
         }
         if (st != ASYFLEXA_OK && (worst == ASYFLEXA_OK || st < 0)) worst = st;
     }
+    BCK(cudaEventRecord(B->ev_out, B->stream), "event record");
+    BCK(cudaStreamWaitEvent(B->user_stream, B->ev_out, 0), "stream wait");
     if (total) {
         std::memset(total, 0, sizeof *total);
         total->sweeps = sweeps;

@@ -69,8 +69,8 @@ __host__ __device__ inline RegLayout make_reg_layout(int rt_rows, int stages) {
     o = align_up_sz(o + kWMax * sizeof(ColCoef), 16);
     L.off_bars = o;
     o = align_up_sz(o + 2 * stages * sizeof(uint64_t), 16);
-    L.off_misc = o;  // abort flag
-    o += 16;
+    L.off_misc = o;  // abort flag; copy-engine cursor of the register-residual kernel
+    o += 128;
     L.total = align_up_sz(o, 128);
     return L;
 }
