@@ -38,12 +38,11 @@ sys.path.insert(0, ROOT)
 METRIC = "time to 1e-6 rel. gap & block-updates/s, async vs sync vs oracle, % HBM peak"
 M, N, K_PLANT, LAM, W_BLOCK, GAMMA = 20000, 100000, 1000, 1.0, 32, 0.9
 WORKLOAD = "lasso_nesterov_20000x100000_fp32_w32"
-SWEEP_SOURCES = ["sweep_async_rr.cuh", "sweep_async.cuh", "sweep.cuh", "ptx.cuh", "types.cuh"]
+SWEEP_SOURCES = ["sweep_async.cuh", "sweep.cuh", "ptx.cuh", "types.cuh"]
 # the async sweep kernel behind each value of asyflexa_opts.variant / stats.kernel_variant
 ASYNC_KERNELS = {
     1: "sweep_kernel<float, async> (staged residual tile)",
     2: "sweep_async_reg_kernel<float, 5> (register increment, residual snapshot in shared memory)",
-    3: "sweep_async_rr_kernel<float, 5> (residual snapshot and increment in registers)",
 }
 
 
@@ -551,19 +550,28 @@ def run_form_gradient(args, ctx=None):
     t0 = time.perf_counter()
     fd = (loss_only(1.0 + h) - loss_only(1.0 - h)) / (2 * h)
     t_fd = time.perf_counter() - t0
-    log_lam, lr = 0.0, 0.1 / max(abs(g0), 1e-30)      # gradient wrt log(lam) is lam * dL/dlam
+    # 20 gradient steps on log(lam) with step control: move against the sign of
+    # dL/dlog(lam) = lam dL/dlam; a step that lowers L is kept and the step grows by 1.5,
+    # otherwise it is undone and the step halves (L(lam) has a sharp minimum near the planted
+    # lam = 1, so plain fixed steps overshoot)
+    log_best, L_best, dlog = 0.0, L0, g0
+    step = 0.05
     traj = []
     t0 = time.perf_counter()
     for _ in range(20):
-        lam_v = math.exp(log_lam)
-        L, g, _, _, _ = fwd_bwd(lam_v)
-        traj.append((lam_v, L))
-        log_lam -= lr * lam_v * g
+        cand = log_best - step * (1.0 if dlog > 0 else -1.0)
+        L, g, _, _, _ = fwd_bwd(math.exp(cand))
+        traj.append((math.exp(cand), L))
+        if L < L_best:
+            log_best, L_best, dlog = cand, L, math.exp(cand) * g
+            step *= 1.5
+        else:
+            step *= 0.5
     t_tune = time.perf_counter() - t0
     return {"workload": f"lasso_train_{m}x{n}_val_2000", "loss_at_lam1": L0, "dL_dlam": g0, "fd_dL_dlam": fd,
             "rel_diff_vs_fd": abs(g0 - fd) / max(abs(fd), 1e-30), "forward_s": t_fwd, "backward_s": t_bwd,
             "fd_two_solves_s": t_fd, "backward_speedup_vs_fd": t_fd / max(t_bwd, 1e-12), "nnz": nnz,
-            "tune_20_steps_s": t_tune, "lambda_final": traj[-1][0], "loss_first": traj[0][1], "loss_last": traj[-1][1]}
+            "tune_20_steps_s": t_tune, "lambda_final": math.exp(log_best), "loss_at_start": L0, "loss_final": L_best}
 
 
 def run_form_batched(args, ctx=None):
@@ -696,7 +704,7 @@ def main():
     ap.add_argument("--ncu-case", action="store_true", help="small profiling case (see run_ncu_case)")
     ap.add_argument("--ncu-mode", default="async", choices=["async", "sync"])
     ap.add_argument("--ncu-launches", type=int, default=3)
-    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2, 3],
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
                     help="async sweep kernel (asyflexa_opts.variant; 0 = automatic)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)

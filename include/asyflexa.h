@@ -115,9 +115,7 @@ typedef struct {
     int32_t variant;            /* async kernel: 0 = automatic (2 if it applies, else 1),
                                    1 = staged residual tile (any m, any dtype), 2 = register
                                    increment with the residual snapshot in shared memory
-                                   (FP32/BF16/FP8, m up to 24576 rows), 3 = residual snapshot and
-                                   increment in registers (FP32 with m up to 20480, BF16/FP8 with
-                                   m up to 16384); EUNSUPPORTED if the requested one does not apply */
+                                   (FP32/BF16/FP8, m up to 24576 rows; EUNSUPPORTED otherwise) */
     double switch_tol;          /* with A_master: solve leaves the low-precision phase when a check
                                    interval lowers F by less than switch_tol * |F| (default 1e-7) */
 } asyflexa_opts;
@@ -146,7 +144,7 @@ typedef struct {
     int64_t polish_sweeps;      /* with A_master: sweeps of the last solve run on the FP32 copy */
     double polish_seconds;      /* with A_master: device time of that FP32 phase */
     int32_t block_w;            /* batched solve: block width used (given or autotuned) */
-    int32_t kernel_variant;     /* async sweep kernel this handle launches (1, 2 or 3, see
+    int32_t kernel_variant;     /* async sweep kernel this handle launches (1 or 2, see
                                    asyflexa_opts.variant); set by solve, check, read_counters */
 } asyflexa_stats;
 

@@ -46,8 +46,8 @@ int cuda_error(asyflexa_s* h, cudaError_t e, const char* where) {
     return set_error(h, e == cudaErrorMemoryAllocation ? ASYFLEXA_ENOMEM : ASYFLEXA_ECUDA, m);
 }
 
-// The async sweep kernel a handle launches: 3 register residual, 2 register increment, 1 staged.
-int async_variant(const asyflexa_s& h) { return h.rr_cpc > 0 ? 3 : (h.reg_upt > 0 ? 2 : 1); }
+// The async sweep kernel a handle launches: 2 register increment, 1 staged residual tile.
+int async_variant(const asyflexa_s& h) { return h.reg_upt > 0 ? 2 : 1; }
 
 #define CK(h, call, where)                                   \
     do {                                                     \
@@ -235,7 +235,7 @@ int validate_opts(const asyflexa_opts* o, std::string* why) {
     if (o->refresh_every < 1 || o->check_every < 1 || o->max_sweeps < 1)
         return *why = "refresh_every, check_every and max_sweeps must be >= 1", 1;
     if (o->num_ctas < 0) return *why = "num_ctas must be >= 0", 1;
-    if (o->variant < 0 || o->variant > 3) return *why = "variant must be 0, 1, 2 or 3", 1;
+    if (o->variant < 0 || o->variant > 2) return *why = "variant must be 0, 1 or 2", 1;
     if (!(o->tol_gap >= 0.0) || !(o->tol_stat >= 0.0)) return *why = "tolerances must be >= 0", 1;
     if (!(o->switch_tol >= 0.0)) return *why = "switch_tol must be >= 0", 1;
     return 0;
@@ -421,25 +421,11 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
         if (rc) CKC(static_cast<cudaError_t>(rc), "set shared-memory attribute");
         rc = dispatch(*h, [&](auto L) { return decltype(L)::choose_reg(*h); });
         if (rc < 0) CKC(static_cast<cudaError_t>(-rc), "set shared-memory attribute (register kernel)");
-        int rrc = dispatch(*h, [&](auto L) { return decltype(L)::choose_rr(*h); });
-        if (rrc < 0) CKC(static_cast<cudaError_t>(-rrc), "set shared-memory attribute (register-residual kernel)");
-        // variant 0 takes the first kernel that applies: register increment, staged.  The
-        // register-residual kernel (3) is only used when asked for: it streams A more slowly
-        // on GB300 (one CTA of 16 warps refills its own ring).
-        if (O->variant == 0) h->rr_cpc = 0;
         if (O->variant == 1) {
             h->reg_upt = 0;
-            h->rr_cpc = 0;
-        } else if (O->variant == 2) {
-            h->rr_cpc = 0;
-            if (rc != 1) {
-                set_error(h, ASYFLEXA_EUNSUPPORTED,
-                          "variant 2 (register increment) needs FP32/BF16/FP8 storage and m <= 24576");
-                return fail(ASYFLEXA_EUNSUPPORTED);
-            }
-        } else if (O->variant == 3 && rrc != 1) {
+        } else if (O->variant == 2 && rc != 1) {
             set_error(h, ASYFLEXA_EUNSUPPORTED,
-                      "variant 3 (register residual) needs FP32 storage with m <= 20480, or BF16/FP8 with m <= 16384");
+                      "variant 2 (register increment) needs FP32/BF16/FP8 storage and m <= 24576");
             return fail(ASYFLEXA_EUNSUPPORTED);
         }
     }

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -136,8 +137,9 @@ const void* batched_kernel(int cpc) {
     }
 }
 
-// Global block list for width w: problem by problem, or (shared A) interleaved by block
-// index so that the problems' reads of the same panel are close in time.
+// Global block list for width w.  Shared A: interleaved by block index, so that the
+// problems' reads of the same panel are close in time.  Otherwise: capped cycles over the
+// problems (below).
 int build_blocks(asyflexa_batch_s& B, int w) {
     std::vector<int> bi, bl;
     std::vector<int> nb(B.count);
@@ -154,11 +156,36 @@ int build_blocks(asyflexa_batch_s& B, int w) {
                     bl.push_back(b);
                 }
     } else {
-        for (int k = 0; k < B.count; ++k)
-            for (int b = 0; b < nb[k]; ++b) {
-                bi.push_back(k);
-                bl.push_back(b);
+        // Independent problems: cycles over the problems, each contributing at most
+        // max(1, m / (4 w)) of its next blocks, so that the blocks a launch works on at the same
+        // time (about one window of `ctas` consecutive entries) hold few columns of any one
+        // problem relative to its m -- the updates in flight of Assumption D1.  A cycle shorter
+        // than the grid (few problems left) is padded with empty entries (-1) for the same reason.
+        const int ctas = B.opts.num_ctas > 0 ? B.opts.num_ctas : B.sm_count;
+        std::vector<int> next(B.count, 0), cap(B.count);
+        for (int k = 0; k < B.count; ++k) {
+            const int64_t c = B.h[k]->prob.m / (4 * static_cast<int64_t>(w));
+            cap[k] = c < 1 ? 1 : static_cast<int>(c);
+        }
+        bool left = true;
+        while (left) {
+            left = false;
+            const size_t start = bi.size();
+            for (int k = 0; k < B.count; ++k) {
+                const int t = std::min(cap[k], nb[k] - next[k]);
+                for (int i = 0; i < t; ++i) {
+                    bi.push_back(k);
+                    bl.push_back(next[k] + i);
+                }
+                next[k] += t;
+                if (next[k] < nb[k]) left = true;
             }
+            const size_t len = bi.size() - start;
+            if (left && len < static_cast<size_t>(ctas)) {
+                bi.insert(bi.end(), ctas - len, -1);
+                bl.insert(bl.end(), ctas - len, 0);
+            }
+        }
     }
     if (B.d_blk_inst) cudaFree(B.d_blk_inst);
     if (B.d_blk_local) cudaFree(B.d_blk_local);

@@ -34,8 +34,7 @@ struct asyflexa_s {
     // register-resident async kernel (0 = not used)
     int reg_upt = 0, reg_cpc = 0, reg_stages = 0;
     size_t reg_smem = 0;
-    int rr_cpc = 0, rr_stages = 0;  // register-residual kernel (0 = not used)
-    size_t rr_smem = 0;
+
 
     int check_ctas = 0;
     size_t check_smem = 0;
@@ -89,7 +88,6 @@ struct Launcher {
     static cudaError_t check(asyflexa_s& h, const void* x);
     static int set_smem_attrs(asyflexa_s& h);
     static int choose_reg(asyflexa_s& h);
-    static int choose_rr(asyflexa_s& h);
 };
 
 }  // namespace asyflexa

@@ -6,7 +6,6 @@
 #include "handle.h"
 #include "sweep.cuh"
 #include "sweep_async.cuh"
-#include "sweep_async_rr.cuh"
 
 namespace asyflexa {
 
@@ -44,61 +43,6 @@ const void* reg_kernel(int cpc) {
         }
         return nullptr;
     }
-}
-
-template <typename TA, int CPC>
-constexpr bool rr_fits() {
-    return kRegKpc * CPC * ATraits<TA>::kVec <= kRRMaxRowsPerThread;
-}
-
-template <typename TA>
-const void* rr_kernel(int cpc) {
-    if constexpr (sizeof(typename ATraits<TA>::TC) != 4) {
-        return nullptr;
-    } else {
-        switch (cpc) {
-            case 1:
-                if constexpr (rr_fits<TA, 1>()) return reinterpret_cast<const void*>(sweep_async_rr_kernel<TA, 1>);
-                break;
-            case 2:
-                if constexpr (rr_fits<TA, 2>()) return reinterpret_cast<const void*>(sweep_async_rr_kernel<TA, 2>);
-                break;
-            case 3:
-                if constexpr (rr_fits<TA, 3>()) return reinterpret_cast<const void*>(sweep_async_rr_kernel<TA, 3>);
-                break;
-            case 4:
-                if constexpr (rr_fits<TA, 4>()) return reinterpret_cast<const void*>(sweep_async_rr_kernel<TA, 4>);
-                break;
-            case 5:
-                if constexpr (rr_fits<TA, 5>()) return reinterpret_cast<const void*>(sweep_async_rr_kernel<TA, 5>);
-                break;
-            default: break;
-        }
-        return nullptr;
-    }
-}
-
-// Choose the register-residual kernel instance (sets h.rr_*).  Same return convention as
-// choose_reg.  Shared memory holds only the chunk ring: one column plus at least one chunk.
-template <typename TA>
-int Launcher<TA>::choose_rr(asyflexa_s& h) {
-    h.rr_cpc = h.rr_stages = 0;
-    h.rr_smem = 0;
-    const int64_t units = h.mcopy / h.vec;
-    const int cpc = static_cast<int>((units + kRegStageUnits - 1) / kRegStageUnits);
-    if (cpc < 1 || cpc > 5) return 0;
-    const void* fn = rr_kernel<TA>(cpc);
-    if (!fn) return 0;
-    const RegLayout L0 = make_reg_layout(0, 0);
-    if (L0.total + 512 + static_cast<size_t>(cpc + 1) * L0.stage_bytes > h.smem_optin) return 0;
-    int stages = static_cast<int>((h.smem_optin - L0.total - 512) / L0.stage_bytes);
-    if (stages > 16) stages = 16;
-    h.rr_cpc = cpc;
-    h.rr_stages = stages;
-    h.rr_smem = make_reg_layout(0, stages).total;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.rr_smem));
-    if (e != cudaSuccess) return -static_cast<int>(e);
-    return 1;
 }
 
 // Choose the register-increment kernel instance that covers the column (sets h.reg_*).
@@ -189,15 +133,6 @@ cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
     p.counters = h.counters;
     p.hist = h.hist;
     p.err = h.err;
-    if (mode == ASYFLEXA_ASYNC && h.rr_cpc > 0) {
-        p.stages = h.rr_stages;
-        p.tile_rows = 0;
-        void* args[] = {&p};
-        const cudaError_t e = cudaLaunchKernel(rr_kernel<TA>(h.rr_cpc), dim3(h.sweep_ctas), dim3(kRRThreads), args,
-                                               h.rr_smem, h.stream);
-        ++h.launches;
-        return e != cudaSuccess ? e : cudaGetLastError();
-    }
     if (mode == ASYFLEXA_ASYNC && h.reg_upt > 0) {
         p.stages = h.reg_stages;
         p.tile_rows = static_cast<int>(h.mcopy);

@@ -69,8 +69,8 @@ __host__ __device__ inline RegLayout make_reg_layout(int rt_rows, int stages) {
     o = align_up_sz(o + kWMax * sizeof(ColCoef), 16);
     L.off_bars = o;
     o = align_up_sz(o + 2 * stages * sizeof(uint64_t), 16);
-    L.off_misc = o;  // abort flag; copy-engine cursor of the register-residual kernel
-    o += 128;
+    L.off_misc = o;  // abort flag
+    o += 16;
     L.total = align_up_sz(o, 128);
     return L;
 }
@@ -99,7 +99,12 @@ __device__ __forceinline__ BlockView<TA> block_view(const SweepParams& p, int b)
     using TX = typename XType<TA>::T;
     BlockView<TA> v;
     if constexpr (BATCHED) {
-        const BatchInst& I = p.batch[p.blk_inst[b]];
+        const int ii = p.blk_inst[b];
+        if (ii < 0) {  // padding entry of the block list: nothing to do
+            v.skip = true;
+            return v;
+        }
+        const BatchInst& I = p.batch[ii];
         v.A = static_cast<const TA*>(I.A);
         v.lda = I.lda;
         v.m = I.m;

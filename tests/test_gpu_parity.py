@@ -186,12 +186,11 @@ def test_sync_parity_quantized_storage(kind):
 # ----------------------------------------------------------------------------- async
 
 @pytest.mark.parametrize("store,tol,variant", [(np.float64, TOL64, 0), (np.float32, TOL32, 1),
-                                               (np.float32, TOL32, 2), (np.float32, TOL32, 3)])
+                                               (np.float32, TOL32, 2)])
 @pytest.mark.parametrize("w", [1, 4, 32])
 def test_async_single_cta_equals_gauss_seidel(store, tol, variant, w):
     """One CTA owns every block and runs them in order: exactly cyclic block Gauss-Seidel.
-    variant 1 = staged-residual kernel, 2 = register-increment kernel, 3 = register-residual
-    kernel."""
+    variant 1 = staged-residual kernel, 2 = register-increment kernel."""
     import torch
     d = random_lasso(301, 200, seed=9, lam=0.3, store_dtype=store, box=0.8)
     p = O.Problem.from_data(d)
@@ -207,13 +206,11 @@ def test_async_single_cta_equals_gauss_seidel(store, tol, variant, w):
 
 
 @pytest.mark.parametrize("m", [1021, 5003, 9001, 17001, 20477, 24571])
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2])
 def test_async_single_cta_shapes(m, variant):
     """Column lengths spanning 1..6 shared-memory stages of the register kernels (ragged last
     unit included), against Gauss-Seidel."""
     import torch
-    if variant == 3 and m > 20480:
-        pytest.skip("the register-residual kernel holds at most 20480 rows")
     d = random_lasso(m, 48, seed=m, lam=0.2, dist="gauss", store_dtype=np.float32, box=2.0)
     p = O.Problem.from_data(d)
     dw = O.surrogate_weights(p, tau=0.05)
@@ -227,7 +224,7 @@ def test_async_single_cta_shapes(m, variant):
 
 
 @pytest.mark.parametrize("m,n", [(2000, 600), (9001, 200), (10000, 96), (4000, 12000)])
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2])
 def test_async_single_cta_ncquad_box_equals_gauss_seidel(m, n, variant):
     """Nonconvex quadratic with the box |x| <= 1 (gradient 2A^T r - 2c x, curvature
     2||a_j||^2 - 2c + tau), one CTA, against the oracle's cyclic Gauss-Seidel sweeps; long
@@ -247,7 +244,7 @@ def test_async_single_cta_ncquad_box_equals_gauss_seidel(m, n, variant):
 
 
 @pytest.mark.parametrize("kind", ["bf16", "fp8"])
-@pytest.mark.parametrize("variant", [1, 2, 3])
+@pytest.mark.parametrize("variant", [1, 2])
 def test_async_single_cta_quantized(kind, variant):
     import torch
     from paper_1701_04900_gb300 import Solver
@@ -279,7 +276,7 @@ def test_async_single_cta_multitile_equals_gauss_seidel():
     assert rel_inf(x.cpu().numpy(), x_ref) < TOL32
 
 
-@pytest.mark.parametrize("store,variant", [(np.float64, 0), (np.float32, 1), (np.float32, 2), (np.float32, 3)])
+@pytest.mark.parametrize("store,variant", [(np.float64, 0), (np.float32, 1), (np.float32, 2)])
 def test_async_reaches_planted_optimum(store, variant):
     """Many CTAs, stale reads: objective within 1e-6 of the optimum, stationarity <= 1e-6.
 
@@ -395,9 +392,9 @@ def test_invalid_inputs_are_rejected():
 def test_unsupported_kernel_variant_is_reported():
     """A requested kernel that does not cover the problem is refused at create (no fallback)."""
     from paper_1701_04900_gb300 import AsyflexaError
-    d = random_lasso(24571, 16, seed=16, store_dtype=np.float32)
+    d = random_lasso(24581, 16, seed=16, store_dtype=np.float32)
     with pytest.raises(AsyflexaError) as ei:
-        make_solver(d, mode="async", variant=3)
+        make_solver(d, mode="async", variant=2)
     assert ei.value.code == -6
     d = random_lasso(300, 16, seed=16, store_dtype=np.float64)
     with pytest.raises(AsyflexaError) as ei:
