@@ -13,6 +13,8 @@ from .problems import (  # noqa: F401
     nesterov_lasso_torch,
     random_lasso,
     ncquad_problem,
+    dc_problem,
+    dc_problem_torch,
     ncquad_problem_torch,
     pad_lda,
     validation_rows,

@@ -28,6 +28,12 @@ Workloads follow the kinds of instance the paper experiments with (Section 4):
   A iid N(0, 1/m), x0 5% sparse with N(0, 1) entries, b = A x0 + 0.01 N(0, 1),
   box |x_i| <= 1.  The constant c of f = ||Ax - b||^2 - c||x||^2 and the weight lam
   are problem parameters chosen as documented on the function.
+
+* ``dc_problem``: the sparse-regression instance of Section 4.3's nonconvex experiment
+  (F = ||Ax - b||^2 + lam H(x) with the log or exp regulariser): A with iid N(0, 1)
+  entries and unit-norm columns, xbar 5% nonzero with N(0, 1) values, b = A xbar + e,
+  e ~ N(0, 0.1^2).  lam is not given in the paper; it is a fixed fraction of the
+  smallest weight for which x = 0 is stationary.
 """
 
 from __future__ import annotations
@@ -264,6 +270,67 @@ def ncquad_problem_torch(m: int, n: int, seed: int = 0, frac: float = 0.05, nois
     return dict(At=At, b=b, x0=x0, c=float(c), lam=float(lam), m=m, n=n, lda=lda,
                 lo=torch.full((n,), -box, dtype=torch.float32, device=device),
                 hi=torch.full((n,), box, dtype=torch.float32, device=device))
+
+
+def dc_problem(m: int, n: int, reg: str = "log", theta: float = 20.0, seed: int = 0, frac: float = 0.05,
+               sigma: float = 0.1, lam_frac: float = 0.1, store_dtype=np.float64) -> dict:
+    """Sparse regression with a nonconvex regulariser (the log or exp penalty).
+
+    A: iid N(0, 1) entries, each column scaled to unit norm; xbar: iid N(0, 1) with a random
+    (1 - frac) of its entries set to 0; b = A xbar + e, e iid N(0, sigma^2).  ``theta`` is the
+    regulariser parameter; lam = lam_frac * lam0 with lam0 = 2 ||A^T b||_inf / eta the
+    smallest weight for which x = 0 is stationary (eta = theta for exp, theta / log(1 +
+    theta) for log).  Returned ``loss`` is "dc_log" or "dc_exp" and ``c`` is unused.
+    """
+    rng = np.random.default_rng(seed)
+    A64 = rng.standard_normal((n, m))
+    A64 /= np.linalg.norm(A64, axis=1, keepdims=True)
+    k = int(round(frac * n))
+    xbar = np.zeros(n)
+    if k:
+        idx = rng.choice(n, size=k, replace=False)
+        xbar[idx] = rng.standard_normal(k)
+    e = sigma * rng.standard_normal(m)
+    elt = np.dtype(store_dtype).itemsize
+    lda = pad_lda(m, elt)
+    At = np.zeros((n, lda), dtype=store_dtype)
+    At[:, :m] = A64.astype(store_dtype)
+    stored = At[:, :m].astype(np.float64)
+    b64 = stored.T @ xbar + e
+    eta = theta if reg == "exp" else theta / math.log1p(theta)
+    lam = lam_frac * 2.0 * float(np.abs(stored @ b64.astype(store_dtype).astype(np.float64)).max()) / eta
+    return dict(At=At, b=b64.astype(store_dtype), xbar=xbar, theta=float(theta), lam=float(lam),
+                loss="dc_" + reg, c=0.0, m=m, n=n, lda=lda)
+
+
+def dc_problem_torch(m: int, n: int, reg: str = "log", theta: float = 20.0, seed: int = 0, frac: float = 0.05,
+                     sigma: float = 0.1, lam_frac: float = 0.1, device="cuda") -> dict:
+    """:func:`dc_problem` generated with torch on ``device`` in FP32 storage; same recipe, a
+    different random stream."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    lda = pad_lda(m, 4)
+    At = torch.zeros((n, lda), dtype=torch.float32, device=device)
+    chunk = 8192
+    for j0 in range(0, n, chunk):
+        j1 = min(n, j0 + chunk)
+        B = torch.randn((j1 - j0, m), generator=g, device=device, dtype=torch.float64)
+        At[j0:j1, :m] = (B / B.norm(dim=1, keepdim=True)).to(torch.float32)
+    k = int(round(frac * n))
+    idx = torch.randperm(n, generator=g, device=device)[:k]
+    xbar = torch.zeros(n, dtype=torch.float64, device=device)
+    xbar[idx] = torch.randn(k, generator=g, device=device, dtype=torch.float64)
+    e = sigma * torch.randn(m, generator=g, device=device, dtype=torch.float64)
+    b = (At[idx, :m].double().T @ xbar[idx] + e).to(torch.float32)
+    atb = torch.empty(n, dtype=torch.float64, device=device)
+    for j0 in range(0, n, chunk):
+        atb[j0:j0 + chunk] = At[j0:j0 + chunk, :m].double() @ b.double()
+    eta = theta if reg == "exp" else theta / math.log1p(theta)
+    lam = lam_frac * 2.0 * float(atb.abs().max()) / eta
+    return dict(At=At, b=b, xbar=xbar, theta=float(theta), lam=float(lam), loss="dc_" + reg, c=0.0,
+                m=m, n=n, lda=lda)
 
 
 def ncquad_problem(m: int, n: int, seed: int = 0, frac: float = 0.05, noise: float = 0.01,

@@ -10,6 +10,16 @@ Algorithms for Nonconvex Big-Data Optimization, Part II"):
     - LASSO (Section 4.2):              f(x) = 0.5 ||Ax - b||^2
     - nonconvex quadratic (Section 4.3): f(x) = ||Ax - b||^2 - c ||x||^2
   Writing r = Ax - b:  grad f = s A^T r - 2 c x  with s = 1 (LASSO) or 2, c = 0 (LASSO).
+* Nonconvex sparse learning (Section 4.3): F(x) = ||Ax - b||^2 + lam H(x), H = sum_j h(x_j),
+  with the exponential regulariser h(x) = 1 - exp(-theta |x|) or the logarithmic one
+  h(x) = log(1 + theta |x|) / log(1 + theta).  Both are DC: h = h+ - h-, h+(x) = eta |x|,
+  h-(x) = eta |x| - h(x) convex and smooth, eta = theta (exp) or theta / log(1 + theta) (log).
+  The split used is f = ||Ax - b||^2 - lam H-(x) (smooth), G = lam eta ||x||_1: the
+  printed assignment (f = h-, G = m + h+) would put the quadratic in G, which is not
+  separable, so it is read as the one that fits Assumption A4.  The best response keeps the
+  quadratic's exact coordinate curvature 2||a_j||^2, linearises -lam H- at the current point
+  and keeps lam h+ (the subproblem of Section 4.3), i.e. the common closed form below with
+  grad_j f = 2 a_j^T r - lam h-'(x_j) and l1 weight lam eta.
 
 * Best response (eq. 2) with the surrogate of Section 4.2: for a scalar block the
   surrogate is f restricted to x_j plus (tau/2)(x_j - x~_j)^2, which for a quadratic f
@@ -54,8 +64,10 @@ __all__ = [
     "gauss_seidel_sweep", "random_sequential", "delayed_sweeps", "mf_measure",
     "xhat_merit", "kkt_violation", "stationarity", "brute_force_lasso",
     "stationary_points_box", "lambda_max_gram", "jacobi_tau_rel", "solve_gs",
-    "solve_jacobi", "lasso_support", "lasso_adjoint_gradient",
+    "solve_jacobi", "lasso_support", "lasso_adjoint_gradient", "dc_eta", "dc_h", "dc_hminus_grad",
 ]
+
+DC_LOSSES = ("dc_log", "dc_exp")
 
 
 @dataclass
@@ -65,8 +77,9 @@ class Problem:
     A: np.ndarray
     b: np.ndarray
     lam: float
-    loss: str = "lasso"          # "lasso" or "ncquad"
+    loss: str = "lasso"          # "lasso", "ncquad", "dc_log" or "dc_exp"
     c: float = 0.0
+    theta: float = 0.0                 # regulariser parameter of the DC losses
     lo: np.ndarray | None = None
     hi: np.ndarray | None = None
     lin: np.ndarray | None = None      # optional linear term of f: f(x) += lin^T x
@@ -85,8 +98,17 @@ class Problem:
         """Factor of A^T r in grad f (1 for 0.5||Ax-b||^2, 2 for ||Ax-b||^2)."""
         return 1.0 if self.loss == "lasso" else 2.0
 
+    @property
+    def dc(self) -> bool:
+        return self.loss in DC_LOSSES
+
+    @property
+    def l1(self) -> float:
+        """Weight of ||x||_1 in G: lam, or lam * eta for the DC losses."""
+        return self.lam * dc_eta(self.loss, self.theta) if self.dc else self.lam
+
     @staticmethod
-    def from_data(d: dict, loss: str = "lasso", c: float | None = None) -> "Problem":
+    def from_data(d: dict, loss: str = "lasso", c: float | None = None, theta: float | None = None) -> "Problem":
         """Build from a generator dict (``At`` of shape (n, lda), column j = row j)."""
         m = d["m"]
         At = np.asarray(d["At"])[:, :m].astype(np.float64)
@@ -95,6 +117,7 @@ class Problem:
         return Problem(
             A=At.T, b=np.asarray(d["b"]).astype(np.float64), lam=float(d["lam"]),
             loss=loss, c=float(d.get("c", 0.0) if c is None else c),
+            theta=float(d.get("theta", 0.0) if theta is None else theta),
             lo=None if lo is None else np.asarray(lo).astype(np.float64),
             hi=None if hi is None else np.asarray(hi).astype(np.float64),
             meta={k: v for k, v in d.items() if k not in ("At", "b", "lo", "hi")})
@@ -114,6 +137,29 @@ def soft(v, t):
     return np.sign(v) * np.maximum(np.abs(v) - t, 0.0)
 
 
+def dc_eta(loss: str, theta: float) -> float:
+    """eta(theta) of the DC split h = eta|x| - h- (Section 4.3)."""
+    return float(theta) if loss == "dc_exp" else float(theta) / np.log1p(theta)
+
+
+def dc_h(loss: str, theta: float, x) -> np.ndarray:
+    """The regulariser h (Section 4.3), elementwise."""
+    a = np.abs(np.asarray(x, dtype=np.float64))
+    if loss == "dc_exp":
+        return 1.0 - np.exp(-theta * a)
+    return np.log1p(theta * a) / np.log1p(theta)
+
+
+def dc_hminus_grad(loss: str, theta: float, x) -> np.ndarray:
+    """Derivative of h-(x) = eta|x| - h(x): eta sign(x) - h'(x), which is 0 at x = 0."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.abs(x)
+    if loss == "dc_exp":
+        return np.sign(x) * theta * (1.0 - np.exp(-theta * a))
+    eta = dc_eta(loss, theta)
+    return np.sign(x) * eta * (theta * a) / (1.0 + theta * a)
+
+
 def residual(p: Problem, x: np.ndarray) -> np.ndarray:
     """r = A x - b."""
     return p.A @ x - p.b
@@ -122,6 +168,9 @@ def residual(p: Problem, x: np.ndarray) -> np.ndarray:
 def objective(p: Problem, x: np.ndarray) -> float:
     """F(x) = f(x) + lam ||x||_1 (eq. 1 with the Section 4 losses)."""
     r = residual(p, x)
+    if p.dc:  # ||Ax - b||^2 + lam H(x)  (eq. of Section 4.3)
+        F = float(r @ r) + p.lam * float(dc_h(p.loss, p.theta, x).sum())
+        return F + (float(p.lin @ x) if p.lin is not None else 0.0)
     if p.loss == "lasso":
         f = 0.5 * float(r @ r)
     else:
@@ -136,8 +185,10 @@ def gradient(p: Problem, x: np.ndarray, r: np.ndarray | None = None) -> np.ndarr
     if r is None:
         r = residual(p, x)
     g = p.s * (p.A.T @ r)
-    if p.loss != "lasso":
+    if p.loss == "ncquad":
         g = g - 2.0 * p.c * x
+    if p.dc:
+        g = g - p.lam * dc_hminus_grad(p.loss, p.theta, x)
     if p.lin is not None:
         g = g + p.lin
     return g
@@ -148,6 +199,8 @@ def coord_curvature(p: Problem) -> np.ndarray:
     sq = np.einsum("ij,ij->j", p.A, p.A)
     if p.loss == "lasso":
         return sq
+    if p.dc:  # the quadratic part; the concave part is linearised in the surrogate
+        return 2.0 * sq
     return 2.0 * sq - 2.0 * p.c
 
 
@@ -181,11 +234,13 @@ def block_ranges(n: int, w: int):
 def _block_step(p: Problem, x, r_tilde, d, gamma, cols, lo, hi):
     """One block update from residual r_tilde; returns Delta on ``cols`` (not applied)."""
     g = p.s * (p.A[:, cols].T @ r_tilde)
-    if p.loss != "lasso":
+    if p.loss == "ncquad":
         g = g - 2.0 * p.c * x[cols]
+    if p.dc:
+        g = g - p.lam * dc_hminus_grad(p.loss, p.theta, x[cols])
     if p.lin is not None:
         g = g + p.lin[cols]
-    xh = best_response(x[cols], g, d[cols], p.lam, lo[cols], hi[cols])
+    xh = best_response(x[cols], g, d[cols], p.l1, lo[cols], hi[cols])
     return gamma * (xh - x[cols])
 
 
@@ -288,13 +343,13 @@ def solve_jacobi(p: Problem, x0, d, gamma, sweeps):
 def mf_measure(p: Problem, x) -> np.ndarray:
     """M_F(x) = x - argmin_y { grad f(x)^T (y - x) + G(y) + 0.5||y - x||^2 } over X."""
     g = gradient(p, x)
-    return x - best_response(x, g, np.ones(p.n), p.lam, p.lo_or_inf(), p.hi_or_inf())
+    return x - best_response(x, g, np.ones(p.n), p.l1, p.lo_or_inf(), p.hi_or_inf())
 
 
 def xhat_merit(p: Problem, x, d) -> np.ndarray:
     """x^(x) - x with the method's surrogate weights d (Section 4.3 merit)."""
     g = gradient(p, x)
-    return best_response(x, g, d, p.lam, p.lo_or_inf(), p.hi_or_inf()) - x
+    return best_response(x, g, d, p.l1, p.lo_or_inf(), p.hi_or_inf()) - x
 
 
 def stationarity(v, x) -> float:

@@ -13,7 +13,7 @@ import pytest
 from scipy.optimize import minimize
 
 import oracle as O
-from inputs import nesterov_lasso, random_lasso, ncquad_problem
+from inputs import dc_problem, nesterov_lasso, random_lasso, ncquad_problem
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -424,3 +424,90 @@ def test_kkt_violation_detects_perturbation():
     assert O.kkt_violation(p, xs) < 1e-11
     xs[d["support"][0]] *= 1.01
     assert O.kkt_violation(p, xs) > 1e-4
+
+
+# ----------------------------------------------------------------- DC regularisers (Section 4.3)
+
+@pytest.mark.parametrize("reg", ["dc_log", "dc_exp"])
+def test_dc_regulariser_definitions_and_split(reg):
+    """h from its definition at points where it is known exactly; h- = eta|x| - h is convex,
+    vanishes with its slope at 0, and its derivative is the central difference of
+    eta|x| - h(x)."""
+    theta = 20.0
+    eta = O.dc_eta(reg, theta)
+    assert eta == pytest.approx(theta if reg == "dc_exp" else theta / np.log(21.0), rel=1e-15)
+    if reg == "dc_log":
+        assert O.dc_h(reg, theta, 1.0) == pytest.approx(1.0, rel=1e-15)     # log(1+theta)/log(1+theta)
+    else:
+        assert O.dc_h(reg, theta, 1.0) == pytest.approx(1.0 - np.exp(-20.0), rel=1e-15)
+    assert O.dc_h(reg, theta, 0.0) == 0.0
+    assert O.dc_hminus_grad(reg, theta, 0.0) == 0.0
+    hm = lambda t: eta * abs(t) - float(O.dc_h(reg, theta, t))
+    for t in (-2.0, -0.3, -0.01, 0.004, 0.05, 0.7, 3.0):
+        e = 1e-6 * max(1.0, abs(t))
+        fd = (hm(t + e) - hm(t - e)) / (2 * e)
+        assert float(O.dc_hminus_grad(reg, theta, t)) == pytest.approx(fd, rel=1e-6, abs=1e-7)
+    grid = np.linspace(-2.0, 2.0, 4001)
+    vals = eta * np.abs(grid) - O.dc_h(reg, theta, grid)
+    assert np.all(vals[:-2] - 2 * vals[1:-1] + vals[2:] >= -1e-12)     # convex
+    assert abs(hm(1e-5)) <= 1e-6                                       # h-(x) = o(x) at 0
+
+
+@pytest.mark.parametrize("reg", ["dc_log", "dc_exp"])
+def test_dc_gauss_seidel_is_monotone(reg):
+    """The coordinate surrogate keeps the quadratic exactly and linearises the concave
+    -lam H- (an upper bound), so every best-response step lowers F (majorise-minimise)."""
+    d = dc_problem(60, 120, reg=reg[3:], seed=3)
+    p = O.Problem.from_data(d, loss=reg)
+    dw = O.surrogate_weights(p)
+    x, r = np.zeros(p.n), O.residual(p, np.zeros(p.n))
+    F = O.objective(p, x)
+    for _ in range(20):
+        x, r = O.gauss_seidel_sweep(p, x, r, dw, 1.0, w=1)
+        Fn = O.objective(p, x)
+        assert Fn <= F + 1e-12 * max(1.0, abs(F))
+        F = Fn
+
+
+@pytest.mark.parametrize("reg", ["dc_log", "dc_exp"])
+def test_dc_fixed_point_is_stationary_for_F(reg):
+    """At a fixed point of the best-response map, F = ||Ax-b||^2 + lam H (evaluated from its
+    definition) has zero partial derivatives on the support and non-negative one-sided
+    directional derivatives off it (central / one-sided differences of F itself)."""
+    d = dc_problem(50, 80, reg=reg[3:], seed=4)
+    p = O.Problem.from_data(d, loss=reg)
+    dw = O.surrogate_weights(p)
+    x, r = np.zeros(p.n), O.residual(p, np.zeros(p.n))
+    for _ in range(3000):
+        x, r = O.gauss_seidel_sweep(p, x, r, dw, 0.9, w=4)
+    assert O.stationarity(O.xhat_merit(p, x, dw), x) < 1e-12
+    assert 0 < np.count_nonzero(x) < p.n
+    F = lambda y: O.objective(p, y)
+    h = 1e-6
+    for j in range(p.n):
+        e = np.zeros(p.n)
+        e[j] = h
+        if x[j] != 0.0:
+            assert abs((F(x + e) - F(x - e)) / (2 * h)) <= 1e-5
+        else:
+            assert (F(x + e) - F(x)) / h >= -1e-5
+            assert (F(x - e) - F(x)) / h >= -1e-5
+
+
+@pytest.mark.parametrize("reg", ["dc_log", "dc_exp"])
+def test_dc_coordinate_step_is_exact_minimisation_without_regulariser(reg):
+    """With lam = 0 the DC loss is the plain quadratic ||Ax - b||^2; a unit step on one
+    coordinate must land on the exact 1-D minimiser x_j - a_j^T r / ||a_j||^2 (pins the
+    coordinate curvature 2||a_j||^2 of the surrogate)."""
+    d = dc_problem(30, 12, reg=reg[3:], seed=5)
+    p = O.Problem.from_data(d, loss=reg)
+    p.lam = 0.0
+    dw = O.surrogate_weights(p)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(p.n)
+    r = O.residual(p, x)
+    for j in range(p.n):
+        xj, rj = O.gauss_seidel_sweep(p, x, r, dw, 1.0, w=1, order=[j])
+        a = p.A[:, j]
+        want = x[j] - float(a @ r) / float(a @ a)
+        assert xj[j] == pytest.approx(want, rel=1e-12, abs=1e-12)
