@@ -347,7 +347,7 @@ def run_ours(args):
         del gen, At, b
         result["forms"] = {}
         for name, fn in (("mixed_precision", run_form_mixed_precision), ("gradient", run_form_gradient),
-                         ("batched", run_form_batched)):
+                         ("batched", run_form_batched), ("dc_regularisers", run_form_dc)):
             try:
                 result["forms"][name] = fn(args, ctx)
             except Exception as exc:  # a failing form is reported, the headline line still prints
@@ -362,25 +362,32 @@ def run_ours(args):
     del np
 
 
+def jacobi_safe_tau_rel(At, m: int, n: int, gamma: float = GAMMA):
+    """Descent-safe relative proximal weight of the Jacobi mode: 1 + tau_rel = (gamma/2) *
+    lambda_max(K^-1/2 A^T A K^-1/2) * 1.01, K = diag(||a_j||^2) (40 power iterations)."""
+    import torch
+    kap = torch.empty(n, dtype=torch.float64, device="cuda")
+    for j0 in range(0, n, 8192):
+        kap[j0:j0 + 8192] = (At[j0:j0 + 8192, :m].double() ** 2).sum(dim=1)
+    sc = (1.0 / kap.sqrt()).float()
+    v = torch.randn(n, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    v /= v.norm()
+    lmax = 0.0
+    for _ in range(40):
+        u = At[:, :m].T @ (sc * v)
+        wv = sc * (At[:, :m] @ u)
+        lmax = float(wv.norm())
+        v = wv / lmax
+    return max(0.0, 0.5 * gamma * lmax * 1.01 - 1.0), lmax
+
+
 def run_sync(gen, f_ref, args):
     """Deterministic Jacobi mode on the same instance, with the descent-safe relative
     proximal weight 1 + tau_rel = (gamma/2) * lambda_max(K^-1/2 A^T A K^-1/2) * 1.01."""
     import torch
     from paper_1701_04900_gb300 import Solver
     At = gen["At"]
-    kap = torch.empty(N, dtype=torch.float64, device="cuda")
-    for j0 in range(0, N, 8192):
-        kap[j0:j0 + 8192] = (At[j0:j0 + 8192, :M].double() ** 2).sum(dim=1)
-    sc = (1.0 / kap.sqrt()).float()
-    v = torch.randn(N, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
-    v /= v.norm()
-    lmax = 0.0
-    for _ in range(40):
-        u = At[:, :M].T @ (sc * v)
-        wv = sc * (At[:, :M] @ u)
-        lmax = float(wv.norm())
-        v = wv / lmax
-    tau_rel = max(0.0, 0.5 * GAMMA * lmax * 1.01 - 1.0)
+    tau_rel, lmax = jacobi_safe_tau_rel(At, M, N)
     s = Solver(At, gen["b"], LAM, m=M, block_w=W_BLOCK, mode="sync", gamma=GAMMA, tau_rel=tau_rel,
                refresh_every=args.refresh_every, check_every=args.check_every, max_sweeps=args.sync_sweeps,
                f_star=f_ref, profile=True)
@@ -673,6 +680,39 @@ def run_form_batched(args, ctx=None):
     f1 = 0.5 * float(r @ r) + float(g["x_star"].abs().sum())
     path["last_lane_rel_gap_vs_planted"] = (per[-1]["F"] - f1) / f1
     return {"batched": batched, "lambda_path": path}
+
+
+def run_form_dc(args, ctx=None):
+    """NEXT row: the nonconvex sparse-learning problem of Section 4.3, F = ||Ax-b||^2 + lam H(x)
+    with the log regulariser (theta = 20) on the 20000 x 40000 instance shape the paper uses
+    (unit-norm Gaussian columns, 5% nonzero xbar, noise sigma = 0.1).  Async and sync (Jacobi)
+    solves from x = 0 to ||xhat(x) - x||_inf / max(1, ||x||_inf) <= 1e-6, plus the exp
+    regulariser in async mode."""
+    import torch
+    from paper_1701_04900_gb300 import Solver
+    from inputs import dc_problem_torch
+    m, n = 20000, 40000
+    out = {}
+    for reg in ("log", "exp"):
+        g = dc_problem_torch(m, n, reg=reg, theta=20.0, seed=0, device="cuda")
+        modes = [("async", {})]
+        if reg == "log":
+            tau_rel, _ = jacobi_safe_tau_rel(g["At"], m, n)
+            modes.append(("sync", {"tau_rel": tau_rel}))
+        res = {"lambda": g["lam"], "theta": g["theta"]}
+        for mode, extra in modes:
+            t, st = _time_solves(lambda: Solver(g["At"], g["b"], g["lam"], m=m, loss="dc_" + reg, theta=g["theta"],
+                                                block_w=W_BLOCK, mode=mode, gamma=GAMMA, max_sweeps=3000,
+                                                check_every=10, refresh_every=10, tol_stat=1e-6, **extra), n)
+            res[mode] = {"seconds": t, "sweeps": st["sweeps"], "stat_xhat": st["stat_xhat"], "F": st["F"],
+                         "nnz": st["nnz"], "status": st["status"],
+                         "block_updates_per_s": st["block_updates"] / t if t else None}
+        if "sync" in res:
+            res["async_speedup_vs_sync"] = res["sync"]["seconds"] / res["async"]["seconds"]
+        out[f"dc_{reg}_{m}x{n}"] = res
+        del g
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_ncu_case(args):

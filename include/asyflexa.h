@@ -8,6 +8,8 @@
  * with f one of
  *     ASYFLEXA_LOSS_LASSO :  f(x) = 0.5 * ||A x - b||^2          (Section 4.2)
  *     ASYFLEXA_LOSS_NCQUAD:  f(x) = ||A x - b||^2 - c * ||x||^2  (Section 4.3, nonconvex)
+ *     ASYFLEXA_LOSS_DC_LOG / DC_EXP: ||A x - b||^2 + lambda * H(x) with a nonconvex
+ *                            regulariser H (Section 4.3), see asyflexa_loss
  * by the fixed-stepsize AsyFLEXA iteration (Algorithm 1): a block of w columns reads a
  * possibly stale residual r = A x - b, forms its gradient, takes the closed-form best
  * response of the proximal-linear surrogate (eq. 2; soft-threshold then clip to the
@@ -55,7 +57,17 @@ typedef enum {
     ASYFLEXA_EUNSUPPORTED = -6  /* valid request this build does not implement */
 } asyflexa_status;
 
-typedef enum { ASYFLEXA_LOSS_LASSO = 0, ASYFLEXA_LOSS_NCQUAD = 1 } asyflexa_loss;
+typedef enum {
+    ASYFLEXA_LOSS_LASSO = 0,    /* f = 0.5 ||Ax - b||^2 */
+    ASYFLEXA_LOSS_NCQUAD = 1,   /* f = ||Ax - b||^2 - c ||x||^2 */
+    ASYFLEXA_LOSS_DC_LOG = 2,   /* F = ||Ax - b||^2 + lambda sum_j h(x_j), h = log(1+theta|x|)/log(1+theta) */
+    ASYFLEXA_LOSS_DC_EXP = 3    /* F = ||Ax - b||^2 + lambda sum_j h(x_j), h = 1 - exp(-theta|x|) */
+} asyflexa_loss;
+/* The DC losses (Section 4.3, nonconvex sparse learning) split h = eta|x| - h-(x) with h-
+ * convex and smooth (eta = theta / log(1+theta) for log, theta for exp) and run the method on
+ * f = ||Ax - b||^2 - lambda sum_j h-(x_j), G = lambda eta ||x||_1: the best response keeps
+ * the quadratic's coordinate curvature 2||a_j||^2 and linearises -lambda h- at the current
+ * point.  theta > 0 is passed in asyflexa_problem.c. */
 
 /* SYNC: deterministic Jacobi sweeps (every block from the same x; bit-reproducible).
  * ASYNC: persistent CTAs, each owning a fixed set of blocks (Assumption D4), reading the
@@ -82,8 +94,8 @@ typedef struct {
     const void* b;              /* length m */
     const void* lo;             /* length n lower bounds, or NULL for -inf */
     const void* hi;             /* length n upper bounds, or NULL for +inf */
-    double lambda;              /* weight of ||x||_1, >= 0 */
-    double c;                   /* NCQUAD concavity weight (ignored for LASSO) */
+    double lambda;              /* weight of ||x||_1 (of H for the DC losses), >= 0 */
+    double c;                   /* NCQUAD concavity weight; theta of the DC losses; ignored for LASSO */
     int32_t loss;               /* asyflexa_loss */
     int32_t reserved0;
     const void* A_master;       /* optional FP32 copy of A (m x n, leading dimension lda_master), only

@@ -34,7 +34,7 @@ class BatchSolver:
                 if pr.get(key) is not None:
                     setattr(p, key, pr[key].data_ptr())
             p.lam, p.c = float(pr["lam"]), float(pr.get("c", 0.0))
-            p.loss = native.LOSS_LASSO if pr.get("loss", "lasso") == "lasso" else native.LOSS_NCQUAD
+            p.loss = native.LOSSES[pr.get("loss", "lasso")]
             self._keep.append(pr)
         o = default_opts()
         o.block_w, o.mode, o.gamma, o.tau, o.tau_rel = int(block_w), native.ASYNC, float(gamma), float(tau), float(tau_rel)

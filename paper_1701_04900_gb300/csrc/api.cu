@@ -110,15 +110,19 @@ int device_error(asyflexa_s& h) {
 }
 
 // F(x) from the handle's residual (must describe x): LASSO 0.5||r||^2 + lam||x||_1,
-// NCQUAD ||r||^2 - c||x||^2 + lam||x||_1.  Synchronises.
+// NCQUAD ||r||^2 - c||x||^2 + lam||x||_1, DC ||r||^2 + lam sum_j h(x_j); plus lin^T x.
+// Synchronises.
 int objective(asyflexa_s& h, const void* x, double* F, double* nnz) {
     cudaError_t e = dispatch(h, [&](auto L) { return decltype(L)::norms(h, x); });
     if (e != cudaSuccess) return cuda_error(&h, e, "norms");
-    double v[5];
+    double v[6];
     CK(&h, cudaMemcpyAsync(v, h.norms_out, sizeof(v), cudaMemcpyDeviceToHost, h.stream), "read norms");
     CK(&h, cudaStreamSynchronize(h.stream), "synchronize");
-    const bool lasso = h.prob.loss == ASYFLEXA_LOSS_LASSO;
-    *F = (lasso ? 0.5 * v[0] : v[0] - h.prob.c * v[2]) + v[4] + h.prob.lambda * v[1];
+    const auto& P = h.prob;
+    if (loss_is_dc(P))
+        *F = v[0] + P.lambda * v[5] + v[4];
+    else
+        *F = (P.loss == ASYFLEXA_LOSS_LASSO ? 0.5 * v[0] : v[0] - P.c * v[2]) + v[4] + P.lambda * v[1];
     if (nnz) *nnz = v[3];
     if (!std::isfinite(*F)) return set_error(&h, ASYFLEXA_ENONFINITE, "objective is not finite");
     return ASYFLEXA_OK;
@@ -310,7 +314,10 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
     if (quant && !P->col_scale) return set_error(nullptr, ASYFLEXA_EINVAL, "BF16/FP8 storage needs col_scale");
     if (!quant && P->col_scale) return set_error(nullptr, ASYFLEXA_EINVAL, "col_scale is only for BF16/FP8 storage");
     if (!(P->lambda >= 0.0) || !std::isfinite(P->lambda)) return set_error(nullptr, ASYFLEXA_EINVAL, "lambda must be finite and >= 0");
-    if (P->loss != ASYFLEXA_LOSS_LASSO && P->loss != ASYFLEXA_LOSS_NCQUAD) return set_error(nullptr, ASYFLEXA_EINVAL, "unknown loss");
+    if (P->loss < ASYFLEXA_LOSS_LASSO || P->loss > ASYFLEXA_LOSS_DC_EXP)
+        return set_error(nullptr, ASYFLEXA_EINVAL, "unknown loss");
+    if (loss_is_dc(*P) && !(P->c > 0.0 && std::isfinite(P->c)))
+        return set_error(nullptr, ASYFLEXA_EINVAL, "the DC losses need theta (passed in c) > 0");
     if (!std::isfinite(P->c)) return set_error(nullptr, ASYFLEXA_EINVAL, "c must be finite");
     if (P->A_master) {
         if (!quant) return set_error(nullptr, ASYFLEXA_EINVAL, "A_master is only for BF16/FP8 storage");

@@ -303,17 +303,17 @@ __global__ void reduce_partials_kernel(double* r, const TP* partial, int nseg, i
 
 // ----------------------------------------------------------------------------- norms
 
-constexpr int kNormsFields = 5;
+constexpr int kNormsFields = 6;
 
-// part[blk*5 + {0..4}] = {sum r_i^2, sum |x_j|, sum x_j^2, nnz(x), sum lin_j x_j} over a
-// fixed stride (lin may be null).
+// part[blk*6 + {0..5}] = {sum r_i^2, sum |x_j|, sum x_j^2, nnz(x), sum lin_j x_j, sum h(x_j)}
+// over a fixed stride (lin may be null; the last field is 0 unless dc.kind != 0).
 template <typename TX>
 __global__ void __launch_bounds__(kAuxThreads) norms_kernel(const double* r, int64_t m, const TX* x, int64_t n,
-                                                            const TX* lin, double* part) {
+                                                            const TX* lin, DcTerm dc, double* part) {
     __shared__ double sh[kAuxThreads / 32];
     const int64_t stride = static_cast<int64_t>(gridDim.x) * kAuxThreads;
     const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kAuxThreads + threadIdx.x;
-    double rr = 0.0, a1 = 0.0, a2 = 0.0, nz = 0.0, lx = 0.0;
+    double rr = 0.0, a1 = 0.0, a2 = 0.0, nz = 0.0, lx = 0.0, hs = 0.0;
     for (int64_t i = i0; i < m; i += stride) rr = fma(r[i], r[i], rr);
     for (int64_t j = i0; j < n; j += stride) {
         const double v = static_cast<double>(x[j]);
@@ -321,12 +321,14 @@ __global__ void __launch_bounds__(kAuxThreads) norms_kernel(const double* r, int
         a2 = fma(v, v, a2);
         nz += (v != 0.0) ? 1.0 : 0.0;
         if (lin) lx = fma(static_cast<double>(lin[j]), v, lx);
+        if (dc.kind) hs += dc_h(dc, v);
     }
     rr = block_sum_256<double>(rr, sh);
     a1 = block_sum_256<double>(a1, sh);
     a2 = block_sum_256<double>(a2, sh);
     nz = block_sum_256<double>(nz, sh);
     lx = block_sum_256<double>(lx, sh);
+    hs = block_sum_256<double>(hs, sh);
     if (threadIdx.x == 0) {
         double* o = part + blockIdx.x * kNormsFields;
         o[0] = rr;
@@ -334,6 +336,7 @@ __global__ void __launch_bounds__(kAuxThreads) norms_kernel(const double* r, int
         o[2] = a2;
         o[3] = nz;
         o[4] = lx;
+        o[5] = hs;
     }
 }
 
@@ -401,8 +404,8 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(const TA* A, int64
                                                             const typename XType<TA>::T* lo,
                                                             const typename XType<TA>::T* hi, const double* dw,
                                                             const typename XType<TA>::T* lin, double lam,
-                                                            double s_loss, double c2, int lasso_nobox, int use_smem,
-                                                            unsigned long long* meas) {
+                                                            double s_loss, double c2, DcTerm dc, int lasso_nobox,
+                                                            int use_smem, unsigned long long* meas) {
     using TC = typename ATraits<TA>::TC;
     constexpr int V = ATraits<TA>::kVec;
     extern __shared__ __align__(16) unsigned char csm[];
@@ -465,7 +468,8 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(const TA* A, int64
         if (lane == 0) {
             const double sc = scale ? static_cast<double>(scale[j]) : 1.0;
             const double xj = static_cast<double>(x[j]);
-            const double grad = s_loss * g * sc - c2 * xj + (lin ? static_cast<double>(lin[j]) : 0.0);
+            const double grad = s_loss * g * sc - c2 * xj + (lin ? static_cast<double>(lin[j]) : 0.0) -
+                                dc.lam * dc_hminus_grad(dc, xj);
             const double l = lo ? static_cast<double>(lo[j]) : -INFINITY;
             const double h = hi ? static_cast<double>(hi[j]) : INFINITY;
             // M_F: unit-weight proximal step

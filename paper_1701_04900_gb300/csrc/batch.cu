@@ -295,6 +295,9 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
     for (int k = 0; k < count; ++k) {
         if (probs[k].a_dtype != ASYFLEXA_F32 || probs[k].A_master)
             return fail(bfail("batched problems use FP32 storage (problem " + std::to_string(k) + ")"));
+        if (probs[k].loss != ASYFLEXA_LOSS_LASSO && probs[k].loss != ASYFLEXA_LOSS_NCQUAD)
+            return fail(bfail("batched problems use the LASSO or NCQUAD loss (problem " + std::to_string(k) + ")",
+                              ASYFLEXA_EUNSUPPORTED));
         asyflexa_t hk = nullptr;
         const int rc = asyflexa_create(&hk, &probs[k], &io, B->stream);
         if (rc) return fail(bfail("problem " + std::to_string(k) + ": " + asyflexa_last_error(nullptr), rc));

@@ -3,12 +3,36 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
 #include <string>
 #include <utility>
 #include <vector>
 
 #include "../../include/asyflexa.h"
+#include "types.cuh"
+
+// Loss-dependent constants of the method (host side).
+inline bool loss_is_dc(const asyflexa_problem& P) {
+    return P.loss == ASYFLEXA_LOSS_DC_LOG || P.loss == ASYFLEXA_LOSS_DC_EXP;
+}
+// factor of A^T r in grad f: 1 for 0.5||Ax-b||^2, 2 for ||Ax-b||^2
+inline double loss_s(const asyflexa_problem& P) { return P.loss == ASYFLEXA_LOSS_LASSO ? 1.0 : 2.0; }
+// 2c of the nonconvex quadratic's -c||x||^2 (0 for the other losses)
+inline double loss_c2(const asyflexa_problem& P) { return P.loss == ASYFLEXA_LOSS_NCQUAD ? 2.0 * P.c : 0.0; }
+// the DC regulariser term (kind 0 for the other losses); theta is passed in P.c
+inline asyflexa::DcTerm loss_dc(const asyflexa_problem& P) {
+    asyflexa::DcTerm d{0, 0.0, 0.0, 0.0};
+    if (loss_is_dc(P)) {
+        d.kind = P.loss == ASYFLEXA_LOSS_DC_LOG ? 1 : 2;
+        d.lam = P.lambda;
+        d.theta = P.c;
+        d.eta = d.kind == 2 ? P.c : P.c / std::log1p(P.c);
+    }
+    return d;
+}
+// weight of ||x||_1 in G: lambda, or lambda * eta for the DC losses
+inline double loss_l1(const asyflexa_problem& P) { return loss_is_dc(P) ? P.lambda * loss_dc(P).eta : P.lambda; }
 
 struct asyflexa_s {
     asyflexa_problem prob{};

@@ -92,11 +92,10 @@ int Launcher<TA>::set_smem_attrs(asyflexa_s& h) {
 template <typename TA>
 cudaError_t Launcher<TA>::colnorm(asyflexa_s& h) {
     const auto& P = h.prob;
-    const bool lasso = P.loss == ASYFLEXA_LOSS_LASSO;
     const int grid = h.sm_count * 4;
     colnorm_kernel<TA><<<grid, kAuxThreads, 0, h.stream>>>(
-        static_cast<const TA*>(P.A), P.lda, P.m, P.n, P.col_scale, lasso ? 1.0 : 2.0, lasso ? 0.0 : 2.0 * P.c,
-        h.opts.tau, h.opts.tau_rel, h.dw, h.flag);
+        static_cast<const TA*>(P.A), P.lda, P.m, P.n, P.col_scale, loss_s(P), loss_c2(P), h.opts.tau,
+        h.opts.tau_rel, h.dw, h.flag);
     ++h.launches;
     return cudaGetLastError();
 }
@@ -104,7 +103,6 @@ cudaError_t Launcher<TA>::colnorm(asyflexa_s& h) {
 template <typename TA>
 cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
     const auto& P = h.prob;
-    const bool lasso = P.loss == ASYFLEXA_LOSS_LASSO;
     SweepParams p{};
     p.A = P.A;
     p.lda = P.lda;
@@ -118,10 +116,11 @@ cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
     p.hi = P.hi;
     p.dw = h.dw;
     p.lin = P.lin;
-    p.lam = P.lambda;
+    p.lam = loss_l1(P);
+    p.dc = loss_dc(P);
     p.gamma = h.opts.gamma;
-    p.s_loss = lasso ? 1.0 : 2.0;
-    p.c2 = lasso ? 0.0 : 2.0 * P.c;
+    p.s_loss = loss_s(P);
+    p.c2 = loss_c2(P);
     p.w = h.opts.block_w;
     p.nblocks = h.nblocks;
     p.sweeps = sweeps;
@@ -196,7 +195,8 @@ template <typename TA>
 cudaError_t Launcher<TA>::norms(asyflexa_s& h, const void* xv) {
     using TX = typename XType<TA>::T;
     norms_kernel<TX><<<kNormsGrid, kAuxThreads, 0, h.stream>>>(h.r, h.prob.m, static_cast<const TX*>(xv), h.prob.n,
-                                                                static_cast<const TX*>(h.prob.lin), h.norms_part);
+                                                                static_cast<const TX*>(h.prob.lin), loss_dc(h.prob),
+                                                                h.norms_part);
     finalize_norms_kernel<double><<<1, 32, 0, h.stream>>>(h.norms_part, kNormsGrid, h.norms_out);
     h.launches += 2;
     return cudaGetLastError();
@@ -210,9 +210,8 @@ cudaError_t Launcher<TA>::check(asyflexa_s& h, const void* xv) {
     const int lasso_nobox = lasso && P.lo == nullptr && P.hi == nullptr;
     check_kernel<TA><<<h.check_ctas, kCheckThreads, h.check_use_smem ? h.check_smem : 0, h.stream>>>(
         static_cast<const TA*>(P.A), P.lda, P.m, P.n, P.col_scale, h.r, static_cast<const TX*>(xv),
-        static_cast<const TX*>(P.lo), static_cast<const TX*>(P.hi), h.dw, static_cast<const TX*>(P.lin), P.lambda,
-        lasso ? 1.0 : 2.0,
-        lasso ? 0.0 : 2.0 * P.c, lasso_nobox, h.check_use_smem ? 1 : 0, h.meas);
+        static_cast<const TX*>(P.lo), static_cast<const TX*>(P.hi), h.dw, static_cast<const TX*>(P.lin), loss_l1(P),
+        loss_s(P), loss_c2(P), loss_dc(P), lasso_nobox, h.check_use_smem ? 1 : 0, h.meas);
     ++h.launches;
     return cudaGetLastError();
 }

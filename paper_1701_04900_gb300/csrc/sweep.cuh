@@ -97,7 +97,8 @@ struct SweepParams {
     const void* hi;          // TX[n] or nullptr
     const double* dw;        // surrogate weights d_j
     const void* lin;         // TX[n] linear term of f, or nullptr
-    double lam, gamma, s_loss, c2;
+    double lam, gamma, s_loss, c2;  // lam: weight of ||x||_1 in G (lam * eta for the DC losses)
+    DcTerm dc;               // linearised concave part -lam H- of f (kind 0: none)
     int w, nblocks, sweeps;
     int tile_rows, ntiles, chunk_rows, stages;
     void* delta;             // Jacobi: TC[n] applied step
@@ -124,9 +125,9 @@ __device__ __forceinline__ TC warp_sum(TC v) {
 template <typename TX>
 __device__ __forceinline__ double coordinate_update(double g_atr, TX* x, const TX* lo, const TX* hi, int64_t j,
                                                     double dj, double lam, double gamma, double s_loss,
-                                                    double c2, double linj) {
+                                                    double c2, double linj, const DcTerm& dc) {
     const double xj = static_cast<double>(x[j]);
-    const double grad = s_loss * g_atr - c2 * xj + linj;
+    const double grad = s_loss * g_atr - c2 * xj + linj - dc.lam * dc_hminus_grad(dc, xj);
     double xh = 0.0;
     if (dj > 0.0) {
         const double v = xj - grad / dj;
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(const SweepPara
                     const double sc = p.scale ? static_cast<double>(p.scale[j]) : 1.0;
                     const double linj = p.lin ? static_cast<double>(static_cast<const TX*>(p.lin)[j]) : 0.0;
                     const double delta = coordinate_update<TX>(g * sc, x, lo, hi, j, p.dw[j], p.lam, p.gamma,
-                                                               p.s_loss, p.c2, linj);
+                                                               p.s_loss, p.c2, linj, p.dc);
                     flag = delta != 0.0;
                     if (MODE == kJacobi) {
                         static_cast<TC*>(p.delta)[j] = static_cast<TC>(delta);

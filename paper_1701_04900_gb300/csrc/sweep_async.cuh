@@ -92,6 +92,7 @@ struct BlockView {
     float s_loss, c2;
     int wb;
     bool skip;
+    DcTerm dc;
 };
 
 template <typename TA, bool BATCHED>
@@ -122,6 +123,7 @@ __device__ __forceinline__ BlockView<TA> block_view(const SweepParams& p, int b)
         v.s_loss = static_cast<float>(I.s_loss);
         v.c2 = static_cast<float>(I.c2);
         v.skip = I.active == 0;
+        v.dc = DcTerm{0, 0.0, 0.0, 0.0};
     } else {
         v.A = static_cast<const TA*>(p.A);
         v.lda = p.lda;
@@ -140,6 +142,7 @@ __device__ __forceinline__ BlockView<TA> block_view(const SweepParams& p, int b)
         v.s_loss = static_cast<float>(p.s_loss);
         v.c2 = static_cast<float>(p.c2);
         v.skip = false;
+        v.dc = p.dc;
     }
     return v;
 }
@@ -275,7 +278,11 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 cf.dinv = dj > 0.0 ? static_cast<float>(1.0 / dj) : 0.f;
                 cf.thr = dj > 0.0 ? static_cast<float>(bv.lam / dj) : 0.f;
                 cf.scale = bv.scale ? bv.scale[j] : 1.f;
-                cf.lin = bv.lin ? static_cast<float>(bv.lin[j]) : 0.f;
+                // linear coefficient of the surrogate: lin_j, minus lam h-'(x_j) for the DC losses
+                // (the concave part is linearised at the block's snapshot of x_j)
+                double lj = bv.lin ? static_cast<double>(bv.lin[j]) : 0.0;
+                if (bv.dc.kind) lj -= bv.dc.lam * dc_hminus_grad(bv.dc, static_cast<double>(bv.x[j]));
+                cf.lin = static_cast<float>(lj);
                 cf.pad0 = 0.f;
                 coef[tid] = cf;
             }

@@ -107,4 +107,27 @@ struct XType<double> {
     using T = double;
 };
 
+// Nonconvex regulariser of the sparse-learning problem of Section 4.3, F = ||Ax-b||^2 + lam H(x)
+// with H = sum_j h(x_j): kind 1 = log, h(x) = log(1 + theta|x|) / log(1 + theta); kind 2 =
+// exp, h(x) = 1 - exp(-theta|x|).  h = eta|x| - h-(x) with h- convex and smooth; the method's
+// smooth part f holds -lam H-, G = lam eta ||x||_1.  kind 0: no such term.
+struct DcTerm {
+    int kind;
+    double lam, theta, eta;
+};
+
+// d/dx h-(x) = eta sign(x) - h'(x) (0 at x = 0).
+__device__ __forceinline__ double dc_hminus_grad(const DcTerm& d, double x) {
+    if (d.kind == 0 || x == 0.0) return 0.0;
+    const double a = fabs(x);
+    const double v = d.kind == 2 ? -d.theta * expm1(-d.theta * a) : d.eta * (d.theta * a) / (1.0 + d.theta * a);
+    return copysign(v, x);
+}
+
+// h(x) itself (for the objective).
+__device__ __forceinline__ double dc_h(const DcTerm& d, double x) {
+    const double a = fabs(x);
+    return d.kind == 2 ? -expm1(-d.theta * a) : log1p(d.theta * a) / log1p(d.theta);
+}
+
 }  // namespace asyflexa

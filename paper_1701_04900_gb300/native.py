@@ -17,7 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libasyflexa.so")
 
 OK, ENOTCONV, EINVAL, ECUDA, ENOMEM, ETIMEOUT, ENONFINITE, EUNSUPPORTED = 0, 1, -1, -2, -3, -4, -5, -6
-LOSS_LASSO, LOSS_NCQUAD = 0, 1
+LOSS_LASSO, LOSS_NCQUAD, LOSS_DC_LOG, LOSS_DC_EXP = 0, 1, 2, 3
+LOSSES = {"lasso": LOSS_LASSO, "ncquad": LOSS_NCQUAD, "dc_log": LOSS_DC_LOG, "dc_exp": LOSS_DC_EXP}
 SYNC, ASYNC = 0, 1
 F64, F32, BF16, FP8E4M3 = 0, 1, 2, 3
 
@@ -172,7 +173,7 @@ class Solver:
     solver exists (the wrapper keeps references).
     """
 
-    def __init__(self, At, b, lam, m=None, *, loss="lasso", c=0.0, lo=None, hi=None, col_scale=None,
+    def __init__(self, At, b, lam, m=None, *, loss="lasso", c=0.0, theta=None, lo=None, hi=None, col_scale=None,
                  block_w=32, mode="sync", gamma=0.9, tau=0.0, tau_rel=0.0, refresh_every=10,
                  check_every=10, max_sweeps=1000, num_ctas=0, tol_gap=1e-6, tol_stat=1e-6,
                  f_star=math.nan, profile=False, variant=0, A_master=None, switch_tol=1e-7, lin=None,
@@ -191,8 +192,11 @@ class Solver:
         p.A, p.col_scale, p.b = At.data_ptr(), (col_scale.data_ptr() if col_scale is not None else None), b.data_ptr()
         p.lo = lo.data_ptr() if lo is not None else None
         p.hi = hi.data_ptr() if hi is not None else None
-        p.lam, p.c = float(lam), float(c)
-        p.loss = LOSS_LASSO if loss == "lasso" else LOSS_NCQUAD
+        if loss not in LOSSES:
+            raise ValueError(f"loss must be one of {sorted(LOSSES)}")
+        p.loss = LOSSES[loss]
+        # the DC losses take their regulariser parameter theta in the c field of the ABI
+        p.lam, p.c = float(lam), float(theta if theta is not None else c)
         if lin is not None:
             p.lin = lin.data_ptr()
         if A_master is not None:

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from inputs import nesterov_lasso, random_lasso, ncquad_problem
+from inputs import dc_problem, nesterov_lasso, random_lasso, ncquad_problem
 from tests._gpu_helpers import quantize_columns, rel_inf, to_cuda
 
 pytestmark = pytest.mark.gpu
@@ -400,3 +400,78 @@ def test_unsupported_kernel_variant_is_reported():
     with pytest.raises(AsyflexaError) as ei:
         make_solver(d, mode="async", variant=2)
     assert ei.value.code == -6
+
+
+# ----------------------------------------------------------------------------- DC regularisers
+
+@pytest.mark.parametrize("reg", ["dc_log", "dc_exp"])
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("m,n", [(700, 500), (9001, 160)])
+def test_async_single_cta_dc_equals_gauss_seidel(reg, variant, m, n):
+    """F = ||Ax-b||^2 + lam H(x) (Section 4.3) with the log / exp regulariser: one CTA against
+    the oracle's cyclic Gauss-Seidel sweeps (concave part linearised at each block's x)."""
+    import torch
+    d = dc_problem(m, n, reg=reg[3:], seed=m + n, store_dtype=np.float32)
+    p = O.Problem.from_data(d, loss=reg)
+    dw = O.surrogate_weights(p, tau=0.1)
+    x_ref, r_ref = np.zeros(p.n), O.residual(p, np.zeros(p.n))
+    s = make_solver(d, block_w=32, mode="async", tau=0.1, num_ctas=1, refresh_every=100, variant=variant,
+                    loss=reg, theta=d["theta"])
+    x = xzeros(d, torch.float32)
+    for sweep in range(4):
+        x_ref, r_ref = O.gauss_seidel_sweep(p, x_ref, r_ref, dw, 0.9, w=32)
+        s.step(x, 1)
+        assert rel_inf(x.cpu().numpy(), x_ref) < TOL32, sweep
+
+
+@pytest.mark.parametrize("reg", ["dc_log", "dc_exp"])
+@pytest.mark.parametrize("store,tol", [(np.float64, TOL64), (np.float32, TOL32)])
+def test_sync_parity_dc(reg, store, tol):
+    d = dc_problem(400, 600, reg=reg[3:], seed=8, store_dtype=store)
+    import torch
+    p = O.Problem.from_data(d, loss=reg)
+    dw = O.surrogate_weights(p, tau_rel=1.0)
+    ref = oracle_jacobi(p, dw, 0.9, 12)
+    s = make_solver(d, block_w=16, mode="sync", gamma=0.9, tau_rel=1.0, loss=reg, theta=d["theta"])
+    x = xzeros(d, torch.float64 if store == np.float64 else torch.float32)
+    done = 0
+    for k in (1, 4, 12):
+        s.step(x, k - done)
+        done = k
+        assert rel_inf(x.cpu().numpy(), ref[k - 1]) < tol, k
+
+
+@pytest.mark.parametrize("reg", ["dc_log", "dc_exp"])
+def test_dc_async_reaches_a_stationary_point(reg):
+    """Many CTAs: the solve stops at ||xhat(x) - x||_inf / max(1, ||x||_inf) <= 1e-6 measured by
+    the library; the oracle confirms the stationarity and the objective at the returned x."""
+    import torch
+    d = dc_problem(2000, 4000, reg=reg[3:], seed=9, store_dtype=np.float32)
+    p = O.Problem.from_data(d, loss=reg)
+    s = make_solver(d, block_w=32, mode="async", num_ctas=16, max_sweeps=3000, check_every=10, refresh_every=10,
+                    tol_stat=1e-6, loss=reg, theta=d["theta"])
+    x = xzeros(d, torch.float32)
+    st = s.solve(x)
+    assert st["status"] == 0, st
+    xr = x.cpu().numpy().astype(np.float64)
+    merit = O.stationarity(O.xhat_merit(p, xr, O.surrogate_weights(p)), xr)
+    assert merit <= 2e-6
+    assert abs(O.objective(p, xr) - st["F"]) <= 1e-9 * abs(st["F"])
+    assert abs(st["stat_xhat"] - merit) <= 1e-7
+
+
+@pytest.mark.parametrize("reg", ["dc_log", "dc_exp"])
+def test_dc_check_measures_match_oracle(reg):
+    import torch
+    d = dc_problem(1500, 900, reg=reg[3:], seed=10, store_dtype=np.float64)
+    p = O.Problem.from_data(d, loss=reg)
+    rng = np.random.default_rng(1)
+    xv = rng.standard_normal(p.n) * (rng.random(p.n) < 0.2)
+    s = make_solver(d, tau=0.2, loss=reg, theta=d["theta"])
+    xt = torch.from_numpy(xv).cuda()
+    s.refresh(xt)
+    st = s.check(xt)
+    dw = O.surrogate_weights(p, tau=0.2)
+    assert st["F"] == pytest.approx(O.objective(p, xv), rel=1e-12)
+    assert st["stat_xhat"] == pytest.approx(O.stationarity(O.xhat_merit(p, xv, dw), xv), rel=1e-9)
+    assert st["stat_mf"] == pytest.approx(O.stationarity(O.mf_measure(p, xv), xv), rel=1e-9)
