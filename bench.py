@@ -621,8 +621,10 @@ def run_form_batched(args, ctx=None):
     t_seq = 0.0
     for i in range(seq_n):
         p = probs[i]
-        s = Solver(p["At"], p["b"], 1.0, m=p["m"], block_w=tot["block_w"], mode="async", refresh_every=10,
-                   check_every=10, max_sweeps=3000, f_star=f_ref[i])
+        # the same cap on updates in flight as the batched form: max(1, m / (4 w)) CTAs
+        wb = tot["block_w"]
+        s = Solver(p["At"], p["b"], 1.0, m=p["m"], block_w=wb, mode="async", refresh_every=10,
+                   check_every=10, max_sweeps=3000, f_star=f_ref[i], num_ctas=max(1, min(152, p["m"] // (4 * wb))))
         x = torch.zeros(p["At"].shape[0], dtype=torch.float32, device="cuda")
         torch.cuda.synchronize()
         t1 = time.perf_counter()

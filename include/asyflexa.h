@@ -130,6 +130,13 @@ typedef struct {
                                    (FP32/BF16/FP8, m up to 24576 rows; EUNSUPPORTED otherwise) */
     double switch_tol;          /* with A_master: solve leaves the low-precision phase when a check
                                    interval lowers F by less than switch_tol * |F| (default 1e-7) */
+    double gamma_mu;            /* 0 (default): fixed step gamma (Algorithm 1).  > 0: the diminishing
+                                   rule of the experiments of Section 4, gamma^0 = gamma and
+                                   gamma^{k+1} = gamma^k (1 - gamma_mu gamma^k), k counting block
+                                   updates from the start of asyflexa_solve (or of the handle /
+                                   asyflexa_reset_counters for asyflexa_step).  Async: update k is the
+                                   one that read the residual after k completed updates (exact for a
+                                   single CTA); sync: block i of the s-th sweep is update s N + i. */
 } asyflexa_opts;
 
 /* Results and counters.  Optimality fields are FP64 and computed from an exact

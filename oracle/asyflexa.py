@@ -34,6 +34,10 @@ Algorithms for Nonconvex Big-Data Optimization, Part II"):
   proximal term) gives x^_j = clip(0, lo_j, hi_j).
 
 * Fixed-step update (Algorithm 1, step S.4):  x_i <- x_i + gamma (x^_i(x~) - x_i).
+  The experiments of Section 4 use the diminishing rule gamma^{k+1} = gamma^k (1 - mu gamma^k)
+  instead, k counting updates; the sweep functions accept a per-update sequence of steps
+  (``diminishing_steps``): update t of a Gauss-Seidel sweep uses steps[t], and in a Jacobi
+  sweep block i uses steps[i].
 
 * Execution orders (Algorithm 1 with different index/delay processes):
     - Jacobi: every block from the same x (the synchronous all-blocks form);
@@ -65,6 +69,7 @@ __all__ = [
     "xhat_merit", "kkt_violation", "stationarity", "brute_force_lasso",
     "stationary_points_box", "lambda_max_gram", "jacobi_tau_rel", "solve_gs",
     "solve_jacobi", "lasso_support", "lasso_adjoint_gradient", "dc_eta", "dc_h", "dc_hminus_grad",
+    "diminishing_steps", "block_steps",
 ]
 
 DC_LOSSES = ("dc_log", "dc_exp")
@@ -224,6 +229,25 @@ def best_response(x, g, d, lam, lo, hi):
     return np.minimum(np.maximum(y, lo), hi)
 
 
+def diminishing_steps(gamma0: float, mu: float, count: int) -> np.ndarray:
+    """gamma^0 = gamma0, gamma^{k+1} = gamma^k (1 - mu gamma^k): the stepsize sequence of the
+    experiments of Section 4 (gamma^0 = 1, mu = 1e-6 there), for k = 0 .. count - 1."""
+    g = np.empty(count)
+    v = float(gamma0)
+    for k in range(count):
+        g[k] = v
+        v = v * (1.0 - mu * v)
+    return g
+
+
+def block_steps(n: int, w: int, steps) -> np.ndarray:
+    """Per-coordinate step for a Jacobi sweep where block i takes steps[i]."""
+    out = np.empty(n)
+    for i, cols in enumerate(block_ranges(n, w)):
+        out[cols] = steps[i]
+    return out
+
+
 def block_ranges(n: int, w: int):
     """Blocks of w consecutive coordinates; the last block may be shorter."""
     return [np.arange(i, min(n, i + w)) for i in range(0, n, w)]
@@ -256,15 +280,17 @@ def jacobi_sweep(p: Problem, x, r, d, gamma):
 
 
 def gauss_seidel_sweep(p: Problem, x, r, d, gamma, w=1, order=None):
-    """Cyclic block Gauss-Seidel sweep: blocks in ``order`` (default 0..N-1)."""
+    """Cyclic block Gauss-Seidel sweep: blocks in ``order`` (default 0..N-1).  ``gamma`` is a
+    fixed step or a sequence with one step per update of the sweep (in update order)."""
     lo, hi = p.lo_or_inf(), p.hi_or_inf()
     blocks = block_ranges(p.n, w)
     x = x.copy()
     r = r.copy()
     seq = range(len(blocks)) if order is None else order
-    for i in seq:
+    per_update = np.ndim(gamma) > 0
+    for t, i in enumerate(seq):
         cols = blocks[i]
-        delta = _block_step(p, x, r, d, gamma, cols, lo, hi)
+        delta = _block_step(p, x, r, d, gamma[t] if per_update else gamma, cols, lo, hi)
         x[cols] += delta
         nz = np.nonzero(delta)[0]
         if nz.size:

@@ -35,7 +35,7 @@ def _nvcc() -> str:
 
 
 def _flags(extra=()):
-    return [ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
+    return [ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE, "-I", CSRC,
             "--expt-relaxed-constexpr", *extra]
 
 

@@ -77,7 +77,7 @@ auto dispatch(asyflexa_s& h, F&& f) {
 
 void free_buffers(asyflexa_s* h) {
     void* ptrs[] = {h->r, h->dw, h->delta, h->list_idx, h->list_val, h->tilecnt, h->count, h->partial,
-                    h->norms_part, h->norms_out, h->counters, h->hist, h->meas, h->err, h->flag};
+                    h->norms_part, h->norms_out, h->counters, h->hist, h->meas, h->err, h->flag, h->gtab};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -175,7 +175,45 @@ int drain_profile(asyflexa_s& h) {
 }
 
 // Launch one sweep kernel (k sweeps), bracketed by events when profiling.
+// Steps of the next launch (k sweeps) from the diminishing rule, into the device table.
+int fill_steps(asyflexa_s& h, int k) {
+    const size_t cnt = static_cast<size_t>(k) * static_cast<size_t>(h.nblocks);
+    if (cnt > h.gtab_cap) {
+        CK(&h, cudaStreamSynchronize(h.stream), "synchronize");
+        if (h.gtab) cudaFree(h.gtab);
+        h.gtab = nullptr;
+        h.gtab_cap = 0;
+        CK(&h, cudaMalloc(&h.gtab, cnt * sizeof(double)), "alloc step table");
+        h.gtab_cap = cnt;
+    }
+    // the previous launch's copy must have left the host buffer before it is rewritten
+    CK(&h, cudaStreamSynchronize(h.stream), "synchronize");
+    h.gtab_host.resize(cnt);
+    double g = h.sched_gamma;
+    const double mu = h.opts.gamma_mu;
+    for (size_t i = 0; i < cnt; ++i) {
+        h.gtab_host[i] = g;
+        const double t = mu * g;  // two roundings, the order of the oracle's recurrence
+        g = g * (1.0 - t);
+    }
+    CK(&h, cudaMemcpyAsync(h.gtab, h.gtab_host.data(), cnt * sizeof(double), cudaMemcpyHostToDevice, h.stream),
+       "upload steps");
+    return ASYFLEXA_OK;
+}
+
+// Restart the diminishing-step sequence (k = 0, gamma^0 = opts.gamma) and the update counter.
+int restart_steps(asyflexa_s& h) {
+    h.sched_k = 0;
+    h.sched_gamma = h.opts.gamma;
+    CK(&h, cudaMemsetAsync(h.counters, 0, sizeof(unsigned long long), h.stream), "clear update counter");
+    return ASYFLEXA_OK;
+}
+
 int launch_sweep(asyflexa_s& h, void* x, int mode, int k) {
+    if (h.opts.gamma_mu > 0.0) {
+        int rc = fill_steps(h, k);
+        if (rc) return rc;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h.opts.profile) {
         if (h.prof_events.size() >= 4096) {
@@ -192,6 +230,11 @@ int launch_sweep(asyflexa_s& h, void* x, int mode, int k) {
         CK(&h, cudaEventRecord(e1, h.stream), "event record");
         h.prof_events.emplace_back(e0, e1);
         h.prof_sweeps.push_back(k);
+    }
+    if (h.opts.gamma_mu > 0.0) {
+        const long long cnt = static_cast<long long>(k) * h.nblocks;
+        h.sched_k += cnt;
+        h.sched_gamma = h.gtab_host[cnt - 1] * (1.0 - h.opts.gamma_mu * h.gtab_host[cnt - 1]);
     }
     return ASYFLEXA_OK;
 }
@@ -242,6 +285,9 @@ int validate_opts(const asyflexa_opts* o, std::string* why) {
     if (o->variant < 0 || o->variant > 2) return *why = "variant must be 0, 1 or 2", 1;
     if (!(o->tol_gap >= 0.0) || !(o->tol_stat >= 0.0)) return *why = "tolerances must be >= 0", 1;
     if (!(o->switch_tol >= 0.0)) return *why = "switch_tol must be >= 0", 1;
+    if (!(o->gamma_mu >= 0.0) || !std::isfinite(o->gamma_mu)) return *why = "gamma_mu must be finite and >= 0", 1;
+    if (o->gamma_mu > 0.0 && o->gamma_mu * o->gamma >= 1.0)
+        return *why = "gamma_mu * gamma must be < 1 (the steps must stay positive)", 1;
     return 0;
 }
 
@@ -288,6 +334,7 @@ void asyflexa_opts_default(asyflexa_opts* o) {
     o->f_star = std::nan("");
     o->seed = 0;
     o->switch_tol = 1e-7;
+    o->gamma_mu = 0.0;
 }
 
 const char* asyflexa_last_error(asyflexa_t h) { return h ? h->msg.c_str() : g_thread_msg.c_str(); }
@@ -419,6 +466,8 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
     CKC(cudaMalloc(&h->flag, sizeof(int)), "alloc flag");
     CKC(cudaMemsetAsync(h->r, 0, h->mcopy * sizeof(double), h->stream), "clear r");
     CKC(cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), h->stream), "clear counters");
+    h->sched_k = 0;
+    h->sched_gamma = O->gamma;
     CKC(cudaMemsetAsync(h->hist, 0, 32 * sizeof(unsigned long long), h->stream), "clear hist");
     CKC(cudaMemsetAsync(h->err, 0, sizeof(int), h->stream), "clear err");
     CKC(cudaMemsetAsync(h->flag, 0, sizeof(int), h->stream), "clear flag");
@@ -571,7 +620,8 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
     CK(h, cudaEventCreate(&e1), "event");
     CK(h, cudaEventRecord(e0, h->stream), "event record");
     int rc = ASYFLEXA_OK;
-    if (!h->r_valid || h->r_x != x) rc = do_refresh(*h, x);
+    if (h->opts.gamma_mu > 0.0) rc = restart_steps(*h);  // each solve runs the step sequence from gamma^0
+    if (!rc && (!h->r_valid || h->r_x != x)) rc = do_refresh(*h, x);
     const double fs = h->opts.f_star;
     const bool known = std::isfinite(fs);
     long long sweeps = 0;
@@ -686,6 +736,8 @@ int asyflexa_reset_counters(asyflexa_t h) {
     int rc = drain_profile(*h);
     if (rc) return rc;
     CK(h, cudaMemsetAsync(h->counters, 0, 4 * sizeof(unsigned long long), h->stream), "clear counters");
+    h->sched_k = 0;
+    h->sched_gamma = h->opts.gamma;
     CK(h, cudaMemsetAsync(h->hist, 0, 32 * sizeof(unsigned long long), h->stream), "clear hist");
     h->total_sweeps = 0;
     h->prof_seconds = 0.0;

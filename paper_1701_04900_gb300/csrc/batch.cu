@@ -106,6 +106,9 @@ struct asyflexa_batch_s {
     cudaGraphExec_t exec = nullptr;
     std::vector<void*> graph_x;
     int graph_w = 0;
+    std::vector<int> cap;  // per problem: blocks it may have in flight, max(1, m / (4 w))
+    int grid = 0;          // CTAs of the next sweep launch
+    int graph_grid = 0;    // CTAs of the captured round
     long long launches = 0;
 };
 
@@ -138,15 +141,20 @@ const void* batched_kernel(int cpc) {
 }
 
 // Global block list for width w.  Shared A: interleaved by block index, so that the
-// problems' reads of the same panel are close in time.  Otherwise: capped cycles over the
-// problems (below).
+// problems' reads of the same panel are close in time.  Otherwise every problem's blocks are
+// spread evenly over the list (ordered by their fractional position (b + 1/2) / nb within
+// their problem), so that any window of consecutive entries -- roughly what the CTAs work on
+// at the same time -- holds blocks of a problem in proportion to its size.
 int build_blocks(asyflexa_batch_s& B, int w) {
     std::vector<int> bi, bl;
     std::vector<int> nb(B.count);
     int maxnb = 0;
+    B.cap.assign(B.count, 1);
     for (int k = 0; k < B.count; ++k) {
         nb[k] = static_cast<int>((B.h[k]->prob.n + w - 1) / w);
         maxnb = nb[k] > maxnb ? nb[k] : maxnb;
+        const int64_t c = B.h[k]->prob.m / (4 * static_cast<int64_t>(w));
+        B.cap[k] = c < 1 ? 1 : static_cast<int>(c);
     }
     if (B.flags & ASYFLEXA_BATCH_SHARED_A) {
         for (int b = 0; b < maxnb; ++b)
@@ -156,35 +164,17 @@ int build_blocks(asyflexa_batch_s& B, int w) {
                     bl.push_back(b);
                 }
     } else {
-        // Independent problems: cycles over the problems, each contributing at most
-        // max(1, m / (4 w)) of its next blocks, so that the blocks a launch works on at the same
-        // time (about one window of `ctas` consecutive entries) hold few columns of any one
-        // problem relative to its m -- the updates in flight of Assumption D1.  A cycle shorter
-        // than the grid (few problems left) is padded with empty entries (-1) for the same reason.
-        const int ctas = B.opts.num_ctas > 0 ? B.opts.num_ctas : B.sm_count;
-        std::vector<int> next(B.count, 0), cap(B.count);
-        for (int k = 0; k < B.count; ++k) {
-            const int64_t c = B.h[k]->prob.m / (4 * static_cast<int64_t>(w));
-            cap[k] = c < 1 ? 1 : static_cast<int>(c);
-        }
-        bool left = true;
-        while (left) {
-            left = false;
-            const size_t start = bi.size();
-            for (int k = 0; k < B.count; ++k) {
-                const int t = std::min(cap[k], nb[k] - next[k]);
-                for (int i = 0; i < t; ++i) {
-                    bi.push_back(k);
-                    bl.push_back(next[k] + i);
-                }
-                next[k] += t;
-                if (next[k] < nb[k]) left = true;
-            }
-            const size_t len = bi.size() - start;
-            if (left && len < static_cast<size_t>(ctas)) {
-                bi.insert(bi.end(), ctas - len, -1);
-                bl.insert(bl.end(), ctas - len, 0);
-            }
+        struct Entry {
+            double key;
+            int k, b;
+        };
+        std::vector<Entry> all;
+        for (int k = 0; k < B.count; ++k)
+            for (int b = 0; b < nb[k]; ++b) all.push_back({(b + 0.5) / nb[k], k, b});
+        std::stable_sort(all.begin(), all.end(), [](const Entry& a, const Entry& c) { return a.key < c.key; });
+        for (const Entry& e : all) {
+            bi.push_back(e.k);
+            bl.push_back(e.b);
         }
     }
     if (B.d_blk_inst) cudaFree(B.d_blk_inst);
@@ -219,12 +209,24 @@ int launch_batched(asyflexa_batch_s& B, int sweeps) {
     p.total_blocks = B.total_blocks;
     p.keep_a_in_l2 = (B.flags & ASYFLEXA_BATCH_SHARED_A) ? 1 : 0;
     void* args[] = {&p};
-    const int grid = B.opts.num_ctas > 0 ? B.opts.num_ctas : B.sm_count;
+    const int full = B.opts.num_ctas > 0 ? B.opts.num_ctas : B.sm_count;
+    const int grid = B.grid > 0 && B.grid < full ? B.grid : full;
     const cudaError_t e =
         cudaLaunchKernel(B.kernel, dim3(grid), dim3(asyflexa::kRegThreads), args, B.smem, B.stream);
     ++B.launches;
     BCK(e, "batched sweep launch");
     return ASYFLEXA_OK;
+}
+
+// CTAs for the next rounds: at most the sum over the active problems of their in-flight
+// caps, so that a few problems left running are not spread over every SM (their updates in
+// flight would then be many columns for few rows; Assumption D1).
+int active_grid(asyflexa_batch_s& B) {
+    const int full = B.opts.num_ctas > 0 ? B.opts.num_ctas : B.sm_count;
+    long long g = 0;
+    for (int k = 0; k < B.count; ++k)
+        if (B.h_inst[k].active) g += B.cap[k];
+    return static_cast<int>(std::max<long long>(1, std::min<long long>(full, g)));
 }
 
 int upload_table(asyflexa_batch_s& B) {
@@ -413,6 +415,7 @@ int asyflexa_batch_solve(asyflexa_batch_t B, void* const* xs, const double* f_st
         c.F = c.F_prev = NAN;
         c.conv_round = -2;
     }
+    B->grid = 0;  // every problem active again: full grid until the first deactivation
     int rc = upload_table(*B);
     if (rc) return rc;
     BCK(cudaMemcpyAsync(B->d_conv, B->h_conv.data(), count * sizeof(ConvState), cudaMemcpyHostToDevice, B->stream),
@@ -458,26 +461,33 @@ int asyflexa_batch_solve(asyflexa_batch_t B, void* const* xs, const double* f_st
         cudaEventDestroy(a0);
         cudaEventDestroy(a1);
     }
-    // capture one round as a CUDA graph (re-captured if the iterates or the width changed)
+    // one round as a CUDA graph, re-captured when the iterates, the width or the grid change
     std::vector<void*> xv(xs, xs + count);
-    if (!B->exec || B->graph_x != xv || B->graph_w != B->w) {
+    auto capture = [&]() -> int {
         if (B->exec) cudaGraphExecDestroy(B->exec);
         if (B->graph) cudaGraphDestroy(B->graph);
         B->exec = nullptr;
         B->graph = nullptr;
         BCK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        rc = enqueue_round(*B, xs);
+        const int erc = enqueue_round(*B, xs);
         cudaGraph_t g = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(B->stream, &g);
-        if (rc) return rc;
+        if (erc) return erc;
         BCK(ce, "end capture");
         B->graph = g;
         BCK(cudaGraphInstantiate(&B->exec, g, 0), "instantiate graph");
         B->graph_x = xv;
         B->graph_w = B->w;
+        B->graph_grid = B->grid;
+        return ASYFLEXA_OK;
+    };
+    B->grid = active_grid(*B);
+    if (!B->exec || B->graph_x != xv || B->graph_w != B->w || B->graph_grid != B->grid) {
+        rc = capture();
+        if (rc) return rc;
     }
     const int per_round = B->opts.refresh_every;
-    int n_active = count;
+    int n_active = count, last_active = count;
     while (sweeps < B->opts.max_sweeps && n_active > 0) {
         BCK(cudaGraphLaunch(B->exec, B->stream), "graph launch");
         sweeps += per_round;
@@ -486,6 +496,18 @@ int asyflexa_batch_solve(asyflexa_batch_t B, void* const* xs, const double* f_st
         int errw = 0;
         BCK(cudaMemcpy(&errw, B->err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
         if (errw) return bfail("a bounded device-side wait expired", ASYFLEXA_ETIMEOUT);
+        if (n_active > 0 && n_active < last_active) {
+            // problems were deactivated on the device: shrink the grid to the active ones
+            last_active = n_active;
+            BCK(cudaMemcpy(B->h_inst.data(), B->d_inst, count * sizeof(BatchInst), cudaMemcpyDeviceToHost),
+                "read problem table");
+            const int g = active_grid(*B);
+            if (g < B->graph_grid) {
+                B->grid = g;
+                rc = capture();
+                if (rc) return rc;
+            }
+        }
     }
     BCK(cudaEventRecord(e1, B->stream), "event record");
     BCK(cudaEventSynchronize(e1), "event sync");

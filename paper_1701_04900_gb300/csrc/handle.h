@@ -56,6 +56,14 @@ struct asyflexa_s {
     // gather-GEMV / compaction geometry
     int nseg = 0, gemv_rowtiles = 0, compact_tiles = 0;
     // register-resident async kernel (0 = not used)
+    // diminishing stepsize (opts.gamma_mu > 0): update index and step at the next launch, and
+    // the device table of the steps of one launch
+    long long sched_k = 0;
+    double sched_gamma = 0.0;
+    double* gtab = nullptr;
+    size_t gtab_cap = 0;
+    std::vector<double> gtab_host;
+
     int reg_upt = 0, reg_cpc = 0, reg_stages = 0;
     size_t reg_smem = 0;
 

@@ -132,6 +132,11 @@ cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
     p.counters = h.counters;
     p.hist = h.hist;
     p.err = h.err;
+    if (h.opts.gamma_mu > 0.0) {
+        p.gtab = h.gtab;
+        p.gtab_len = static_cast<long long>(sweeps) * h.nblocks;
+        p.k_base = static_cast<unsigned long long>(h.sched_k);
+    }
     if (mode == ASYFLEXA_ASYNC && h.reg_upt > 0) {
         p.stages = h.reg_stages;
         p.tile_rows = static_cast<int>(h.mcopy);

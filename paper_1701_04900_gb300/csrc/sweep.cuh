@@ -99,6 +99,9 @@ struct SweepParams {
     const void* lin;         // TX[n] linear term of f, or nullptr
     double lam, gamma, s_loss, c2;  // lam: weight of ||x||_1 in G (lam * eta for the DC losses)
     DcTerm dc;               // linearised concave part -lam H- of f (kind 0: none)
+    const double* gtab;      // diminishing steps of this launch (nullptr: fixed step gamma)
+    long long gtab_len;      // entries of gtab (sweeps * nblocks)
+    unsigned long long k_base;  // update index of gtab[0] (async: value of counters[0] at launch)
     int w, nblocks, sweeps;
     int tile_rows, ntiles, chunk_rows, stages;
     void* delta;             // Jacobi: TC[n] applied step
@@ -112,6 +115,13 @@ struct SweepParams {
     int total_blocks;
     int keep_a_in_l2;              // 1: load A with normal L2 priority (several problems share A)
 };
+
+// Step of update index `idx` within this launch's table (clamped), or the fixed step.
+__device__ __forceinline__ double launch_step(const SweepParams& p, long long idx) {
+    if (!p.gtab) return p.gamma;
+    idx = idx < 0 ? 0 : (idx >= p.gtab_len ? p.gtab_len - 1 : idx);
+    return p.gtab[idx];
+}
 
 template <typename TC>
 __device__ __forceinline__ TC warp_sum(TC v) {
@@ -160,6 +170,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(const SweepPara
     uint64_t* empty = full + p.stages;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.off_misc);
     int* s_nact = reinterpret_cast<int*>(smem + L.off_misc + 4);
+    unsigned long long* s_u0 = reinterpret_cast<unsigned long long*>(smem + L.off_misc + 8);
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -245,7 +256,10 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(const SweepPara
                 const int64_t rows = min64(p.tile_rows, p.mcopy - row0);
                 if (MODE == kAsync || p.ntiles > 1 || !rt_valid) {
                     named_bar_sync(1, kConsThreads);  // every consumer is done with the old tile
-                    if (MODE == kAsync && t == 0 && tid == 0) u0 = ld_relaxed_u64(&p.counters[0]);
+                    if (MODE == kAsync && t == 0 && tid == 0) {
+                        u0 = ld_relaxed_u64(&p.counters[0]);
+                        *s_u0 = u0;  // read by the epilogue threads (several barriers later)
+                    }
                     const double2* rsrc = reinterpret_cast<const double2*>(p.r + row0);
                     for (int64_t i = tid; i < rows / 2; i += kConsThreads) {
                         const double2 v = __ldcg(rsrc + i);
@@ -340,7 +354,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(const SweepPara
                     const int64_t j = c0 + tid;
                     const double sc = p.scale ? static_cast<double>(p.scale[j]) : 1.0;
                     const double linj = p.lin ? static_cast<double>(static_cast<const TX*>(p.lin)[j]) : 0.0;
-                    const double delta = coordinate_update<TX>(g * sc, x, lo, hi, j, p.dw[j], p.lam, p.gamma,
+                    // step of this block update: the update index is the number of updates completed
+                    // before its residual read (async) or its position in the sweep (Jacobi)
+                    const double gam =
+                        launch_step(p, MODE == kAsync ? static_cast<long long>(*s_u0 - p.k_base)
+                                                      : static_cast<long long>(s) * p.nblocks + b);
+                    const double delta = coordinate_update<TX>(g * sc, x, lo, hi, j, p.dw[j], p.lam, gam,
                                                                p.s_loss, p.c2, linj, p.dc);
                     flag = delta != 0.0;
                     if (MODE == kJacobi) {

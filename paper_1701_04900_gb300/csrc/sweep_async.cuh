@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.off_bars);
     uint64_t* empty = full + p.stages;
     volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.off_misc);
+    float* s_gamma = reinterpret_cast<float*>(smem + L.off_misc + 8);  // step of the current block
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
@@ -230,7 +231,6 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
     // ------------------------------------------------------------------ consumers
     uint32_t stage = 0, phase = 0;
     unsigned long long u_read = 0, my_updates = 0, my_active = 0;
-    const float gamma = static_cast<float>(p.gamma);
 
     float inc[UPT][V];
     int buf = 0;
@@ -247,7 +247,12 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
             // S.2: stale read of the residual into shared memory (rows >= m hold 0), and the
             // block's per-column coefficients.  The barrier that ended the previous block
             // guarantees nobody still reads rt or coef.
-            if (tid == 0) u_read = ld_relaxed_u64(&p.counters[0]);
+            if (tid == 0) {
+                u_read = ld_relaxed_u64(&p.counters[0]);
+                // step of this block update (the update index is the number of updates completed
+                // before this read of the residual)
+                *s_gamma = static_cast<float>(launch_step(p, static_cast<long long>(u_read - p.k_base)));
+            }
             {
                 // 8 independent 16-byte L2 loads in flight per thread
                 constexpr int kB = 8;
@@ -292,6 +297,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 for (int e = 0; e < V; ++e) inc[k][e] = 0.f;
             bool any = false;
             named_bar_sync(1, kRegConsThreads);
+            const float gamma = *s_gamma;
 
             for (int jl = 0; jl < bv.wb; ++jl) {
                 // ---- dot a_j^T r~ over this thread's rows

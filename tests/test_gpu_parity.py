@@ -475,3 +475,63 @@ def test_dc_check_measures_match_oracle(reg):
     assert st["F"] == pytest.approx(O.objective(p, xv), rel=1e-12)
     assert st["stat_xhat"] == pytest.approx(O.stationarity(O.xhat_merit(p, xv, dw), xv), rel=1e-9)
     assert st["stat_mf"] == pytest.approx(O.stationarity(O.mf_measure(p, xv), xv), rel=1e-9)
+
+
+# ----------------------------------------------------------------------------- diminishing step
+
+@pytest.mark.parametrize("store,tol,variant", [(np.float64, TOL64, 0), (np.float32, TOL32, 1),
+                                               (np.float32, TOL32, 2)])
+def test_async_single_cta_diminishing_step_equals_gauss_seidel(store, tol, variant):
+    """gamma^{k+1} = gamma^k (1 - mu gamma^k) (the experiments' rule, Section 4) with k counting
+    block updates: one CTA performs them in order, so update k of the run takes gamma^k."""
+    import torch
+    d = random_lasso(1201, 300, seed=21, lam=0.2, store_dtype=store, box=1.5)
+    p = O.Problem.from_data(d)
+    dw = O.surrogate_weights(p, tau=0.1)
+    w = 16
+    N = len(O.block_ranges(p.n, w))
+    steps = O.diminishing_steps(1.0, 0.02, 5 * N)
+    x_ref, r_ref = np.zeros(p.n), O.residual(p, np.zeros(p.n))
+    s = make_solver(d, block_w=w, mode="async", tau=0.1, gamma=1.0, gamma_mu=0.02, num_ctas=1, refresh_every=3,
+                    variant=variant)
+    x = xzeros(d, torch.float64 if store == np.float64 else torch.float32)
+    for sweep in range(5):
+        x_ref, r_ref = O.gauss_seidel_sweep(p, x_ref, r_ref, dw, steps[sweep * N:(sweep + 1) * N], w=w)
+        s.step(x, 1)
+        assert rel_inf(x.cpu().numpy(), x_ref) < tol, sweep
+    assert steps[-1] < 0.5     # the sequence did diminish over the run
+
+
+@pytest.mark.parametrize("store,tol", [(np.float64, TOL64), (np.float32, TOL32)])
+def test_sync_diminishing_step_parity(store, tol):
+    """Jacobi sweeps: block i of sweep s is update s N + i of the sequence."""
+    import torch
+    d = nesterov_lasso(300, 1200, 20, seed=22, store_dtype=store)
+    p = O.Problem.from_data(d)
+    w = 32
+    N = len(O.block_ranges(p.n, w))
+    tr = O.jacobi_tau_rel(p, 1.0)
+    dw = O.surrogate_weights(p, tau_rel=tr)
+    steps = O.diminishing_steps(1.0, 0.01, 8 * N)
+    x_ref, r_ref = np.zeros(p.n), O.residual(p, np.zeros(p.n))
+    s = make_solver(d, block_w=w, mode="sync", gamma=1.0, gamma_mu=0.01, tau_rel=tr)
+    x = xzeros(d, torch.float64 if store == np.float64 else torch.float32)
+    for sweep in range(8):
+        x_ref, r_ref = O.jacobi_sweep(p, x_ref, r_ref, dw, O.block_steps(p.n, w, steps[sweep * N:(sweep + 1) * N]))
+    s.step(x, 8)
+    assert rel_inf(x.cpu().numpy(), x_ref) < tol
+
+
+def test_diminishing_step_solve_restarts_the_sequence():
+    """Every solve runs the sequence from gamma^0: two Jacobi solves from x = 0 agree bitwise."""
+    import torch
+    d = nesterov_lasso(300, 1200, 20, seed=23, store_dtype=np.float32)
+    p = O.Problem.from_data(d)
+    s = make_solver(d, block_w=32, mode="sync", gamma=1.0, gamma_mu=1e-3, tau_rel=O.jacobi_tau_rel(p, 1.0),
+                    max_sweeps=40, check_every=10, tol_stat=0.0)
+    xs = []
+    for _ in range(2):
+        x = xzeros(d, torch.float32)
+        s.solve(x)
+        xs.append(x.cpu().numpy())
+    assert np.array_equal(xs[0], xs[1])

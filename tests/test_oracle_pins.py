@@ -511,3 +511,36 @@ def test_dc_coordinate_step_is_exact_minimisation_without_regulariser(reg):
         a = p.A[:, j]
         want = x[j] - float(a @ r) / float(a @ a)
         assert xj[j] == pytest.approx(want, rel=1e-12, abs=1e-12)
+
+
+# ------------------------------------------------------------ diminishing stepsize (Section 4)
+
+def test_diminishing_steps_recurrence_values():
+    """gamma^{k+1} = gamma^k (1 - mu gamma^k): with gamma^0 = 1 and mu = 1/2 the sequence is
+    exact in binary: 1, 1/2, 3/8, 39/128, ...; and 1/gamma^k - 1/gamma^0 lies between mu k and
+    mu k + mu^2 sum_i gamma^i / (1 - mu gamma^i) (the recurrence of 1/gamma)."""
+    g = O.diminishing_steps(1.0, 0.5, 4)
+    assert list(g) == [1.0, 0.5, 0.375, 39.0 / 128.0]
+    mu, K = 1e-3, 5000
+    g = O.diminishing_steps(0.95, mu, K)
+    assert np.all(np.diff(g) < 0) and g[-1] > 0
+    inv = 1.0 / g - 1.0 / 0.95
+    k = np.arange(K)
+    assert np.all(inv >= mu * k - 1e-12)
+    upper = mu * k + mu ** 2 * np.concatenate([[0.0], np.cumsum(g / (1 - mu * g))[:-1]])
+    assert np.all(inv <= upper + 1e-9)
+
+
+def test_gauss_seidel_with_step_sequence_equals_block_by_block_updates():
+    """A sweep with a per-update step sequence applies steps[t] to its t-th update: the same
+    as running the sweep one block at a time with that fixed step."""
+    d = random_lasso(40, 24, seed=31, lam=0.1)
+    p = O.Problem.from_data(d)
+    dw = O.surrogate_weights(p, tau=0.1)
+    steps = O.diminishing_steps(1.0, 0.05, 6)
+    x0, r0 = np.zeros(p.n), O.residual(p, np.zeros(p.n))
+    xa, ra = O.gauss_seidel_sweep(p, x0, r0, dw, steps, w=4)
+    xb, rb = x0, r0
+    for t in range(6):
+        xb, rb = O.gauss_seidel_sweep(p, xb, rb, dw, steps[t], w=4, order=[t])
+    assert np.array_equal(xa, xb)
