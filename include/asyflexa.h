@@ -165,6 +165,11 @@ typedef struct {
     int32_t block_w;            /* batched solve: block width used (given or autotuned) */
     int32_t kernel_variant;     /* async sweep kernel this handle launches (1 or 2, see
                                    asyflexa_opts.variant); set by solve, check, read_counters */
+    double dual_gap;            /* plain LASSO (no box, no linear term): (P(x) - D(nu)) / max(1, |P(x)|)
+                                   with the feasible dual point nu = theta r, theta = min(1, lambda /
+                                   ||A^T r||_inf) -- an upper bound of the relative optimality gap
+                                   that needs no optimum; NaN for other problems.  Without f_star,
+                                   solve on the plain LASSO also requires dual_gap <= tol_gap. */
 } asyflexa_stats;
 
 /* Library version (ASYFLEXA_ABI_VERSION).  Never fails. */

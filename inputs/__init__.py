@@ -14,6 +14,8 @@ from .problems import (  # noqa: F401
     random_lasso,
     ncquad_problem,
     dc_problem,
+    liu_wright_lasso,
+    liu_wright_lasso_torch,
     dc_problem_torch,
     ncquad_problem_torch,
     pad_lda,

@@ -29,6 +29,9 @@ Workloads follow the kinds of instance the paper experiments with (Section 4):
   box |x_i| <= 1.  The constant c of f = ||Ax - b||^2 - c||x||^2 and the weight lam
   are problem parameters chosen as documented on the function.
 
+* ``liu_wright_lasso``: the Gaussian LASSO set of Section 4.2 (A iid N(0, 1), s-sparse
+  xbar, b = A xbar + N(0, sigma^2) noise, lam = 20 sqrt(m log n) sigma).
+
 * ``dc_problem``: the sparse-regression instance of Section 4.3's nonconvex experiment
   (F = ||Ax - b||^2 + lam H(x) with the log or exp regulariser): A with iid N(0, 1)
   entries and unit-norm columns, xbar 5% nonzero with N(0, 1) values, b = A xbar + e,
@@ -270,6 +273,47 @@ def ncquad_problem_torch(m: int, n: int, seed: int = 0, frac: float = 0.05, nois
     return dict(At=At, b=b, x0=x0, c=float(c), lam=float(lam), m=m, n=n, lda=lda,
                 lo=torch.full((n,), -box, dtype=torch.float32, device=device),
                 hi=torch.full((n,), box, dtype=torch.float32, device=device))
+
+
+def liu_wright_lasso(m: int, n: int, s: int, sigma: float = 0.01, seed: int = 0, store_dtype=np.float64) -> dict:
+    """The Gaussian LASSO set of Section 4.2: A with iid N(0, 1) entries, xbar with s nonzeros
+    (iid N(0, 1) values at uniformly drawn positions), b = A xbar + e with e iid N(0, sigma^2),
+    lam = 20 sqrt(m log n) sigma.  The optimum is not known in closed form."""
+    rng = np.random.default_rng(seed)
+    A64 = rng.standard_normal((n, m))
+    xbar = np.zeros(n)
+    idx = rng.choice(n, size=s, replace=False)
+    xbar[idx] = rng.standard_normal(s)
+    e = sigma * rng.standard_normal(m)
+    elt = np.dtype(store_dtype).itemsize
+    lda = pad_lda(m, elt)
+    At = np.zeros((n, lda), dtype=store_dtype)
+    At[:, :m] = A64.astype(store_dtype)
+    b64 = At[:, :m].astype(np.float64).T @ xbar + e
+    lam = 20.0 * math.sqrt(m * math.log(n)) * sigma
+    return dict(At=At, b=b64.astype(store_dtype), xbar=xbar, lam=float(lam), m=m, n=n, lda=lda)
+
+
+def liu_wright_lasso_torch(m: int, n: int, s: int, sigma: float = 0.01, seed: int = 0, device="cuda") -> dict:
+    """:func:`liu_wright_lasso` generated with torch on ``device`` in FP32 storage; same recipe,
+    a different random stream."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    lda = pad_lda(m, 4)
+    At = torch.zeros((n, lda), dtype=torch.float32, device=device)
+    chunk = 8192
+    for j0 in range(0, n, chunk):
+        j1 = min(n, j0 + chunk)
+        At[j0:j1, :m] = torch.randn((j1 - j0, m), generator=g, device=device, dtype=torch.float32)
+    idx = torch.randperm(n, generator=g, device=device)[:s]
+    xbar = torch.zeros(n, dtype=torch.float64, device=device)
+    xbar[idx] = torch.randn(s, generator=g, device=device, dtype=torch.float64)
+    e = sigma * torch.randn(m, generator=g, device=device, dtype=torch.float64)
+    b = (At[idx, :m].double().T @ xbar[idx] + e).to(torch.float32)
+    lam = 20.0 * math.sqrt(m * math.log(n)) * sigma
+    return dict(At=At, b=b, xbar=xbar, lam=float(lam), m=m, n=n, lda=lda)
 
 
 def dc_problem(m: int, n: int, reg: str = "log", theta: float = 20.0, seed: int = 0, frac: float = 0.05,

@@ -69,7 +69,7 @@ __all__ = [
     "xhat_merit", "kkt_violation", "stationarity", "brute_force_lasso",
     "stationary_points_box", "lambda_max_gram", "jacobi_tau_rel", "solve_gs",
     "solve_jacobi", "lasso_support", "lasso_adjoint_gradient", "dc_eta", "dc_h", "dc_hminus_grad",
-    "diminishing_steps", "block_steps",
+    "diminishing_steps", "block_steps", "lasso_dual_gap",
 ]
 
 DC_LOSSES = ("dc_log", "dc_exp")
@@ -381,6 +381,19 @@ def xhat_merit(p: Problem, x, d) -> np.ndarray:
 def stationarity(v, x) -> float:
     """||v||_inf / max(1, ||x||_inf)."""
     return float(np.abs(v).max(initial=0.0) / max(1.0, float(np.abs(x).max(initial=0.0))))
+
+
+def lasso_dual_gap(p: Problem, x) -> tuple[float, float]:
+    """(P(x), P(x) - D(nu)) for the plain LASSO (no box, no linear term): nu = theta r with
+    r = A x - b and theta = min(1, lam / ||A^T r||_inf) is feasible for the dual
+    max -0.5||nu||^2 - b^T nu  s.t. ||A^T nu||_inf <= lam, so P(x) - D(nu) >= P(x) - F*
+    (weak duality) bounds the optimality gap without knowing F*."""
+    r = residual(p, x)
+    P = 0.5 * float(r @ r) + p.lam * float(np.abs(x).sum())
+    atr = float(np.abs(p.A.T @ r).max(initial=0.0))
+    theta = 1.0 if atr <= p.lam else p.lam / atr
+    D = -0.5 * theta * theta * float(r @ r) - theta * float(p.b @ r)
+    return P, P - D
 
 
 def kkt_violation(p: Problem, x) -> float:

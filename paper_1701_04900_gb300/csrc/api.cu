@@ -111,11 +111,11 @@ int device_error(asyflexa_s& h) {
 
 // F(x) from the handle's residual (must describe x): LASSO 0.5||r||^2 + lam||x||_1,
 // NCQUAD ||r||^2 - c||x||^2 + lam||x||_1, DC ||r||^2 + lam sum_j h(x_j); plus lin^T x.
-// Synchronises.
-int objective(asyflexa_s& h, const void* x, double* F, double* nnz) {
+// Optionally also ||r||^2 and b^T r (for the LASSO duality gap).  Synchronises.
+int objective(asyflexa_s& h, const void* x, double* F, double* nnz, double* rr = nullptr, double* br = nullptr) {
     cudaError_t e = dispatch(h, [&](auto L) { return decltype(L)::norms(h, x); });
     if (e != cudaSuccess) return cuda_error(&h, e, "norms");
-    double v[6];
+    double v[7];
     CK(&h, cudaMemcpyAsync(v, h.norms_out, sizeof(v), cudaMemcpyDeviceToHost, h.stream), "read norms");
     CK(&h, cudaStreamSynchronize(h.stream), "synchronize");
     const auto& P = h.prob;
@@ -124,12 +124,29 @@ int objective(asyflexa_s& h, const void* x, double* F, double* nnz) {
     else
         *F = (P.loss == ASYFLEXA_LOSS_LASSO ? 0.5 * v[0] : v[0] - P.c * v[2]) + v[4] + P.lambda * v[1];
     if (nnz) *nnz = v[3];
+    if (rr) *rr = v[0];
+    if (br) *br = v[6];
     if (!std::isfinite(*F)) return set_error(&h, ASYFLEXA_ENONFINITE, "objective is not finite");
     return ASYFLEXA_OK;
 }
 
+// The plain LASSO (no box, no linear term) has the dual max -0.5||nu||^2 - b^T nu subject to
+// ||A^T nu||_inf <= lam; nu = theta r, theta = min(1, lam / ||A^T r||_inf), is feasible, and
+// P(x) - D(nu) >= P(x) - F* (weak duality): a certificate of the gap without F*.  Relative to
+// max(1, |P|); NaN for the other problems.
+bool plain_lasso(const asyflexa_s& h) {
+    return h.prob.loss == ASYFLEXA_LOSS_LASSO && !h.prob.lo && !h.prob.hi && !h.prob.lin;
+}
+double lasso_dual_gap(const asyflexa_s& h, double P, double rr, double br, double atr) {
+    if (!plain_lasso(h)) return std::nan("");
+    const double lam = h.prob.lambda;
+    const double theta = atr <= lam ? 1.0 : lam / atr;
+    const double D = -0.5 * theta * theta * rr - theta * br;
+    return (P - D) / std::max(1.0, std::fabs(P));
+}
+
 struct Measures {
-    double mf, xh, kkt, xmax;
+    double mf, xh, kkt, xmax, atr;
     long long nnz;
     bool nonfinite;
 };
@@ -152,6 +169,7 @@ int measure(asyflexa_s& h, const void* x, Measures* M) {
     M->xmax = asd(v[3]);
     M->nnz = static_cast<long long>(v[4]);
     M->nonfinite = v[5] != 0;
+    M->atr = asd(v[6]);
     if (M->nonfinite) return set_error(&h, ASYFLEXA_ENONFINITE, "non-finite value in the optimality check");
     return ASYFLEXA_OK;
 }
@@ -589,8 +607,8 @@ int asyflexa_check(asyflexa_t h, const void* x, asyflexa_stats* out) {
     }
     int rc = do_refresh(*h, x);
     if (rc) return rc;
-    double F = 0.0, nnz = 0.0;
-    rc = objective(*h, x, &F, &nnz);
+    double F = 0.0, nnz = 0.0, rr = 0.0, br = 0.0;
+    rc = objective(*h, x, &F, &nnz, &rr, &br);
     Measures M{};
     if (!rc) rc = measure(*h, x, &M);
     if (!rc) rc = device_error(*h);
@@ -603,6 +621,7 @@ int asyflexa_check(asyflexa_t h, const void* x, asyflexa_stats* out) {
     const bool lasso_nobox = h->prob.loss == ASYFLEXA_LOSS_LASSO && !h->prob.lo && !h->prob.hi;
     out->kkt_viol = lasso_nobox ? M.kkt : std::nan("");
     out->nnz = M.nnz;
+    out->dual_gap = lasso_dual_gap(*h, F, rr, br, M.atr);
     out->checked = 1;
     out->kernel_variant = async_variant(*h);
     out->status = rc;
@@ -636,7 +655,8 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
         rc = run_sweeps(*h, x, k);
         if (rc) break;
         sweeps += k;
-        rc = objective(*h, x, &F, nullptr);
+        double rr = 0.0, br = 0.0;
+        rc = objective(*h, x, &F, nullptr, &rr, &br);
         if (rc) break;
         rc = device_error(*h);
         if (rc) break;
@@ -648,7 +668,10 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
         rc = h->master ? measure(*h->master, x, &M) : measure(*h, x, &M);
         if (rc) break;
         const double stat = M.xh / std::max(1.0, M.xmax);
-        if (stat <= h->opts.tol_stat && (!known || gap <= h->opts.tol_gap)) {
+        // without a known optimum, the plain LASSO also needs the duality-gap certificate
+        const double dgap = lasso_dual_gap(h->master ? *h->master : *h, F, rr, br, M.atr);
+        const bool gap_ok = known ? gap <= h->opts.tol_gap : (!plain_lasso(*h) || dgap <= h->opts.tol_gap);
+        if (stat <= h->opts.tol_stat && gap_ok) {
             status = ASYFLEXA_OK;
             break;
         }

@@ -303,18 +303,21 @@ __global__ void reduce_partials_kernel(double* r, const TP* partial, int nseg, i
 
 // ----------------------------------------------------------------------------- norms
 
-constexpr int kNormsFields = 6;
+constexpr int kNormsFields = 7;
 
-// part[blk*6 + {0..5}] = {sum r_i^2, sum |x_j|, sum x_j^2, nnz(x), sum lin_j x_j, sum h(x_j)}
-// over a fixed stride (lin may be null; the last field is 0 unless dc.kind != 0).
+// part[blk*7 + {0..6}] = {sum r_i^2, sum |x_j|, sum x_j^2, nnz(x), sum lin_j x_j, sum h(x_j),
+// sum b_i r_i} over a fixed stride (lin may be null; field 5 is 0 unless dc.kind != 0).
 template <typename TX>
-__global__ void __launch_bounds__(kAuxThreads) norms_kernel(const double* r, int64_t m, const TX* x, int64_t n,
-                                                            const TX* lin, DcTerm dc, double* part) {
+__global__ void __launch_bounds__(kAuxThreads) norms_kernel(const double* r, const TX* b, int64_t m, const TX* x,
+                                                            int64_t n, const TX* lin, DcTerm dc, double* part) {
     __shared__ double sh[kAuxThreads / 32];
     const int64_t stride = static_cast<int64_t>(gridDim.x) * kAuxThreads;
     const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kAuxThreads + threadIdx.x;
-    double rr = 0.0, a1 = 0.0, a2 = 0.0, nz = 0.0, lx = 0.0, hs = 0.0;
-    for (int64_t i = i0; i < m; i += stride) rr = fma(r[i], r[i], rr);
+    double rr = 0.0, a1 = 0.0, a2 = 0.0, nz = 0.0, lx = 0.0, hs = 0.0, br = 0.0;
+    for (int64_t i = i0; i < m; i += stride) {
+        rr = fma(r[i], r[i], rr);
+        br = fma(static_cast<double>(b[i]), r[i], br);
+    }
     for (int64_t j = i0; j < n; j += stride) {
         const double v = static_cast<double>(x[j]);
         a1 += fabs(v);
@@ -329,6 +332,7 @@ __global__ void __launch_bounds__(kAuxThreads) norms_kernel(const double* r, int
     nz = block_sum_256<double>(nz, sh);
     lx = block_sum_256<double>(lx, sh);
     hs = block_sum_256<double>(hs, sh);
+    br = block_sum_256<double>(br, sh);
     if (threadIdx.x == 0) {
         double* o = part + blockIdx.x * kNormsFields;
         o[0] = rr;
@@ -337,6 +341,7 @@ __global__ void __launch_bounds__(kAuxThreads) norms_kernel(const double* r, int
         o[3] = nz;
         o[4] = lx;
         o[5] = hs;
+        o[6] = br;
     }
 }
 
@@ -424,7 +429,7 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(const TA* A, int64
     const int lane = threadIdx.x & 31;
     const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = (static_cast<int64_t>(gridDim.x) * blockDim.x) >> 5;
-    double mmf = 0.0, mxh = 0.0, mkkt = 0.0, mx = 0.0;
+    double mmf = 0.0, mxh = 0.0, mkkt = 0.0, mx = 0.0, matr = 0.0;
     unsigned long long nnz = 0;
     int nonfinite = 0;
     constexpr int kU = 4;  // independent 16-byte loads in flight per lane
@@ -495,6 +500,7 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(const TA* A, int64
             mxh = fmax(mxh, dx);
             mkkt = fmax(mkkt, kkt);
             mx = fmax(mx, fabs(xj));
+            matr = fmax(matr, fabs(s_loss * g * sc));  // ||s A^T r||_inf, for the LASSO dual point
             nnz += (xj != 0.0);
         }
     }
@@ -505,6 +511,7 @@ __global__ void __launch_bounds__(kCheckThreads) check_kernel(const TA* A, int64
         if (mx > 0.0) atomic_max_nonneg(&meas[3], mx);
         if (nnz) atomicAdd(&meas[4], nnz);
         if (nonfinite) atomicOr(&meas[5], 1ull);
+        if (matr > 0.0) atomic_max_nonneg(&meas[6], matr);
     }
 }
 

@@ -199,7 +199,8 @@ cudaError_t Launcher<TA>::refresh(asyflexa_s& h, const void* xv) {
 template <typename TA>
 cudaError_t Launcher<TA>::norms(asyflexa_s& h, const void* xv) {
     using TX = typename XType<TA>::T;
-    norms_kernel<TX><<<kNormsGrid, kAuxThreads, 0, h.stream>>>(h.r, h.prob.m, static_cast<const TX*>(xv), h.prob.n,
+    norms_kernel<TX><<<kNormsGrid, kAuxThreads, 0, h.stream>>>(h.r, static_cast<const TX*>(h.prob.b), h.prob.m,
+                                                                static_cast<const TX*>(xv), h.prob.n,
                                                                 static_cast<const TX*>(h.prob.lin), loss_dc(h.prob),
                                                                 h.norms_part);
     finalize_norms_kernel<double><<<1, 32, 0, h.stream>>>(h.norms_part, kNormsGrid, h.norms_out);

@@ -58,7 +58,7 @@ class Stats(C.Structure):
         ("sweep_kernel_sweeps", C.c_int64),
         ("status", C.c_int32), ("checked", C.c_int32),
         ("polish_sweeps", C.c_int64), ("polish_seconds", C.c_double),
-        ("block_w", C.c_int32), ("kernel_variant", C.c_int32),
+        ("block_w", C.c_int32), ("kernel_variant", C.c_int32), ("dual_gap", C.c_double),
     ]
 
     def as_dict(self) -> dict:

@@ -57,7 +57,9 @@ int main(void) {
   printf("asyflexa_stats %zu\n", sizeof(asyflexa_stats));
   P(asyflexa_problem, lambda) P(asyflexa_problem, loss) P(asyflexa_problem, hi)
   P(asyflexa_opts, gamma) P(asyflexa_opts, num_ctas) P(asyflexa_opts, f_star) P(asyflexa_opts, seed)
+  P(asyflexa_opts, switch_tol) P(asyflexa_opts, gamma_mu)
   P(asyflexa_stats, staleness_hist) P(asyflexa_stats, kernel_launches) P(asyflexa_stats, checked)
+  P(asyflexa_stats, kernel_variant) P(asyflexa_stats, dual_gap)
   return 0;
 }
 """
@@ -85,6 +87,7 @@ def test_defaults_and_status_strings(L):
     assert o.block_w == 32 and o.mode == native.SYNC and o.gamma == 0.9
     assert o.refresh_every == 10 and o.max_sweeps == 1000
     assert o.f_star != o.f_star  # NaN
+    assert o.gamma_mu == 0.0 and o.variant == 0
     assert L.asyflexa_version() == 1
     assert L.asyflexa_status_string(-1) == b"ASYFLEXA_EINVAL"
     assert L.asyflexa_status_string(1) == b"ASYFLEXA_ENOTCONV"

@@ -535,3 +535,40 @@ def test_diminishing_step_solve_restarts_the_sequence():
         s.solve(x)
         xs.append(x.cpu().numpy())
     assert np.array_equal(xs[0], xs[1])
+
+
+# ------------------------------------------------------------- duality-gap certificate (LASSO)
+
+def test_dual_gap_certificate_matches_oracle():
+    import torch
+    d = random_lasso(900, 700, seed=24, lam=0.4, dist="gauss")
+    p = O.Problem.from_data(d)
+    rng = np.random.default_rng(3)
+    xv = rng.standard_normal(p.n) * (rng.random(p.n) < 0.1) * 0.1
+    s = make_solver(d)
+    xt = torch.from_numpy(xv).cuda()
+    s.refresh(xt)
+    st = s.check(xt)
+    P, gap = O.lasso_dual_gap(p, xv)
+    assert st["F"] == pytest.approx(P, rel=1e-12)
+    assert st["dual_gap"] == pytest.approx(gap / max(1.0, abs(P)), rel=1e-9)
+
+
+def test_liu_wright_solve_is_certified_without_an_optimum():
+    """The Gaussian LASSO set of Section 4.2 (no closed-form optimum): the async solve stops on
+    the duality-gap certificate <= 1e-6 and stationarity <= 1e-6; the oracle's Gauss-Seidel
+    optimum confirms the gap."""
+    import torch
+    from inputs import liu_wright_lasso
+    d = liu_wright_lasso(1500, 3000, 15, seed=25, store_dtype=np.float32)
+    p = O.Problem.from_data(d)
+    s = make_solver(d, block_w=32, mode="async", num_ctas=8, max_sweeps=3000, check_every=10, refresh_every=10,
+                    tol_stat=1e-6, tol_gap=1e-6)
+    x = xzeros(d, torch.float32)
+    st = s.solve(x)
+    assert st["status"] == 0, st
+    assert st["dual_gap"] <= 1e-6
+    _, F_or, _ = O.solve_gs(p, w=32, gamma=1.0, max_sweeps=2000, tol=1e-15)
+    F = O.objective(p, x.cpu().numpy().astype(np.float64))
+    assert (F - F_or) / F_or <= 1.1e-6
+    assert O.lasso_dual_gap(p, x.cpu().numpy().astype(np.float64))[1] / F <= 1.1e-6

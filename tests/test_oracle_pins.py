@@ -544,3 +544,31 @@ def test_gauss_seidel_with_step_sequence_equals_block_by_block_updates():
     for t in range(6):
         xb, rb = O.gauss_seidel_sweep(p, xb, rb, dw, steps[t], w=4, order=[t])
     assert np.array_equal(xa, xb)
+
+
+# ---------------------------------------------------------------- LASSO duality-gap certificate
+
+def test_lasso_dual_gap_bounds_the_gap_and_vanishes_at_the_optimum():
+    """Weak duality: P(x) - D(nu(x)) >= P(x) - F* >= 0 for any x, with F* from the exact
+    enumeration; at the exact minimiser the certificate is ~0 (strong duality)."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((14, 8))
+    b = rng.standard_normal(14)
+    lam = 0.6
+    xs = O.brute_force_lasso(A, b, lam)
+    assert len(xs) == 1
+    p = O.Problem(A=A, b=b, lam=lam)
+    Fstar = O.objective(p, xs[0])
+    P, gap = O.lasso_dual_gap(p, xs[0])
+    assert P == pytest.approx(Fstar, rel=1e-14) and abs(gap) <= 1e-10
+    for _ in range(50):
+        x = rng.standard_normal(8) * (rng.random(8) < 0.5)
+        P, gap = O.lasso_dual_gap(p, x)
+        assert gap >= P - Fstar - 1e-12 and P - Fstar >= -1e-12
+
+
+def test_liu_wright_lambda_rule():
+    from inputs import liu_wright_lasso
+    d = liu_wright_lasso(200, 400, 5, sigma=0.01, seed=1)
+    assert d["lam"] == pytest.approx(20 * np.sqrt(200 * np.log(400)) * 0.01, rel=1e-15)
+    assert np.count_nonzero(d["xbar"]) == 5
