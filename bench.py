@@ -702,8 +702,9 @@ def run_form_batched(args, ctx=None):
 
 def run_form_liu_wright(args, ctx=None):
     """NEXT row: the Gaussian LASSO set of Section 4.2 (m = 20000, n = 40000, s = 40, sigma =
-    0.01, lam = 20 sqrt(m log n) sigma), whose optimum is not known: async and sync solves stop
-    when the duality-gap certificate and the stationarity are both <= 1e-6."""
+    0.01, lam = 20 sqrt(m log n) sigma), whose optimum is not known: async and sync solves to
+    stationarity <= 1e-6, with the duality-gap certificate reported and the relative difference
+    of the two final objectives (the paper estimates F* by a long synchronous run)."""
     import torch
     from paper_1701_04900_gb300 import Solver
     from inputs import liu_wright_lasso_torch
@@ -714,10 +715,11 @@ def run_form_liu_wright(args, ctx=None):
     for mode, extra in (("async", {}), ("sync", {"tau_rel": tau_rel})):
         t, st = _time_solves(lambda: Solver(g["At"], g["b"], g["lam"], m=m, block_w=W_BLOCK, mode=mode, gamma=GAMMA,
                                             max_sweeps=3000, check_every=10, refresh_every=10, tol_stat=1e-6,
-                                            tol_gap=1e-6, **extra), n)
+                                            **extra), n)
         out[mode] = {"seconds": t, "sweeps": st["sweeps"], "dual_gap": st["dual_gap"], "stat_xhat": st["stat_xhat"],
                      "F": st["F"], "nnz": st["nnz"], "status": st["status"]}
     out["async_speedup_vs_sync"] = out["sync"]["seconds"] / out["async"]["seconds"]
+    out["rel_objective_difference_async_sync"] = abs(out["async"]["F"] - out["sync"]["F"]) / abs(out["sync"]["F"])
     del g
     torch.cuda.empty_cache()
     return out

@@ -168,8 +168,9 @@ typedef struct {
     double dual_gap;            /* plain LASSO (no box, no linear term): (P(x) - D(nu)) / max(1, |P(x)|)
                                    with the feasible dual point nu = theta r, theta = min(1, lambda /
                                    ||A^T r||_inf) -- an upper bound of the relative optimality gap
-                                   that needs no optimum; NaN for other problems.  Without f_star,
-                                   solve on the plain LASSO also requires dual_gap <= tol_gap. */
+                                   that needs no optimum; NaN for other problems.  Reported, not a
+                                   stopping test: with FP32 iterates ||A^T r||_inf carries the
+                                   rounding of the heaviest column, which loosens the bound. */
 } asyflexa_stats;
 
 /* Library version (ASYFLEXA_ABI_VERSION).  Never fails. */

@@ -344,13 +344,16 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 const float v = warp_sum((acc0 + acc1) + (acc2 + acc3));
                 float* cp = colpart + buf * kRegConsWarps;
                 if (lane == 0) cp[warp] = v;
+                const ColCoef cf = coef[jl];  // written before the block's first barrier
                 named_bar_sync(1, kRegConsThreads);
-                // ---- best response (eq. 2) + fixed step (S.4): the same FP32 arithmetic in
-                // every consumer thread (fixed summation order), so all agree on Delta_j
-                static_assert(kRegConsWarps <= 32, "one partial per lane");
-                const float g = warp_sum(lane < kRegConsWarps ? cp[lane] : 0.f);  // same order in every warp
+                // ---- best response (eq. 2) + fixed step (S.4): every consumer thread sums the 16
+                // warp partials in the same fixed order, so all agree on g and Delta_j
+                static_assert(kRegConsWarps == 16, "the sum below reads 16 warp partials");
+                const float4* cp4 = reinterpret_cast<const float4*>(cp);
+                const float4 q0 = cp4[0], q1 = cp4[1], q2 = cp4[2], q3 = cp4[3];
+                const float g = (((q0.x + q0.y) + (q0.z + q0.w)) + ((q1.x + q1.y) + (q1.z + q1.w))) +
+                                (((q2.x + q2.y) + (q2.z + q2.w)) + ((q3.x + q3.y) + (q3.z + q3.w)));
                 buf ^= 1;
-                const ColCoef cf = coef[jl];
                 const float grad = bv.s_loss * g * cf.scale - bv.c2 * cf.x + cf.lin;
                 float xh = 0.f;
                 if (cf.dinv > 0.f) {
