@@ -137,6 +137,12 @@ typedef struct {
                                    asyflexa_reset_counters for asyflexa_step).  Async: update k is the
                                    one that read the residual after k completed updates (exact for a
                                    single CTA); sync: block i of the s-th sweep is update s N + i. */
+    int32_t tau_adapt;          /* 1: solve adapts the proximal weight between checks (a rule in the
+                                   spirit of FLEXA's, which the paper does not restate): when a check
+                                   interval raised F, every d_j grows by tau_extra (doubled; the first
+                                   time 0.05 * mean d_j); after 5 intervals in a row that lowered F it
+                                   shrinks by half.  Restarts at 0 in every solve.  0 (default): off */
+    int32_t reserved3;
 } asyflexa_opts;
 
 /* Results and counters.  Optimality fields are FP64 and computed from an exact
@@ -171,6 +177,7 @@ typedef struct {
                                    that needs no optimum; NaN for other problems.  Reported, not a
                                    stopping test: with FP32 iterates ||A^T r||_inf carries the
                                    rounding of the heaviest column, which loosens the bound. */
+    double tau_extra;           /* solve with tau_adapt: the proximal weight added at the end */
 } asyflexa_stats;
 
 /* Library version (ASYFLEXA_ABI_VERSION).  Never fails. */

@@ -219,6 +219,15 @@ int fill_steps(asyflexa_s& h, int k) {
     return ASYFLEXA_OK;
 }
 
+// Move the adaptive proximal weight to t (every d_j changes by t - tau_extra).
+int set_tau_extra(asyflexa_s& h, double t) {
+    if (t == h.tau_extra) return ASYFLEXA_OK;
+    cudaError_t e = dispatch(h, [&](auto L) { return decltype(L)::shift_weights(h, t - h.tau_extra); });
+    if (e != cudaSuccess) return cuda_error(&h, e, "shift weights");
+    h.tau_extra = t;
+    return ASYFLEXA_OK;
+}
+
 // Restart the diminishing-step sequence (k = 0, gamma^0 = opts.gamma) and the update counter.
 int restart_steps(asyflexa_s& h) {
     h.sched_k = 0;
@@ -304,6 +313,7 @@ int validate_opts(const asyflexa_opts* o, std::string* why) {
     if (!(o->tol_gap >= 0.0) || !(o->tol_stat >= 0.0)) return *why = "tolerances must be >= 0", 1;
     if (!(o->switch_tol >= 0.0)) return *why = "switch_tol must be >= 0", 1;
     if (!(o->gamma_mu >= 0.0) || !std::isfinite(o->gamma_mu)) return *why = "gamma_mu must be finite and >= 0", 1;
+    if (o->tau_adapt != 0 && o->tau_adapt != 1) return *why = "tau_adapt must be 0 or 1", 1;
     if (o->gamma_mu > 0.0 && o->gamma_mu * o->gamma >= 1.0)
         return *why = "gamma_mu * gamma must be < 1 (the steps must stay positive)", 1;
     return 0;
@@ -353,6 +363,7 @@ void asyflexa_opts_default(asyflexa_opts* o) {
     o->seed = 0;
     o->switch_tol = 1e-7;
     o->gamma_mu = 0.0;
+    o->tau_adapt = 0;
 }
 
 const char* asyflexa_last_error(asyflexa_t h) { return h ? h->msg.c_str() : g_thread_msg.c_str(); }
@@ -516,6 +527,14 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
             return fail(ASYFLEXA_EINVAL);
         }
     }
+    if (O->tau_adapt) {
+        // the adaptive proximal weight starts from 5% of the mean surrogate weight
+        std::vector<double> dv(static_cast<size_t>(n));
+        CKC(cudaMemcpy(dv.data(), h->dw, n * sizeof(double), cudaMemcpyDeviceToHost), "read weights");
+        double sum = 0.0;
+        for (double v : dv) sum += v > 0.0 ? v : 0.0;
+        h->tau_unit = 0.05 * (sum > 0.0 ? sum / static_cast<double>(n) : 1.0);
+    }
     if (P->lo || P->hi) {
         std::vector<double> lo(n, -INFINITY), hi(n, INFINITY);
         if (f64) {
@@ -640,6 +659,10 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
     CK(h, cudaEventRecord(e0, h->stream), "event record");
     int rc = ASYFLEXA_OK;
     if (h->opts.gamma_mu > 0.0) rc = restart_steps(*h);  // each solve runs the step sequence from gamma^0
+    if (!rc && h->opts.tau_adapt) {
+        rc = set_tau_extra(*h, 0.0);  // and the adaptive proximal weight from 0
+        h->tau_down = 0;
+    }
     if (!rc && (!h->r_valid || h->r_x != x)) rc = do_refresh(*h, x);
     const double fs = h->opts.f_star;
     const bool known = std::isfinite(fs);
@@ -661,6 +684,19 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
         if (rc) break;
         const double gap = known ? (F - fs) / std::fabs(fs) : NAN;
         const bool stalled = h->master && std::isfinite(F_prev) && (F_prev - F) <= h->opts.switch_tol * std::fabs(F);
+        if (h->opts.tau_adapt && std::isfinite(F_prev)) {
+            if (F > F_prev + 1e-12 * std::fabs(F_prev)) {
+                // the interval raised F: stronger proximal term
+                rc = set_tau_extra(*h, h->tau_extra > 0.0 ? 2.0 * h->tau_extra : h->tau_unit);
+                h->tau_down = 0;
+            } else if (++h->tau_down >= 5 && h->tau_extra > 0.0) {
+                // five intervals in a row lowered F: relax it again
+                const double t = 0.5 * h->tau_extra;
+                rc = set_tau_extra(*h, t < 0.01 * h->tau_unit ? 0.0 : t);
+                h->tau_down = 0;
+            }
+            if (rc) break;
+        }
         F_prev = F;
         if (known && !(gap <= h->opts.tol_gap) && !stalled) continue;
         Measures M{};
@@ -723,6 +759,7 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
     }
     st.kernel_launches = h->launches + (h->master ? h->master->launches : 0);
     st.kernel_variant = async_variant(*h);
+    st.tau_extra = h->tau_extra;
     if (!rc) rc = status;
     st.status = rc;
     if (out) *out = st;

@@ -301,6 +301,15 @@ __global__ void reduce_partials_kernel(double* r, const TP* partial, int nseg, i
     }
 }
 
+// ----------------------------------------------------------------------------- proximal weight
+
+// d_j += delta for every coordinate (the proximal weight tau of all surrogates changes by delta).
+template <typename T>
+__global__ void __launch_bounds__(kAuxThreads) shift_weights_kernel(T* dw, int64_t n, T delta) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * kAuxThreads;
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * kAuxThreads + threadIdx.x; j < n; j += stride) dw[j] += delta;
+}
+
 // ----------------------------------------------------------------------------- norms
 
 constexpr int kNormsFields = 7;

@@ -60,6 +60,10 @@ struct asyflexa_s {
     // the device table of the steps of one launch
     long long sched_k = 0;
     double sched_gamma = 0.0;
+    // adaptive proximal weight (opts.tau_adapt): tau added on top of opts.tau, its starting
+    // increment, and the number of consecutive check intervals that lowered F
+    double tau_extra = 0.0, tau_unit = 0.0;
+    int tau_down = 0;
     double* gtab = nullptr;
     size_t gtab_cap = 0;
     std::vector<double> gtab_host;
@@ -118,6 +122,7 @@ struct Launcher {
     static cudaError_t refresh(asyflexa_s& h, const void* x);
     static cudaError_t norms(asyflexa_s& h, const void* x);
     static cudaError_t check(asyflexa_s& h, const void* x);
+    static cudaError_t shift_weights(asyflexa_s& h, double delta);
     static int set_smem_attrs(asyflexa_s& h);
     static int choose_reg(asyflexa_s& h);
 };

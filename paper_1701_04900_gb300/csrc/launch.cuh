@@ -222,6 +222,13 @@ cudaError_t Launcher<TA>::check(asyflexa_s& h, const void* xv) {
     return cudaGetLastError();
 }
 
+template <typename TA>
+cudaError_t Launcher<TA>::shift_weights(asyflexa_s& h, double delta) {
+    shift_weights_kernel<double><<<h.sm_count * 2, kAuxThreads, 0, h.stream>>>(h.dw, h.prob.n, delta);
+    ++h.launches;
+    return cudaGetLastError();
+}
+
 }  // namespace asyflexa
 
 #define ASYFLEXA_INSTANTIATE(TA) template struct asyflexa::Launcher<TA>;

@@ -45,6 +45,7 @@ class Opts(C.Structure):
         ("tol_gap", C.c_double), ("tol_stat", C.c_double), ("f_star", C.c_double),
         ("seed", C.c_uint64), ("profile", C.c_int32), ("variant", C.c_int32),
         ("switch_tol", C.c_double), ("gamma_mu", C.c_double),
+        ("tau_adapt", C.c_int32), ("reserved3", C.c_int32),
     ]
 
 
@@ -59,6 +60,7 @@ class Stats(C.Structure):
         ("status", C.c_int32), ("checked", C.c_int32),
         ("polish_sweeps", C.c_int64), ("polish_seconds", C.c_double),
         ("block_w", C.c_int32), ("kernel_variant", C.c_int32), ("dual_gap", C.c_double),
+        ("tau_extra", C.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -177,7 +179,7 @@ class Solver:
                  block_w=32, mode="sync", gamma=0.9, tau=0.0, tau_rel=0.0, refresh_every=10,
                  check_every=10, max_sweeps=1000, num_ctas=0, tol_gap=1e-6, tol_stat=1e-6,
                  f_star=math.nan, profile=False, variant=0, A_master=None, switch_tol=1e-7, lin=None,
-                 gamma_mu=0.0, stream=None):
+                 gamma_mu=0.0, tau_adapt=False, stream=None):
         import torch
         L = lib()
         if At.dim() != 2 or not At.is_contiguous() or not At.is_cuda:
@@ -213,6 +215,7 @@ class Solver:
         o.variant = int(variant)
         o.switch_tol = float(switch_tol)
         o.gamma_mu = float(gamma_mu)
+        o.tau_adapt = 1 if tau_adapt else 0
         self.problem, self.opts = p, o
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream

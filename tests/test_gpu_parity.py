@@ -573,3 +573,40 @@ def test_liu_wright_solve_reaches_the_oracle_optimum():
     assert (F - F_or) / F_or <= 1e-6
     P, gap = O.lasso_dual_gap(p, xr)
     assert st["dual_gap"] == pytest.approx(gap / max(1.0, abs(P)), rel=1e-6, abs=1e-12)
+
+
+# ---------------------------------------------------------------- adaptive proximal weight
+
+def test_adaptive_tau_recovers_an_unstable_async_run():
+    """Every block of a small problem in flight at once with no proximal weight is the setting
+    that can diverge (test above); with tau_adapt the solve raises tau whenever a check
+    interval raised F, and reaches the planted optimum."""
+    import torch
+    d = nesterov_lasso(2000, 10000, 100, lam=1.0, seed=11, store_dtype=np.float64)
+    p = O.Problem.from_data(d)
+    f_ref = O.objective(p, d["x_star"])
+    s = make_solver(d, block_w=32, mode="async", gamma=0.9, max_sweeps=3000, check_every=1, refresh_every=1,
+                    tau_adapt=True, f_star=f_ref, tol_stat=1e-6)
+    x = xzeros(d, torch.float64)
+    st = s.solve(x)
+    assert st["status"] == 0, st
+    assert st["rel_gap"] <= 1e-6
+    assert O.objective(p, x.cpu().numpy()) == pytest.approx(st["F"], rel=1e-12)
+
+
+def test_adaptive_tau_leaves_a_descent_run_unchanged():
+    """One CTA is cyclic Gauss-Seidel, whose LASSO objective never rises: tau stays 0 and the
+    iterates are the oracle's."""
+    import torch
+    d = random_lasso(600, 300, seed=26, lam=0.3, store_dtype=np.float64)
+    p = O.Problem.from_data(d)
+    dw = O.surrogate_weights(p)
+    x_ref, r_ref = np.zeros(p.n), O.residual(p, np.zeros(p.n))
+    for _ in range(30):
+        x_ref, r_ref = O.gauss_seidel_sweep(p, x_ref, r_ref, dw, 0.9, w=16)
+    s = make_solver(d, block_w=16, mode="async", gamma=0.9, num_ctas=1, max_sweeps=30, check_every=1,
+                    tau_adapt=True, tol_stat=0.0)
+    x = xzeros(d, torch.float64)
+    st = s.solve(x)
+    assert st["tau_extra"] == 0.0
+    assert rel_inf(x.cpu().numpy(), x_ref) < TOL64
