@@ -689,9 +689,22 @@ def run_form_batched(args, ctx=None):
         s.close()
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
+    # sequential cold starts (every lambda from x = 0, as the batched lanes start)
+    t0 = time.perf_counter()
+    cold_sweeps = 0
+    for l in lams:
+        x = torch.zeros(n, dtype=torch.float32, device="cuda")
+        s = Solver(At, b, l, m=m, block_w=32, mode="async", refresh_every=10, check_every=10, max_sweeps=3000,
+                   tol_stat=1e-6)
+        cold_sweeps += s.solve(x)["sweeps"]
+        s.close()
+    torch.cuda.synchronize()
+    t_cold = time.perf_counter() - t0
     path = {"lambdas": 64, "lambda_max": lam_max, "seconds_batched": t_path, "status": tot["status"],
             "sweeps_batched": tot["sweeps"], "seconds_sequential_warm": t_seq, "sweeps_sequential": seq_sweeps,
-            "speedup_vs_sequential": t_seq / t_path, "last_lane_stat_xhat": per[-1]["stat_xhat"],
+            "speedup_vs_sequential": t_seq / t_path, "seconds_sequential_cold": t_cold,
+            "sweeps_sequential_cold": cold_sweeps, "speedup_vs_sequential_cold": t_cold / t_path,
+            "last_lane_stat_xhat": per[-1]["stat_xhat"],
             "last_lane_rel_gap_vs_planted": None, "sequential_last_stat_xhat": seq_last["stat_xhat"]}
     sup = g["support"]
     r = At[sup, :m].double().T @ g["x_star"][sup] - b.double()
