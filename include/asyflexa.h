@@ -323,6 +323,33 @@ int asyflexa_batch_solve(asyflexa_batch_t hb, void* const* xs, const double* f_s
 int asyflexa_batch_destroy(asyflexa_batch_t hb);
 
 /* Last error message of the handle (or of the calling thread for NULL).  Never NULL. */
+/* ---------------------------------------------------------------- multi-lane form
+ * k LASSO problems ("lanes") that share A and differ in b and lambda -- a lambda path or
+ * several data vectors -- solved together: every block update of Algorithm 1 is done for all
+ * lanes at once, its two products G = A_i^T R~ (w x k) and R += A_i Delta_i (m x k) on the
+ * tensor cores (TF32 with a hi/lo split, FP32-grade products, FP64 residuals), so each byte of
+ * A serves k lanes.  Blocks of w = 32 columns; async mode; at most max(1, m / 128) CTAs by
+ * default (opts.num_ctas overrides), so that each lane has few columns in flight.
+ *
+ * prob:    FP32 A (m x n, lda) and FP32 vectors; LASSO loss; no box, linear term or master
+ *          copy (EUNSUPPORTED otherwise).  prob->b and prob->lambda are ignored.
+ * k:       1..64 lanes.  B: device FP32, lane l's b at B + l * ldb (ldb >= m).
+ * lambdas: host, k weights.  opts: gamma, tau, tau_rel, refresh_every (exact residual
+ *          recomputation), check_every, max_sweeps, tol_gap, tol_stat, switch_tol (stall test
+ *          for lanes without f_star), num_ctas.
+ * Borrowed like asyflexa_create's pointers; the handle owns its residuals and iterates. */
+typedef struct asyflexa_multi_s* asyflexa_multi_t;
+int asyflexa_multi_create(asyflexa_multi_t* h, const asyflexa_problem* prob, int32_t k, const void* B, int64_t ldb,
+                          const double* lambdas, const asyflexa_opts* opts, void* cuda_stream);
+/* Solve all lanes from the iterates in X (device FP32, lane l's x at X + l * ldx, ldx >= n),
+ * written back in place.  A lane is done when (F - f_star[l]) / |f_star[l]| <= tol_gap (or,
+ * with f_star NULL or NaN, when a check interval lowers F by <= switch_tol |F|) and its
+ * ||xhat(x) - x||_inf / max(1, ||x||_inf) <= tol_stat.  per (k entries) and total may be NULL.
+ * Returns OK when every lane is done, ENOTCONV at max_sweeps, or an error. */
+int asyflexa_multi_solve(asyflexa_multi_t h, void* X, int64_t ldx, const double* f_star, asyflexa_stats* per,
+                         asyflexa_stats* total);
+int asyflexa_multi_destroy(asyflexa_multi_t h);
+
 const char* asyflexa_last_error(asyflexa_t h);
 
 #ifdef __cplusplus

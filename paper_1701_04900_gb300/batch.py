@@ -73,3 +73,69 @@ class BatchSolver:
             self.close()
         except Exception:
             pass
+
+
+class MultiLaneSolver:
+    """k LASSO lanes sharing one FP32 matrix (a lambda path or several data vectors), every
+    block update done for all lanes at once on the tensor cores (asyflexa_multi_*).
+
+    ``At`` (n, lda) CUDA float32; ``B`` (k, m) CUDA float32 (row l = lane l's b); ``lambdas``
+    k floats.  ``solve(X)`` takes X (k, n) CUDA float32 (row l = lane l's x), in place.
+    """
+
+    def __init__(self, At, B, lambdas, m, *, gamma=0.9, tau=0.0, tau_rel=0.0, refresh_every=10, check_every=10,
+                 max_sweeps=1000, num_ctas=0, tol_gap=1e-6, tol_stat=1e-6, switch_tol=1e-9, stream=None):
+        import torch
+        L = lib()
+        if At.dtype != torch.float32 or not At.is_contiguous() or not At.is_cuda:
+            raise ValueError("At must be a contiguous float32 CUDA tensor (n, lda)")
+        if B.dtype != torch.float32 or not B.is_contiguous() or B.dim() != 2:
+            raise ValueError("B must be a contiguous float32 CUDA tensor (k, ldb)")
+        n, lda = At.shape
+        k = B.shape[0]
+        p = Problem()
+        p.m, p.n, p.lda = int(m), n, lda
+        p.a_dtype = p.x_dtype = native.F32
+        p.A, p.b = At.data_ptr(), B.data_ptr()
+        p.loss = native.LOSS_LASSO
+        o = default_opts()
+        o.mode, o.gamma, o.tau, o.tau_rel = native.ASYNC, float(gamma), float(tau), float(tau_rel)
+        o.refresh_every, o.check_every, o.max_sweeps, o.num_ctas = int(refresh_every), int(check_every), \
+            int(max_sweeps), int(num_ctas)
+        o.tol_gap, o.tol_stat, o.switch_tol = float(tol_gap), float(tol_stat), float(switch_tol)
+        lam = (C.c_double * k)(*[float(v) for v in lambdas])
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        h = C.c_void_p()
+        rc = L.asyflexa_multi_create(C.byref(h), C.byref(p), k, B.data_ptr(), B.shape[1], lam, C.byref(o),
+                                     C.c_void_p(stream))
+        if rc != native.OK:
+            raise AsyflexaError(rc, L.asyflexa_last_error(None).decode())
+        self.h, self.k, self.n = h, k, n
+        self._keep = (At, B)
+
+    def solve(self, X, f_star=None):
+        """Solve every lane from X (k, ldx) in place; returns (per-lane stats, total stats)."""
+        L = lib()
+        if X.shape[0] != self.k or X.shape[1] < self.n or not X.is_contiguous():
+            raise ValueError("X must be a contiguous (k, >= n) float32 CUDA tensor")
+        fs = None
+        if f_star is not None:
+            fs = (C.c_double * self.k)(*[math.nan if v is None else float(v) for v in f_star])
+        per = (Stats * self.k)()
+        tot = Stats()
+        rc = L.asyflexa_multi_solve(self.h, X.data_ptr(), X.shape[1], fs, per, C.byref(tot))
+        if rc < 0:
+            raise AsyflexaError(rc, L.asyflexa_last_error(None).decode())
+        return [s.as_dict() for s in per], tot.as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().asyflexa_multi_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

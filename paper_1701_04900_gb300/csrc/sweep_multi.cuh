@@ -1,0 +1,355 @@
+// Multi-right-hand-side asynchronous sweep: k problems ("lanes") that share the matrix A and
+// differ in b and lambda (a lambda path, or several data vectors), LASSO loss, FP32 A.
+//
+// The block update of Algorithm 1 for every lane at once: for block i the lanes' gradients are
+// the dense product G = A_i^T R~ (w x k, R~ the lanes' stale residuals, S.2), the best
+// responses and fixed steps are elementwise (eq. 2, S.4), and the scatter is the dense product
+// R += A_i Delta_i (m x k).  With k lanes every byte of A serves k products, so both products
+// run on the tensor cores (mma.sync m16n8k8, TF32).  TF32 keeps 10 bits of mantissa, so every
+// operand is split x = hi + lo (both TF32) and a*b is formed as hi*hi + hi*lo + lo*hi with FP32
+// accumulation: the error of the dropped lo*lo term is about 2^-22 relative, FP32-grade.
+//
+// Layout: A column-major (column j = A + j*lda), R FP64 row-major m x kp (row i holds the kp
+// lanes' residuals), X FP32 row-major n x kp, kp = lanes padded to a multiple of 8 (padding
+// lanes have lambda = +inf, stay at 0 and get zero steps).  Each CTA owns the blocks b = cta,
+// cta + grid, ... (Assumption D4) and streams its block in row tiles of kMT rows twice:
+// gradient pass (row tiles of A and R~ through shared memory, G accumulated in registers) and,
+// after the elementwise step, the scatter pass (the same A tiles, now mostly L2 hits, times
+// Delta, added to R with FP64 atomics).
+#pragma once
+
+#include "ptx.cuh"
+#include "sweep.cuh"
+#include "types.cuh"
+
+namespace asyflexa {
+
+constexpr int kMW = 32;               // block width (columns)
+constexpr int kMT = 64;               // rows per tile
+constexpr int kMThreads = 256;        // 8 warps
+constexpr int kMKMax = 64;            // lanes (padded) per launch
+constexpr int kMAS = kMT + 4;         // A tile stride (floats): conflict-free fragment loads
+constexpr int kMRS = kMKMax + 8;      // R tile / Delta stride (floats)
+
+struct MultiParams {
+    const float* A;
+    int64_t lda, m, n;
+    double* R;            // m x kp (row-major), FP64
+    float* X;             // n x kp (row-major)
+    const double* dw;     // n surrogate weights (shared by the lanes)
+    const double* lam;    // kp (padding lanes: +inf)
+    double gamma;
+    int kp, nblocks, sweeps;
+    int mode;             // 0: sweep; 1: refresh (R += A X, no step); 2: gradient only (G out)
+    float* G;             // mode 2: n x kp gradients A^T R
+    unsigned long long* counters;  // [0] update counter, [1] block updates
+    unsigned long long* hist;      // staleness histogram
+};
+
+struct MultiSmem {
+    float a_hi[kMW * kMAS], a_lo[kMW * kMAS];   // A tile, column-major (j * kMAS + t)
+    float r_hi[kMT * kMRS], r_lo[kMT * kMRS];   // R~ tile, row-major (t * kMRS + lane)
+    float g[kMW * kMRS];                        // G (j * kMRS + lane)
+    float d_hi[kMW * kMRS], d_lo[kMW * kMRS];   // Delta (j * kMRS + lane)
+};
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+    const uint32_t h = to_tf32(x);
+    hi = __uint_as_float(h);
+    lo = __uint_as_float(to_tf32(x - hi));
+}
+
+// D += A (16x8, row) * B (8x8, col), TF32 in, FP32 accumulate.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const float (&a)[4], const float (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(__float_as_uint(a[0])), "r"(__float_as_uint(a[1])), "r"(__float_as_uint(a[2])),
+          "r"(__float_as_uint(a[3])), "r"(__float_as_uint(b[0])), "r"(__float_as_uint(b[1])));
+}
+
+// Load the A tile rows [row0, row0 + kMT) of columns c0 .. c0 + wb - 1 (zeros elsewhere),
+// split into TF32 hi / lo.  Thread t loads 8 consecutive rows of column t / 8.
+__device__ __forceinline__ void load_a_tile(const MultiParams& p, MultiSmem& s, int64_t c0, int wb, int64_t row0) {
+    const int tid = threadIdx.x;
+    const int j = tid >> 3;
+    const int t0 = (tid & 7) * 8;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const int64_t row = row0 + t0 + e;
+        const float v = (j < wb && row < p.m) ? __ldg(p.A + (c0 + j) * p.lda + row) : 0.f;
+        float hi, lo;
+        split_tf32(v, hi, lo);
+        s.a_hi[j * kMAS + t0 + e] = hi;
+        s.a_lo[j * kMAS + t0 + e] = lo;
+    }
+}
+
+template <int KP>
+__global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParams p) {
+    static_assert(KP % 8 == 0 && KP <= kMKMax, "lanes padded to a multiple of 8");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MultiSmem& s = *reinterpret_cast<MultiSmem*>(smem_raw);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int grp = lane >> 2;  // groupID of the mma fragments
+    const int tig = lane & 3;   // thread in group
+    constexpr int kNT = KP / 8;                 // n tiles (lanes)
+    constexpr int kP1 = 2 * kNT;                // gradient pass: (m tile, n tile) pairs over j
+    constexpr int kP1W = (kP1 + 7) / 8;         // pairs per warp
+    constexpr int kP2 = (kMT / 16) * kNT;       // scatter pass: pairs over rows
+    constexpr int kP2W = (kP2 + 7) / 8;
+    __shared__ int s_any;
+    __shared__ unsigned long long s_uread;
+
+    for (int sw = 0; sw < p.sweeps; ++sw) {
+        for (int b = blockIdx.x; b < p.nblocks; b += gridDim.x) {
+            const int64_t c0 = static_cast<int64_t>(b) * kMW;
+            const int wb = static_cast<int>(min64(kMW, p.n - c0));
+            if (tid == 0) s_uread = ld_relaxed_u64(&p.counters[0]);
+            // ---- gradient pass: G = A_i^T R~ (S.2: R~ is read tile by tile, a stale read)
+            // per row tile an FP32 accumulator (tensor cores), summed over the tiles in FP64, so the
+            // FP32 rounding of G grows with the tile (kMT rows), not with m
+            double acc[kP1W][4];
+#pragma unroll
+            for (int q = 0; q < kP1W; ++q)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[q][e] = 0.0;
+            if (p.mode != 1) {
+                for (int64_t row0 = 0; row0 < p.m; row0 += kMT) {
+                    __syncthreads();  // previous tile consumed
+                    load_a_tile(p, s, c0, wb, row0);
+                    for (int i = tid; i < kMT * KP; i += kMThreads) {
+                        const int t = i / KP, l = i % KP;
+                        const int64_t row = row0 + t;
+                        const float v = row < p.m ? static_cast<float>(__ldcg(p.R + row * KP + l)) : 0.f;
+                        float hi, lo;
+                        split_tf32(v, hi, lo);
+                        s.r_hi[t * kMRS + l] = hi;
+                        s.r_lo[t * kMRS + l] = lo;
+                    }
+                    __syncthreads();
+#pragma unroll
+                    for (int q = 0; q < kP1W; ++q) {
+                        const int pr = warp + 8 * q;
+                        if (pr < kP1) {
+                            const int mt = pr / kNT, nt = pr % kNT;
+                            const int j0 = mt * 16 + grp;
+                            float tacc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 2
+                            for (int k0 = 0; k0 < kMT; k0 += 8) {
+                                float ah[4], al[4], bh[2], bl[2];
+                                ah[0] = s.a_hi[j0 * kMAS + k0 + tig];
+                                ah[1] = s.a_hi[(j0 + 8) * kMAS + k0 + tig];
+                                ah[2] = s.a_hi[j0 * kMAS + k0 + tig + 4];
+                                ah[3] = s.a_hi[(j0 + 8) * kMAS + k0 + tig + 4];
+                                al[0] = s.a_lo[j0 * kMAS + k0 + tig];
+                                al[1] = s.a_lo[(j0 + 8) * kMAS + k0 + tig];
+                                al[2] = s.a_lo[j0 * kMAS + k0 + tig + 4];
+                                al[3] = s.a_lo[(j0 + 8) * kMAS + k0 + tig + 4];
+                                bh[0] = s.r_hi[(k0 + tig) * kMRS + nt * 8 + grp];
+                                bh[1] = s.r_hi[(k0 + tig + 4) * kMRS + nt * 8 + grp];
+                                bl[0] = s.r_lo[(k0 + tig) * kMRS + nt * 8 + grp];
+                                bl[1] = s.r_lo[(k0 + tig + 4) * kMRS + nt * 8 + grp];
+                                mma_tf32(tacc, al, bh);
+                                mma_tf32(tacc, ah, bl);
+                                mma_tf32(tacc, ah, bh);
+                            }
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) acc[q][e] += static_cast<double>(tacc[e]);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            // G to shared memory (fragment rows = columns j, fragment columns = lanes)
+#pragma unroll
+            for (int q = 0; q < kP1W; ++q) {
+                const int pr = warp + 8 * q;
+                if (pr < kP1) {
+                    const int mt = pr / kNT, nt = pr % kNT;
+                    const int j0 = mt * 16 + grp, l0 = nt * 8 + 2 * tig;
+                    s.g[j0 * kMRS + l0] = static_cast<float>(acc[q][0]);
+                    s.g[j0 * kMRS + l0 + 1] = static_cast<float>(acc[q][1]);
+                    s.g[(j0 + 8) * kMRS + l0] = static_cast<float>(acc[q][2]);
+                    s.g[(j0 + 8) * kMRS + l0 + 1] = static_cast<float>(acc[q][3]);
+                }
+            }
+            if (tid == 0) s_any = 0;
+            __syncthreads();
+            // ---- elementwise: best response (eq. 2) + fixed step (S.4) per (column, lane); in
+            // refresh mode Delta = x (R += A X), in gradient mode G is written out
+            int any = 0;
+            for (int i = tid; i < kMW * KP; i += kMThreads) {
+                const int j = i / KP, l = i % KP;
+                float dlt = 0.f;
+                if (j < wb) {
+                    const int64_t jj = c0 + j;
+                    if (p.mode == 1) {
+                        dlt = p.X[jj * KP + l];
+                    } else if (p.mode == 2) {
+                        p.G[jj * KP + l] = s.g[j * kMRS + l];
+                    } else {
+                        const double d = p.dw[jj];
+                        const float x = p.X[jj * KP + l];
+                        float xh = 0.f;
+                        if (d > 0.0) {
+                            const float dinv = static_cast<float>(1.0 / d);
+                            const float thr = static_cast<float>(p.lam[l] / d);  // +inf for padding lanes
+                            const float v = fmaf(-s.g[j * kMRS + l], dinv, x);
+                            const float av = fabsf(v) - thr;
+                            xh = av > 0.f ? copysignf(av, v) : 0.f;
+                        }
+                        const float xn = fmaf(static_cast<float>(p.gamma), xh - x, x);
+                        dlt = xn - x;
+                        if (dlt != 0.f) p.X[jj * KP + l] = xn;
+                    }
+                }
+                float hi, lo;
+                split_tf32(dlt, hi, lo);
+                s.d_hi[j * kMRS + l] = hi;
+                s.d_lo[j * kMRS + l] = lo;
+                any |= dlt != 0.f;
+            }
+            if (any) s_any = 1;
+            __syncthreads();
+            // ---- scatter pass: R += A_i Delta (FP64 atomics; rows >= m skipped)
+            if (s_any && p.mode != 2) {
+                for (int64_t row0 = 0; row0 < p.m; row0 += kMT) {
+                    load_a_tile(p, s, c0, wb, row0);
+                    __syncthreads();
+#pragma unroll
+                    for (int q = 0; q < kP2W; ++q) {
+                        const int pr = warp + 8 * q;
+                        if (pr < kP2) {
+                            const int mt = pr / kNT, nt = pr % kNT;
+                            const int t0 = mt * 16 + grp;
+                            float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                            for (int k0 = 0; k0 < kMW; k0 += 8) {
+                                float ah[4], al[4], bh[2], bl[2];
+                                // A operand (rows t, columns j) = A tile transposed
+                                ah[0] = s.a_hi[(k0 + tig) * kMAS + t0];
+                                ah[1] = s.a_hi[(k0 + tig) * kMAS + t0 + 8];
+                                ah[2] = s.a_hi[(k0 + tig + 4) * kMAS + t0];
+                                ah[3] = s.a_hi[(k0 + tig + 4) * kMAS + t0 + 8];
+                                al[0] = s.a_lo[(k0 + tig) * kMAS + t0];
+                                al[1] = s.a_lo[(k0 + tig) * kMAS + t0 + 8];
+                                al[2] = s.a_lo[(k0 + tig + 4) * kMAS + t0];
+                                al[3] = s.a_lo[(k0 + tig + 4) * kMAS + t0 + 8];
+                                bh[0] = s.d_hi[(k0 + tig) * kMRS + nt * 8 + grp];
+                                bh[1] = s.d_hi[(k0 + tig + 4) * kMRS + nt * 8 + grp];
+                                bl[0] = s.d_lo[(k0 + tig) * kMRS + nt * 8 + grp];
+                                bl[1] = s.d_lo[(k0 + tig + 4) * kMRS + nt * 8 + grp];
+                                mma_tf32(c, al, bh);
+                                mma_tf32(c, ah, bl);
+                                mma_tf32(c, ah, bh);
+                            }
+                            const int l0 = nt * 8 + 2 * tig;
+                            const int64_t r0 = row0 + t0, r1 = row0 + t0 + 8;
+                            if (r0 < p.m) {
+                                if (c[0] != 0.f) red_add_f64(p.R + r0 * KP + l0, static_cast<double>(c[0]));
+                                if (c[1] != 0.f) red_add_f64(p.R + r0 * KP + l0 + 1, static_cast<double>(c[1]));
+                            }
+                            if (r1 < p.m) {
+                                if (c[2] != 0.f) red_add_f64(p.R + r1 * KP + l0, static_cast<double>(c[2]));
+                                if (c[3] != 0.f) red_add_f64(p.R + r1 * KP + l0 + 1, static_cast<double>(c[3]));
+                            }
+                        }
+                    }
+                    __syncthreads();  // tile consumed before the next load
+                }
+                // a single CTA runs its blocks in order (cyclic Gauss-Seidel per lane): its next
+                // read of R must see this scatter
+                if (gridDim.x == 1) __threadfence();
+            }
+            __syncthreads();
+            if (tid == 0 && p.mode == 0) {
+                const unsigned long long u1 = atomicAdd(&p.counters[0], 1ull);
+                const unsigned long long dly = u1 - s_uread;
+                int bucket = 63 - __clzll(static_cast<long long>(dly + 1ull));
+                bucket = bucket > 31 ? 31 : bucket;
+                atomicAdd(&p.hist[bucket], 1ull);
+                atomicAdd(&p.counters[1], 1ull);
+            }
+        }
+    }
+}
+
+// Per-lane objective pieces: out[l] += sum_i R[i][l]^2 (first KP entries), out[KP + l] +=
+// sum_j |X[j][l]| and out[2 KP + l] += nnz of lane l, FP64 atomics.  The grid stride is a
+// multiple of KP (256 threads, KP in {8, 16, 32, 64}), so each thread stays on one lane.
+template <int KP>
+__global__ void __launch_bounds__(256) multi_norms_kernel(const double* R, int64_t m, const float* X, int64_t n,
+                                                          double* out) {
+    static_assert(256 % KP == 0, "one lane per thread");
+    __shared__ double sh[3 * KP];
+    for (int l = threadIdx.x; l < 3 * KP; l += blockDim.x) sh[l] = 0.0;
+    __syncthreads();
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t t0 = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int l = threadIdx.x % KP;
+    double rr = 0.0, ax = 0.0, nz = 0.0;
+    for (int64_t e = t0; e < m * KP; e += stride) rr = fma(R[e], R[e], rr);
+    for (int64_t e = t0; e < n * KP; e += stride) {
+        const double v = static_cast<double>(X[e]);
+        ax += fabs(v);
+        nz += v != 0.0 ? 1.0 : 0.0;
+    }
+    atomicAdd(&sh[l], rr);
+    atomicAdd(&sh[KP + l], ax);
+    atomicAdd(&sh[2 * KP + l], nz);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 3 * KP; i += blockDim.x) atomicAdd(&out[i], sh[i]);
+}
+
+// Layout changes between the caller's per-lane vectors (lane l at src + l * lds, length len)
+// and the row-major len x KP array; lanes >= k are zero.  dir 0: lanes -> rows; 1: back.
+template <typename TS, typename TD>
+__global__ void __launch_bounds__(256) multi_transpose_kernel(const TS* src, int64_t lds, TD* dst, int64_t ldd,
+                                                              int64_t len, int k, int kp, int dir, double scale) {
+    const int64_t total = len * kp;
+    for (int64_t e = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t i = e / kp;
+        const int l = static_cast<int>(e % kp);
+        if (dir == 0) {
+            dst[e] = l < k ? static_cast<TD>(scale * static_cast<double>(src[l * lds + i])) : TD(0);
+        } else if (l < k) {
+            dst[l * ldd + i] = static_cast<TD>(src[e]);
+        }
+    }
+}
+
+// Per-lane stationarity: out[l] = max_j |xhat_j - x_j| (FP64 bits, atomic max) and
+// out[kp + l] = max_j |x_j|, from the gradients G = A^T R (gradient pass, mode 2).
+template <int KP>
+__global__ void __launch_bounds__(256) multi_stat_kernel(const float* G, const float* X, const double* dw,
+                                                         const double* lam, int64_t n, unsigned long long* out) {
+    const int64_t total = n * KP;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t j = i / KP;
+        const int l = static_cast<int>(i % KP);
+        const double x = X[i], d = dw[j], g = G[i];
+        double xh = 0.0;
+        if (d > 0.0) {
+            const double v = x - g / d;
+            const double av = fabs(v) - lam[l] / d;
+            xh = av > 0.0 ? copysign(av, v) : 0.0;
+        }
+        const double dx = fabs(xh - x), ax = fabs(x);
+        if (dx > 0.0) atomicMax(&out[l], static_cast<unsigned long long>(__double_as_longlong(dx)));
+        if (ax > 0.0) atomicMax(&out[KP + l], static_cast<unsigned long long>(__double_as_longlong(ax)));
+    }
+}
+
+}  // namespace asyflexa

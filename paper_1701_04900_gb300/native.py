@@ -76,6 +76,7 @@ EXPORTS = [
     "asyflexa_read_counters", "asyflexa_reset_counters", "asyflexa_get_residual", "asyflexa_get_weights",
     "asyflexa_last_error", "asyflexa_residual_noalloc", "asyflexa_quantize", "asyflexa_gather_columns",
     "asyflexa_batch_create", "asyflexa_batch_solve", "asyflexa_batch_destroy",
+    "asyflexa_multi_create", "asyflexa_multi_solve", "asyflexa_multi_destroy",
 ]
 BATCH_SHARED_A = 1
 
@@ -128,6 +129,12 @@ def lib(path: str | None = None):
     L.asyflexa_batch_solve.argtypes = [vp, C.POINTER(vp), vp, C.POINTER(Stats), C.POINTER(Stats)]
     L.asyflexa_batch_destroy.restype = C.c_int
     L.asyflexa_batch_destroy.argtypes = [vp]
+    L.asyflexa_multi_create.restype = C.c_int
+    L.asyflexa_multi_create.argtypes = [C.POINTER(vp), C.POINTER(Problem), i32, vp, C.c_int64, vp, C.POINTER(Opts), vp]
+    L.asyflexa_multi_solve.restype = C.c_int
+    L.asyflexa_multi_solve.argtypes = [vp, vp, C.c_int64, vp, C.POINTER(Stats), C.POINTER(Stats)]
+    L.asyflexa_multi_destroy.restype = C.c_int
+    L.asyflexa_multi_destroy.argtypes = [vp]
     L.asyflexa_gather_columns.restype = C.c_int
     L.asyflexa_gather_columns.argtypes = [vp, C.c_int64, i32, C.c_int64, vp, C.c_int64, vp, C.c_int64, vp]
     del dbl
