@@ -75,20 +75,51 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const float (&a)[4], con
           "r"(__float_as_uint(a[3])), "r"(__float_as_uint(b[0])), "r"(__float_as_uint(b[1])));
 }
 
-// Load the A tile rows [row0, row0 + kMT) of columns c0 .. c0 + wb - 1 (zeros elsewhere),
-// split into TF32 hi / lo.  Thread t loads 8 consecutive rows of column t / 8.
-__device__ __forceinline__ void load_a_tile(const MultiParams& p, MultiSmem& s, int64_t c0, int wb, int64_t row0) {
-    const int tid = threadIdx.x;
-    const int j = tid >> 3;
-    const int t0 = (tid & 7) * 8;
+// The A tile rows [row0, row0 + kMT) of columns c0 .. c0 + wb - 1 (zeros elsewhere): thread t
+// holds 8 consecutive rows of column t / 8.  fetch loads them into registers (the next tile's
+// loads overlap the current tile's MMAs); store splits them into TF32 hi / lo in shared memory.
+__device__ __forceinline__ void fetch_a_tile(const MultiParams& p, int64_t c0, int wb, int64_t row0, float (&v)[8]) {
+    const int j = threadIdx.x >> 3;
+    const int t0 = (threadIdx.x & 7) * 8;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
         const int64_t row = row0 + t0 + e;
-        const float v = (j < wb && row < p.m) ? __ldg(p.A + (c0 + j) * p.lda + row) : 0.f;
+        v[e] = (j < wb && row < p.m) ? __ldg(p.A + (c0 + j) * p.lda + row) : 0.f;
+    }
+}
+
+__device__ __forceinline__ void store_a_tile(MultiSmem& s, const float (&v)[8]) {
+    const int j = threadIdx.x >> 3;
+    const int t0 = (threadIdx.x & 7) * 8;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
         float hi, lo;
-        split_tf32(v, hi, lo);
+        split_tf32(v[e], hi, lo);
         s.a_hi[j * kMAS + t0 + e] = hi;
         s.a_lo[j * kMAS + t0 + e] = lo;
+    }
+}
+
+// The lanes' residual tile R~[row0 .. row0 + kMT) x KP: element i = tid + kMThreads * q.
+template <int KP>
+__device__ __forceinline__ void fetch_r_tile(const MultiParams& p, int64_t row0, float (&v)[kMT * KP / kMThreads]) {
+#pragma unroll
+    for (int q = 0; q < kMT * KP / kMThreads; ++q) {
+        const int i = threadIdx.x + kMThreads * q;
+        const int64_t row = row0 + i / KP;
+        v[q] = row < p.m ? static_cast<float>(__ldcg(p.R + row * KP + i % KP)) : 0.f;
+    }
+}
+
+template <int KP>
+__device__ __forceinline__ void store_r_tile(MultiSmem& s, const float (&v)[kMT * KP / kMThreads]) {
+#pragma unroll
+    for (int q = 0; q < kMT * KP / kMThreads; ++q) {
+        const int i = threadIdx.x + kMThreads * q;
+        float hi, lo;
+        split_tf32(v[q], hi, lo);
+        s.r_hi[(i / KP) * kMRS + i % KP] = hi;
+        s.r_lo[(i / KP) * kMRS + i % KP] = lo;
     }
 }
 
@@ -124,17 +155,16 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[q][e] = 0.0;
             if (p.mode != 1) {
+                float av[8], rv[kMT * KP / kMThreads];
+                fetch_a_tile(p, c0, wb, 0, av);
+                fetch_r_tile<KP>(p, 0, rv);
                 for (int64_t row0 = 0; row0 < p.m; row0 += kMT) {
                     __syncthreads();  // previous tile consumed
-                    load_a_tile(p, s, c0, wb, row0);
-                    for (int i = tid; i < kMT * KP; i += kMThreads) {
-                        const int t = i / KP, l = i % KP;
-                        const int64_t row = row0 + t;
-                        const float v = row < p.m ? static_cast<float>(__ldcg(p.R + row * KP + l)) : 0.f;
-                        float hi, lo;
-                        split_tf32(v, hi, lo);
-                        s.r_hi[t * kMRS + l] = hi;
-                        s.r_lo[t * kMRS + l] = lo;
+                    store_a_tile(s, av);
+                    store_r_tile<KP>(s, rv);
+                    if (row0 + kMT < p.m) {  // next tile's loads in flight during this tile's MMAs
+                        fetch_a_tile(p, c0, wb, row0 + kMT, av);
+                        fetch_r_tile<KP>(p, row0 + kMT, rv);
                     }
                     __syncthreads();
 #pragma unroll
@@ -223,9 +253,12 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
             __syncthreads();
             // ---- scatter pass: R += A_i Delta (FP64 atomics; rows >= m skipped)
             if (s_any && p.mode != 2) {
+                float av[8];
+                fetch_a_tile(p, c0, wb, 0, av);
                 for (int64_t row0 = 0; row0 < p.m; row0 += kMT) {
-                    load_a_tile(p, s, c0, wb, row0);
+                    store_a_tile(s, av);
                     __syncthreads();
+                    if (row0 + kMT < p.m) fetch_a_tile(p, c0, wb, row0 + kMT, av);
 #pragma unroll
                     for (int q = 0; q < kP2W; ++q) {
                         const int pr = warp + 8 * q;
