@@ -200,6 +200,57 @@ def planted_f_ref(gen):
     return 0.5 * float(r @ r) + LAM * float(np.abs(xs).sum())
 
 
+def run_cpu_core_study(args):
+    """Section 4.2's core-count study: time to a relative error of F below 1e-4 on the
+    Nesterov LASSO the paper uses for it (20000 x 40000, lambda = 1, 1 % nonzero), for the
+    multi-core CPU oracle on c = 1, 2, 4, ... host threads (variables partitioned among the
+    threads, lock-free) in both of its forms, next to the GPU's async solve to the same error.
+    The Gram form precomputes A^T A and A^T b (as the paper's experiments do; the precompute is
+    timed apart); the residual form shares r = Ax - b as the GPU does.  The CPU times leave the
+    per-sweep check out; the GPU time is the whole solve, checks included."""
+    import numpy as np
+    import torch
+    from paper_1701_04900_gb300 import Solver
+    from inputs import nesterov_lasso_torch
+    from oracle import cores as oc
+    m, n, k, tol = 20000, 40000, 400, 1e-4
+    gen = nesterov_lasso_torch(m, n, k, lam=LAM, seed=0, device="cuda")
+    sup = gen["support"]
+    r = gen["At"][sup, :m].double().T @ gen["x_star"][sup] - gen["b"].double()
+    f_star = 0.5 * float(r @ r) + LAM * float(gen["x_star"].abs().sum())
+    out = {"workload": f"lasso_nesterov_{m}x{n}", "nonzeros": k, "lambda": LAM, "tol_rel_err": tol,
+           "f_star": "closed form of the generator, on the stored FP32 data"}
+    t, st = _time_solves(lambda: Solver(gen["At"], gen["b"], LAM, m=m, block_w=W_BLOCK, mode="async", gamma=GAMMA,
+                                        f_star=f_star, tol_gap=tol, tol_stat=1.0, check_every=1, refresh_every=10,
+                                        max_sweeps=2000), n)
+    out["gpu"] = {"seconds": t, "sweeps": st["sweeps"], "rel_gap": st["rel_gap"], "status": st["status"],
+                  "block_w": W_BLOCK, "note": "async solve from x = 0, check every sweep, checks included"}
+    At = gen["At"].cpu().numpy()
+    b = gen["b"].double().cpu().numpy()
+    del gen, r
+    torch.cuda.empty_cache()
+    avail = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    counts = [c for c in (1, 2, 4, 8, 16, 32, 64) if c <= avail]
+    if counts[-1] != avail:
+        counts.append(avail)
+    out["host_cores"] = avail
+    t0 = time.perf_counter()
+    Q, q = oc.gram(At, b, m)
+    out["gram_precompute_seconds"] = time.perf_counter() - t0
+    for form, extra in (("gram", {"Q": Q, "q": q}), ("residual", {})):
+        runs = []
+        for c in counts:
+            _, cs = oc.partitioned_lasso(At, b, m, LAM, gamma=GAMMA, w=1, threads=c, max_sweeps=500, f_star=f_star,
+                                         tol=tol, **extra)
+            runs.append({"cores": c, "seconds": cs["seconds"], "sweeps": cs["sweeps"],
+                         "rel_err": (cs["F"] - f_star) / abs(f_star), "check_seconds": cs["check_seconds"]})
+        for rr in runs:
+            rr["speedup"] = runs[0]["seconds"] / rr["seconds"]
+            rr["gpu_speedup_vs_this"] = rr["seconds"] / t
+        out[form] = runs
+    return out
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -341,6 +392,11 @@ def run_ours(args):
             "sample": f"FP64 numpy cyclic Gauss-Seidel sweeps (w={W_BLOCK}) over the first {ncols} columns "
                       f"({ncols // W_BLOCK} blocks) of this {M}x{N} instance for {r['seconds']:.1f} s "
                       f"({r['sweeps']} sweeps)"}
+        if args.cpu_speedup:
+            try:
+                result["cpu_baseline"]["core_study"] = run_cpu_core_study(args)
+            except Exception as exc:  # reported, the headline line still prints
+                result["cpu_baseline"]["core_study"] = {"error": f"{type(exc).__name__}: {exc}"[:400]}
     s.close()
     if rank == 0 and not args.no_forms:
         ctx = {"gen": gen, "f_ref": f_ref}
@@ -790,16 +846,41 @@ def run_form_dc(args, ctx=None):
     return out
 
 
+def run_ncu_case_multi():
+    """ncu case of the multi-lane kernel: the 64-lane lambda path on the 5000 x 20000 instance
+    (A = 400 MB, larger than L2), one solve capped at 10 sweeps: a refresh launch, then one
+    launch of 10 sweeps of every lane (mode 0), then the objective and gradient launches."""
+    import torch
+    from paper_1701_04900_gb300.batch import MultiLaneSolver
+    from inputs import nesterov_lasso_torch
+    m, n, k = 5000, 20000, 64
+    g = nesterov_lasso_torch(m, n, 200, lam=1.0, seed=7, device="cuda")
+    lam_max = float((g["At"][:, :m].double() @ g["b"].double()).abs().max())
+    lams = [lam_max * (1.0 / lam_max) ** (i / (k - 1)) for i in range(k)]
+    B = g["b"].reshape(1, -1).expand(k, -1).contiguous()
+    ml = MultiLaneSolver(g["At"], B, lams, m, refresh_every=10, check_every=10, max_sweeps=10)
+    X = torch.zeros((k, n), dtype=torch.float32, device="cuda")
+    per, tot = ml.solve(X)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": True, "mode": "multi", "lanes": k, "sweeps": tot["sweeps"],
+                      "F_last_lane": per[-1]["F"]}))
+    ml.close()
+
+
 def run_ncu_case(args):
     """Small case for ncu captures: the same generator with n = 12800 (A = 1 GB, larger
     than L2), one refresh, then `--ncu-launches` async sweep launches of 10 sweeps each
-    (or Jacobi sweeps with --ncu-mode sync).  Used by the commands in profiles/."""
+    (or Jacobi sweeps with --ncu-mode sync; --ncu-mode multi: the multi-lane case).  Used by
+    the commands in profiles/."""
     import torch
     from paper_1701_04900_gb300.build import build_library
     build_library()
     from paper_1701_04900_gb300 import Solver
     from inputs import nesterov_lasso_torch
     torch.cuda.set_device(0)
+    if args.ncu_mode == "multi":
+        run_ncu_case_multi()
+        return
     n = 12800
     gen = nesterov_lasso_torch(M, n, K_PLANT * n // N, lam=LAM, seed=0, device="cuda")
     s = Solver(gen["At"], gen["b"], LAM, m=M, block_w=W_BLOCK, mode=args.ncu_mode, gamma=GAMMA,
@@ -817,7 +898,7 @@ def run_ncu_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--ncu-case", action="store_true", help="small profiling case (see run_ncu_case)")
-    ap.add_argument("--ncu-mode", default="async", choices=["async", "sync"])
+    ap.add_argument("--ncu-mode", default="async", choices=["async", "sync", "multi"])
     ap.add_argument("--ncu-launches", type=int, default=3)
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
                     help="async sweep kernel (asyflexa_opts.variant; 0 = automatic)")
@@ -834,10 +915,18 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--cpu-speedup", action="store_true",
+                    help="add the core-count study of the CPU oracle (a few minutes of host time)")
+    ap.add_argument("--cpu-speedup-only", action="store_true",
+                    help="run only the core-count study and print it as one JSON line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.ncu_case:
+    if args.cpu_speedup_only:
+        from paper_1701_04900_gb300.build import build_library
+        build_library()
+        print(json.dumps({"cpu_core_study": run_cpu_core_study(args)}), flush=True)
+    elif args.ncu_case:
         run_ncu_case(args)
     elif args.impl == "reference":
         run_reference(args)
