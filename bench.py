@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "time to 1e-6 rel. gap & block-updates/s, async vs sync vs oracle, % HBM peak"
 M, N, K_PLANT, LAM, W_BLOCK, GAMMA = 20000, 100000, 1000, 1.0, 32, 0.9
 WORKLOAD = "lasso_nesterov_20000x100000_fp32_w32"
-SWEEP_SOURCES = ["sweep_async.cuh", "sweep.cuh", "ptx.cuh", "types.cuh"]
+SWEEP_SOURCES = ["sweep_async.cuh", "sweep.cuh", "ptx.cuh", "types.cuh", "convert.cuh"]
 # the async sweep kernel behind each value of asyflexa_opts.variant / stats.kernel_variant
 ASYNC_KERNELS = {
     1: "sweep_kernel<float, async> (staged residual tile)",

@@ -29,6 +29,7 @@
 // only changed between launches).
 #pragma once
 
+#include "convert.cuh"
 #include "ptx.cuh"
 #include "sweep.cuh"
 #include "types.cuh"
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
 #pragma unroll
                     for (int t = 0; t < kB; ++t) {
                         const int i = i0 + t * kRegConsThreads;
-                        if (i < pairs) rdst[i] = make_float2(static_cast<float>(v[t].x), static_cast<float>(v[t].y));
+                        if (i < pairs) rdst[i] = make_float2(f64_to_f32(v[t].x), f64_to_f32(v[t].y));
                     }
                 }
             }
@@ -410,7 +411,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
 #pragma unroll
                         for (int e = 0; e < V; ++e) {
                             const int64_t row = u * V + e;
-                            if (row < bv.m && inc[k][e] != 0.f) red_add_f64(bv.r + row, static_cast<double>(inc[k][e]));
+                            if (row < bv.m && inc[k][e] != 0.f) red_add_f64(bv.r + row, f32_to_f64(inc[k][e]));
                         }
                     }
                 }

@@ -53,6 +53,15 @@ struct MultiSmem {
     float d_hi[kMW * kMRS], d_lo[kMW * kMRS];   // Delta (j * kMRS + lane)
 };
 
+// TwoSum (Knuth): s + e == a + b exactly, s = fl(a + b).  Accumulates the per-tile FP32 sums
+// in a float-float pair (hi, lo) with about 44 significant bits, on the FP32 pipe.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float b) {
+    const float s = hi + b;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (b - bb);
+    hi = s;
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -147,13 +156,14 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
             const int wb = static_cast<int>(min64(kMW, p.n - c0));
             if (tid == 0) s_uread = ld_relaxed_u64(&p.counters[0]);
             // ---- gradient pass: G = A_i^T R~ (S.2: R~ is read tile by tile, a stale read)
-            // per row tile an FP32 accumulator (tensor cores), summed over the tiles in FP64, so the
-            // FP32 rounding of G grows with the tile (kMT rows), not with m
-            double acc[kP1W][4];
+            // per row tile FP32 accumulators (tensor cores; the three split products in separate
+            // chains), summed over the tiles in float-float, so the FP32 rounding of G grows with
+            // the tile (kMT rows), not with m
+            float acc_hi[kP1W][4], acc_lo[kP1W][4];
 #pragma unroll
             for (int q = 0; q < kP1W; ++q)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) acc[q][e] = 0.0;
+                for (int e = 0; e < 4; ++e) acc_hi[q][e] = acc_lo[q][e] = 0.f;
             if (p.mode != 1) {
                 float av[8], rv[kMT * KP / kMThreads];
                 fetch_a_tile(p, c0, wb, 0, av);
@@ -173,7 +183,8 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
                         if (pr < kP1) {
                             const int mt = pr / kNT, nt = pr % kNT;
                             const int j0 = mt * 16 + grp;
-                            float tacc[4] = {0.f, 0.f, 0.f, 0.f};
+                            float t_ab[4] = {0.f, 0.f, 0.f, 0.f}, t_ba[4] = {0.f, 0.f, 0.f, 0.f},
+                                  t_hh[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 2
                             for (int k0 = 0; k0 < kMT; k0 += 8) {
                                 float ah[4], al[4], bh[2], bl[2];
@@ -189,12 +200,12 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
                                 bh[1] = s.r_hi[(k0 + tig + 4) * kMRS + nt * 8 + grp];
                                 bl[0] = s.r_lo[(k0 + tig) * kMRS + nt * 8 + grp];
                                 bl[1] = s.r_lo[(k0 + tig + 4) * kMRS + nt * 8 + grp];
-                                mma_tf32(tacc, al, bh);
-                                mma_tf32(tacc, ah, bl);
-                                mma_tf32(tacc, ah, bh);
+                                mma_tf32(t_ab, al, bh);
+                                mma_tf32(t_ba, ah, bl);
+                                mma_tf32(t_hh, ah, bh);
                             }
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) acc[q][e] += static_cast<double>(tacc[e]);
+                            for (int e = 0; e < 4; ++e) two_sum_acc(acc_hi[q][e], acc_lo[q][e], t_hh[e] + (t_ab[e] + t_ba[e]));
                         }
                     }
                 }
@@ -207,10 +218,10 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
                 if (pr < kP1) {
                     const int mt = pr / kNT, nt = pr % kNT;
                     const int j0 = mt * 16 + grp, l0 = nt * 8 + 2 * tig;
-                    s.g[j0 * kMRS + l0] = static_cast<float>(acc[q][0]);
-                    s.g[j0 * kMRS + l0 + 1] = static_cast<float>(acc[q][1]);
-                    s.g[(j0 + 8) * kMRS + l0] = static_cast<float>(acc[q][2]);
-                    s.g[(j0 + 8) * kMRS + l0 + 1] = static_cast<float>(acc[q][3]);
+                    s.g[j0 * kMRS + l0] = acc_hi[q][0] + acc_lo[q][0];
+                    s.g[j0 * kMRS + l0 + 1] = acc_hi[q][1] + acc_lo[q][1];
+                    s.g[(j0 + 8) * kMRS + l0] = acc_hi[q][2] + acc_lo[q][2];
+                    s.g[(j0 + 8) * kMRS + l0 + 1] = acc_hi[q][3] + acc_lo[q][3];
                 }
             }
             if (tid == 0) s_any = 0;
@@ -265,7 +276,8 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
                         if (pr < kP2) {
                             const int mt = pr / kNT, nt = pr % kNT;
                             const int t0 = mt * 16 + grp;
-                            float c[4] = {0.f, 0.f, 0.f, 0.f};
+                            float c_ab[4] = {0.f, 0.f, 0.f, 0.f}, c_ba[4] = {0.f, 0.f, 0.f, 0.f},
+                                  c_hh[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                             for (int k0 = 0; k0 < kMW; k0 += 8) {
                                 float ah[4], al[4], bh[2], bl[2];
@@ -282,10 +294,13 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
                                 bh[1] = s.d_hi[(k0 + tig + 4) * kMRS + nt * 8 + grp];
                                 bl[0] = s.d_lo[(k0 + tig) * kMRS + nt * 8 + grp];
                                 bl[1] = s.d_lo[(k0 + tig + 4) * kMRS + nt * 8 + grp];
-                                mma_tf32(c, al, bh);
-                                mma_tf32(c, ah, bl);
-                                mma_tf32(c, ah, bh);
+                                mma_tf32(c_ab, al, bh);
+                                mma_tf32(c_ba, ah, bl);
+                                mma_tf32(c_hh, ah, bh);
                             }
+                            float c[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) c[e] = c_hh[e] + (c_ab[e] + c_ba[e]);
                             const int l0 = nt * 8 + 2 * tig;
                             const int64_t r0 = row0 + t0, r1 = row0 + t0 + 8;
                             if (r0 < p.m) {

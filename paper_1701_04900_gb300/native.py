@@ -77,6 +77,7 @@ EXPORTS = [
     "asyflexa_last_error", "asyflexa_residual_noalloc", "asyflexa_quantize", "asyflexa_gather_columns",
     "asyflexa_batch_create", "asyflexa_batch_solve", "asyflexa_batch_destroy",
     "asyflexa_multi_create", "asyflexa_multi_solve", "asyflexa_multi_destroy",
+    "asyflexa_convert_check",
 ]
 BATCH_SHARED_A = 1
 
@@ -121,6 +122,8 @@ def lib(path: str | None = None):
     L.asyflexa_last_error.argtypes = [vp]
     L.asyflexa_residual_noalloc.restype = C.c_int
     L.asyflexa_residual_noalloc.argtypes = [C.POINTER(Problem), vp, vp, vp]
+    L.asyflexa_convert_check.restype = C.c_int
+    L.asyflexa_convert_check.argtypes = [i32, vp, vp, C.c_int64, vp]
     L.asyflexa_quantize.restype = C.c_int
     L.asyflexa_quantize.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, i32, vp, C.c_int64, vp, vp]
     L.asyflexa_batch_create.restype = C.c_int
@@ -317,6 +320,22 @@ class Solver:
 
     def __exit__(self, *a):
         self.close()
+
+
+def convert_check(src, stream=None):
+    """The kernels' own FP32 <-> FP64 conversions (asyflexa_convert_check) applied to a CUDA
+    tensor: float64 -> float32 (round to nearest even) or float32 -> float64 (exact)."""
+    import torch
+    if not src.is_cuda or not src.is_contiguous() or src.dtype not in (torch.float64, torch.float32):
+        raise ValueError("src must be a contiguous float64 or float32 CUDA tensor")
+    d = 0 if src.dtype == torch.float64 else 1
+    out = torch.empty(src.shape, dtype=torch.float32 if d == 0 else torch.float64, device=src.device)
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = lib().asyflexa_convert_check(d, src.data_ptr(), out.data_ptr(), src.numel(), C.c_void_p(stream))
+    if rc != OK:
+        raise AsyflexaError(rc, lib().asyflexa_last_error(None).decode())
+    return out
 
 
 def quantize(At, m: int, kind: str, stream=None):
