@@ -476,6 +476,8 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
         h->check_ctas = h->sm_count;
         h->check_smem = static_cast<size_t>(2 * h->mcopy * h->elt_c);
         h->check_use_smem = h->check_smem + 1024 <= h->smem_optin;
+        const int rc = dispatch(*h, [&](auto L) { return decltype(L)::setup_pipe(*h); });
+        if (rc) CKC(static_cast<cudaError_t>(rc), "pipelined gather set-up");
     }
 
     CKC(cudaMalloc(&h->r, h->mcopy * sizeof(double)), "alloc r");
@@ -485,7 +487,8 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
     CKC(cudaMalloc(&h->list_val, n * h->elt_c), "alloc list");
     CKC(cudaMalloc(&h->tilecnt, h->compact_tiles * sizeof(int)), "alloc tiles");
     CKC(cudaMalloc(&h->count, sizeof(int)), "alloc count");
-    CKC(cudaMalloc(&h->partial, static_cast<size_t>(h->nseg) * h->mcopy * sizeof(double)), "alloc partials");
+    CKC(cudaMalloc(&h->partial, static_cast<size_t>(std::max(h->nseg, h->pipe_nseg)) * h->mcopy * sizeof(double)),
+        "alloc partials");
     CKC(cudaMalloc(&h->norms_part, kNormsGridHost * 8 * sizeof(double)), "alloc norms");
     CKC(cudaMalloc(&h->norms_out, 8 * sizeof(double)), "alloc norms");
     CKC(cudaMalloc(&h->counters, 4 * sizeof(unsigned long long)), "alloc counters");

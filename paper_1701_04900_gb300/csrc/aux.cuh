@@ -1,7 +1,10 @@
 // Auxiliary kernels around the sweep:
 //   * colnorm_kernel      surrogate weights d_j = (1+tau_rel) kappa_j + tau   (create time)
 //   * count/compact       deterministic ordered list of the nonzero entries of a vector
-//   * gather_gemv_kernel  partial[seg] = sum_{k in seg} a_{j_k} v_k  (fixed segmentation)
+//   * gather_gemv_pipe_kernel  partial[seg] = sum_{k in seg} a_{j_k} v_k  (fixed segmentation;
+//                         compensated products for the exact refresh, plain ones for the
+//                         Jacobi scatter); gather_gemv_exact_kernel is the register-batched
+//                         form kept for the no-allocation residual
 //   * reduce_partials     r = r + sum_seg partial  (Jacobi scatter)  or
 //                         r = sum_seg partial - b  (exact residual refresh, FP64 accumulation)
 //   * norms / finalize    ||r||^2, ||x||_1, ||x||^2, nnz with fixed-order reductions
@@ -11,6 +14,8 @@
 // bit-reproducible run to run.
 #pragma once
 
+#include <type_traits>
+
 #include "ptx.cuh"
 #include "types.cuh"
 
@@ -19,7 +24,9 @@ namespace asyflexa {
 constexpr int kAuxThreads = 256;
 constexpr int kCompactPerThread = 16;
 constexpr int kCompactTile = kAuxThreads * kCompactPerThread;
-constexpr int kGemvUnits = 2;     // 16-byte units of A per thread in gather_gemv
+constexpr int kGemvUnits = 2;     // 16-byte units of A per thread in gather_gemv_exact
+constexpr int kPipeStages = 6;    // list entries (columns) in flight per thread in gather_gemv_pipe
+constexpr int kPipeElems = 16;    // elements of A per thread per column in gather_gemv_pipe
 constexpr int kNormsGrid = 256;
 constexpr int kCheckThreads = 1024;
 
@@ -155,73 +162,99 @@ __global__ void compact_kernel(const TV* v, int64_t n, const int* tilecnt, int n
 
 // ----------------------------------------------------------------------------- gather GEMV
 
-// grid = (row tiles, nseg).  partial[seg * mcopy + row] = sum over the seg-th slice of the
-// list of a_{idx[k]}[row] * val[k] * scale[idx[k]], accumulated in TP in list order.
-template <typename TA, typename TV, typename TP>
-__global__ void __launch_bounds__(kAuxThreads) gather_gemv_kernel(const TA* A, int64_t lda, int64_t mcopy,
-                                                                  const float* scale, const int* idx, const TV* val,
-                                                                  const int* count, TP* partial) {
+// grid = (row tiles of kAuxThreads * kPipeElems rows, nseg); dynamic shared memory
+// kPipeStages * kAuxThreads * kPipeElems * sizeof(TA) bytes.
+// partial[seg * mcopy + row] = sum over the seg-th slice of the list of
+// a_{idx[k]}[row] * val[k] * scale[idx[k]], accumulated in list order: with compensated
+// (error-free) FP32 products and an FP64 result when kExact (the exact residual), else in the
+// compute type TC (the Jacobi scatter).  Each thread streams its own 16-byte units of the next
+// kPipeStages - 1 columns into a shared-memory ring with cp.async while it accumulates the
+// current one, and reads back only what it copied itself, so no barrier is needed.
+template <typename TA, typename TV, bool kExact>
+__global__ void __launch_bounds__(kAuxThreads) gather_gemv_pipe_kernel(const TA* A, int64_t lda, int64_t mcopy,
+                                                                       const float* scale, const int* idx,
+                                                                       const TV* val, const int* count,
+                                                                       void* partial_out) {
     using TC = typename ATraits<TA>::TC;
+    using TP = typename std::conditional<kExact, double, TC>::type;
     constexpr int V = ATraits<TA>::kVec;
+    constexpr int U = kPipeElems / V;  // 16-byte units per thread per column
+    static_assert(U >= 1 && U * V == kPipeElems, "whole units per thread");
+    extern __shared__ __align__(16) uint4 ring[];  // [stage][U][kAuxThreads]
     const int cnt = *count;
     const int nseg = gridDim.y;
     const int seg = blockIdx.y;
     const int k0 = static_cast<int>((static_cast<int64_t>(cnt) * seg) / nseg);
     const int k1 = static_cast<int>((static_cast<int64_t>(cnt) * (seg + 1)) / nseg);
     const int64_t units = mcopy / V;
-    int64_t uu[kGemvUnits];
+    int64_t uu[U];
 #pragma unroll
-    for (int q = 0; q < kGemvUnits; ++q)
-        uu[q] = (static_cast<int64_t>(blockIdx.x) * kGemvUnits + q) * kAuxThreads + threadIdx.x;
-    TP acc[kGemvUnits][V];
+    for (int q = 0; q < U; ++q) uu[q] = (static_cast<int64_t>(blockIdx.x) * U + q) * kAuxThreads + threadIdx.x;
+    // copies of list entry kk into ring stage st (one commit group per entry, empty past k1)
+    auto issue = [&](int kk, int st) {
+        if (kk < k1) {
+            const TA* col = A + static_cast<int64_t>(__ldg(idx + kk)) * lda;
 #pragma unroll
-    for (int q = 0; q < kGemvUnits; ++q)
+            for (int q = 0; q < U; ++q)
+                if (uu[q] < units) cp_async_16(&ring[(st * U + q) * kAuxThreads + threadIdx.x], col + uu[q] * V);
+        }
+        cp_async_commit();
+    };
 #pragma unroll
-        for (int e = 0; e < V; ++e) acc[q][e] = TP(0);
-    constexpr int KU = 4;  // list entries whose loads are in flight together
-    for (int k = k0; k < k1; k += KU) {
-        uint4 q4[KU][kGemvUnits];
-        TP vk[KU];
+    for (int t = 0; t < kPipeStages - 1; ++t) issue(k0 + t, t);
+    typename std::conditional<kExact, ProdAcc<TC>, TP>::type acc[U][V];
+    if constexpr (!kExact) {
 #pragma unroll
-        for (int t = 0; t < KU; ++t) {
-            vk[t] = TP(0);
-            if (k + t < k1) {
-                const int j = __ldg(idx + k + t);
-                vk[t] = static_cast<TP>(__ldg(val + k + t));
-                if (scale) vk[t] *= static_cast<TP>(__ldg(scale + j));
-                const TA* col = A + static_cast<int64_t>(j) * lda;
+        for (int q = 0; q < U; ++q)
 #pragma unroll
-                for (int q = 0; q < kGemvUnits; ++q)
-                    if (uu[q] < units) q4[t][q] = ld_stream_u4(col + uu[q] * V);
-            }
+            for (int e = 0; e < V; ++e) acc[q][e] = TP(0);
+    }
+    int st = 0;
+    for (int k = k0; k < k1; ++k) {
+        issue(k + kPipeStages - 1, st == 0 ? kPipeStages - 1 : st - 1);
+        cp_async_wait<kPipeStages - 1>();  // entry k's copies have landed
+        TC vh, vl = TC(0);
+        if constexpr (kExact) {
+            double v = static_cast<double>(__ldg(val + k));
+            if (scale) v *= static_cast<double>(__ldg(scale + __ldg(idx + k)));
+            vh = static_cast<TC>(v);
+            vl = static_cast<TC>(v - static_cast<double>(vh));
+        } else {
+            vh = static_cast<TC>(__ldg(val + k));
+            if (scale) vh *= static_cast<TC>(__ldg(scale + __ldg(idx + k)));
         }
 #pragma unroll
-        for (int t = 0; t < KU; ++t) {
-            if (k + t < k1) {
+        for (int q = 0; q < U; ++q) {
+            if (uu[q] < units) {
+                TC a[V];
+                ATraits<TA>::unpack(ring[(st * U + q) * kAuxThreads + threadIdx.x], a);
 #pragma unroll
-                for (int q = 0; q < kGemvUnits; ++q) {
-                    if (uu[q] < units) {
-                        TC a[V];
-                        ATraits<TA>::unpack(q4[t][q], a);
-#pragma unroll
-                        for (int e = 0; e < V; ++e) acc[q][e] = fmac(static_cast<TP>(a[e]), vk[t], acc[q][e]);
+                for (int e = 0; e < V; ++e) {
+                    if constexpr (kExact) {
+                        acc[q][e].add_prod(a[e], vh);
+                        if (vl != TC(0)) acc[q][e].add_prod(a[e], vl);
+                    } else {
+                        acc[q][e] = fmac(a[e], vh, acc[q][e]);
                     }
                 }
             }
         }
+        st = st + 1 == kPipeStages ? 0 : st + 1;
     }
-    TP* out = partial + static_cast<int64_t>(seg) * mcopy;
+    cp_async_wait<0>();
+    TP* out = static_cast<TP*>(partial_out) + static_cast<int64_t>(seg) * mcopy;
 #pragma unroll
-    for (int q = 0; q < kGemvUnits; ++q)
+    for (int q = 0; q < U; ++q)
         if (uu[q] < units)
 #pragma unroll
-            for (int e = 0; e < V; ++e) out[uu[q] * V + e] = acc[q][e];
+            for (int e = 0; e < V; ++e) {
+                if constexpr (kExact)
+                    out[uu[q] * V + e] = acc[q][e].value();
+                else
+                    out[uu[q] * V + e] = acc[q][e];
+            }
 }
 
-// Exact-accumulation variant for the residual refresh: same slicing as gather_gemv_kernel,
-// products a * (val * scale) summed with ProdAcc (FP64 FMAs for FP64 storage, the
-// double-FP32 pair otherwise), written as FP64 partials.  The factor val * scale is formed
-// in FP64 and split into hi + lo parts in the compute type.
 template <typename TA, typename TV>
 __global__ void __launch_bounds__(kAuxThreads) gather_gemv_exact_kernel(const TA* A, int64_t lda, int64_t mcopy,
                                                                         const float* scale, const int* idx,

@@ -55,6 +55,8 @@ struct asyflexa_s {
 
     // gather-GEMV / compaction geometry
     int nseg = 0, gemv_rowtiles = 0, compact_tiles = 0;
+    int pipe_nseg = 0, pipe_rowtiles = 0;  // pipelined gather (refresh, Jacobi scatter)
+    size_t pipe_smem = 0;
     // register-resident async kernel (0 = not used)
     // diminishing stepsize (opts.gamma_mu > 0): update index and step at the next launch, and
     // the device table of the steps of one launch
@@ -124,6 +126,7 @@ struct Launcher {
     static cudaError_t check(asyflexa_s& h, const void* x);
     static cudaError_t shift_weights(asyflexa_s& h, double delta);
     static int set_smem_attrs(asyflexa_s& h);
+    static int setup_pipe(asyflexa_s& h);
     static int choose_reg(asyflexa_s& h);
 };
 

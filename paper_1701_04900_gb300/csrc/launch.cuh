@@ -72,6 +72,36 @@ int Launcher<TA>::choose_reg(asyflexa_s& h) {
     return 1;
 }
 
+// Geometry of the pipelined gather (refresh and Jacobi scatter): row tiles of
+// kAuxThreads * kPipeElems rows, and as many list segments as fill the resident blocks of
+// every SM once (at most 64).  Sets the kernels' shared-memory attribute.
+template <typename TA>
+int Launcher<TA>::setup_pipe(asyflexa_s& h) {
+    using TX = typename XType<TA>::T;
+    using TC = typename ATraits<TA>::TC;
+    constexpr int U = kPipeElems / ATraits<TA>::kVec;
+    h.pipe_smem = static_cast<size_t>(kPipeStages) * U * kAuxThreads * sizeof(uint4);
+    const int64_t units = h.mcopy / h.vec;
+    const int64_t per_cta = static_cast<int64_t>(kAuxThreads) * U;
+    h.pipe_rowtiles = static_cast<int>((units + per_cta - 1) / per_cta);
+    const void* fns[2] = {reinterpret_cast<const void*>(gather_gemv_pipe_kernel<TA, TX, true>),
+                          reinterpret_cast<const void*>(gather_gemv_pipe_kernel<TA, TC, false>)};
+    int bps = 64;
+    for (const void* fn : fns) {
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(h.pipe_smem));
+        if (e != cudaSuccess) return static_cast<int>(e);
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kAuxThreads, h.pipe_smem);
+        if (e != cudaSuccess) return static_cast<int>(e);
+        bps = b < bps ? b : bps;
+    }
+    if (bps < 1) bps = 1;
+    const int nseg = static_cast<int>((static_cast<int64_t>(bps) * h.sm_count) / h.pipe_rowtiles);
+    h.pipe_nseg = nseg < 1 ? 1 : (nseg > 64 ? 64 : nseg);
+    return 0;
+}
+
 template <typename TA>
 int Launcher<TA>::set_smem_attrs(asyflexa_s& h) {
     cudaError_t e;
@@ -165,13 +195,14 @@ cudaError_t Launcher<TA>::jacobi_apply(asyflexa_s& h) {
     count_nonzero_kernel<TC><<<h.compact_tiles, kAuxThreads, 0, h.stream>>>(d, P.n, h.tilecnt);
     compact_kernel<TC><<<h.compact_tiles, kAuxThreads, 0, h.stream>>>(d, P.n, h.tilecnt, h.compact_tiles, h.list_idx,
                                                                       static_cast<TC*>(h.list_val), h.count);
-    dim3 g(h.gemv_rowtiles, h.nseg);
-    gather_gemv_kernel<TA, TC, TC><<<g, kAuxThreads, 0, h.stream>>>(
+    dim3 g(h.pipe_rowtiles, h.pipe_nseg);
+    gather_gemv_pipe_kernel<TA, TC, false><<<g, kAuxThreads, h.pipe_smem, h.stream>>>(
         static_cast<const TA*>(P.A), P.lda, h.mcopy, P.col_scale, h.list_idx, static_cast<const TC*>(h.list_val),
-        h.count, static_cast<TC*>(h.partial));
+        h.count, h.partial);
     const int rg = static_cast<int>((h.mcopy + kAuxThreads - 1) / kAuxThreads);
-    reduce_partials_kernel<TC, TX><<<rg, kAuxThreads, 0, h.stream>>>(h.r, static_cast<const TC*>(h.partial), h.nseg,
-                                                                      P.m, h.mcopy, static_cast<const TX*>(P.b), 0);
+    reduce_partials_kernel<TC, TX><<<rg, kAuxThreads, 0, h.stream>>>(h.r, static_cast<const TC*>(h.partial),
+                                                                      h.pipe_nseg, P.m, h.mcopy,
+                                                                      static_cast<const TX*>(P.b), 0);
     h.launches += 4;
     return cudaGetLastError();
 }
@@ -185,13 +216,13 @@ cudaError_t Launcher<TA>::refresh(asyflexa_s& h, const void* xv) {
     count_nonzero_kernel<TX><<<h.compact_tiles, kAuxThreads, 0, h.stream>>>(x, P.n, h.tilecnt);
     compact_kernel<TX><<<h.compact_tiles, kAuxThreads, 0, h.stream>>>(x, P.n, h.tilecnt, h.compact_tiles, h.list_idx,
                                                                       static_cast<TX*>(h.list_val), h.count);
-    dim3 g(h.gemv_rowtiles, h.nseg);
-    gather_gemv_exact_kernel<TA, TX><<<g, kAuxThreads, 0, h.stream>>>(
+    dim3 g(h.pipe_rowtiles, h.pipe_nseg);
+    gather_gemv_pipe_kernel<TA, TX, true><<<g, kAuxThreads, h.pipe_smem, h.stream>>>(
         static_cast<const TA*>(P.A), P.lda, h.mcopy, P.col_scale, h.list_idx, static_cast<const TX*>(h.list_val),
-        h.count, static_cast<double*>(h.partial));
+        h.count, h.partial);
     const int rg = static_cast<int>((h.mcopy + kAuxThreads - 1) / kAuxThreads);
     reduce_partials_kernel<double, TX><<<rg, kAuxThreads, 0, h.stream>>>(
-        h.r, static_cast<const double*>(h.partial), h.nseg, P.m, h.mcopy, static_cast<const TX*>(P.b), 1);
+        h.r, static_cast<const double*>(h.partial), h.pipe_nseg, P.m, h.mcopy, static_cast<const TX*>(P.b), 1);
     h.launches += 4;
     return cudaGetLastError();
 }

@@ -118,6 +118,20 @@ __device__ __forceinline__ uint4 ld_stream_u4(const void* p) {
 }
 
 // Named barrier over `nthreads` threads (a multiple of 32) with id `id` (1..15).
+// Per-thread asynchronous 16-byte copy global -> shared (L2 only), grouped by commit_group;
+// wait_group N returns once at most N of the calling thread's groups are still in flight,
+// and the completed copies are then visible to the calling thread.
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* gmem_src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(smem_dst)), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ void named_bar_sync(uint32_t id, uint32_t nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
