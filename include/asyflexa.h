@@ -142,7 +142,12 @@ typedef struct {
                                    interval raised F, every d_j grows by tau_extra (doubled; the first
                                    time 0.05 * mean d_j); after 5 intervals in a row that lowered F it
                                    shrinks by half.  Restarts at 0 in every solve.  0 (default): off */
-    int32_t reserved3;
+    int32_t exact_grad;         /* gradient arithmetic of the asynchronous register kernel (kernel
+                                   variant 2): 0 (default) FP32 accumulation; 1: compensated (Dot2)
+                                   accumulation, as accurate as FP64 accumulation of the FP32
+                                   residual snapshot, about 1.6x the sweep time (FP32 storage only:
+                                   EUNSUPPORTED otherwise, or when the register kernel does not
+                                   apply).  The batched and multi-lane forms ignore it */
 } asyflexa_opts;
 
 /* Results and counters.  Optimality fields are FP64 and computed from an exact
@@ -218,7 +223,11 @@ int asyflexa_step(asyflexa_t h, void* x, int32_t n_sweeps);
  * or max_sweeps is reached (ENOTCONV).  Every check_every sweeps F is evaluated from an
  * exact residual; once (F - f_star)/|f_star| <= tol_gap (or always, if f_star is NaN) the
  * stationarity ||xhat(x) - x||_inf / max(1, ||x||_inf) is evaluated and the solve stops when
- * it is <= tol_stat.  With A_master set, these sweeps run on the BF16/FP8 matrix while
+ * it is <= tol_stat.  A stationarity check that fails within 2 tol_stat is repeated after
+ * 2 sweeps instead of check_every (at most check_every times; not with A_master or
+ * tau_adapt): near tol_stat the stationarity of FP32 iterates fluctuates from sweep to sweep.
+ * The stopping decision and the returned stats come from the same exact check.
+ * With A_master set, these sweeps run on the BF16/FP8 matrix while
  * F, the residual refreshes and the stationarity are those of the FP32 problem; when a check
  * interval lowers F by less than switch_tol * |F| the solve continues with FP32 sweeps on
  * A_master ("polish") until the same stopping rule holds.  Fills *out (may be NULL);

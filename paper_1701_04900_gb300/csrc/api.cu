@@ -314,6 +314,7 @@ int validate_opts(const asyflexa_opts* o, std::string* why) {
     if (!(o->switch_tol >= 0.0)) return *why = "switch_tol must be >= 0", 1;
     if (!(o->gamma_mu >= 0.0) || !std::isfinite(o->gamma_mu)) return *why = "gamma_mu must be finite and >= 0", 1;
     if (o->tau_adapt != 0 && o->tau_adapt != 1) return *why = "tau_adapt must be 0 or 1", 1;
+    if (o->exact_grad != 0 && o->exact_grad != 1) return *why = "exact_grad must be 0 or 1", 1;
     if (o->gamma_mu > 0.0 && o->gamma_mu * o->gamma >= 1.0)
         return *why = "gamma_mu * gamma must be < 1 (the steps must stay positive)", 1;
     return 0;
@@ -364,6 +365,7 @@ void asyflexa_opts_default(asyflexa_opts* o) {
     o->switch_tol = 1e-7;
     o->gamma_mu = 0.0;
     o->tau_adapt = 0;
+    o->exact_grad = 0;
 }
 
 const char* asyflexa_last_error(asyflexa_t h) { return h ? h->msg.c_str() : g_thread_msg.c_str(); }
@@ -516,6 +518,11 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
                       "variant 2 (register increment) needs FP32/BF16/FP8 storage and m <= 24576");
             return fail(ASYFLEXA_EUNSUPPORTED);
         }
+        if (O->exact_grad == 1 && !(h->reg_upt > 0 && h->reg_exact_ok && O->mode == ASYFLEXA_ASYNC)) {
+            set_error(h, ASYFLEXA_EUNSUPPORTED,
+                      "exact_grad 1 needs the asynchronous register kernel on FP32 storage (m <= 24576)");
+            return fail(ASYFLEXA_EUNSUPPORTED);
+        }
     }
     {
         cudaError_t e = dispatch(*h, [&](auto L) { return decltype(L)::colnorm(*h); });
@@ -613,6 +620,23 @@ int asyflexa_step(asyflexa_t h, void* x, int32_t n_sweeps) {
     return run_sweeps(*h, x, n_sweeps);
 }
 
+// The optimality part of asyflexa_stats from an exact residual's objective pieces and the
+// check kernel's measures.
+void fill_check_stats(asyflexa_s& h, double F, double rr, double br, const Measures& M, asyflexa_stats* out) {
+    const double fs = h.opts.f_star;
+    out->F = F;
+    out->rel_gap = std::isfinite(fs) ? (F - fs) / std::fabs(fs) : std::nan("");
+    const double xs = std::max(1.0, M.xmax);
+    out->stat_xhat = M.xh / xs;
+    out->stat_mf = M.mf / xs;
+    const bool lasso_nobox = h.prob.loss == ASYFLEXA_LOSS_LASSO && !h.prob.lo && !h.prob.hi;
+    out->kkt_viol = lasso_nobox ? M.kkt : std::nan("");
+    out->nnz = M.nnz;
+    out->dual_gap = lasso_dual_gap(h, F, rr, br, M.atr);
+    out->checked = 1;
+    out->kernel_variant = async_variant(h);
+}
+
 int asyflexa_check(asyflexa_t h, const void* x, asyflexa_stats* out) {
     if (!h) return set_error(nullptr, ASYFLEXA_EINVAL, "h is NULL");
     if (!x || !out) return set_error(h, ASYFLEXA_EINVAL, "x or out is NULL");
@@ -634,18 +658,7 @@ int asyflexa_check(asyflexa_t h, const void* x, asyflexa_stats* out) {
     Measures M{};
     if (!rc) rc = measure(*h, x, &M);
     if (!rc) rc = device_error(*h);
-    const double fs = h->opts.f_star;
-    out->F = F;
-    out->rel_gap = std::isfinite(fs) ? (F - fs) / std::fabs(fs) : std::nan("");
-    const double xs = std::max(1.0, M.xmax);
-    out->stat_xhat = M.xh / xs;
-    out->stat_mf = M.mf / xs;
-    const bool lasso_nobox = h->prob.loss == ASYFLEXA_LOSS_LASSO && !h->prob.lo && !h->prob.hi;
-    out->kkt_viol = lasso_nobox ? M.kkt : std::nan("");
-    out->nnz = M.nnz;
-    out->dual_gap = lasso_dual_gap(*h, F, rr, br, M.atr);
-    out->checked = 1;
-    out->kernel_variant = async_variant(*h);
+    fill_check_stats(*h, F, rr, br, M, out);
     out->status = rc;
     out->kernel_launches = h->launches;
     return rc;
@@ -671,17 +684,28 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
     const bool known = std::isfinite(fs);
     long long sweeps = 0;
     int status = ASYFLEXA_ENOTCONV;
-    double F = NAN, F_prev = NAN;
+    double F = NAN, F_prev = NAN, rr = 0.0, br = 0.0;
     bool polish = false;
+    // F is evaluated on an exact residual every check_every sweeps, and the exact stationarity
+    // check follows once the gap test passes.  A stationarity check that fails within a factor
+    // kNear of tol_stat is repeated after kNearSweeps sweeps (at most check_every times): near
+    // tol_stat the stationarity of the FP32 iterates fluctuates from sweep to sweep around the
+    // level that the FP32 residual snapshot allows.
+    constexpr double kNear = 2.0;
+    constexpr int kNearSweeps = 2;
+    int next_k = h->opts.check_every, near_checks = 0;
+    bool final_ok = false;  // the last exact check describes the returned x
+    Measures Mf{};
     // With an FP32 master copy the loop below is the low-precision phase: F and the
     // stationarity are those of the FP32 problem (the refreshes use the master copy), and the
     // phase ends early when a check interval no longer lowers F by switch_tol * |F|.
     while (!rc && sweeps < h->opts.max_sweeps) {
-        const int k = static_cast<int>(std::min<long long>(h->opts.check_every, h->opts.max_sweeps - sweeps));
+        const int k = static_cast<int>(std::min<long long>(next_k, h->opts.max_sweeps - sweeps));
         rc = run_sweeps(*h, x, k);
         if (rc) break;
         sweeps += k;
-        rc = objective(*h, x, &F, nullptr);
+        next_k = h->opts.check_every;
+        rc = objective(*h, x, &F, nullptr, &rr, &br);
         if (rc) break;
         rc = device_error(*h);
         if (rc) break;
@@ -708,12 +732,17 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
         const double stat = M.xh / std::max(1.0, M.xmax);
         if (stat <= h->opts.tol_stat && (!known || gap <= h->opts.tol_gap)) {
             status = ASYFLEXA_OK;
+            final_ok = !h->master;
+            Mf = M;
             break;
         }
         if (stalled) {
             polish = true;
             break;
         }
+        if (!h->master && !h->opts.tau_adapt && stat <= kNear * h->opts.tol_stat &&
+            ++near_checks <= h->opts.check_every)
+            next_k = std::min(kNearSweeps, h->opts.check_every);
     }
     CK(h, cudaEventRecord(e1, h->stream), "event record");
     CK(h, cudaEventSynchronize(e1), "event sync");
@@ -745,7 +774,13 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
         return rc;
     }
     // final evaluation at the returned x
-    rc = asyflexa_check(h, x, &st);
+    if (final_ok) {
+        // the loop ended on an exact refresh, objective and check of this x: report them
+        fill_check_stats(*h, F, rr, br, Mf, &st);
+        rc = device_error(*h);
+    } else {
+        rc = asyflexa_check(h, x, &st);
+    }
     st.sweeps = sweeps;
     st.seconds = ms * 1e-3 + polish_seconds;
     st.polish_sweeps = polish_sweeps;

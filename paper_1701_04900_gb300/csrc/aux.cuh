@@ -399,13 +399,6 @@ __global__ void finalize_norms_kernel(const T* part, int nparts, T* out) {
 
 // ----------------------------------------------------------------------------- check
 
-// Error-free transformations (Ogita, Rump, Oishi, "Accurate sum and dot product", 2005).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    const float z = s - a;
-    e = (a - (s - z)) + (b - z);
-}
-
 template <typename TA>
 struct CheckDot;
 

@@ -294,6 +294,7 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
     io.mode = ASYFLEXA_ASYNC;
     io.block_w = opts->block_w > 0 ? opts->block_w : 32;
     io.profile = 0;
+    io.exact_grad = 0;  // the batched kernel accumulates in FP32
     for (int k = 0; k < count; ++k) {
         if (probs[k].a_dtype != ASYFLEXA_F32 || probs[k].A_master)
             return fail(bfail("batched problems use FP32 storage (problem " + std::to_string(k) + ")"));

@@ -94,6 +94,8 @@ struct asyflexa_s {
     unsigned long long* meas = nullptr;     // 8
     int* err = nullptr;                     // 1
     int* flag = nullptr;                    // 1
+    // the compensated-gradient form of the register kernel exists (FP32 storage)
+    bool reg_exact_ok = false;
 
     // profile=1: event pairs around sweep launches (start, stop, sweeps), drained on read
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_events;

@@ -2,6 +2,8 @@
 // unit per type (inst_*.cu), which instantiates Launcher<TA>.
 #pragma once
 
+#include <type_traits>
+
 #include "aux.cuh"
 #include "handle.h"
 #include "sweep.cuh"
@@ -15,33 +17,42 @@ constexpr bool reg_fits() {
     return kRegKpc * CPC * ATraits<TA>::kVec <= kRegMaxRowsPerThread;
 }
 
+template <typename TA, bool EXACT>
+const void* reg_kernel_inst(int cpc) {
+    switch (cpc) {
+        case 1:
+            if constexpr (reg_fits<TA, 1>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 1, false, EXACT>);
+            break;
+        case 2:
+            if constexpr (reg_fits<TA, 2>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 2, false, EXACT>);
+            break;
+        case 3:
+            if constexpr (reg_fits<TA, 3>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 3, false, EXACT>);
+            break;
+        case 4:
+            if constexpr (reg_fits<TA, 4>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 4, false, EXACT>);
+            break;
+        case 5:
+            if constexpr (reg_fits<TA, 5>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 5, false, EXACT>);
+            break;
+        case 6:
+            if constexpr (reg_fits<TA, 6>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 6, false, EXACT>);
+            break;
+        default: break;
+    }
+    return nullptr;
+}
+
+// The register-increment kernel instance for CPC stages per column; exact: the compensated
+// gradient form (FP32 storage only; nullptr otherwise).
 template <typename TA>
-const void* reg_kernel(int cpc) {
+const void* reg_kernel(int cpc, bool exact = false) {
     if constexpr (sizeof(typename ATraits<TA>::TC) != 4) {
         return nullptr;  // FP64 problems use the staged kernel
+    } else if constexpr (std::is_same<TA, float>::value) {
+        return exact ? reg_kernel_inst<TA, true>(cpc) : reg_kernel_inst<TA, false>(cpc);
     } else {
-        switch (cpc) {
-            case 1:
-                if constexpr (reg_fits<TA, 1>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 1>);
-                break;
-            case 2:
-                if constexpr (reg_fits<TA, 2>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 2>);
-                break;
-            case 3:
-                if constexpr (reg_fits<TA, 3>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 3>);
-                break;
-            case 4:
-                if constexpr (reg_fits<TA, 4>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 4>);
-                break;
-            case 5:
-                if constexpr (reg_fits<TA, 5>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 5>);
-                break;
-            case 6:
-                if constexpr (reg_fits<TA, 6>()) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 6>);
-                break;
-            default: break;
-        }
-        return nullptr;
+        return exact ? nullptr : reg_kernel_inst<TA, false>(cpc);
     }
 }
 
@@ -52,6 +63,7 @@ const void* reg_kernel(int cpc) {
 template <typename TA>
 int Launcher<TA>::choose_reg(asyflexa_s& h) {
     h.reg_upt = h.reg_cpc = h.reg_stages = 0;
+    h.reg_exact_ok = false;
     h.reg_smem = 0;
     const int64_t units = h.mcopy / h.vec;
     const int cpc = static_cast<int>((units + kRegStageUnits - 1) / kRegStageUnits);
@@ -69,6 +81,12 @@ int Launcher<TA>::choose_reg(asyflexa_s& h) {
     h.reg_smem = make_reg_layout(rt_rows, stages).total;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.reg_smem));
     if (e != cudaSuccess) return -static_cast<int>(e);
+    const void* fx = reg_kernel<TA>(cpc, true);
+    h.reg_exact_ok = fx != nullptr;
+    if (fx) {
+        e = cudaFuncSetAttribute(fx, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.reg_smem));
+        if (e != cudaSuccess) return -static_cast<int>(e);
+    }
     return 1;
 }
 
@@ -171,7 +189,9 @@ cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
         p.stages = h.reg_stages;
         p.tile_rows = static_cast<int>(h.mcopy);
         void* args[] = {&p};
-        const cudaError_t e = cudaLaunchKernel(reg_kernel<TA>(h.reg_cpc), dim3(h.sweep_ctas), dim3(kRegThreads), args,
+        const bool exact = h.reg_exact_ok && h.opts.exact_grad == 1;
+        const cudaError_t e = cudaLaunchKernel(reg_kernel<TA>(h.reg_cpc, exact),
+                                               dim3(h.sweep_ctas), dim3(kRegThreads), args,
                                                h.reg_smem, h.stream);
         ++h.launches;
         return e != cudaSuccess ? e : cudaGetLastError();

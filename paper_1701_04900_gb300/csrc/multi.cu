@@ -201,6 +201,7 @@ int asyflexa_multi_create(asyflexa_multi_t* out, const asyflexa_problem* prob, i
     o.mode = ASYFLEXA_ASYNC;
     o.block_w = asyflexa::kMW;
     o.profile = 0;
+    o.exact_grad = 0;  // the multi-lane kernel has its own split-TF32 arithmetic
     int rc = asyflexa_create(&H->base, &p0, &o, stream);
     if (rc) return fail(mfail(std::string("lane 0: ") + asyflexa_last_error(nullptr), rc));
     H->opts = o;

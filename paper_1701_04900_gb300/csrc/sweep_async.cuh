@@ -64,8 +64,8 @@ __host__ __device__ inline RegLayout make_reg_layout(int rt_rows, int stages) {
     o += L.stage_bytes * stages;
     L.off_rt = o;
     o = align_up_sz(o + static_cast<size_t>(rt_rows) * sizeof(float), 16);
-    L.off_colpart = o;  // two buffers of per-warp partial sums
-    o = align_up_sz(o + 2 * kRegConsWarps * sizeof(float), 16);
+    L.off_colpart = o;  // two buffers of per-warp partial sums (FP32 pairs in the compensated form)
+    o = align_up_sz(o + 2 * kRegConsWarps * 2 * sizeof(float), 16);
     L.off_coef = o;
     o = align_up_sz(o + kWMax * sizeof(ColCoef), 16);
     L.off_bars = o;
@@ -148,7 +148,35 @@ __device__ __forceinline__ BlockView<TA> block_view(const SweepParams& p, int b)
     return v;
 }
 
-template <typename TA, int CPC, bool BATCHED = false>
+// Compensated sum of the 16 warp partials (s, c) in a fixed pairwise order; every thread
+// evaluates it and gets the same value.
+__device__ __forceinline__ float sum_pairs_16(const float2* q) {
+    float s[8], c[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float e;
+        two_sum(q[2 * i].x, q[2 * i + 1].x, s[i], e);
+        c[i] = (q[2 * i].y + q[2 * i + 1].y) + e;
+    }
+#pragma unroll
+    for (int w = 4; w >= 1; w >>= 1)
+#pragma unroll
+        for (int i = 0; i < w; ++i) {
+            float t, e;
+            two_sum(s[2 * i], s[2 * i + 1], t, e);
+            c[i] = (c[2 * i] + c[2 * i + 1]) + e;
+            s[i] = t;
+        }
+    return s[0] + c[0];
+}
+
+// EXACT = true forms each block gradient g_j = a_j^T r~ with compensated arithmetic (Dot2 of
+// Ogita, Rump and Oishi per accumulation chain, TwoSum in the warp and cross-warp sums), as
+// accurate as FP64 accumulation of the FP32 snapshot r~; the plain form accumulates in FP32.
+// At the 20000-row LASSO workload the compensated form lowers the level at which
+// ||xhat(x) - x|| stops falling (the FP32 snapshot and staleness set the rest of it) and,
+// above all, its sweep-to-sweep spikes, at about 1.6x the sweep time.
+template <typename TA, int CPC, bool BATCHED = false, bool EXACT = false>
 __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const SweepParams p) {
     using TC = typename ATraits<TA>::TC;
     static_assert(sizeof(TC) == 4, "register kernel computes in FP32");
@@ -303,6 +331,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
             for (int jl = 0; jl < bv.wb; ++jl) {
                 // ---- dot a_j^T r~ over this thread's rows
                 float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+                DFAcc dacc0, dacc1, dacc2, dacc3;  // compensated chains (EXACT)
                 uint32_t st_c = stage, ph_c = phase;
                 bool ok = !*abort_flag;
 #pragma unroll 1
@@ -322,16 +351,29 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
 #pragma unroll
                                         for (int e = 0; e < V; e += 4) {
                                             const float4 r4 = *reinterpret_cast<const float4*>(rv + e);
-                                            acc0 = fmaf(a[e], r4.x, acc0);
-                                            acc1 = fmaf(a[e + 1], r4.y, acc1);
-                                            acc2 = fmaf(a[e + 2], r4.z, acc2);
-                                            acc3 = fmaf(a[e + 3], r4.w, acc3);
+                                            if constexpr (EXACT) {
+                                                dacc0.add_prod(a[e], r4.x);
+                                                dacc1.add_prod(a[e + 1], r4.y);
+                                                dacc2.add_prod(a[e + 2], r4.z);
+                                                dacc3.add_prod(a[e + 3], r4.w);
+                                            } else {
+                                                acc0 = fmaf(a[e], r4.x, acc0);
+                                                acc1 = fmaf(a[e + 1], r4.y, acc1);
+                                                acc2 = fmaf(a[e + 2], r4.z, acc2);
+                                                acc3 = fmaf(a[e + 3], r4.w, acc3);
+                                            }
                                         }
                                     } else {
                                         const int valid = static_cast<int>(bv.m - u * V);
 #pragma unroll
-                                        for (int e = 0; e < V; ++e)
-                                            if (e < valid) acc0 = fmaf(a[e], rv[e], acc0);
+                                        for (int e = 0; e < V; ++e) {
+                                            if (e < valid) {
+                                                if constexpr (EXACT)
+                                                    dacc0.add_prod(a[e], rv[e]);
+                                                else
+                                                    acc0 = fmaf(a[e], rv[e], acc0);
+                                            }
+                                        }
                                     }
                                 }
                             }
@@ -342,18 +384,44 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                         }
                     }
                 }
-                const float v = warp_sum((acc0 + acc1) + (acc2 + acc3));
-                float* cp = colpart + buf * kRegConsWarps;
-                if (lane == 0) cp[warp] = v;
+                static_assert(kRegConsWarps == 16, "the sums below read 16 warp partials");
+                float* cp = colpart + buf * kRegConsWarps * (EXACT ? 2 : 1);
+                if constexpr (EXACT) {
+                    float ts, tc;
+                    {
+                        float t1, e1, t2, e2, e;
+                        two_sum(dacc0.s, dacc1.s, t1, e1);
+                        two_sum(dacc2.s, dacc3.s, t2, e2);
+                        two_sum(t1, t2, ts, e);
+                        tc = ((dacc0.c + dacc1.c) + (dacc2.c + dacc3.c)) + ((e1 + e2) + e);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {  // both lanes of a pair form the same exact sum
+                        const float so = __shfl_xor_sync(0xffffffffu, ts, o);
+                        const float co = __shfl_xor_sync(0xffffffffu, tc, o);
+                        float t, e;
+                        two_sum(ts, so, t, e);
+                        tc = (tc + co) + e;
+                        ts = t;
+                    }
+                    if (lane == 0) reinterpret_cast<float2*>(cp)[warp] = make_float2(ts, tc);
+                } else {
+                    const float v = warp_sum((acc0 + acc1) + (acc2 + acc3));
+                    if (lane == 0) cp[warp] = v;
+                }
                 const ColCoef cf = coef[jl];  // written before the block's first barrier
                 named_bar_sync(1, kRegConsThreads);
                 // ---- best response (eq. 2) + fixed step (S.4): every consumer thread sums the 16
                 // warp partials in the same fixed order, so all agree on g and Delta_j
-                static_assert(kRegConsWarps == 16, "the sum below reads 16 warp partials");
-                const float4* cp4 = reinterpret_cast<const float4*>(cp);
-                const float4 q0 = cp4[0], q1 = cp4[1], q2 = cp4[2], q3 = cp4[3];
-                const float g = (((q0.x + q0.y) + (q0.z + q0.w)) + ((q1.x + q1.y) + (q1.z + q1.w))) +
-                                (((q2.x + q2.y) + (q2.z + q2.w)) + ((q3.x + q3.y) + (q3.z + q3.w)));
+                float g;
+                if constexpr (EXACT) {
+                    g = sum_pairs_16(reinterpret_cast<const float2*>(cp));
+                } else {
+                    const float4* cp4 = reinterpret_cast<const float4*>(cp);
+                    const float4 q0 = cp4[0], q1 = cp4[1], q2 = cp4[2], q3 = cp4[3];
+                    g = (((q0.x + q0.y) + (q0.z + q0.w)) + ((q1.x + q1.y) + (q1.z + q1.w))) +
+                        (((q2.x + q2.y) + (q2.z + q2.w)) + ((q3.x + q3.y) + (q3.z + q3.w)));
+                }
                 buf ^= 1;
                 const float grad = bv.s_loss * g * cf.scale - bv.c2 * cf.x + cf.lin;
                 float xh = 0.f;

@@ -83,6 +83,13 @@ __device__ __forceinline__ double fmac(double a, double b, double c) { return ::
 // Comput. 26(6), 2005).  The result is as accurate as a dot product computed in twice the
 // working precision, without FP64 arithmetic in the loop (FP64 throughput on GB300 is a
 // small fraction of FP32).
+// TwoSum (Knuth): s = fl(a + b) and s + e = a + b exactly (Ogita, Rump, Oishi 2005).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
 struct DFAcc {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add_prod(float a, float b) {

@@ -45,7 +45,7 @@ class Opts(C.Structure):
         ("tol_gap", C.c_double), ("tol_stat", C.c_double), ("f_star", C.c_double),
         ("seed", C.c_uint64), ("profile", C.c_int32), ("variant", C.c_int32),
         ("switch_tol", C.c_double), ("gamma_mu", C.c_double),
-        ("tau_adapt", C.c_int32), ("reserved3", C.c_int32),
+        ("tau_adapt", C.c_int32), ("exact_grad", C.c_int32),
     ]
 
 
@@ -189,7 +189,7 @@ class Solver:
                  block_w=32, mode="sync", gamma=0.9, tau=0.0, tau_rel=0.0, refresh_every=10,
                  check_every=10, max_sweeps=1000, num_ctas=0, tol_gap=1e-6, tol_stat=1e-6,
                  f_star=math.nan, profile=False, variant=0, A_master=None, switch_tol=1e-7, lin=None,
-                 gamma_mu=0.0, tau_adapt=False, stream=None):
+                 gamma_mu=0.0, tau_adapt=False, exact_grad=0, stream=None):
         import torch
         L = lib()
         if At.dim() != 2 or not At.is_contiguous() or not At.is_cuda:
@@ -226,6 +226,7 @@ class Solver:
         o.switch_tol = float(switch_tol)
         o.gamma_mu = float(gamma_mu)
         o.tau_adapt = 1 if tau_adapt else 0
+        o.exact_grad = int(exact_grad)
         self.problem, self.opts = p, o
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream

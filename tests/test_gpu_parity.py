@@ -610,3 +610,61 @@ def test_adaptive_tau_leaves_a_descent_run_unchanged():
     st = s.solve(x)
     assert st["tau_extra"] == 0.0
     assert rel_inf(x.cpu().numpy(), x_ref) < TOL64
+
+
+# ----------------------------------------------------------------------------- compensated gradient
+
+@pytest.mark.parametrize("m,w", [(301, 1), (301, 32), (17001, 8), (20477, 32)])
+def test_async_single_cta_exact_grad_equals_gauss_seidel(m, w):
+    """exact_grad = 1 (Dot2 accumulation of a_j^T r~): one CTA is still cyclic Gauss-Seidel, now
+    within 2e-6 of the FP64 oracle (the FP32 snapshot of r and the FP32 x remain)."""
+    import torch
+    d = random_lasso(m, 64, seed=m + w, lam=0.3, dist="gauss", store_dtype=np.float32, box=0.8)
+    p = O.Problem.from_data(d)
+    dw = O.surrogate_weights(p, tau=0.2)
+    x_ref, r_ref = np.zeros(p.n), O.residual(p, np.zeros(p.n))
+    s = make_solver(d, block_w=w, mode="async", tau=0.2, num_ctas=1, refresh_every=100, variant=2, exact_grad=1)
+    x = xzeros(d, torch.float32)
+    for sweep in range(3):
+        x_ref, r_ref = O.gauss_seidel_sweep(p, x_ref, r_ref, dw, 0.9, w=w)
+        s.step(x, 1)
+        assert rel_inf(x.cpu().numpy(), x_ref) < 2e-6, sweep
+
+
+def test_exact_grad_option_is_validated():
+    from paper_1701_04900_gb300 import AsyflexaError
+    d32 = random_lasso(300, 16, seed=3, store_dtype=np.float32)
+    d64 = random_lasso(300, 16, seed=3, store_dtype=np.float64)
+    for d, kw in ((d64, {"mode": "async"}), (d32, {"mode": "sync"}), (d32, {"mode": "async", "variant": 1})):
+        with pytest.raises(AsyflexaError) as ei:
+            make_solver(d, exact_grad=1, **kw)
+        assert ei.value.code == -6, kw
+    with pytest.raises(AsyflexaError) as ei:
+        make_solver(d32, mode="async", exact_grad=2)
+    assert ei.value.code == -1
+
+
+@pytest.mark.parametrize("known", [True, False])
+@pytest.mark.parametrize("exact_grad", [0, 1])
+def test_solve_stats_are_an_exact_check_of_the_result(known, exact_grad):
+    """Whatever the check schedule, the solve stops on an exact check and returns its values:
+    a separate check of the returned x gives the same F and stationarity, and both tolerances
+    hold for the returned x against the oracle."""
+    import torch
+    d = nesterov_lasso(3000, 12000, 120, lam=1.0, seed=21, store_dtype=np.float32)
+    p = O.Problem.from_data(d)
+    f_ref = O.objective(p, d["x_star"])
+    s = make_solver(d, block_w=32, mode="async", gamma=0.9, f_star=f_ref if known else math.nan,
+                    tol_stat=1e-6, max_sweeps=3000, check_every=10, refresh_every=10, num_ctas=24, variant=2,
+                    exact_grad=exact_grad)
+    x = xzeros(d, torch.float32)
+    st = s.solve(x)
+    assert st["status"] == 0, st
+    assert st["stat_xhat"] <= 1e-6
+    chk = s.check(x)
+    assert abs(chk["F"] - st["F"]) <= 1e-12 * abs(st["F"])
+    assert abs(chk["stat_xhat"] - st["stat_xhat"]) <= 1e-9 * max(st["stat_xhat"], 1e-30) + 1e-15
+    xg = x.cpu().numpy().astype(np.float64)
+    assert O.stationarity(O.xhat_merit(p, xg, O.surrogate_weights(p)), xg) <= 1.5e-6
+    if known:
+        assert st["rel_gap"] <= 1e-6 and (O.objective(p, xg) - f_ref) / f_ref <= 1.5e-6
