@@ -474,40 +474,27 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
             // (the abort flag is read once per warp: the FP32 path below shuffles within the warp)
             const bool aborted = __shfl_sync(0xffffffffu, *abort_flag != 0, 0);
             if (any && !aborted) {
-                if constexpr (V == 4) {
-                    // The warp's units k*512 + 32*warp + l (l < 32) cover 128 consecutive rows; a
-                    // thread holds 4 consecutive ones.  Transposed through shuffles, so that in
-                    // round q lane l adds row 32 q + l of that span: every red instruction then
-                    // covers 32 consecutive doubles (8 whole sectors) instead of 32 rows 32 bytes
-                    // apart.
+                // The warp's units k*512 + 32*warp + l (l < 32) cover 32 V consecutive rows; a thread
+                // holds V consecutive ones.  Transposed through shuffles, so that in round q lane l
+                // adds row 32 q + l of that span (element l mod V of the unit held by lane
+                // q 32/V + l/V): every red instruction then covers 32 consecutive doubles (8 whole
+                // sectors) instead of 32 rows 8 V bytes apart.
+                static_assert(32 % V == 0, "units of at most 32 rows");
 #pragma unroll
-                    for (int k = 0; k < UPT; ++k) {
-                        const int64_t row0 = (static_cast<int64_t>(k) * kRegConsThreads + warp * 32) * V;
+                for (int k = 0; k < UPT; ++k) {
+                    const int64_t row0 = (static_cast<int64_t>(k) * kRegConsThreads + warp * 32) * V;
 #pragma unroll
-                        for (int q = 0; q < V; ++q) {
-                            const int src = q * 8 + (lane >> 2);  // the lane holding row 32 q + lane
-                            const int esel = lane & 3;            // and its element there
-                            float v = 0.f;
+                    for (int q = 0; q < V; ++q) {
+                        const int src = q * (32 / V) + lane / V;
+                        const int esel = lane % V;
+                        float v = 0.f;
 #pragma unroll
-                            for (int e = 0; e < V; ++e) {
-                                const float t = __shfl_sync(0xffffffffu, inc[k][e], src);
-                                v = e == esel ? t : v;
-                            }
-                            const int64_t row = row0 + q * 32 + lane;
-                            if (row < bv.m && v != 0.f) red_add_f64(bv.r + row, f32_to_f64(v));
+                        for (int e = 0; e < V; ++e) {
+                            const float t = __shfl_sync(0xffffffffu, inc[k][e], src);
+                            v = e == esel ? t : v;
                         }
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < UPT; ++k) {
-                        const int64_t u = static_cast<int64_t>(k) * kRegConsThreads + tid;
-                        if (u < units) {
-#pragma unroll
-                            for (int e = 0; e < V; ++e) {
-                                const int64_t row = u * V + e;
-                                if (row < bv.m && inc[k][e] != 0.f) red_add_f64(bv.r + row, f32_to_f64(inc[k][e]));
-                            }
-                        }
+                        const int64_t row = row0 + q * 32 + lane;
+                        if (row < bv.m && v != 0.f) red_add_f64(bv.r + row, f32_to_f64(v));
                     }
                 }
                 // A single CTA runs its blocks strictly in order (cyclic Gauss-Seidel), so its
