@@ -338,7 +338,27 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 for (int c = 0; c < CPC; ++c) {
                     if (c < nchunks) {
                         if (ok) ok = mbar_wait_bounded(&full[st_c], ph_c, abort_flag, p.err);
-                        if (ok) {
+                        // a stage whose units all hold rows < m (every stage but a column's last
+                        // when m is not a multiple of the stage rows) needs no per-unit checks
+                        const bool whole = static_cast<int64_t>(c + 1) * kRegStageUnits <= units_full;
+                        if (ok && whole && !EXACT) {
+                            const uint4* src = reinterpret_cast<const uint4*>(ring + st_c * L.stage_bytes);
+#pragma unroll
+                            for (int kk = 0; kk < kRegKpc; ++kk) {
+                                const int64_t u = static_cast<int64_t>(c * kRegKpc + kk) * kRegConsThreads + tid;
+                                float a[V];
+                                ATraits<TA>::unpack(src[kk * kRegConsThreads + tid], a);
+                                const float* rv = rt + u * V;
+#pragma unroll
+                                for (int e = 0; e < V; e += 4) {
+                                    const float4 r4 = *reinterpret_cast<const float4*>(rv + e);
+                                    acc0 = fmaf(a[e], r4.x, acc0);
+                                    acc1 = fmaf(a[e + 1], r4.y, acc1);
+                                    acc2 = fmaf(a[e + 2], r4.z, acc2);
+                                    acc3 = fmaf(a[e + 3], r4.w, acc3);
+                                }
+                            }
+                        } else if (ok) {
                             const uint4* src = reinterpret_cast<const uint4*>(ring + st_c * L.stage_bytes);
 #pragma unroll
                             for (int kk = 0; kk < kRegKpc; ++kk) {
@@ -447,15 +467,26 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                     if (c < nchunks) {
                         if (dj != 0.f) {
                             const uint4* src = reinterpret_cast<const uint4*>(ring + st_c * L.stage_bytes);
+                            if (static_cast<int64_t>(c + 1) * kRegStageUnits <= units) {  // every unit present
 #pragma unroll
-                            for (int kk = 0; kk < kRegKpc; ++kk) {
-                                const int k = c * kRegKpc + kk;
-                                const int64_t u = static_cast<int64_t>(k) * kRegConsThreads + tid;
-                                if (u < units) {
+                                for (int kk = 0; kk < kRegKpc; ++kk) {
+                                    const int k = c * kRegKpc + kk;
                                     float a[V];
                                     ATraits<TA>::unpack(src[kk * kRegConsThreads + tid], a);
 #pragma unroll
                                     for (int e = 0; e < V; ++e) inc[k][e] = fmaf(a[e], dj, inc[k][e]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int kk = 0; kk < kRegKpc; ++kk) {
+                                    const int k = c * kRegKpc + kk;
+                                    const int64_t u = static_cast<int64_t>(k) * kRegConsThreads + tid;
+                                    if (u < units) {
+                                        float a[V];
+                                        ATraits<TA>::unpack(src[kk * kRegConsThreads + tid], a);
+#pragma unroll
+                                        for (int e = 0; e < V; ++e) inc[k][e] = fmaf(a[e], dj, inc[k][e]);
+                                    }
                                 }
                             }
                         }
