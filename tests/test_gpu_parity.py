@@ -205,11 +205,12 @@ def test_async_single_cta_equals_gauss_seidel(store, tol, variant, w):
         assert rel_inf(x.cpu().numpy(), x_ref) < tol, sweep
 
 
-@pytest.mark.parametrize("m", [1021, 5003, 9001, 17001, 20477, 24571])
+@pytest.mark.parametrize("m", [1021, 5003, 8192, 9001, 16384, 17001, 20477, 24571])
 @pytest.mark.parametrize("variant", [1, 2])
 def test_async_single_cta_shapes(m, variant):
     """Column lengths spanning 1..6 shared-memory stages of the register kernels (ragged last
-    unit included), against Gauss-Seidel."""
+    unit included; 8192 and 16384 fill every stage, so no stage takes the checked path),
+    against Gauss-Seidel."""
     import torch
     d = random_lasso(m, 48, seed=m, lam=0.2, dist="gauss", store_dtype=np.float32, box=2.0)
     p = O.Problem.from_data(d)
