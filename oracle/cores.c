@@ -2,8 +2,8 @@
  * experiments in Section 4 (variables partitioned among the cores, one core per partition,
  * no locks), used to time the method against the number of cores as Section 4.2 does.
  *
- * TEST AND BASELINE INFRASTRUCTURE ONLY: loaded by the tests and by the CPU-baseline leg of
- * the benchmark, never by the product path.  Plain C, no blocking or vectorisation beyond
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests and by the CPU timing leg of the benchmark,
+ * never by the product path.  Plain C, no blocking or vectorisation beyond
  * what the compiler does on its own; the GPU library shares nothing with it.
  *
  * Problem (Section 4.2): F(x) = 0.5 ||Ax - b||^2 + lam ||x||_1 over R^n, A m x n stored in

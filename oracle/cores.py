@@ -3,7 +3,7 @@ Algorithm 1 for LASSO (Section 4.2), FP64, timed against the number of cores, wi
 threads sharing the residual r = Ax - b (residual form) or x with A^T A precomputed (Gram
 form, the setup of the paper's experiments).
 
-TEST AND BASELINE INFRASTRUCTURE ONLY (see ``cores.c``).  The library is compiled with gcc
+TEST INFRASTRUCTURE ONLY (see ``cores.c``).  The library is compiled with gcc
 on first use into ``oracle/_build/``.
 """
 

@@ -1,7 +1,7 @@
 """Build the CUDA C-ABI library ``libasyflexa.so`` in-tree for sm_103a with nvcc.
 
 Each translation unit compiles in parallel; the result is linked with the static CUDA
-runtime so the library only needs the driver at run time.  Usage:
+runtime so the library only needs the CUDA driver at run time.  Usage:
 
     python -m paper_1701_04900_gb300.build          # build if sources changed
     python -m paper_1701_04900_gb300.build --force  # always rebuild
