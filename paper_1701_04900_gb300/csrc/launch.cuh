@@ -56,6 +56,18 @@ const void* reg_kernel(int cpc, bool exact = false) {
     }
 }
 
+// Instances holding fewer units per thread than 2 per stage: FP8 columns of up to 24576 rows
+// (1536 units of 16 rows) span 2 stages but need only 3 units per thread.
+template <typename TA>
+const void* reg_kernel_partial(int cpc, int upt) {
+    if constexpr (std::is_same<TA, __nv_fp8_e4m3>::value) {
+        if (cpc == 2 && upt <= 3) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 2, false, false, 3>);
+    }
+    (void)cpc;
+    (void)upt;
+    return nullptr;
+}
+
 // Choose the register-increment kernel instance that covers the column (sets h.reg_*).
 // Returns 0 if none applies (the staged kernel is used), 1 if chosen, or a negative
 // cudaError_t if setting its shared-memory attribute failed.  The ring must hold one
@@ -68,14 +80,20 @@ int Launcher<TA>::choose_reg(asyflexa_s& h) {
     const int64_t units = h.mcopy / h.vec;
     const int cpc = static_cast<int>((units + kRegStageUnits - 1) / kRegStageUnits);
     if (cpc < 1 || cpc > 6) return 0;
+    const int upt_needed = static_cast<int>((units + kRegConsThreads - 1) / kRegConsThreads);
     const void* fn = reg_kernel<TA>(cpc);
+    int upt = kRegKpc * cpc;
+    if (!fn) {
+        fn = reg_kernel_partial<TA>(cpc, upt_needed);
+        upt = 3;
+    }
     if (!fn) return 0;
     const int rt_rows = static_cast<int>(h.mcopy);
     const RegLayout L0 = make_reg_layout(rt_rows, 0);
     if (L0.total + 512 + static_cast<size_t>(cpc + 1) * L0.stage_bytes > h.smem_optin) return 0;
     int stages = static_cast<int>((h.smem_optin - L0.total - 512) / L0.stage_bytes);
     if (stages > 16) stages = 16;
-    h.reg_upt = kRegKpc * cpc;
+    h.reg_upt = upt;
     h.reg_cpc = cpc;
     h.reg_stages = stages;
     h.reg_smem = make_reg_layout(rt_rows, stages).total;
@@ -190,7 +208,9 @@ cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
         p.tile_rows = static_cast<int>(h.mcopy);
         void* args[] = {&p};
         const bool exact = h.reg_exact_ok && h.opts.exact_grad == 1;
-        const cudaError_t e = cudaLaunchKernel(reg_kernel<TA>(h.reg_cpc, exact),
+        const void* fn = h.reg_upt == kRegKpc * h.reg_cpc ? reg_kernel<TA>(h.reg_cpc, exact)
+                                                          : reg_kernel_partial<TA>(h.reg_cpc, h.reg_upt);
+        const cudaError_t e = cudaLaunchKernel(fn,
                                                dim3(h.sweep_ctas), dim3(kRegThreads), args,
                                                h.reg_smem, h.stream);
         ++h.launches;

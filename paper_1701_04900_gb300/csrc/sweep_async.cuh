@@ -1,5 +1,5 @@
 // Asynchronous sweep kernel with a register-resident block increment (FP32/BF16/FP8
-// storage; m up to 24576 rows for FP32/BF16 and 16384 for FP8).
+// storage; m up to 24576 rows).
 //
 // Same method step as sweep.cuh (Algorithm 1, S.1-S.5; eq. 2 best response; Section 4
 // surrogate), organised so that A is read from HBM exactly once per sweep even when many
@@ -176,14 +176,17 @@ __device__ __forceinline__ float sum_pairs_16(const float2* q) {
 // At the 20000-row LASSO workload the compensated form lowers the level at which
 // ||xhat(x) - x|| stops falling (the FP32 snapshot and staleness set the rest of it) and,
 // above all, its sweep-to-sweep spikes, at about 1.6x the sweep time.
-template <typename TA, int CPC, bool BATCHED = false, bool EXACT = false>
+// UPTX > 0: this thread's units per column when fewer than the 2 per stage of CPC stages
+// (the column's last stage only partly filled), so that fewer increment registers are held.
+template <typename TA, int CPC, bool BATCHED = false, bool EXACT = false, int UPTX = 0>
 __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const SweepParams p) {
     using TC = typename ATraits<TA>::TC;
     static_assert(sizeof(TC) == 4, "register kernel computes in FP32");
     using TX = typename XType<TA>::T;
     static_assert(sizeof(TX) == 4, "register kernel updates FP32 x");
     constexpr int V = ATraits<TA>::kVec;
-    constexpr int UPT = kRegKpc * CPC;
+    constexpr int UPT = UPTX > 0 ? UPTX : kRegKpc * CPC;
+    static_assert(UPT <= kRegKpc * CPC, "units beyond the column's stages");
     static_assert(UPT * V <= kRegMaxRowsPerThread, "too many rows per thread");
 
     extern __shared__ __align__(128) unsigned char smem[];
@@ -471,17 +474,19 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
 #pragma unroll
                                 for (int kk = 0; kk < kRegKpc; ++kk) {
                                     const int k = c * kRegKpc + kk;
-                                    float a[V];
-                                    ATraits<TA>::unpack(src[kk * kRegConsThreads + tid], a);
+                                    if (k < UPT) {  // compile-time: units k >= UPT lie past the column
+                                        float a[V];
+                                        ATraits<TA>::unpack(src[kk * kRegConsThreads + tid], a);
 #pragma unroll
-                                    for (int e = 0; e < V; ++e) inc[k][e] = fmaf(a[e], dj, inc[k][e]);
+                                        for (int e = 0; e < V; ++e) inc[k][e] = fmaf(a[e], dj, inc[k][e]);
+                                    }
                                 }
                             } else {
 #pragma unroll
                                 for (int kk = 0; kk < kRegKpc; ++kk) {
                                     const int k = c * kRegKpc + kk;
                                     const int64_t u = static_cast<int64_t>(k) * kRegConsThreads + tid;
-                                    if (u < units) {
+                                    if (k < UPT && u < units) {
                                         float a[V];
                                         ATraits<TA>::unpack(src[kk * kRegConsThreads + tid], a);
 #pragma unroll

@@ -247,9 +247,20 @@ def test_async_single_cta_ncquad_box_equals_gauss_seidel(m, n, variant):
 @pytest.mark.parametrize("kind", ["bf16", "fp8"])
 @pytest.mark.parametrize("variant", [1, 2])
 def test_async_single_cta_quantized(kind, variant):
+    _single_cta_quantized(kind, variant, 3001)
+
+
+@pytest.mark.parametrize("m", [16385, 20000, 24576])
+def test_async_single_cta_fp8_two_stage_columns(m):
+    """FP8 columns of 16385..24576 rows span 2 shared-memory stages but need only 3 units per
+    thread: the register kernel's partial-unit instance, against Gauss-Seidel."""
+    _single_cta_quantized("fp8", 2, m, n=96)
+
+
+def _single_cta_quantized(kind, variant, m, n=300):
     import torch
     from paper_1701_04900_gb300 import Solver
-    d = random_lasso(3001, 300, seed=17, lam=0.02, dist="gauss", store_dtype=np.float32)
+    d = random_lasso(m, n, seed=17, lam=0.02, dist="gauss", store_dtype=np.float32)
     q, scale, deq = quantize_columns(d["At"], d["m"], kind)
     p = O.Problem(A=deq.T, b=d["b"].astype(np.float64), lam=d["lam"])
     dw = O.surrogate_weights(p, tau=0.1)
