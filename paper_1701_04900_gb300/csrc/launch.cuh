@@ -56,15 +56,28 @@ const void* reg_kernel(int cpc, bool exact = false) {
     }
 }
 
-// Instances holding fewer units per thread than 2 per stage: FP8 columns of up to 24576 rows
-// (1536 units of 16 rows) span 2 stages but need only 3 units per thread.
+// Instances holding fewer units per thread than 2 per stage, for columns whose last stage is
+// only partly filled: FP8 columns of up to 24576 rows (1536 units of 16 rows) span 2 stages
+// but need 3 units per thread; BF16 columns of up to 20480 rows need 5 of the 6.  Returns the
+// instance for cpc stages and at most `upt` units per thread (its unit count in *upt_out), or
+// nullptr.
 template <typename TA>
-const void* reg_kernel_partial(int cpc, int upt) {
+const void* reg_kernel_partial(int cpc, int upt, int* upt_out) {
     if constexpr (std::is_same<TA, __nv_fp8_e4m3>::value) {
-        if (cpc == 2 && upt <= 3) return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 2, false, false, 3>);
+        if (cpc == 2 && upt <= 3) {
+            *upt_out = 3;
+            return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 2, false, false, 3>);
+        }
+    }
+    if constexpr (std::is_same<TA, __nv_bfloat16>::value) {
+        if (cpc == 3 && upt <= 5) {
+            *upt_out = 5;
+            return reinterpret_cast<const void*>(sweep_async_reg_kernel<TA, 3, false, false, 5>);
+        }
     }
     (void)cpc;
     (void)upt;
+    (void)upt_out;
     return nullptr;
 }
 
@@ -81,12 +94,10 @@ int Launcher<TA>::choose_reg(asyflexa_s& h) {
     const int cpc = static_cast<int>((units + kRegStageUnits - 1) / kRegStageUnits);
     if (cpc < 1 || cpc > 6) return 0;
     const int upt_needed = static_cast<int>((units + kRegConsThreads - 1) / kRegConsThreads);
-    const void* fn = reg_kernel<TA>(cpc);
+    // the instance holding the fewest units per thread that covers the column
     int upt = kRegKpc * cpc;
-    if (!fn) {
-        fn = reg_kernel_partial<TA>(cpc, upt_needed);
-        upt = 3;
-    }
+    const void* fn = reg_kernel_partial<TA>(cpc, upt_needed, &upt);
+    if (!fn) fn = reg_kernel<TA>(cpc);
     if (!fn) return 0;
     const int rt_rows = static_cast<int>(h.mcopy);
     const RegLayout L0 = make_reg_layout(rt_rows, 0);
@@ -208,8 +219,9 @@ cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
         p.tile_rows = static_cast<int>(h.mcopy);
         void* args[] = {&p};
         const bool exact = h.reg_exact_ok && h.opts.exact_grad == 1;
+        int upt_unused = 0;
         const void* fn = h.reg_upt == kRegKpc * h.reg_cpc ? reg_kernel<TA>(h.reg_cpc, exact)
-                                                          : reg_kernel_partial<TA>(h.reg_cpc, h.reg_upt);
+                                                          : reg_kernel_partial<TA>(h.reg_cpc, h.reg_upt, &upt_unused);
         const cudaError_t e = cudaLaunchKernel(fn,
                                                dim3(h.sweep_ctas), dim3(kRegThreads), args,
                                                h.reg_smem, h.stream);
