@@ -280,18 +280,23 @@ int asyflexa_get_weights(asyflexa_t h, double* d_out);
  * value a call reads is written earlier in the same call, so nothing needs clearing. */
 int asyflexa_residual_noalloc(const asyflexa_problem* prob, const void* x, double* r_out, void* cuda_stream);
 
-/* Diagnostic: run the kernels' own FP32 <-> FP64 conversions over an array.  The kernels
- * convert the FP64 residual to its FP32 snapshot (step S.2 of Algorithm 1) and each FP32
- * scatter increment to the FP64 reduction operand with integer operations on the IEEE 754
- * fields instead of the conversion instructions; this entry point exposes exactly those
- * functions so that a test can compare them bit for bit with round-to-nearest-even.
+/* Diagnostic: run the kernels' own number conversions over an array.  The kernels convert
+ * the FP64 residual to its FP32 snapshot (step S.2 of Algorithm 1) and each FP32 scatter
+ * increment to the FP64 reduction operand with integer operations on the IEEE 754 fields
+ * instead of the conversion instructions, and decode BF16 / FP8-e4m3 storage of A to FP32;
+ * this entry point exposes exactly those functions so that a test can compare them bit for
+ * bit with round-to-nearest-even and with the storage formats' definitions.
  *
  * dir 0: in = n doubles, out = n floats (FP64 -> FP32, round to nearest even);
- * dir 1: in = n floats, out = n doubles (FP32 -> FP64, exact).
- * in, out: caller-owned device buffers; cuda_stream: the stream the kernel is enqueued on
- * (NULL = legacy default stream); the call does not synchronise.  Returns ASYFLEXA_OK, or
- * ASYFLEXA_EINVAL (bad dir, n < 0, NULL buffers with n > 0) / ASYFLEXA_ECUDA (launch
- * failure) with a message in asyflexa_last_error(NULL). */
+ * dir 1: in = n floats, out = n doubles (FP32 -> FP64, exact);
+ * dir 2: in = n FP8-e4m3 bytes, out = n floats (exact; the NaN codes 0x7f / 0xff give NaN);
+ * dir 3: in = n BF16 values, out = n floats (exact).
+ * For dir 2 and 3, n is a multiple of 16 and 8 (whole 16-byte units) and `in` is 16-byte
+ * aligned.  in, out: caller-owned device buffers; cuda_stream: the stream the kernel is
+ * enqueued on (NULL = legacy default stream); the call does not synchronise.  Returns
+ * ASYFLEXA_OK, or ASYFLEXA_EINVAL (bad dir, n < 0, n not a whole number of units, NULL
+ * buffers with n > 0, misaligned `in`) / ASYFLEXA_ECUDA (launch failure) with a message in
+ * asyflexa_last_error(NULL). */
 int asyflexa_convert_check(int dir, const void* in, void* out, int64_t n, void* cuda_stream);
 
 /* Per-column scaled low-precision storage of an FP32 matrix, for the BF16/FP8 form of the

@@ -1,12 +1,16 @@
 // Diagnostic entry point asyflexa_convert_check: runs the kernels' own FP32 <-> FP64
-// conversions (convert.cuh) over a caller's array, so that they can be compared bit for bit
-// with IEEE 754 round-to-nearest-even conversions computed elsewhere.
+// conversions (convert.cuh) and their decoding of BF16 / FP8-e4m3 storage (ATraits in
+// types.cuh) over a caller's array, so that they can be compared bit for bit with IEEE 754
+// conversions and the formats' definitions computed elsewhere.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
 #include <string>
 
 #include "../../include/asyflexa.h"
 #include "convert.cuh"
+#include "types.cuh"
 
 namespace asyflexa_internal {
 void set_thread_error(const std::string& msg);
@@ -25,6 +29,19 @@ __global__ void __launch_bounds__(256) convert_kernel(int dir, const void* in, v
     }
 }
 
+// One 16-byte unit of stored elements per thread, decoded by the same unpack the kernels use.
+template <typename TA>
+__global__ void __launch_bounds__(256) decode_kernel(const uint4* in, float* out, int64_t units) {
+    constexpr int V = asyflexa::ATraits<TA>::kVec;
+    for (int64_t u = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; u < units;
+         u += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float a[V];
+        asyflexa::ATraits<TA>::unpack(in[u], a);
+#pragma unroll
+        for (int k = 0; k < V; ++k) out[u * V + k] = a[k];
+    }
+}
+
 int fail(int code, const std::string& m) {
     asyflexa_internal::set_thread_error(m);
     return code;
@@ -33,14 +50,28 @@ int fail(int code, const std::string& m) {
 }  // namespace
 
 extern "C" int asyflexa_convert_check(int dir, const void* in, void* out, int64_t n, void* cuda_stream) {
-    if (dir != 0 && dir != 1) return fail(ASYFLEXA_EINVAL, "dir must be 0 (FP64 -> FP32) or 1 (FP32 -> FP64)");
+    if (dir < 0 || dir > 3)
+        return fail(ASYFLEXA_EINVAL, "dir must be 0 (FP64 -> FP32), 1 (FP32 -> FP64), 2 (FP8-e4m3 -> FP32) or "
+                                     "3 (BF16 -> FP32)");
     if (n < 0) return fail(ASYFLEXA_EINVAL, "n must be >= 0");
+    const int vec = dir == 2 ? 16 : dir == 3 ? 8 : 1;
+    if (n % vec != 0) return fail(ASYFLEXA_EINVAL, "n must be a multiple of 16 (dir 2) or 8 (dir 3)");
     if (n == 0) return ASYFLEXA_OK;
     if (!in || !out) return fail(ASYFLEXA_EINVAL, "in or out is NULL");
+    if (dir >= 2 && reinterpret_cast<uintptr_t>(in) % 16 != 0)
+        return fail(ASYFLEXA_EINVAL, "in must be 16-byte aligned for dir 2 and 3");
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-    const int64_t want = (n + 255) / 256;
+    const int64_t want = (n / vec + 255) / 256;
     const int blocks = static_cast<int>(want < 4096 ? want : 4096);
-    convert_kernel<<<blocks, 256, 0, st>>>(dir, in, out, n);
+    if (dir == 2) {
+        decode_kernel<__nv_fp8_e4m3><<<blocks, 256, 0, st>>>(static_cast<const uint4*>(in), static_cast<float*>(out),
+                                                              n / vec);
+    } else if (dir == 3) {
+        decode_kernel<__nv_bfloat16><<<blocks, 256, 0, st>>>(static_cast<const uint4*>(in), static_cast<float*>(out),
+                                                              n / vec);
+    } else {
+        convert_kernel<<<blocks, 256, 0, st>>>(dir, in, out, n);
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ASYFLEXA_ECUDA, std::string("convert_check launch: ") + cudaGetErrorString(e));
     return ASYFLEXA_OK;

@@ -323,14 +323,27 @@ class Solver:
         self.close()
 
 
-def convert_check(src, stream=None):
-    """The kernels' own FP32 <-> FP64 conversions (asyflexa_convert_check) applied to a CUDA
-    tensor: float64 -> float32 (round to nearest even) or float32 -> float64 (exact)."""
+def convert_check(src, stream=None, storage: str | None = None):
+    """The kernels' own conversions (asyflexa_convert_check) applied to a CUDA tensor:
+    float64 -> float32 (round to nearest even), float32 -> float64 (exact), or, with
+    ``storage`` = "fp8" / "bf16", the decoding of stored A elements (a uint8 tensor of e4m3
+    codes or a bfloat16 tensor) to float32."""
     import torch
-    if not src.is_cuda or not src.is_contiguous() or src.dtype not in (torch.float64, torch.float32):
-        raise ValueError("src must be a contiguous float64 or float32 CUDA tensor")
-    d = 0 if src.dtype == torch.float64 else 1
-    out = torch.empty(src.shape, dtype=torch.float32 if d == 0 else torch.float64, device=src.device)
+    if not src.is_cuda or not src.is_contiguous():
+        raise ValueError("src must be a contiguous CUDA tensor")
+    if storage is None:
+        if src.dtype not in (torch.float64, torch.float32):
+            raise ValueError("src must be float64 or float32")
+        d = 0 if src.dtype == torch.float64 else 1
+        out = torch.empty(src.shape, dtype=torch.float32 if d == 0 else torch.float64, device=src.device)
+    elif storage in ("fp8", "bf16"):
+        want = torch.uint8 if storage == "fp8" else torch.bfloat16
+        if src.dtype != want:
+            raise ValueError(f"storage {storage!r} takes a {want} tensor")
+        d = 2 if storage == "fp8" else 3
+        out = torch.empty(src.shape, dtype=torch.float32, device=src.device)
+    else:
+        raise ValueError("storage must be None, 'fp8' or 'bf16'")
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
     rc = lib().asyflexa_convert_check(d, src.data_ptr(), out.data_ptr(), src.numel(), C.c_void_p(stream))

@@ -60,3 +60,62 @@ def test_rejects_bad_arguments():
     assert L.asyflexa_convert_check(0, None, None, 5, None) == native.EINVAL
     assert L.asyflexa_convert_check(0, None, None, -1, None) == native.EINVAL
     assert L.asyflexa_convert_check(0, None, None, 0, None) == native.OK
+
+
+def _e4m3_value(code):
+    """FP8-e4m3 (OCP 8-bit floating point, E4M3: bias 7, no infinities) from its definition:
+    (-1)^s 2^(e-7) (1 + f/8) for e > 0, (-1)^s 2^-6 (f/8) for e = 0."""
+    s, e, f = code >> 7, (code >> 3) & 0xF, code & 0x7
+    mag = 2.0 ** (e - 7) * (1 + f / 8) if e else 2.0 ** -6 * (f / 8)
+    return -mag if s else mag
+
+
+def test_fp8_decode_every_code():
+    """Every one of the 256 codes, in buffer order (code i at byte i of 16 units), decodes to
+    its exact value; the two NaN codes give NaN."""
+    import torch
+    from paper_1701_04900_gb300 import native
+    codes = np.arange(256, dtype=np.uint8)
+    got = native.convert_check(torch.from_numpy(codes).cuda(), storage="fp8").cpu().numpy()
+    ref = np.array([_e4m3_value(c) for c in range(256)], dtype=np.float64)
+    nan = (codes & 0x7F) == 0x7F
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].astype(np.float64), ref[~nan])
+    assert np.array_equal(np.signbit(got[~nan]), codes[~nan] >= 0x80)     # -0 keeps its sign
+    assert ref[0x7E] == 448.0 and ref[0x01] == 2.0 ** -9 and ref[0x08] == 2.0 ** -6
+
+
+def test_fp8_decode_random_layout():
+    import torch
+    from paper_1701_04900_gb300 import native
+    rng = np.random.default_rng(13)
+    codes = rng.integers(0, 256, 16 * 4099, dtype=np.uint8)
+    got = native.convert_check(torch.from_numpy(codes).cuda(), storage="fp8").cpu().numpy()
+    table = np.array([_e4m3_value(c) for c in range(256)], dtype=np.float64)
+    table[0x7F] = table[0xFF] = np.nan
+    ref = table[codes]
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].astype(np.float64), ref[~nan])
+
+
+def test_bf16_decode_is_exact():
+    import torch
+    from paper_1701_04900_gb300 import native
+    rng = np.random.default_rng(14)
+    bits = rng.integers(0, 2 ** 16, 8 * 5003, dtype=np.uint32).astype(np.uint16)
+    src = torch.from_numpy(bits.view(np.int16)).view(torch.bfloat16).cuda()
+    got = native.convert_check(src, storage="bf16").cpu().numpy()
+    ref = (bits.astype(np.uint32) << 16).view(np.float32)     # bf16 is the top half of binary32
+    nan = np.isnan(ref)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(got[~nan].view(np.uint32), ref[~nan].view(np.uint32))
+
+
+def test_decode_rejects_partial_units():
+    import torch
+    from paper_1701_04900_gb300 import native
+    with pytest.raises(native.AsyflexaError):
+        native.convert_check(torch.zeros(24, dtype=torch.uint8, device="cuda"), storage="fp8")
+    with pytest.raises(native.AsyflexaError):
+        native.convert_check(torch.zeros(12, dtype=torch.bfloat16, device="cuda"), storage="bf16")
