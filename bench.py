@@ -42,7 +42,9 @@ SWEEP_SOURCES = ["sweep_async.cuh", "sweep.cuh", "ptx.cuh", "types.cuh", "conver
 # the async sweep kernel behind each value of asyflexa_opts.variant / stats.kernel_variant
 ASYNC_KERNELS = {
     1: "sweep_kernel<float, async> (staged residual tile)",
-    2: "sweep_async_reg_kernel<float, 5> (register increment, residual snapshot in shared memory)",
+    2: "sweep_async_rc_kernel<float, 5> (register increment, column held in registers, residual snapshot "
+       "in shared memory)",
+    3: "sweep_async_reg_kernel<float, 5> (register increment with a producer warp)",
 }
 
 

@@ -126,8 +126,12 @@ typedef struct {
                                    asyflexa_read_counters); 0: off */
     int32_t variant;            /* async kernel: 0 = automatic (2 if it applies, else 1),
                                    1 = staged residual tile (any m, any dtype), 2 = register
-                                   increment with the residual snapshot in shared memory
-                                   (FP32/BF16/FP8, m up to 24576 rows; EUNSUPPORTED otherwise) */
+                                   increment with the residual snapshot in shared memory, each
+                                   thread holding its rows of the current column in registers
+                                   (16 warps that also refill the ring), 3 = the same with a
+                                   producer warp and the column read from shared memory twice
+                                   (variants 2 and 3: FP32/BF16/FP8, m up to 24576 rows;
+                                   EUNSUPPORTED otherwise).  exact_grad 1 runs the form of 3 */
     double switch_tol;          /* with A_master: solve leaves the low-precision phase when a check
                                    interval lowers F by less than switch_tol * |F| (default 1e-7) */
     double gamma_mu;            /* 0 (default): fixed step gamma (Algorithm 1).  > 0: the diminishing
@@ -143,7 +147,7 @@ typedef struct {
                                    time 0.05 * mean d_j); after 5 intervals in a row that lowered F it
                                    shrinks by half.  Restarts at 0 in every solve.  0 (default): off */
     int32_t exact_grad;         /* gradient arithmetic of the asynchronous register kernel (kernel
-                                   variant 2): 0 (default) FP32 accumulation; 1: compensated (Dot2)
+                                   variants 2 and 3): 0 (default) FP32 accumulation; 1: compensated (Dot2)
                                    accumulation, as accurate as FP64 accumulation of the FP32
                                    residual snapshot, about 1.6x the sweep time (FP32 storage only:
                                    EUNSUPPORTED otherwise, or when the register kernel does not
@@ -174,7 +178,7 @@ typedef struct {
     int64_t polish_sweeps;      /* with A_master: sweeps of the last solve run on the FP32 copy */
     double polish_seconds;      /* with A_master: device time of that FP32 phase */
     int32_t block_w;            /* batched solve: block width used (given or autotuned) */
-    int32_t kernel_variant;     /* async sweep kernel this handle launches (1 or 2, see
+    int32_t kernel_variant;     /* async sweep kernel this handle launches (1, 2 or 3, see
                                    asyflexa_opts.variant); set by solve, check, read_counters */
     double dual_gap;            /* plain LASSO (no box, no linear term): (P(x) - D(nu)) / max(1, |P(x)|)
                                    with the feasible dual point nu = theta r, theta = min(1, lambda /

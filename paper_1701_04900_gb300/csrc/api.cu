@@ -47,7 +47,11 @@ int cuda_error(asyflexa_s* h, cudaError_t e, const char* where) {
 }
 
 // The async sweep kernel a handle launches: 2 register increment, 1 staged residual tile.
-int async_variant(const asyflexa_s& h) { return h.reg_upt > 0 ? 2 : 1; }
+int async_variant(const asyflexa_s& h) {
+    if (h.reg_upt <= 0) return 1;
+    const bool exact = h.reg_exact_ok && h.opts.exact_grad == 1;
+    return (h.reg_rc_ok && !h.reg_rc_off && !exact) ? 2 : 3;
+}
 
 #define CK(h, call, where)                                   \
     do {                                                     \
@@ -309,7 +313,7 @@ int validate_opts(const asyflexa_opts* o, std::string* why) {
     if (o->refresh_every < 1 || o->check_every < 1 || o->max_sweeps < 1)
         return *why = "refresh_every, check_every and max_sweeps must be >= 1", 1;
     if (o->num_ctas < 0) return *why = "num_ctas must be >= 0", 1;
-    if (o->variant < 0 || o->variant > 2) return *why = "variant must be 0, 1 or 2", 1;
+    if (o->variant < 0 || o->variant > 3) return *why = "variant must be 0, 1, 2 or 3", 1;
     if (!(o->tol_gap >= 0.0) || !(o->tol_stat >= 0.0)) return *why = "tolerances must be >= 0", 1;
     if (!(o->switch_tol >= 0.0)) return *why = "switch_tol must be >= 0", 1;
     if (!(o->gamma_mu >= 0.0) || !std::isfinite(o->gamma_mu)) return *why = "gamma_mu must be finite and >= 0", 1;
@@ -513,11 +517,12 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
         if (rc < 0) CKC(static_cast<cudaError_t>(-rc), "set shared-memory attribute (register kernel)");
         if (O->variant == 1) {
             h->reg_upt = 0;
-        } else if (O->variant == 2 && rc != 1) {
+        } else if ((O->variant == 2 || O->variant == 3) && rc != 1) {
             set_error(h, ASYFLEXA_EUNSUPPORTED,
-                      "variant 2 (register increment) needs FP32/BF16/FP8 storage and m <= 24576");
+                      "variants 2 and 3 (register increment) need FP32/BF16/FP8 storage and m <= 24576");
             return fail(ASYFLEXA_EUNSUPPORTED);
         }
+        h->reg_rc_off = O->variant == 3;
         if (O->exact_grad == 1 && !(h->reg_upt > 0 && h->reg_exact_ok && O->mode == ASYFLEXA_ASYNC)) {
             set_error(h, ASYFLEXA_EUNSUPPORTED,
                       "exact_grad 1 needs the asynchronous register kernel on FP32 storage (m <= 24576)");

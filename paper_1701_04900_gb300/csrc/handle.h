@@ -72,6 +72,9 @@ struct asyflexa_s {
 
     int reg_upt = 0, reg_cpc = 0, reg_stages = 0;
     size_t reg_smem = 0;
+    // the column-in-registers form of the register kernel exists for this problem, and whether
+    // the form with a producer warp was asked for instead (asyflexa_opts.variant 3)
+    bool reg_rc_ok = false, reg_rc_off = false;
 
 
     int check_ctas = 0;

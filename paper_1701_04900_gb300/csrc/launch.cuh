@@ -81,6 +81,40 @@ const void* reg_kernel_partial(int cpc, int upt, int* upt_out) {
     return nullptr;
 }
 
+// The column-in-registers instance (sweep_async_rc_kernel) for cpc stages and upt units per
+// thread, or nullptr.
+template <typename TA, int CPC>
+const void* rc_inst() {
+    if constexpr (reg_fits<TA, CPC>())
+        return reinterpret_cast<const void*>(sweep_async_rc_kernel<TA, CPC>);
+    else
+        return nullptr;
+}
+
+template <typename TA>
+const void* rc_kernel(int cpc, int upt) {
+    if constexpr (sizeof(typename ATraits<TA>::TC) != 4) {
+        return nullptr;
+    } else {
+        if (upt != kRegKpc * cpc) {
+            if constexpr (std::is_same<TA, __nv_fp8_e4m3>::value)
+                if (cpc == 2 && upt == 3) return reinterpret_cast<const void*>(sweep_async_rc_kernel<TA, 2, 3>);
+            if constexpr (std::is_same<TA, __nv_bfloat16>::value)
+                if (cpc == 3 && upt == 5) return reinterpret_cast<const void*>(sweep_async_rc_kernel<TA, 3, 5>);
+            return nullptr;
+        }
+        switch (cpc) {
+            case 1: return rc_inst<TA, 1>();
+            case 2: return rc_inst<TA, 2>();
+            case 3: return rc_inst<TA, 3>();
+            case 4: return rc_inst<TA, 4>();
+            case 5: return rc_inst<TA, 5>();
+            case 6: return rc_inst<TA, 6>();
+            default: return nullptr;
+        }
+    }
+}
+
 // Choose the register-increment kernel instance that covers the column (sets h.reg_*).
 // Returns 0 if none applies (the staged kernel is used), 1 if chosen, or a negative
 // cudaError_t if setting its shared-memory attribute failed.  The ring must hold one
@@ -88,7 +122,7 @@ const void* reg_kernel_partial(int cpc, int upt, int* upt_out) {
 template <typename TA>
 int Launcher<TA>::choose_reg(asyflexa_s& h) {
     h.reg_upt = h.reg_cpc = h.reg_stages = 0;
-    h.reg_exact_ok = false;
+    h.reg_exact_ok = h.reg_rc_ok = false;
     h.reg_smem = 0;
     const int64_t units = h.mcopy / h.vec;
     const int cpc = static_cast<int>((units + kRegStageUnits - 1) / kRegStageUnits);
@@ -114,6 +148,12 @@ int Launcher<TA>::choose_reg(asyflexa_s& h) {
     h.reg_exact_ok = fx != nullptr;
     if (fx) {
         e = cudaFuncSetAttribute(fx, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.reg_smem));
+        if (e != cudaSuccess) return -static_cast<int>(e);
+    }
+    const void* fr = rc_kernel<TA>(cpc, upt);
+    h.reg_rc_ok = fr != nullptr;
+    if (fr) {
+        e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.reg_smem));
         if (e != cudaSuccess) return -static_cast<int>(e);
     }
     return 1;
@@ -219,6 +259,12 @@ cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
         p.tile_rows = static_cast<int>(h.mcopy);
         void* args[] = {&p};
         const bool exact = h.reg_exact_ok && h.opts.exact_grad == 1;
+        if (!exact && h.reg_rc_ok && !h.reg_rc_off) {  // the column-in-registers form
+            const cudaError_t e = cudaLaunchKernel(rc_kernel<TA>(h.reg_cpc, h.reg_upt), dim3(h.sweep_ctas),
+                                                   dim3(kRcThreads), args, h.reg_smem, h.stream);
+            ++h.launches;
+            return e != cudaSuccess ? e : cudaGetLastError();
+        }
         int upt_unused = 0;
         const void* fn = h.reg_upt == kRegKpc * h.reg_cpc ? reg_kernel<TA>(h.reg_cpc, exact)
                                                           : reg_kernel_partial<TA>(h.reg_cpc, h.reg_upt, &upt_unused);

@@ -557,4 +557,330 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
     }
 }
 
+
+// ---------------------------------------------------------------------------------------
+// Column-in-registers form of the same kernel (one problem, plain FP32 accumulation).
+//
+// 16 warps and no producer warp: with 16 warps (4 per SM sub-partition) a thread may hold 128
+// registers instead of 96, which is room for its units of the current column next to its
+// block increment.  Each thread keeps the units it read for a_j^T r~ in registers and forms
+// the increment a_j * Delta_j from them, so a column is read from shared memory once instead
+// of twice, and the column's ring stages are refilled at the column's barrier instead of
+// after the increment pass.
+//
+// The ring is refilled at the column barrier: the stages of the CTA's columns form one
+// sequence (sweep, owned block, column, stage) and item k lives in slot k mod S.  Every warp
+// has read all stages of column j before it arrives at the column's barrier, so right after
+// that barrier warp c (c < nchunks) refills the slot of the column's stage c with the item S
+// further on, with no release barriers or waits and one copy per warp.  Column j + 1's items are then issued before its dot
+// pass starts (nchunks <= S), so no wait forms a cycle.
+// ---------------------------------------------------------------------------------------
+
+constexpr int kRcThreads = kRegConsThreads;
+
+// Position of a ring item in the CTA's sequence: sweep, owned block, column in the block,
+// stage in the column.
+struct RcPos {
+    int s, b, jl, c;
+};
+
+// Advances q by `steps` items (stages per column: nchunks); false past the CTA's last item.
+__device__ __forceinline__ bool rc_next(RcPos& q, int steps, const SweepParams& p, int nchunks) {
+    q.c += steps;
+    while (q.c >= nchunks) {
+        q.c -= nchunks;
+        const int wb = static_cast<int>(min64(p.w, p.n - static_cast<int64_t>(q.b) * p.w));
+        if (++q.jl >= wb) {
+            q.jl = 0;
+            q.b += gridDim.x;
+            if (q.b >= p.nblocks) {
+                q.b = blockIdx.x;
+                if (++q.s >= p.sweeps) return false;
+            }
+        }
+    }
+    return true;
+}
+
+// Issues the bulk copy of item q into ring slot st (one thread); fills[st] counts the copies
+// ever issued into the slot, for the drain at exit.
+template <typename TA>
+__device__ __forceinline__ void rc_issue(const SweepParams& p, const RcPos& q, int st, unsigned char* ring,
+                                         size_t stage_bytes, uint64_t* full, uint32_t* fills, int64_t units) {
+    constexpr int V = ATraits<TA>::kVec;
+    const int64_t u0 = static_cast<int64_t>(q.c) * kRegStageUnits;
+    const uint32_t nbytes = static_cast<uint32_t>(min64(kRegStageUnits, units - u0) * 16);
+    const TA* col = static_cast<const TA*>(p.A) + (static_cast<int64_t>(q.b) * p.w + q.jl) * p.lda;
+    fills[st] += 1u;
+    fence_proxy_async_smem();
+    mbar_arrive_expect_tx(&full[st], nbytes);
+    bulk_load(ring + st * stage_bytes, col + u0 * V, nbytes, &full[st], l2_policy_evict_first());
+}
+
+template <typename TA, int CPC, int UPTX = 0>
+__global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const SweepParams p) {
+    using TC = typename ATraits<TA>::TC;
+    static_assert(sizeof(TC) == 4, "register kernel computes in FP32");
+    using TX = typename XType<TA>::T;
+    static_assert(sizeof(TX) == 4, "register kernel updates FP32 x");
+    constexpr int V = ATraits<TA>::kVec;
+    constexpr int UPT = UPTX > 0 ? UPTX : kRegKpc * CPC;
+    static_assert(UPT <= kRegKpc * CPC, "units beyond the column's stages");
+    static_assert(UPT * V <= kRegMaxRowsPerThread, "too many rows per thread");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    const RegLayout L = make_reg_layout(p.tile_rows, p.stages);
+    unsigned char* ring = smem + L.off_ring;
+    float* rt = reinterpret_cast<float*>(smem + L.off_rt);
+    float* colpart = reinterpret_cast<float*>(smem + L.off_colpart);
+    ColCoef* coef = reinterpret_cast<ColCoef*>(smem + L.off_coef);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.off_bars);
+    uint32_t* fills = reinterpret_cast<uint32_t*>(full + p.stages);  // in the layout's second barrier array
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + L.off_misc);
+    float* s_gamma = reinterpret_cast<float*>(smem + L.off_misc + 8);
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int S = p.stages;
+    const int64_t units = p.mcopy / V;
+    const int64_t units_full = p.m / V;  // units whose rows are all < m
+    int nchunks = 0;                     // stages per column
+    for (int c = 0; c < CPC; ++c)
+        if (static_cast<int64_t>(c) * kRegStageUnits < units) ++nchunks;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            fills[s] = 0u;
+        }
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (tid == 0 && static_cast<int>(blockIdx.x) < p.nblocks && p.sweeps > 0) {
+        RcPos q{0, static_cast<int>(blockIdx.x), 0, 0};
+        for (int i = 0; i < S; ++i) {
+            rc_issue<TA>(p, q, i, ring, L.stage_bytes, full, fills, units);
+            if (!rc_next(q, 1, p, nchunks)) break;
+        }
+    }
+
+    uint32_t stage = 0, phase = 0;
+    unsigned long long u_read = 0, my_updates = 0, my_active = 0;
+    float inc[UPT][V];
+    int buf = 0;
+
+    for (int s = 0; s < p.sweeps; ++s) {
+        for (int b = blockIdx.x; b < p.nblocks; b += gridDim.x) {
+            const BlockView<TA> bv = block_view<TA, false>(p, b);
+            // S.2: stale read of the residual into shared memory (rows >= m hold 0), and the
+            // block's per-column coefficients (the barrier that ended the previous block
+            // guarantees nobody still reads rt or coef)
+            if (tid == 0) {
+                u_read = ld_relaxed_u64(&p.counters[0]);
+                *s_gamma = static_cast<float>(launch_step(p, static_cast<long long>(u_read - p.k_base)));
+            }
+            {
+                constexpr int kB = 8;
+                const double2* rsrc = reinterpret_cast<const double2*>(bv.r);
+                float2* rdst = reinterpret_cast<float2*>(rt);
+                const int pairs = static_cast<int>(bv.mcopy / 2);
+                for (int i0 = tid; i0 < pairs; i0 += kB * kRcThreads) {
+                    double2 v[kB];
+#pragma unroll
+                    for (int t = 0; t < kB; ++t) {
+                        const int i = i0 + t * kRcThreads;
+                        v[t] = i < pairs ? __ldcg(rsrc + i) : make_double2(0.0, 0.0);
+                    }
+#pragma unroll
+                    for (int t = 0; t < kB; ++t) {
+                        const int i = i0 + t * kRcThreads;
+                        if (i < pairs) rdst[i] = make_float2(f64_to_f32(v[t].x), f64_to_f32(v[t].y));
+                    }
+                }
+            }
+            if (tid < bv.wb) {
+                const int64_t j = bv.c0 + tid;
+                const double dj = bv.dw[j];
+                ColCoef cf;
+                cf.x = static_cast<float>(bv.x[j]);
+                cf.lo = bv.lo ? static_cast<float>(bv.lo[j]) : -INFINITY;
+                cf.hi = bv.hi ? static_cast<float>(bv.hi[j]) : INFINITY;
+                cf.dinv = dj > 0.0 ? static_cast<float>(1.0 / dj) : 0.f;
+                cf.thr = dj > 0.0 ? static_cast<float>(bv.lam / dj) : 0.f;
+                cf.scale = bv.scale ? bv.scale[j] : 1.f;
+                double lj = bv.lin ? static_cast<double>(bv.lin[j]) : 0.0;
+                if (bv.dc.kind) lj -= bv.dc.lam * dc_hminus_grad(bv.dc, static_cast<double>(bv.x[j]));
+                cf.lin = static_cast<float>(lj);
+                cf.pad0 = 0.f;
+                coef[tid] = cf;
+            }
+#pragma unroll
+            for (int k = 0; k < UPT; ++k)
+#pragma unroll
+                for (int e = 0; e < V; ++e) inc[k][e] = 0.f;
+            bool any = false;
+            named_bar_sync(1, kRcThreads);
+            const float gamma = *s_gamma;
+
+            for (int jl = 0; jl < bv.wb; ++jl) {
+                // ---- dot a_j^T r~ over this thread's rows; the units stay in registers
+                float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+                uint4 colr[UPT];
+                bool ok = !*abort_flag;
+                const uint32_t st0 = stage;  // slot of the column's first stage
+#pragma unroll
+                for (int c = 0; c < CPC; ++c) {
+                    if (c < nchunks) {
+                        if (ok) ok = mbar_wait_bounded(&full[stage], phase, abort_flag, p.err);
+                        const uint4* src = reinterpret_cast<const uint4*>(ring + stage * L.stage_bytes);
+                        const bool whole = static_cast<int64_t>(c + 1) * kRegStageUnits <= units_full;
+#pragma unroll
+                        for (int kk = 0; kk < kRegKpc; ++kk) {
+                            const int k = c * kRegKpc + kk;
+                            if (k < UPT) {
+                                const int64_t u = static_cast<int64_t>(k) * kRcThreads + tid;
+                                colr[k] = (ok && (whole || u < units)) ? src[kk * kRcThreads + tid]
+                                                                       : make_uint4(0u, 0u, 0u, 0u);
+                                float a[V];
+                                ATraits<TA>::unpack(colr[k], a);
+                                const float* rv = rt + u * V;
+                                if (whole || u < units_full) {
+#pragma unroll
+                                    for (int e = 0; e < V; e += 4) {
+                                        const float4 r4 = *reinterpret_cast<const float4*>(rv + e);
+                                        acc0 = fmaf(a[e], r4.x, acc0);
+                                        acc1 = fmaf(a[e + 1], r4.y, acc1);
+                                        acc2 = fmaf(a[e + 2], r4.z, acc2);
+                                        acc3 = fmaf(a[e + 3], r4.w, acc3);
+                                    }
+                                } else if (u < units) {
+                                    const int valid = static_cast<int>(bv.m - u * V);
+#pragma unroll
+                                    for (int e = 0; e < V; ++e)
+                                        if (e < valid) acc0 = fmaf(a[e], rv[e], acc0);
+                                }
+                            }
+                        }
+                        if (++stage == static_cast<uint32_t>(S)) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < kRegKpc; ++kk)
+                            if (c * kRegKpc + kk < UPT) colr[c * kRegKpc + kk] = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
+                static_assert(kRegConsWarps == 16, "the sums below read 16 warp partials");
+                float* cp = colpart + buf * kRegConsWarps;
+                {
+                    const float v = warp_sum((acc0 + acc1) + (acc2 + acc3));
+                    if (lane == 0) cp[warp] = v;
+                }
+                const ColCoef cf = coef[jl];
+                named_bar_sync(1, kRcThreads);
+                // every warp has read the column's stages: warp c refills the slot of stage c
+                // with the item S further on
+                if (warp < nchunks && lane == 0 && !*abort_flag) {
+                    RcPos q{s, b, jl, 0};
+                    if (rc_next(q, S + warp, p, nchunks)) {
+                        uint32_t st = st0 + static_cast<uint32_t>(warp);
+                        if (st >= static_cast<uint32_t>(S)) st -= static_cast<uint32_t>(S);
+                        rc_issue<TA>(p, q, static_cast<int>(st), ring, L.stage_bytes, full, fills, units);
+                    }
+                }
+                // ---- best response (eq. 2) + fixed step (S.4), identical in every thread
+                float g;
+                {
+                    const float4* cp4 = reinterpret_cast<const float4*>(cp);
+                    const float4 q0 = cp4[0], q1 = cp4[1], q2 = cp4[2], q3 = cp4[3];
+                    g = (((q0.x + q0.y) + (q0.z + q0.w)) + ((q1.x + q1.y) + (q1.z + q1.w))) +
+                        (((q2.x + q2.y) + (q2.z + q2.w)) + ((q3.x + q3.y) + (q3.z + q3.w)));
+                }
+                buf ^= 1;
+                const float grad = bv.s_loss * g * cf.scale - bv.c2 * cf.x + cf.lin;
+                float xh = 0.f;
+                if (cf.dinv > 0.f) {
+                    const float vv = fmaf(-grad, cf.dinv, cf.x);
+                    const float av = fabsf(vv) - cf.thr;
+                    xh = av > 0.f ? copysignf(av, vv) : 0.f;
+                }
+                xh = fminf(fmaxf(xh, cf.lo), cf.hi);
+                const float xn = fmaf(gamma, xh - cf.x, cf.x);
+                const float dlt = xn - cf.x;
+                float dj = 0.f;
+                if (!*abort_flag) {
+                    if (tid == 0) bv.x[bv.c0 + jl] = static_cast<TX>(xn);
+                    dj = dlt * cf.scale;
+                    any |= dlt != 0.f;
+                }
+                // ---- fold a_j * Delta_j into the register increment (units past the column
+                // hold zeros)
+                if (dj != 0.f) {
+#pragma unroll
+                    for (int k = 0; k < UPT; ++k) {
+                        float a[V];
+                        ATraits<TA>::unpack(colr[k], a);
+#pragma unroll
+                        for (int e = 0; e < V; ++e) inc[k][e] = fmaf(a[e], dj, inc[k][e]);
+                    }
+                }
+            }
+            // ---- r += A_i Delta_i : one FP64 atomic per row (skipping exact zeros), transposed
+            // through shuffles so that each red instruction covers 32 consecutive rows
+            const bool aborted = __shfl_sync(0xffffffffu, *abort_flag != 0, 0);
+            if (any && !aborted) {
+                static_assert(32 % V == 0, "units of at most 32 rows");
+#pragma unroll
+                for (int k = 0; k < UPT; ++k) {
+                    const int64_t row0 = (static_cast<int64_t>(k) * kRcThreads + warp * 32) * V;
+#pragma unroll
+                    for (int q = 0; q < V; ++q) {
+                        const int src = q * (32 / V) + lane / V;
+                        const int esel = lane % V;
+                        float v = 0.f;
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            const float t = __shfl_sync(0xffffffffu, inc[k][e], src);
+                            v = e == esel ? t : v;
+                        }
+                        const int64_t row = row0 + q * 32 + lane;
+                        if (row < bv.m && v != 0.f) red_add_f64(bv.r + row, f32_to_f64(v));
+                    }
+                }
+                // a single CTA runs its blocks strictly in order (cyclic Gauss-Seidel): its next
+                // read of r must see this scatter
+                if (gridDim.x == 1) __threadfence();
+            }
+            named_bar_sync(1, kRcThreads);  // scatter issued; rt and coef free
+            if (tid == 0) {
+                ++my_updates;
+                if (any) ++my_active;
+                const unsigned long long u1 = atomicAdd(&p.counters[0], 1ull);
+                const unsigned long long dly = u1 - u_read;
+                int bucket = 63 - __clzll(static_cast<long long>(dly + 1ull));
+                bucket = bucket > 31 ? 31 : bucket;
+                atomicAdd(&p.hist[bucket], 1ull);
+            }
+        }
+    }
+    // no bulk copy may still be writing shared memory when the CTA exits (only after an
+    // abort can an issued item be left unconsumed): wait for the last copy into every slot
+    __syncthreads();
+    if (tid == 0) {
+        atomicAdd(&p.counters[1], my_updates);
+        atomicAdd(&p.counters[2], my_active);
+        for (int st = 0; st < S; ++st) {
+            const uint32_t f = fills[st];
+            if (f == 0u) continue;
+            const uint64_t t0 = global_timer_ns();
+            while (!mbar_try_wait(&full[st], (f - 1u) & 1u)) {
+                if (global_timer_ns() - t0 > kWaitLimitNs) break;
+            }
+        }
+    }
+}
+
 }  // namespace asyflexa

@@ -186,11 +186,12 @@ def test_sync_parity_quantized_storage(kind):
 # ----------------------------------------------------------------------------- async
 
 @pytest.mark.parametrize("store,tol,variant", [(np.float64, TOL64, 0), (np.float32, TOL32, 1),
-                                               (np.float32, TOL32, 2)])
+                                               (np.float32, TOL32, 2), (np.float32, TOL32, 3)])
 @pytest.mark.parametrize("w", [1, 4, 32])
 def test_async_single_cta_equals_gauss_seidel(store, tol, variant, w):
     """One CTA owns every block and runs them in order: exactly cyclic block Gauss-Seidel.
-    variant 1 = staged-residual kernel, 2 = register-increment kernel."""
+    variant 1 = staged-residual kernel, 2 = register-increment kernel with the column held in
+    registers, 3 = register-increment kernel with a producer warp."""
     import torch
     d = random_lasso(301, 200, seed=9, lam=0.3, store_dtype=store, box=0.8)
     p = O.Problem.from_data(d)
@@ -206,7 +207,7 @@ def test_async_single_cta_equals_gauss_seidel(store, tol, variant, w):
 
 
 @pytest.mark.parametrize("m", [1021, 5003, 8192, 9001, 16384, 17001, 20477, 24571])
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_async_single_cta_shapes(m, variant):
     """Column lengths spanning 1..6 shared-memory stages of the register kernels (ragged last
     unit included; 8192 and 16384 fill every stage, so no stage takes the checked path),
@@ -225,7 +226,7 @@ def test_async_single_cta_shapes(m, variant):
 
 
 @pytest.mark.parametrize("m,n", [(2000, 600), (9001, 200), (10000, 96), (4000, 12000)])
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_async_single_cta_ncquad_box_equals_gauss_seidel(m, n, variant):
     """Nonconvex quadratic with the box |x| <= 1 (gradient 2A^T r - 2c x, curvature
     2||a_j||^2 - 2c + tau), one CTA, against the oracle's cyclic Gauss-Seidel sweeps; long
@@ -245,7 +246,7 @@ def test_async_single_cta_ncquad_box_equals_gauss_seidel(m, n, variant):
 
 
 @pytest.mark.parametrize("kind", ["bf16", "fp8"])
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 def test_async_single_cta_quantized(kind, variant):
     _single_cta_quantized(kind, variant, 3001)
 
@@ -288,7 +289,7 @@ def test_async_single_cta_multitile_equals_gauss_seidel():
     assert rel_inf(x.cpu().numpy(), x_ref) < TOL32
 
 
-@pytest.mark.parametrize("store,variant", [(np.float64, 0), (np.float32, 1), (np.float32, 2)])
+@pytest.mark.parametrize("store,variant", [(np.float64, 0), (np.float32, 1), (np.float32, 2), (np.float32, 3)])
 def test_async_reaches_planted_optimum(store, variant):
     """Many CTAs, stale reads: objective within 1e-6 of the optimum, stationarity <= 1e-6.
 
@@ -401,23 +402,40 @@ def test_invalid_inputs_are_rejected():
         s.step(torch.zeros(30, dtype=torch.float32, device="cuda"), 1)
 
 
+def test_kernel_variant_reports_the_form_launched():
+    """Automatic choice on FP32 storage: the column-in-registers form (2); variant 3: the form
+    with a producer warp; the compensated gradient runs the producer-warp form (3); variant 1
+    and FP64 storage: the staged kernel (1)."""
+    d = random_lasso(5000, 64, seed=17, store_dtype=np.float32)
+    for kw, want in (({}, 2), ({"variant": 2}, 2), ({"variant": 3}, 3), ({"variant": 2, "exact_grad": 1}, 3),
+                     ({"variant": 1}, 1)):
+        s = make_solver(d, mode="async", **kw)
+        assert s.read_counters()["kernel_variant"] == want, kw
+        s.close()
+    s = make_solver(random_lasso(300, 16, seed=16, store_dtype=np.float64), mode="async")
+    assert s.read_counters()["kernel_variant"] == 1
+    s.close()
+
+
 def test_unsupported_kernel_variant_is_reported():
     """A requested kernel that does not cover the problem is refused at create (no fallback)."""
     from paper_1701_04900_gb300 import AsyflexaError
     d = random_lasso(24581, 16, seed=16, store_dtype=np.float32)
-    with pytest.raises(AsyflexaError) as ei:
-        make_solver(d, mode="async", variant=2)
-    assert ei.value.code == -6
+    for v in (2, 3):
+        with pytest.raises(AsyflexaError) as ei:
+            make_solver(d, mode="async", variant=v)
+        assert ei.value.code == -6
     d = random_lasso(300, 16, seed=16, store_dtype=np.float64)
-    with pytest.raises(AsyflexaError) as ei:
-        make_solver(d, mode="async", variant=2)
-    assert ei.value.code == -6
+    for v in (2, 3):
+        with pytest.raises(AsyflexaError) as ei:
+            make_solver(d, mode="async", variant=v)
+        assert ei.value.code == -6
 
 
 # ----------------------------------------------------------------------------- DC regularisers
 
 @pytest.mark.parametrize("reg", ["dc_log", "dc_exp"])
-@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("variant", [1, 2, 3])
 @pytest.mark.parametrize("m,n", [(700, 500), (9001, 160)])
 def test_async_single_cta_dc_equals_gauss_seidel(reg, variant, m, n):
     """F = ||Ax-b||^2 + lam H(x) (Section 4.3) with the log / exp regulariser: one CTA against
@@ -492,7 +510,7 @@ def test_dc_check_measures_match_oracle(reg):
 # ----------------------------------------------------------------------------- diminishing step
 
 @pytest.mark.parametrize("store,tol,variant", [(np.float64, TOL64, 0), (np.float32, TOL32, 1),
-                                               (np.float32, TOL32, 2)])
+                                               (np.float32, TOL32, 2), (np.float32, TOL32, 3)])
 def test_async_single_cta_diminishing_step_equals_gauss_seidel(store, tol, variant):
     """gamma^{k+1} = gamma^k (1 - mu gamma^k) (the experiments' rule, Section 4) with k counting
     block updates: one CTA performs them in order, so update k of the run takes gamma^k."""
