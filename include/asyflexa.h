@@ -124,13 +124,14 @@ typedef struct {
     uint64_t seed;              /* reserved */
     int32_t profile;            /* 1: time every sweep-kernel launch with CUDA events (see
                                    asyflexa_read_counters); 0: off */
-    int32_t variant;            /* async kernel: 0 = automatic (2 if it applies, else 1),
-                                   1 = staged residual tile (any m, any dtype), 2 = register
-                                   increment with the residual snapshot in shared memory, each
-                                   thread holding its rows of the current column in registers
-                                   (16 warps that also refill the ring), 3 = the same with a
-                                   producer warp and the column read from shared memory twice
-                                   (variants 2 and 3: FP32/BF16/FP8, m up to 24576 rows;
+    int32_t variant;            /* async kernel: 0 = automatic (2 for FP32 with m > 12288 and
+                                   BF16/FP8 with m > 16384, 3 for smaller m, 1 where neither
+                                   applies), 1 = staged residual tile (any m, any dtype),
+                                   2 = register increment with the residual snapshot in shared
+                                   memory, each thread holding its rows of the current column in
+                                   registers (16 warps that also refill the ring), 3 = the same
+                                   with a producer warp and the column read from shared memory
+                                   twice (variants 2 and 3: FP32/BF16/FP8, m up to 24576 rows;
                                    EUNSUPPORTED otherwise).  exact_grad 1 runs the form of 3 */
     double switch_tol;          /* with A_master: solve leaves the low-precision phase when a check
                                    interval lowers F by less than switch_tol * |F| (default 1e-7) */

@@ -522,7 +522,11 @@ int asyflexa_create(asyflexa_t* out, const asyflexa_problem* P, const asyflexa_o
                       "variants 2 and 3 (register increment) need FP32/BF16/FP8 storage and m <= 24576");
             return fail(ASYFLEXA_EUNSUPPORTED);
         }
-        h->reg_rc_off = O->variant == 3;
+        // automatic choice between the two register-kernel forms: the column-in-registers form
+        // issues the ring's refills from the consumer warps after each column barrier, which
+        // pays only when a column carries enough work (measured on GB300: FP32 from 4 stages
+        // per column, m > 12288; BF16 from 3 and FP8 from 2 stages, m > 16384)
+        h->reg_rc_off = O->variant == 3 || (O->variant == 0 && h->prob.m <= (h->vec == 4 ? 12288 : 16384));
         if (O->exact_grad == 1 && !(h->reg_upt > 0 && h->reg_exact_ok && O->mode == ASYFLEXA_ASYNC)) {
             set_error(h, ASYFLEXA_EUNSUPPORTED,
                       "exact_grad 1 needs the asynchronous register kernel on FP32 storage (m <= 24576)");

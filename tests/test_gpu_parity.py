@@ -251,11 +251,20 @@ def test_async_single_cta_quantized(kind, variant):
     _single_cta_quantized(kind, variant, 3001)
 
 
+@pytest.mark.parametrize("variant", [2, 3])
 @pytest.mark.parametrize("m", [16385, 20000, 24576])
-def test_async_single_cta_fp8_two_stage_columns(m):
+def test_async_single_cta_fp8_two_stage_columns(m, variant):
     """FP8 columns of 16385..24576 rows span 2 shared-memory stages but need only 3 units per
     thread: the register kernel's partial-unit instance, against Gauss-Seidel."""
-    _single_cta_quantized("fp8", 2, m, n=96)
+    _single_cta_quantized("fp8", variant, m, n=96)
+
+
+@pytest.mark.parametrize("variant", [2, 3])
+@pytest.mark.parametrize("m", [16385, 20480])
+def test_async_single_cta_bf16_three_stage_columns(m, variant):
+    """BF16 columns of 16385..20480 rows span 3 stages but need only 5 of their 6 units per
+    thread: the 5-unit instance, against Gauss-Seidel."""
+    _single_cta_quantized("bf16", variant, m, n=96)
 
 
 def _single_cta_quantized(kind, variant, m, n=300):
@@ -403,12 +412,17 @@ def test_invalid_inputs_are_rejected():
 
 
 def test_kernel_variant_reports_the_form_launched():
-    """Automatic choice on FP32 storage: the column-in-registers form (2); variant 3: the form
-    with a producer warp; the compensated gradient runs the producer-warp form (3); variant 1
-    and FP64 storage: the staged kernel (1)."""
+    """Automatic choice on FP32 storage: the producer-warp form (3) up to 12288 rows, the
+    column-in-registers form (2) above; variants 2 and 3 force a form; the compensated
+    gradient runs the producer-warp form; variant 1 and FP64 storage: the staged kernel (1)."""
     d = random_lasso(5000, 64, seed=17, store_dtype=np.float32)
-    for kw, want in (({}, 2), ({"variant": 2}, 2), ({"variant": 3}, 3), ({"variant": 2, "exact_grad": 1}, 3),
+    for kw, want in (({}, 3), ({"variant": 2}, 2), ({"variant": 3}, 3), ({"variant": 2, "exact_grad": 1}, 3),
                      ({"variant": 1}, 1)):
+        s = make_solver(d, mode="async", **kw)
+        assert s.read_counters()["kernel_variant"] == want, kw
+        s.close()
+    d = random_lasso(12289, 40, seed=18, store_dtype=np.float32)
+    for kw, want in (({}, 2), ({"variant": 3}, 3)):
         s = make_solver(d, mode="async", **kw)
         assert s.read_counters()["kernel_variant"] == want, kw
         s.close()
