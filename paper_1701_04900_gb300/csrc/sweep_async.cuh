@@ -676,8 +676,21 @@ __global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const Swe
             const BlockView<TA> bv = block_view<TA, false>(p, b);
             // S.2: stale read of the residual into shared memory (rows >= m hold 0), and the
             // block's per-column coefficients (the barrier that ended the previous block
-            // guarantees nobody still reads rt or coef)
-            if (tid == 0) {
+            // guarantees nobody still reads rt or coef).  The coefficient loads go out before
+            // the residual reload, and the last thread reads the update counter, so that
+            // neither latency waits behind the other.
+            double c_dw = 0.0, c_x = 0.0, c_lo = -INFINITY, c_hi = INFINITY, c_lin = 0.0;
+            float c_scale = 1.f;
+            if (tid < bv.wb) {
+                const int64_t j = bv.c0 + tid;
+                c_dw = bv.dw[j];
+                c_x = static_cast<double>(bv.x[j]);
+                if (bv.lo) c_lo = static_cast<double>(bv.lo[j]);
+                if (bv.hi) c_hi = static_cast<double>(bv.hi[j]);
+                if (bv.lin) c_lin = static_cast<double>(bv.lin[j]);
+                if (bv.scale) c_scale = bv.scale[j];
+            }
+            if (tid == kRcThreads - 1) {
                 u_read = ld_relaxed_u64(&p.counters[0]);
                 *s_gamma = static_cast<float>(launch_step(p, static_cast<long long>(u_read - p.k_base)));
             }
@@ -701,17 +714,16 @@ __global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const Swe
                 }
             }
             if (tid < bv.wb) {
-                const int64_t j = bv.c0 + tid;
-                const double dj = bv.dw[j];
+                const double dj = c_dw;
                 ColCoef cf;
-                cf.x = static_cast<float>(bv.x[j]);
-                cf.lo = bv.lo ? static_cast<float>(bv.lo[j]) : -INFINITY;
-                cf.hi = bv.hi ? static_cast<float>(bv.hi[j]) : INFINITY;
+                cf.x = static_cast<float>(c_x);
+                cf.lo = static_cast<float>(c_lo);
+                cf.hi = static_cast<float>(c_hi);
                 cf.dinv = dj > 0.0 ? static_cast<float>(1.0 / dj) : 0.f;
                 cf.thr = dj > 0.0 ? static_cast<float>(bv.lam / dj) : 0.f;
-                cf.scale = bv.scale ? bv.scale[j] : 1.f;
-                double lj = bv.lin ? static_cast<double>(bv.lin[j]) : 0.0;
-                if (bv.dc.kind) lj -= bv.dc.lam * dc_hminus_grad(bv.dc, static_cast<double>(bv.x[j]));
+                cf.scale = c_scale;
+                double lj = c_lin;
+                if (bv.dc.kind) lj -= bv.dc.lam * dc_hminus_grad(bv.dc, c_x);
                 cf.lin = static_cast<float>(lj);
                 cf.pad0 = 0.f;
                 coef[tid] = cf;
@@ -855,7 +867,7 @@ __global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const Swe
                 if (gridDim.x == 1) __threadfence();
             }
             named_bar_sync(1, kRcThreads);  // scatter issued; rt and coef free
-            if (tid == 0) {
+            if (tid == kRcThreads - 1) {
                 ++my_updates;
                 if (any) ++my_active;
                 const unsigned long long u1 = atomicAdd(&p.counters[0], 1ull);
@@ -868,10 +880,12 @@ __global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const Swe
     }
     // no bulk copy may still be writing shared memory when the CTA exits (only after an
     // abort can an issued item be left unconsumed): wait for the last copy into every slot
-    __syncthreads();
-    if (tid == 0) {
+    if (tid == kRcThreads - 1) {
         atomicAdd(&p.counters[1], my_updates);
         atomicAdd(&p.counters[2], my_active);
+    }
+    __syncthreads();
+    if (tid == 0) {
         for (int st = 0; st < S; ++st) {
             const uint32_t f = fills[st];
             if (f == 0u) continue;
