@@ -170,6 +170,143 @@ __device__ __forceinline__ float sum_pairs_16(const float2* q) {
     return s[0] + c[0];
 }
 
+// ---------------------------------------------------------------------------------------
+// Pieces shared by the register-increment kernels (one block update, Algorithm 1).
+// ---------------------------------------------------------------------------------------
+
+// S.2 stale read: the FP64 residual rows [0, mcopy) rounded to FP32 into shared memory (rows
+// >= m hold 0), kB independent 16-byte L2 loads in flight per thread.
+template <int kThreads>
+__device__ __forceinline__ void stage_residual(const double* r, int64_t mcopy, float* rt, int tid) {
+    constexpr int kB = 8;
+    const double2* rsrc = reinterpret_cast<const double2*>(r);
+    float2* rdst = reinterpret_cast<float2*>(rt);
+    const int pairs = static_cast<int>(mcopy / 2);
+    for (int i0 = tid; i0 < pairs; i0 += kB * kThreads) {
+        double2 v[kB];
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+            const int i = i0 + t * kThreads;
+            v[t] = i < pairs ? __ldcg(rsrc + i) : make_double2(0.0, 0.0);
+        }
+#pragma unroll
+        for (int t = 0; t < kB; ++t) {
+            const int i = i0 + t * kThreads;
+            if (i < pairs) rdst[i] = make_float2(f64_to_f32(v[t].x), f64_to_f32(v[t].y));
+        }
+    }
+}
+
+// The per-column data of a block coordinate j = c0 + jl: loaded first (so that the loads
+// overlap the residual reload), then turned into the epilogue's FP32 coefficients.
+struct CoefLoads {
+    double dw, x, lo, hi, lin;
+    float scale;
+};
+
+template <typename TA>
+__device__ __forceinline__ CoefLoads load_coef(const BlockView<TA>& bv, int jl) {
+    const int64_t j = bv.c0 + jl;
+    CoefLoads c;
+    c.dw = bv.dw[j];
+    c.x = static_cast<double>(bv.x[j]);
+    c.lo = bv.lo ? static_cast<double>(bv.lo[j]) : -INFINITY;
+    c.hi = bv.hi ? static_cast<double>(bv.hi[j]) : INFINITY;
+    c.lin = bv.lin ? static_cast<double>(bv.lin[j]) : 0.0;
+    c.scale = bv.scale ? bv.scale[j] : 1.f;
+    return c;
+}
+
+template <typename TA>
+__device__ __forceinline__ ColCoef finish_coef(const BlockView<TA>& bv, const CoefLoads& c) {
+    ColCoef cf;
+    cf.x = static_cast<float>(c.x);
+    cf.lo = static_cast<float>(c.lo);
+    cf.hi = static_cast<float>(c.hi);
+    cf.dinv = c.dw > 0.0 ? static_cast<float>(1.0 / c.dw) : 0.f;
+    cf.thr = c.dw > 0.0 ? static_cast<float>(bv.lam / c.dw) : 0.f;
+    cf.scale = c.scale;
+    // linear coefficient of the surrogate: lin_j, minus lam h-'(x_j) for the DC losses (the
+    // concave part is linearised at the block's snapshot of x_j)
+    double lj = c.lin;
+    if (bv.dc.kind) lj -= bv.dc.lam * dc_hminus_grad(bv.dc, c.x);
+    cf.lin = static_cast<float>(lj);
+    cf.pad0 = 0.f;
+    return cf;
+}
+
+// Sum of the 16 warp partials of g_j in a fixed order (every thread gets the same value).
+__device__ __forceinline__ float sum_partials_16(const float* cp) {
+    const float4* cp4 = reinterpret_cast<const float4*>(cp);
+    const float4 q0 = cp4[0], q1 = cp4[1], q2 = cp4[2], q3 = cp4[3];
+    return (((q0.x + q0.y) + (q0.z + q0.w)) + ((q1.x + q1.y) + (q1.z + q1.w))) +
+           (((q2.x + q2.y) + (q2.z + q2.w)) + ((q3.x + q3.y) + (q3.z + q3.w)));
+}
+
+// Best response (eq. 2) and fixed step (S.4) of coordinate j from g_j = a_j^T r~, in FP32:
+// returns the new x_j.
+template <typename TA>
+__device__ __forceinline__ float best_response_step(const BlockView<TA>& bv, const ColCoef& cf, float g,
+                                                    float gamma) {
+    const float grad = bv.s_loss * g * cf.scale - bv.c2 * cf.x + cf.lin;
+    float xh = 0.f;
+    if (cf.dinv > 0.f) {
+        const float vv = fmaf(-grad, cf.dinv, cf.x);
+        const float av = fabsf(vv) - cf.thr;
+        xh = av > 0.f ? copysignf(av, vv) : 0.f;
+    }
+    xh = fminf(fmaxf(xh, cf.lo), cf.hi);
+    return fmaf(gamma, xh - cf.x, cf.x);
+}
+
+// r += A_i Delta_i from the register increments: one FP64 atomic per row (skipping exact
+// zeros).  The warp's units k*kThreads + 32*warp + l (l < 32) cover 32 V consecutive rows; a
+// thread holds V consecutive ones.  Transposed through shuffles, so that in round q lane l
+// adds row 32 q + l of that span (element l mod V of the unit held by lane q 32/V + l/V):
+// every red instruction then covers 32 consecutive doubles (8 whole sectors) instead of 32
+// rows 8 V bytes apart.
+template <int V, int UPT, int kThreads>
+__device__ __forceinline__ void scatter_increment(const float (&inc)[UPT][V], double* r, int64_t m, int warp,
+                                                  int lane) {
+    static_assert(32 % V == 0, "units of at most 32 rows");
+#pragma unroll
+    for (int k = 0; k < UPT; ++k) {
+        const int64_t row0 = (static_cast<int64_t>(k) * kThreads + warp * 32) * V;
+#pragma unroll
+        for (int q = 0; q < V; ++q) {
+            const int src = q * (32 / V) + lane / V;
+            const int esel = lane % V;
+            float v = 0.f;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const float t = __shfl_sync(0xffffffffu, inc[k][e], src);
+                v = e == esel ? t : v;
+            }
+            const int64_t row = row0 + q * 32 + lane;
+            if (row < m && v != 0.f) red_add_f64(r + row, f32_to_f64(v));
+        }
+    }
+    // A single CTA runs its blocks strictly in order (cyclic Gauss-Seidel), so its next read
+    // of r must see this scatter.  With several CTAs the next read may miss it: that is one
+    // more update in flight, within the bounded-delay model (Assumption D1), so no fence is
+    // spent there.
+    if (gridDim.x == 1) __threadfence();
+}
+
+// Block-end accounting (S.5, one thread): the global update counter, and the staleness of
+// this update (updates completed between its read of r and its own completion) in a log2
+// histogram.
+__device__ __forceinline__ void account_block(const SweepParams& p, unsigned long long u_read, bool any,
+                                              unsigned long long& my_updates, unsigned long long& my_active) {
+    ++my_updates;
+    if (any) ++my_active;
+    const unsigned long long u1 = atomicAdd(&p.counters[0], 1ull);
+    const unsigned long long dly = u1 - u_read;
+    int bucket = 63 - __clzll(static_cast<long long>(dly + 1ull));
+    bucket = bucket > 31 ? 31 : bucket;
+    atomicAdd(&p.hist[bucket], 1ull);
+}
+
 // EXACT = true forms each block gradient g_j = a_j^T r~ with compensated arithmetic (Dot2 of
 // Ogita, Rump and Oishi per accumulation chain, TwoSum in the warp and cross-warp sums), as
 // accurate as FP64 accumulation of the FP32 snapshot r~; the plain form accumulates in FP32.
@@ -276,53 +413,21 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
             int nchunks = 0;                      // stages per column actually present
             for (int c = 0; c < CPC; ++c)
                 if (static_cast<int64_t>(c) * kRegStageUnits < units) ++nchunks;
-            // S.2: stale read of the residual into shared memory (rows >= m hold 0), and the
-            // block's per-column coefficients.  The barrier that ended the previous block
-            // guarantees nobody still reads rt or coef.
-            if (tid == 0) {
+            // S.2: stale read of the residual into shared memory, and the block's per-column
+            // coefficients (the barrier that ended the previous block guarantees nobody still
+            // reads rt or coef).  The coefficient loads go out before the residual reload, and
+            // the last consumer thread reads the update counter, so that neither latency waits
+            // behind the other.
+            CoefLoads cl{};
+            if (tid < bv.wb) cl = load_coef(bv, tid);
+            if (tid == kRegConsThreads - 1) {
                 u_read = ld_relaxed_u64(&p.counters[0]);
-                // step of this block update (the update index is the number of updates completed
-                // before this read of the residual)
+                // step of this block update (the update index is the number of updates
+                // completed before this read of the residual)
                 *s_gamma = static_cast<float>(launch_step(p, static_cast<long long>(u_read - p.k_base)));
             }
-            {
-                // 8 independent 16-byte L2 loads in flight per thread
-                constexpr int kB = 8;
-                const double2* rsrc = reinterpret_cast<const double2*>(bv.r);
-                float2* rdst = reinterpret_cast<float2*>(rt);
-                const int pairs = static_cast<int>(bv.mcopy / 2);
-                for (int i0 = tid; i0 < pairs; i0 += kB * kRegConsThreads) {
-                    double2 v[kB];
-#pragma unroll
-                    for (int t = 0; t < kB; ++t) {
-                        const int i = i0 + t * kRegConsThreads;
-                        v[t] = i < pairs ? __ldcg(rsrc + i) : make_double2(0.0, 0.0);
-                    }
-#pragma unroll
-                    for (int t = 0; t < kB; ++t) {
-                        const int i = i0 + t * kRegConsThreads;
-                        if (i < pairs) rdst[i] = make_float2(f64_to_f32(v[t].x), f64_to_f32(v[t].y));
-                    }
-                }
-            }
-            if (tid < bv.wb) {
-                const int64_t j = bv.c0 + tid;
-                const double dj = bv.dw[j];
-                ColCoef cf;
-                cf.x = static_cast<float>(bv.x[j]);
-                cf.lo = bv.lo ? static_cast<float>(bv.lo[j]) : -INFINITY;
-                cf.hi = bv.hi ? static_cast<float>(bv.hi[j]) : INFINITY;
-                cf.dinv = dj > 0.0 ? static_cast<float>(1.0 / dj) : 0.f;
-                cf.thr = dj > 0.0 ? static_cast<float>(bv.lam / dj) : 0.f;
-                cf.scale = bv.scale ? bv.scale[j] : 1.f;
-                // linear coefficient of the surrogate: lin_j, minus lam h-'(x_j) for the DC losses
-                // (the concave part is linearised at the block's snapshot of x_j)
-                double lj = bv.lin ? static_cast<double>(bv.lin[j]) : 0.0;
-                if (bv.dc.kind) lj -= bv.dc.lam * dc_hminus_grad(bv.dc, static_cast<double>(bv.x[j]));
-                cf.lin = static_cast<float>(lj);
-                cf.pad0 = 0.f;
-                coef[tid] = cf;
-            }
+            stage_residual<kRegConsThreads>(bv.r, bv.mcopy, rt, tid);
+            if (tid < bv.wb) coef[tid] = finish_coef(bv, cl);
 #pragma unroll
             for (int k = 0; k < UPT; ++k)
 #pragma unroll
@@ -437,24 +542,12 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
                 // ---- best response (eq. 2) + fixed step (S.4): every consumer thread sums the 16
                 // warp partials in the same fixed order, so all agree on g and Delta_j
                 float g;
-                if constexpr (EXACT) {
+                if constexpr (EXACT)
                     g = sum_pairs_16(reinterpret_cast<const float2*>(cp));
-                } else {
-                    const float4* cp4 = reinterpret_cast<const float4*>(cp);
-                    const float4 q0 = cp4[0], q1 = cp4[1], q2 = cp4[2], q3 = cp4[3];
-                    g = (((q0.x + q0.y) + (q0.z + q0.w)) + ((q1.x + q1.y) + (q1.z + q1.w))) +
-                        (((q2.x + q2.y) + (q2.z + q2.w)) + ((q3.x + q3.y) + (q3.z + q3.w)));
-                }
+                else
+                    g = sum_partials_16(cp);
                 buf ^= 1;
-                const float grad = bv.s_loss * g * cf.scale - bv.c2 * cf.x + cf.lin;
-                float xh = 0.f;
-                if (cf.dinv > 0.f) {
-                    const float vv = fmaf(-grad, cf.dinv, cf.x);
-                    const float av = fabsf(vv) - cf.thr;
-                    xh = av > 0.f ? copysignf(av, vv) : 0.f;
-                }
-                xh = fminf(fmaxf(xh, cf.lo), cf.hi);
-                const float xn = fmaf(gamma, xh - cf.x, cf.x);
+                const float xn = best_response_step(bv, cf, g, gamma);
                 const float dlt = xn - cf.x;
                 float dj = 0.f;
                 if (!*abort_flag) {
@@ -509,49 +602,12 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
             // ---- r += A_i Delta_i : one FP64 atomic per row (skipping exact zeros)
             // (the abort flag is read once per warp: the FP32 path below shuffles within the warp)
             const bool aborted = __shfl_sync(0xffffffffu, *abort_flag != 0, 0);
-            if (any && !aborted) {
-                // The warp's units k*512 + 32*warp + l (l < 32) cover 32 V consecutive rows; a thread
-                // holds V consecutive ones.  Transposed through shuffles, so that in round q lane l
-                // adds row 32 q + l of that span (element l mod V of the unit held by lane
-                // q 32/V + l/V): every red instruction then covers 32 consecutive doubles (8 whole
-                // sectors) instead of 32 rows 8 V bytes apart.
-                static_assert(32 % V == 0, "units of at most 32 rows");
-#pragma unroll
-                for (int k = 0; k < UPT; ++k) {
-                    const int64_t row0 = (static_cast<int64_t>(k) * kRegConsThreads + warp * 32) * V;
-#pragma unroll
-                    for (int q = 0; q < V; ++q) {
-                        const int src = q * (32 / V) + lane / V;
-                        const int esel = lane % V;
-                        float v = 0.f;
-#pragma unroll
-                        for (int e = 0; e < V; ++e) {
-                            const float t = __shfl_sync(0xffffffffu, inc[k][e], src);
-                            v = e == esel ? t : v;
-                        }
-                        const int64_t row = row0 + q * 32 + lane;
-                        if (row < bv.m && v != 0.f) red_add_f64(bv.r + row, f32_to_f64(v));
-                    }
-                }
-                // A single CTA runs its blocks strictly in order (cyclic Gauss-Seidel), so its
-                // next read of r must see this scatter.  With several CTAs the next read may
-                // miss it: that is one more update in flight, within the bounded-delay model
-                // (Assumption D1), so no fence is spent there.
-                if (gridDim.x == 1) __threadfence();
-            }
+            if (any && !aborted) scatter_increment<V, UPT, kRegConsThreads>(inc, bv.r, bv.m, warp, lane);
             named_bar_sync(1, kRegConsThreads);  // scatter issued; rt and coef free
-            if (tid == 0) {
-                ++my_updates;
-                if (any) ++my_active;
-                const unsigned long long u1 = atomicAdd(&p.counters[0], 1ull);
-                const unsigned long long dly = u1 - u_read;
-                int bucket = 63 - __clzll(static_cast<long long>(dly + 1ull));
-                bucket = bucket > 31 ? 31 : bucket;
-                atomicAdd(&p.hist[bucket], 1ull);
-            }
+            if (tid == kRegConsThreads - 1) account_block(p, u_read, any, my_updates, my_active);
         }
     }
-    if (tid == 0) {
+    if (tid == kRegConsThreads - 1) {
         atomicAdd(&p.counters[1], my_updates);
         atomicAdd(&p.counters[2], my_active);
     }
@@ -674,60 +730,19 @@ __global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const Swe
     for (int s = 0; s < p.sweeps; ++s) {
         for (int b = blockIdx.x; b < p.nblocks; b += gridDim.x) {
             const BlockView<TA> bv = block_view<TA, false>(p, b);
-            // S.2: stale read of the residual into shared memory (rows >= m hold 0), and the
-            // block's per-column coefficients (the barrier that ended the previous block
-            // guarantees nobody still reads rt or coef).  The coefficient loads go out before
-            // the residual reload, and the last thread reads the update counter, so that
-            // neither latency waits behind the other.
-            double c_dw = 0.0, c_x = 0.0, c_lo = -INFINITY, c_hi = INFINITY, c_lin = 0.0;
-            float c_scale = 1.f;
-            if (tid < bv.wb) {
-                const int64_t j = bv.c0 + tid;
-                c_dw = bv.dw[j];
-                c_x = static_cast<double>(bv.x[j]);
-                if (bv.lo) c_lo = static_cast<double>(bv.lo[j]);
-                if (bv.hi) c_hi = static_cast<double>(bv.hi[j]);
-                if (bv.lin) c_lin = static_cast<double>(bv.lin[j]);
-                if (bv.scale) c_scale = bv.scale[j];
-            }
+            // S.2: stale read of the residual into shared memory, and the block's per-column
+            // coefficients (the barrier that ended the previous block guarantees nobody still
+            // reads rt or coef).  The coefficient loads go out before the residual reload, and
+            // the last thread reads the update counter, so that neither latency waits behind
+            // the other.
+            CoefLoads cl{};
+            if (tid < bv.wb) cl = load_coef(bv, tid);
             if (tid == kRcThreads - 1) {
                 u_read = ld_relaxed_u64(&p.counters[0]);
                 *s_gamma = static_cast<float>(launch_step(p, static_cast<long long>(u_read - p.k_base)));
             }
-            {
-                constexpr int kB = 8;
-                const double2* rsrc = reinterpret_cast<const double2*>(bv.r);
-                float2* rdst = reinterpret_cast<float2*>(rt);
-                const int pairs = static_cast<int>(bv.mcopy / 2);
-                for (int i0 = tid; i0 < pairs; i0 += kB * kRcThreads) {
-                    double2 v[kB];
-#pragma unroll
-                    for (int t = 0; t < kB; ++t) {
-                        const int i = i0 + t * kRcThreads;
-                        v[t] = i < pairs ? __ldcg(rsrc + i) : make_double2(0.0, 0.0);
-                    }
-#pragma unroll
-                    for (int t = 0; t < kB; ++t) {
-                        const int i = i0 + t * kRcThreads;
-                        if (i < pairs) rdst[i] = make_float2(f64_to_f32(v[t].x), f64_to_f32(v[t].y));
-                    }
-                }
-            }
-            if (tid < bv.wb) {
-                const double dj = c_dw;
-                ColCoef cf;
-                cf.x = static_cast<float>(c_x);
-                cf.lo = static_cast<float>(c_lo);
-                cf.hi = static_cast<float>(c_hi);
-                cf.dinv = dj > 0.0 ? static_cast<float>(1.0 / dj) : 0.f;
-                cf.thr = dj > 0.0 ? static_cast<float>(bv.lam / dj) : 0.f;
-                cf.scale = c_scale;
-                double lj = c_lin;
-                if (bv.dc.kind) lj -= bv.dc.lam * dc_hminus_grad(bv.dc, c_x);
-                cf.lin = static_cast<float>(lj);
-                cf.pad0 = 0.f;
-                coef[tid] = cf;
-            }
+            stage_residual<kRcThreads>(bv.r, bv.mcopy, rt, tid);
+            if (tid < bv.wb) coef[tid] = finish_coef(bv, cl);
 #pragma unroll
             for (int k = 0; k < UPT; ++k)
 #pragma unroll
@@ -804,23 +819,9 @@ __global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const Swe
                     }
                 }
                 // ---- best response (eq. 2) + fixed step (S.4), identical in every thread
-                float g;
-                {
-                    const float4* cp4 = reinterpret_cast<const float4*>(cp);
-                    const float4 q0 = cp4[0], q1 = cp4[1], q2 = cp4[2], q3 = cp4[3];
-                    g = (((q0.x + q0.y) + (q0.z + q0.w)) + ((q1.x + q1.y) + (q1.z + q1.w))) +
-                        (((q2.x + q2.y) + (q2.z + q2.w)) + ((q3.x + q3.y) + (q3.z + q3.w)));
-                }
+                const float g = sum_partials_16(cp);
                 buf ^= 1;
-                const float grad = bv.s_loss * g * cf.scale - bv.c2 * cf.x + cf.lin;
-                float xh = 0.f;
-                if (cf.dinv > 0.f) {
-                    const float vv = fmaf(-grad, cf.dinv, cf.x);
-                    const float av = fabsf(vv) - cf.thr;
-                    xh = av > 0.f ? copysignf(av, vv) : 0.f;
-                }
-                xh = fminf(fmaxf(xh, cf.lo), cf.hi);
-                const float xn = fmaf(gamma, xh - cf.x, cf.x);
+                const float xn = best_response_step(bv, cf, g, gamma);
                 const float dlt = xn - cf.x;
                 float dj = 0.f;
                 if (!*abort_flag) {
@@ -840,42 +841,11 @@ __global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const Swe
                     }
                 }
             }
-            // ---- r += A_i Delta_i : one FP64 atomic per row (skipping exact zeros), transposed
-            // through shuffles so that each red instruction covers 32 consecutive rows
+            // ---- r += A_i Delta_i
             const bool aborted = __shfl_sync(0xffffffffu, *abort_flag != 0, 0);
-            if (any && !aborted) {
-                static_assert(32 % V == 0, "units of at most 32 rows");
-#pragma unroll
-                for (int k = 0; k < UPT; ++k) {
-                    const int64_t row0 = (static_cast<int64_t>(k) * kRcThreads + warp * 32) * V;
-#pragma unroll
-                    for (int q = 0; q < V; ++q) {
-                        const int src = q * (32 / V) + lane / V;
-                        const int esel = lane % V;
-                        float v = 0.f;
-#pragma unroll
-                        for (int e = 0; e < V; ++e) {
-                            const float t = __shfl_sync(0xffffffffu, inc[k][e], src);
-                            v = e == esel ? t : v;
-                        }
-                        const int64_t row = row0 + q * 32 + lane;
-                        if (row < bv.m && v != 0.f) red_add_f64(bv.r + row, f32_to_f64(v));
-                    }
-                }
-                // a single CTA runs its blocks strictly in order (cyclic Gauss-Seidel): its next
-                // read of r must see this scatter
-                if (gridDim.x == 1) __threadfence();
-            }
+            if (any && !aborted) scatter_increment<V, UPT, kRcThreads>(inc, bv.r, bv.m, warp, lane);
             named_bar_sync(1, kRcThreads);  // scatter issued; rt and coef free
-            if (tid == kRcThreads - 1) {
-                ++my_updates;
-                if (any) ++my_active;
-                const unsigned long long u1 = atomicAdd(&p.counters[0], 1ull);
-                const unsigned long long dly = u1 - u_read;
-                int bucket = 63 - __clzll(static_cast<long long>(dly + 1ull));
-                bucket = bucket > 31 ? 31 : bucket;
-                atomicAdd(&p.hist[bucket], 1ull);
-            }
+            if (tid == kRcThreads - 1) account_block(p, u_read, any, my_updates, my_active);
         }
     }
     // no bulk copy may still be writing shared memory when the CTA exits (only after an
