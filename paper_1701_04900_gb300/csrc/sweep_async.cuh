@@ -621,15 +621,14 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
 // registers instead of 96, which is room for its units of the current column next to its
 // block increment.  Each thread keeps the units it read for a_j^T r~ in registers and forms
 // the increment a_j * Delta_j from them, so a column is read from shared memory once instead
-// of twice, and the column's ring stages are refilled at the column's barrier instead of
-// after the increment pass.
+// of twice.
 //
-// The ring is refilled at the column barrier: the stages of the CTA's columns form one
-// sequence (sweep, owned block, column, stage) and item k lives in slot k mod S.  Every warp
+// The ring is refilled at the column barrier.  The stages of the CTA's columns form one
+// sequence (sweep, owned block, column, stage), and item k lives in slot k mod S.  Every warp
 // has read all stages of column j before it arrives at the column's barrier, so right after
 // that barrier warp c (c < nchunks) refills the slot of the column's stage c with the item S
-// further on, with no release barriers or waits and one copy per warp.  Column j + 1's items are then issued before its dot
-// pass starts (nchunks <= S), so no wait forms a cycle.
+// further on: no release barriers or waits, one copy per warp.  Column j + 1's items are then
+// issued before its gradient pass starts (nchunks <= S), so no wait forms a cycle.
 // ---------------------------------------------------------------------------------------
 
 constexpr int kRcThreads = kRegConsThreads;
@@ -668,7 +667,7 @@ __device__ __forceinline__ void rc_issue(const SweepParams& p, const RcPos& q, i
     const uint32_t nbytes = static_cast<uint32_t>(min64(kRegStageUnits, units - u0) * 16);
     const TA* col = static_cast<const TA*>(p.A) + (static_cast<int64_t>(q.b) * p.w + q.jl) * p.lda;
     fills[st] += 1u;
-    fence_proxy_async_smem();
+    fence_proxy_async_smem();  // the slot's earlier generic reads before the copy's async writes
     mbar_arrive_expect_tx(&full[st], nbytes);
     bulk_load(ring + st * stage_bytes, col + u0 * V, nbytes, &full[st], l2_policy_evict_first());
 }
