@@ -304,6 +304,19 @@ int asyflexa_residual_noalloc(const asyflexa_problem* prob, const void* x, doubl
  * asyflexa_last_error(NULL). */
 int asyflexa_convert_check(int dir, const void* in, void* out, int64_t n, void* cuda_stream);
 
+/* Diagnostic: run the kernels' bounded wait on a shared-memory mbarrier that expects one
+ * arrival.  Every wait of the sweep kernels gives up after a time limit (2 s of the GPU's
+ * global timer), records a timeout for the host and returns, instead of spinning; this entry
+ * point runs that same wait with a caller's limit in a one-thread kernel.  arrive_first = 1:
+ * the thread arrives before waiting, so the wait completes at once; 0: nothing ever
+ * arrives, so the wait runs out after limit_ns nanoseconds (1e3 <= limit_ns <= 1e9).
+ * result: host array of 4 ints, written on return: [1 if the wait completed else 0, the
+ * recorded error (0, or ASYFLEXA_ETIMEOUT), the CTA's abort flag, elapsed microseconds].
+ * Synchronous (allocates 16 bytes of device memory, legacy default stream).  Returns
+ * ASYFLEXA_OK if the wait completed, ASYFLEXA_ETIMEOUT if it ran out (the context stays
+ * usable), ASYFLEXA_EINVAL / ENOMEM / ECUDA otherwise. */
+int asyflexa_wait_check(int arrive_first, int64_t limit_ns, int* result);
+
 /* Per-column scaled low-precision storage of an FP32 matrix, for the BF16/FP8 form of the
  * method: Q[:, j] = round(A[:, j] / scale[j]) in `dtype` (ASYFLEXA_BF16 or ASYFLEXA_FP8E4M3,
  * round-to-nearest, FP8 saturating to finite values), with scale[j] = max_i |A[i, j]| / qmax

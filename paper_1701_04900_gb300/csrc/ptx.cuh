@@ -56,23 +56,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity.  Returns false (after latching
-// kDevTimeout into *err and setting *abort) if the limit expires or another thread of
-// the CTA already aborted.  Never spins forever.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort,
-                                                  int* err) {
+// kDevTimeout into *err and setting *abort) if limit_ns of the global timer expire or another
+// thread of the CTA already aborted.  Never spins forever.
+__device__ __forceinline__ bool mbar_wait_bounded_for(uint64_t* bar, uint32_t parity, volatile int* abort, int* err,
+                                                      uint64_t limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 255u) == 0u) {
             if (*abort) return false;
-            if (global_timer_ns() - t0 > kWaitLimitNs) {
+            if (global_timer_ns() - t0 > limit_ns) {
                 *abort = 1;
                 atomicExch(err, kDevTimeout);
                 return false;
             }
         }
     }
+}
+
+// The kernels' wait: limit kWaitLimitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                                  int* err) {
+    return mbar_wait_bounded_for(bar, parity, abort, err, kWaitLimitNs);
 }
 
 // Orders this thread's earlier generic-proxy shared-memory accesses before later async-proxy

@@ -1,7 +1,9 @@
-// Diagnostic entry point asyflexa_convert_check: runs the kernels' own FP32 <-> FP64
+// Diagnostic entry points.  asyflexa_convert_check runs the kernels' own FP32 <-> FP64
 // conversions (convert.cuh) and their decoding of BF16 / FP8-e4m3 storage (ATraits in
 // types.cuh) over a caller's array, so that they can be compared bit for bit with IEEE 754
-// conversions and the formats' definitions computed elsewhere.
+// conversions and the formats' definitions computed elsewhere.  asyflexa_wait_check runs the
+// kernels' bounded mbarrier wait (ptx.cuh) on a barrier that is, or is never, arrived at, so
+// that a test can see a wait give up with the timeout status and the context stay usable.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -10,6 +12,7 @@
 
 #include "../../include/asyflexa.h"
 #include "convert.cuh"
+#include "ptx.cuh"
 #include "types.cuh"
 
 namespace asyflexa_internal {
@@ -40,6 +43,25 @@ __global__ void __launch_bounds__(256) decode_kernel(const uint4* in, float* out
 #pragma unroll
         for (int k = 0; k < V; ++k) out[u * V + k] = a[k];
     }
+}
+
+// One thread: an mbarrier expecting one arrival, arrived at first or never, then the bounded
+// wait.  out: [completed (1/0), err (0 or kDevTimeout), abort flag, elapsed microseconds].
+__global__ void wait_check_kernel(int arrive_first, unsigned long long limit_ns, int* out) {
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    asyflexa::mbar_init(&bar, 1);
+    abort_flag = 0;
+    asyflexa::fence_barrier_init();
+    out[1] = 0;
+    if (arrive_first) asyflexa::mbar_arrive(&bar);
+    const uint64_t t0 = asyflexa::global_timer_ns();
+    const bool ok = asyflexa::mbar_wait_bounded_for(&bar, 0u, &abort_flag, out + 1, limit_ns);
+    const uint64_t t1 = asyflexa::global_timer_ns();
+    out[0] = ok ? 1 : 0;
+    out[2] = abort_flag;
+    out[3] = static_cast<int>((t1 - t0) / 1000u);
 }
 
 int fail(int code, const std::string& m) {
@@ -75,4 +97,19 @@ extern "C" int asyflexa_convert_check(int dir, const void* in, void* out, int64_
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(ASYFLEXA_ECUDA, std::string("convert_check launch: ") + cudaGetErrorString(e));
     return ASYFLEXA_OK;
+}
+
+extern "C" int asyflexa_wait_check(int arrive_first, int64_t limit_ns, int* result) {
+    if (!result) return fail(ASYFLEXA_EINVAL, "result is NULL");
+    if (limit_ns < 1000 || limit_ns > 1000000000)
+        return fail(ASYFLEXA_EINVAL, "limit_ns must be within [1e3, 1e9]");
+    int* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 4 * sizeof(int));
+    if (e != cudaSuccess) return fail(ASYFLEXA_ENOMEM, std::string("wait_check: ") + cudaGetErrorString(e));
+    wait_check_kernel<<<1, 1>>>(arrive_first ? 1 : 0, static_cast<unsigned long long>(limit_ns), d);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(result, d, 4 * sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(ASYFLEXA_ECUDA, std::string("wait_check: ") + cudaGetErrorString(e));
+    return result[0] ? ASYFLEXA_OK : ASYFLEXA_ETIMEOUT;
 }

@@ -77,7 +77,7 @@ EXPORTS = [
     "asyflexa_last_error", "asyflexa_residual_noalloc", "asyflexa_quantize", "asyflexa_gather_columns",
     "asyflexa_batch_create", "asyflexa_batch_solve", "asyflexa_batch_destroy",
     "asyflexa_multi_create", "asyflexa_multi_solve", "asyflexa_multi_destroy",
-    "asyflexa_convert_check",
+    "asyflexa_convert_check", "asyflexa_wait_check",
 ]
 BATCH_SHARED_A = 1
 
@@ -124,6 +124,8 @@ def lib(path: str | None = None):
     L.asyflexa_residual_noalloc.argtypes = [C.POINTER(Problem), vp, vp, vp]
     L.asyflexa_convert_check.restype = C.c_int
     L.asyflexa_convert_check.argtypes = [i32, vp, vp, C.c_int64, vp]
+    L.asyflexa_wait_check.restype = C.c_int
+    L.asyflexa_wait_check.argtypes = [i32, C.c_int64, C.POINTER(C.c_int)]
     L.asyflexa_quantize.restype = C.c_int
     L.asyflexa_quantize.argtypes = [vp, C.c_int64, C.c_int64, C.c_int64, i32, vp, C.c_int64, vp, vp]
     L.asyflexa_batch_create.restype = C.c_int
@@ -350,6 +352,16 @@ def convert_check(src, stream=None, storage: str | None = None):
     if rc != OK:
         raise AsyflexaError(rc, lib().asyflexa_last_error(None).decode())
     return out
+
+
+def wait_check(arrive_first: bool, limit_ns: int):
+    """The kernels' bounded mbarrier wait in a one-thread kernel (asyflexa_wait_check):
+    returns (status, completed, recorded error, abort flag, elapsed microseconds)."""
+    res = (C.c_int * 4)()
+    rc = lib().asyflexa_wait_check(1 if arrive_first else 0, int(limit_ns), res)
+    if rc not in (OK, ETIMEOUT):
+        raise AsyflexaError(rc, lib().asyflexa_last_error(None).decode())
+    return rc, res[0], res[1], res[2], res[3]
 
 
 def quantize(At, m: int, kind: str, stream=None):
