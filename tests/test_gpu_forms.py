@@ -2,7 +2,7 @@
 
 Mixed precision: A stored as per-column scaled BF16 / FP8-e4m3 codes (library quantiser),
 sweeps on the codes, exact residual refreshes and checks on the FP32 master copy, and a
-final FP32 polish; the returned x is judged by the oracle on the FP32 (master) problem.
+final FP32 polish; the returned x is checked by the oracle on the FP32 (master) problem.
 """
 
 import math
