@@ -572,3 +572,68 @@ def test_liu_wright_lambda_rule():
     d = liu_wright_lasso(200, 400, 5, sigma=0.01, seed=1)
     assert d["lam"] == pytest.approx(20 * np.sqrt(200 * np.log(400)) * 0.01, rel=1e-15)
     assert np.count_nonzero(d["xbar"]) == 5
+
+
+# ---------------------------------------------------------------- block tables and orders
+
+def test_block_steps_hand_table_ragged():
+    """Jacobi step table (Algorithm 1 with the Section 4 stepsize rule, block i of a sweep
+    takes steps[i]): n = 10 coordinates in blocks of w = 4 are {0..3}, {4..7}, {8, 9}."""
+    got = O.block_steps(10, 4, [0.5, 0.25, 0.125])
+    want = [0.5, 0.5, 0.5, 0.5, 0.25, 0.25, 0.25, 0.25, 0.125, 0.125]
+    assert list(got) == want
+    assert list(O.block_steps(3, 1, [1.0, 2.0, 3.0])) == [1.0, 2.0, 3.0]
+    assert list(O.block_steps(5, 8, [0.75])) == [0.75] * 5
+
+
+@pytest.mark.parametrize("w", [1, 3])
+def test_random_sequential_visit_counts_on_a_diagonal_design(w):
+    """Random-sequential order (the Corollary of Section 3: a uniformly drawn block, no delay)
+    on A = diag(s), lam = 0.3: blocks decouple and the exact coordinate minimiser is
+    x*_j = soft(s_j b_j, lam) / s_j^2, so a block visited k times with step gamma holds
+    x* + (1 - gamma)^k (x0 - x*) and an unvisited block keeps x0.  The draws are over the
+    ceil(n / w) blocks, reproduced here from the same seed."""
+    n, gamma, count = 11, 0.6, 9
+    rng = np.random.default_rng(3)
+    s = rng.uniform(0.5, 2.0, n)
+    b = rng.standard_normal(n) * 2
+    lam = 0.3
+    p = _prob(np.diag(s), b, lam)
+    d = O.surrogate_weights(p)
+    xstar = np.sign(s * b) * np.maximum(np.abs(s * b) - lam, 0) / s ** 2
+    x0 = rng.standard_normal(n)
+    x, r = O.random_sequential(p, x0, O.residual(p, x0), d, gamma, w, count, np.random.default_rng(17))
+    nb = -(-n // w)
+    draws = np.random.default_rng(17).integers(0, nb, size=count)
+    visits = np.bincount(draws, minlength=nb)
+    want = np.empty(n)
+    for i in range(nb):
+        cols = np.arange(i * w, min(n, (i + 1) * w))
+        want[cols] = xstar[cols] + (1 - gamma) ** visits[i] * (x0[cols] - xstar[cols])
+    np.testing.assert_allclose(x, want, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(r, s * x - b, rtol=0, atol=1e-13)
+    # 9 draws: at w = 1 (11 blocks) some block stays unvisited, at w = 3 (4 blocks) some
+    # block is visited more than once
+    assert (visits == 0).any() if w == 1 else (visits > 1).any()
+
+
+@pytest.mark.parametrize("gamma", [1.0, 0.7])
+def test_solve_jacobi_is_damped_jacobi_for_the_normal_equations(gamma):
+    """lam = 0, no box, d_j = ||a_j||^2: the Jacobi form of the block update is the textbook
+    (damped) Jacobi iteration for A^T A x = A^T b, x_{k+1} = x_k - gamma D^{-1} A^T (A x_k - b),
+    D = diag(A^T A); the residual it returns is A x - b."""
+    rng = np.random.default_rng(8)
+    m, n = 60, 12
+    A = rng.standard_normal((m, n)) + 3.0 * np.eye(m, n) * 4
+    b = rng.standard_normal(m)
+    p = _prob(A, b, 0.0)
+    d = O.surrogate_weights(p)
+    x0 = rng.standard_normal(n)
+    x, r = O.solve_jacobi(p, x0, d, gamma, 7)
+    G = A.T @ A
+    Dinv = 1.0 / np.diag(G)
+    xr = x0.copy()
+    for _ in range(7):
+        xr = xr - gamma * Dinv * (G @ xr - A.T @ b)
+    np.testing.assert_allclose(x, xr, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(r, A @ x - b, rtol=1e-12, atol=1e-12)
