@@ -188,6 +188,8 @@ typedef struct {
                                    stopping test: with FP32 iterates ||A^T r||_inf carries the
                                    rounding of the heaviest column, which loosens the bound. */
     double tau_extra;           /* solve with tau_adapt: the proximal weight added at the end */
+    int32_t batch_form;         /* batched solve: ASYFLEXA_BATCH_FORM_ASYNC or ASYFLEXA_BATCH_FORM_GS */
+    int32_t ctas_per_sm;        /* batched solve, Gauss-Seidel form: CTAs resident per SM (autotuned) */
 } asyflexa_stats;
 
 /* Library version (ASYFLEXA_ABI_VERSION).  Never fails. */
@@ -336,34 +338,94 @@ int asyflexa_quantize(const float* A, int64_t m, int64_t n, int64_t lda, int32_t
 int asyflexa_gather_columns(const void* A, int64_t lda, int32_t dtype, int64_t m, const int32_t* idx, int64_t k,
                             void* out, int64_t ldo, void* cuda_stream);
 
+/* Adjoint of the LASSO solution map x*(lambda, b) (system form 3; not in the paper, derived
+ * from the LASSO optimality conditions of eq. 1 with f = 0.5||Ax - b||^2, Section 4.2).  On
+ * the support S = { j : |x_j| > rel_tol * max(1, ||x||_inf) } with signs s = sign(x_S), the
+ * conditions A_S^T (A_S x_S - b) + lambda s = 0 are smooth in (lambda, b); for a loss with
+ * v = dL/dx* and w solving (A_S^T A_S) w = v_S:
+ *     *out_dlam = dL/dlambda = -s^T w,        out_db = dL/db = A_S w.
+ * w is computed by the library's block update on the gathered columns A_S (an internal
+ * handle with b = 0, lambda = 0 and linear term -v_S, whose minimiser solves that system);
+ * out_db is that handle's exact residual at w.
+ *
+ * A: m x n column-major, F64 or F32 storage (EUNSUPPORTED otherwise), lda as for
+ * asyflexa_create.  x (the solution) and v: device, n entries of A's type.  rel_tol >= 0.
+ * opts: the support solve's options (NULL = async, one CTA, block_w 8, gamma 1, tol_stat
+ * 1e-7, max_sweeps 2000); f_star is ignored.  out_dlam: host double.  out_db: device, m
+ * doubles.  out_support (host, may be NULL): |S|.  out_stats (host, may be NULL): the
+ * support solve's statistics.  An empty support gives 0 and db = 0.
+ *
+ * Allocates (and frees) device memory for A_S and its vectors; enqueued on cuda_stream and
+ * synchronises it.  Returns OK, ENOTCONV (the support solve hit max_sweeps; the results are
+ * those of its last iterate), or EINVAL / EUNSUPPORTED / ENOMEM / ECUDA / ENONFINITE with a
+ * message in asyflexa_last_error(NULL). */
+int asyflexa_adjoint(const void* A, int64_t lda, int32_t a_dtype, int64_t m, int64_t n, const void* x,
+                     const void* v, double rel_tol, const asyflexa_opts* opts, double* out_dlam, double* out_db,
+                     int64_t* out_support, asyflexa_stats* out_stats, void* cuda_stream);
+
 /* ---------------------------------------------------------------- batched problems
  * Many independent problems (e.g. LASSO instances of uneven sizes, or one matrix with many
- * lambda values) solved together: one persistent asynchronous sweep launch covers the blocks
- * of every problem (each block still has a single owning CTA, Assumption D4), and every
- * round of refresh_every sweeps, exact residual refreshes, objectives and a device-side
- * convergence test is replayed as one captured CUDA graph. */
+ * lambda values) solved together, in one of two forms:
+ *
+ *   ASYFLEXA_BATCH_FORM_GS (Gauss-Seidel form): ONE persistent launch for the whole batch.
+ *     Each CTA takes the next problem from a queue (largest first), runs Algorithm 1 on it
+ *     alone -- a single owner for every block, so exact cyclic Gauss-Seidel over scalar
+ *     blocks (Section 4.1) with the fixed step of S.4 and the best response of eq. 2 -- with
+ *     the residual held in registers, and runs its own stopping test (exact residual, F,
+ *     gap, and the Section 4.3 merit) before taking the next problem.  FP32 problems with
+ *     m <= 8192.  The launch is captured in a CUDA graph and replayed by later solves.
+ *   ASYFLEXA_BATCH_FORM_ASYNC (rounds of the asynchronous kernel): every round of
+ *     refresh_every sweeps is one persistent launch covering the blocks of every problem
+ *     (each block still has a single owning CTA, Assumption D4), followed by exact residual
+ *     refreshes, objectives and a device-side convergence test, the round replayed as a
+ *     captured CUDA graph.  FP32 problems with m <= 24576.
+ *
+ * The form is chosen at create (flags) or automatically: the Gauss-Seidel form when every
+ * problem fits it and there are at least (SM count / 4) problems, else the async rounds.  An
+ * autotuner then picks the form's launch shape at the first solve by timing one real sweep of
+ * every problem per candidate -- Gauss-Seidel form: 8 or 16 consumer warps per CTA (2 or 1
+ * CTAs per SM) with the ring depth that fits; async rounds: the block width 16, 32 or 64 --
+ * and caches the choice per batch shape (problem count, total size, largest m, flags) for
+ * the life of the process. */
 typedef struct asyflexa_batch_s* asyflexa_batch_t;
 
 /* flags for asyflexa_batch_create */
-#define ASYFLEXA_BATCH_SHARED_A 1   /* problems share A: blocks are interleaved across problems so
-                                       that their reads of the same panel hit L2 */
+#define ASYFLEXA_BATCH_SHARED_A 1     /* problems share A: normal L2 priority for its reads (and,
+                                         in the async rounds, blocks interleaved across problems
+                                         so that their reads of the same panel hit L2) */
+#define ASYFLEXA_BATCH_FORM_ASYNC 2   /* force the async rounds form */
+#define ASYFLEXA_BATCH_FORM_GS 4      /* force the Gauss-Seidel form (EUNSUPPORTED if a problem
+                                         does not fit it) */
 
-/* probs: count FP32 problems (as for asyflexa_create; m <= 24576 each).  opts: shared method
- * parameters (mode is always ASYNC; block_w = 0 lets an autotuner pick the width from
- * {16, 32, 64} by timing one sweep each at the first solve).  All problems and their device
- * buffers must outlive the batch.  Errors: asyflexa_last_error(NULL). */
+/* probs: count FP32 problems (as for asyflexa_create; LASSO or NCQUAD loss).  opts: shared
+ * method parameters: gamma, tau, tau_rel, tol_gap, tol_stat, max_sweeps, num_ctas (0 = all
+ * SMs; in the Gauss-Seidel form the most CTAs that run problems at once), check_every
+ * (Gauss-Seidel form: sweeps between stopping tests), refresh_every (async rounds: sweeps per
+ * round), switch_tol, block_w (async rounds; 0 lets the autotuner pick it).  All problems and
+ * their device buffers must outlive the batch.  Errors: asyflexa_last_error(NULL). */
 int asyflexa_batch_create(asyflexa_batch_t* hb, const asyflexa_problem* probs, int32_t count,
                           const asyflexa_opts* opts, int32_t flags, void* cuda_stream);
 
 /* Solve every problem from its iterate xs[k] (device, in place).  f_star: count optimal values
- * or NULL; problem k stops when (F_k - f_star[k])/|f_star[k]| <= tol_gap, or, when f_star[k]
- * is NaN (or f_star is NULL), when a round lowers F_k by no more than switch_tol * |F_k|.
- * Converged problems are skipped by later rounds.  per (count entries, may be NULL): each
- * problem's check at its returned x (F, gap, stationarity) with its sweeps and status;
- * total: sweeps (rounds x refresh_every, plus autotuning sweeps), block_updates, seconds
- * (CUDA events around the whole solve), block_w, status (OK if all converged). */
+ * or NULL.  Problem k is done when ||xhat(x) - x||_inf / max(1, ||x||_inf) <= tol_stat and, if
+ * f_star[k] is a number, (F_k - f_star[k]) / |f_star[k]| <= tol_gap.  Gauss-Seidel form: both
+ * are evaluated by the problem's CTA every check_every sweeps (every 2 sweeps once the merit is
+ * within 2 tol_stat).  Async rounds: a problem leaves the rounds when its gap meets tol_gap
+ * (without f_star: when a round lowers F_k by no more than switch_tol * |F_k|); the exact
+ * stationarity check then runs for it, and a problem that fails it rejoins the rounds.
+ * per (count entries, may be NULL): each problem's F, rel_gap, stat_xhat, nnz, sweeps,
+ * block_updates and status (ENOTCONV at max_sweeps, ENONFINITE if F became non-finite) as the
+ * stopping test saw them; for the exact check of asyflexa_check use asyflexa_batch_check.
+ * total: sweeps (the largest number of sweeps of any problem, tuning sweeps included),
+ * block_updates (all problems), seconds (CUDA events around the solve), block_w (1 in the
+ * Gauss-Seidel form: scalar blocks), batch_form, ctas_per_sm, status (OK if all done). */
 int asyflexa_batch_solve(asyflexa_batch_t hb, void* const* xs, const double* f_star, asyflexa_stats* per,
                          asyflexa_stats* total);
+
+/* The exact check of asyflexa_check (exact residual, F, gap with f_star[k], stat_xhat,
+ * stat_mf, KKT, nnz) for every problem at xs[k]; f_star may be NULL.  per: count entries.
+ * Synchronises.  Returns the first error, else OK. */
+int asyflexa_batch_check(asyflexa_batch_t hb, void* const* xs, const double* f_star, asyflexa_stats* per);
 
 /* Release the batch and its internal handles.  NULL is a no-op. */
 int asyflexa_batch_destroy(asyflexa_batch_t hb);

@@ -5,10 +5,10 @@ Backward, given v = dL/dx*: on the support S of x* with signs s the optimality c
 A_S^T (A_S x_S - b) + lam s = 0 are smooth in (lam, b), so with w solving
 (A_S^T A_S) w = v_S,
     dL/dlam = -s^T w,     dL/db = A_S w.
-w is computed by the library's own block update restricted to the support: the columns A_S
-are gathered (asyflexa_gather_columns) and the method is run on
+The library computes both in one call (asyflexa_adjoint): it selects S by
+|x_j| > SUPPORT_REL_TOL * max(1, ||x||_inf), gathers A_S, runs its own block update on
     min_w 0.5||A_S w||^2 - v_S^T w      (b = 0, lam = 0, linear term -v_S),
-whose minimiser solves the system above; the exact residual of that run is A_S w = dL/db.
+whose minimiser solves the system above, and returns -s^T w and the exact residual A_S w.
 Valid where the support and the signs of x* are locally constant.
 """
 
@@ -21,7 +21,13 @@ import torch
 from . import native
 from .native import AsyflexaError, Solver, lib
 
+# The fixed step leaves geometric tails (1 - gamma)^k on coordinates that are zero at the
+# optimum; the support excludes them with this relative threshold.
 SUPPORT_REL_TOL = 1e-5
+
+# The support problem is small: one CTA runs exact cyclic Gauss-Seidel on it.
+ADJOINT_DEFAULTS = dict(mode="async", num_ctas=1, block_w=8, gamma=1.0, max_sweeps=2000, check_every=5,
+                        refresh_every=5, tol_stat=1e-6)
 
 
 def gather_columns(At, idx, m: int):
@@ -39,11 +45,24 @@ def gather_columns(At, idx, m: int):
     return out
 
 
-def support(x, rel_tol: float = SUPPORT_REL_TOL):
-    """Indices with |x_j| > rel_tol * max(1, ||x||_inf) (the fixed step leaves geometric
-    tails (1 - gamma)^k on coordinates that are zero at the optimum; they are excluded)."""
-    scale = max(1.0, float(x.abs().max())) if x.numel() else 1.0
-    return torch.nonzero(x.abs() > rel_tol * scale).flatten()
+def adjoint(At, m: int, x, v, rel_tol: float = SUPPORT_REL_TOL, **opts):
+    """(dL/dlam, dL/db, |S|, stats of the support solve) for v = dL/dx* at the solution x
+    (asyflexa_adjoint).  x and v: (n,) CUDA tensors of x's dtype; dL/db is FP64 (m,)."""
+    if At.dim() != 2 or not At.is_contiguous():
+        raise ValueError("At must be a contiguous (n, lda) CUDA tensor")
+    xt = x.detach().contiguous()
+    vt = v.detach().to(xt.dtype).contiguous()
+    db = torch.empty(m, dtype=torch.float64, device=x.device)
+    dlam = C.c_double(0.0)
+    k = C.c_int64(0)
+    st = native.Stats()
+    o = native.make_opts(**dict(ADJOINT_DEFAULTS, **opts))
+    rc = lib().asyflexa_adjoint(At.data_ptr(), At.shape[1], native._dtype_code(At), m, At.shape[0], xt.data_ptr(),
+                                vt.data_ptr(), float(rel_tol), C.byref(o), C.byref(dlam), db.data_ptr(),
+                                C.byref(k), C.byref(st), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if rc not in (native.OK, native.ENOTCONV):
+        raise AsyflexaError(rc, lib().asyflexa_last_error(None).decode())
+    return dlam.value, db, int(k.value), st.as_dict()
 
 
 class LassoSolution(torch.autograd.Function):
@@ -67,28 +86,10 @@ class LassoSolution(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gx):
         (x,) = ctx.saved_tensors
-        At, m = ctx.At, ctx.m
-        S = support(x)
-        k = int(S.numel())
-        dlam = torch.zeros((), dtype=torch.float64, device=x.device)
-        db = torch.zeros(m, dtype=torch.float64, device=x.device)
-        if k > 0:
-            AS = gather_columns(At, S, m)
-            lin = (-gx[S]).to(torch.float32).contiguous()
-            zero_b = torch.zeros(m, dtype=torch.float32, device=x.device)
-            kw = dict(mode="async", num_ctas=1, block_w=8, gamma=1.0, max_sweeps=2000, check_every=5,
-                      refresh_every=5, tol_stat=1e-6)
-            kw.update(ctx.adjoint_kwargs or {})
-            adj = Solver(AS, zero_b, 0.0, m=m, lin=lin, **kw)
-            w = torch.zeros(k, dtype=torch.float32, device=x.device)
-            st = adj.solve(w)
-            if st["status"] not in (native.OK, native.ENOTCONV):
-                raise AsyflexaError(st["status"], "adjoint solve failed")
-            db = adj.residual()                      # A_S w - 0, FP64
-            adj.close()
-            dlam = -(torch.sign(x[S]).double() * w.double()).sum()
+        dlam, db, _, _ = adjoint(ctx.At, ctx.m, x, gx, **(ctx.adjoint_kwargs or {}))
         lam_like = ctx.lam_like
-        g_lam = dlam.to(lam_like.dtype).reshape(lam_like.shape) if torch.is_tensor(lam_like) else None
+        g_lam = torch.tensor(dlam, dtype=lam_like.dtype, device=x.device).reshape(lam_like.shape) \
+            if torch.is_tensor(lam_like) else None
         return g_lam, db.to(ctx.b_dtype), None, None, None, None
 
 

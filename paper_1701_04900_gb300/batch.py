@@ -9,16 +9,23 @@ from . import native
 from .native import AsyflexaError, Problem, Stats, default_opts, lib
 
 
+FORMS = {"auto": 0, "async": native.BATCH_FORM_ASYNC, "gs": native.BATCH_FORM_GS}
+
+
 class BatchSolver:
-    """Many FP32 problems solved together (one sweep launch per round, CUDA-graph rounds).
+    """Many FP32 problems solved together (asyflexa_batch_*).
 
     ``problems``: list of dicts with keys At (n, lda) CUDA float32, b, lam, m and optional
-    lo, hi, lin, loss ("lasso"/"ncquad"), c.  ``block_w = 0`` autotunes the block width.
-    ``shared_a``: the problems share one matrix (blocks are interleaved for L2 reuse).
+    lo, hi, lin, loss ("lasso"/"ncquad"), c.  ``form``: "gs" (one persistent launch, one CTA
+    per problem at a time, exact Gauss-Seidel with in-kernel stopping tests), "async" (rounds
+    of the asynchronous kernel over all problems' blocks) or "auto".  ``block_w = 0``
+    autotunes the block width of the async rounds.  ``shared_a``: the problems share one
+    matrix.
     """
 
     def __init__(self, problems, *, block_w=32, gamma=0.9, tau=0.0, tau_rel=0.0, refresh_every=10,
-                 max_sweeps=1000, num_ctas=0, tol_gap=1e-6, switch_tol=1e-9, shared_a=False, stream=None):
+                 check_every=10, max_sweeps=1000, num_ctas=0, tol_gap=1e-6, tol_stat=1e-6, switch_tol=1e-9,
+                 shared_a=False, form="auto", stream=None):
         import torch
         L = lib()
         n = len(problems)
@@ -39,12 +46,15 @@ class BatchSolver:
         o = default_opts()
         o.block_w, o.mode, o.gamma, o.tau, o.tau_rel = int(block_w), native.ASYNC, float(gamma), float(tau), float(tau_rel)
         o.refresh_every, o.max_sweeps, o.num_ctas = int(refresh_every), int(max_sweeps), int(num_ctas)
-        o.tol_gap, o.switch_tol = float(tol_gap), float(switch_tol)
+        o.check_every = int(check_every)
+        o.tol_gap, o.tol_stat, o.switch_tol = float(tol_gap), float(tol_stat), float(switch_tol)
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
+        if form not in FORMS:
+            raise ValueError(f"form must be one of {sorted(FORMS)}")
+        flags = (native.BATCH_SHARED_A if shared_a else 0) | FORMS[form]
         h = C.c_void_p()
-        rc = L.asyflexa_batch_create(C.byref(h), arr, n, C.byref(o), native.BATCH_SHARED_A if shared_a else 0,
-                                     C.c_void_p(stream))
+        rc = L.asyflexa_batch_create(C.byref(h), arr, n, C.byref(o), flags, C.c_void_p(stream))
         if rc != native.OK:
             raise AsyflexaError(rc, L.asyflexa_last_error(None).decode())
         self.h, self.count, self.problems = h, n, arr
@@ -59,9 +69,23 @@ class BatchSolver:
         per = (Stats * self.count)()
         tot = Stats()
         rc = L.asyflexa_batch_solve(self.h, ptrs, fs, per, C.byref(tot))
-        if rc < 0:
+        # ENOTCONV / ENONFINITE describe problems (their own status is in per): not raised
+        if rc < 0 and rc != native.ENONFINITE:
             raise AsyflexaError(rc, L.asyflexa_last_error(None).decode())
         return [s.as_dict() for s in per], tot.as_dict()
+
+    def check(self, xs, f_star=None):
+        """The library's exact check (asyflexa_check) of every problem at xs; list of dicts."""
+        L = lib()
+        ptrs = (C.c_void_p * self.count)(*[x.data_ptr() for x in xs])
+        fs = None
+        if f_star is not None:
+            fs = (C.c_double * self.count)(*[math.nan if v is None else float(v) for v in f_star])
+        per = (Stats * self.count)()
+        rc = L.asyflexa_batch_check(self.h, ptrs, fs, per)
+        if rc != native.OK:
+            raise AsyflexaError(rc, L.asyflexa_last_error(None).decode())
+        return [s.as_dict() for s in per]
 
     def close(self):
         if getattr(self, "h", None):

@@ -24,7 +24,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libasyflexa.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 UNITS = ["api.cu", "inst_f64.cu", "inst_f32.cu", "inst_bf16.cu", "inst_fp8.cu", "noalloc.cu", "quantize.cu",
-         "batch.cu", "multi.cu", "selftest.cu"]
+         "batch.cu", "multi.cu", "selftest.cu", "adjoint.cu"]
 
 
 def _nvcc() -> str:

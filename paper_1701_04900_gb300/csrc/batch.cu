@@ -1,25 +1,35 @@
 // Batched form: many independent problems (uneven sizes, or one matrix with many lambda
-// values) solved by one persistent asynchronous sweep launch per round, each round (sweeps,
-// exact residual refreshes, objectives, device-side convergence test) replayed as a
-// captured CUDA graph.
+// values) solved together, in one of two forms.
+//
+// Gauss-Seidel form (batch_gs.cuh): ONE persistent launch for the whole batch; each CTA
+// solves whole problems from a queue (largest first), one at a time, by exact cyclic
+// Gauss-Seidel with its own stopping test.  The launch is captured in a CUDA graph.
+//
+// Async rounds: one persistent asynchronous sweep launch per round covers the blocks of
+// every problem; each round (sweeps, exact residual refreshes, objectives, device-side
+// convergence test) is replayed as a captured CUDA graph.  The sweep kernel is the
+// register-increment async kernel of sweep_async.cuh in its BATCHED form: the blocks of all
+// problems form one global list, CTA c owns the global blocks c, c + G, ..., and a converged
+// problem's blocks are skipped from the next round on.
 //
 // Every problem keeps its own internal handle for the surrogate weights, the FP64 residual
-// and the refresh / objective / check kernels.  The sweep kernel is the register-increment
-// async kernel of sweep_async.cuh in its BATCHED form: the blocks of all problems form one
-// global list, CTA c owns the global blocks c, c + G, ..., and a converged problem's blocks
-// are skipped from the next round on.  The block width is fixed by the options or, with
-// block_w = 0, picked by a small autotuner that times one sweep per candidate width.
+// and the refresh / objective / check kernels.  An autotuner picks the launch shape of the
+// chosen form by timing one real sweep per candidate and caches it per batch shape.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <algorithm>
+#include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "handle.h"
 #include "sweep_async.cuh"
+#include "batch_gs.cuh"
 
 extern template struct asyflexa::Launcher<float>;
 
@@ -74,6 +84,57 @@ __global__ void batch_converge_kernel(ConvState* cs, BatchInst* inst, int count,
 
 constexpr int kCandidates[] = {16, 32, 64};
 
+// Launch shape of the Gauss-Seidel form.
+struct GsChoice {
+    int nw = 0, upt = 0, stages = 0, ctas_per_sm = 0, grid = 0;
+    int64_t slot_bytes = 0;
+    size_t smem = 0;
+    const void* kernel = nullptr;
+    bool operator==(const GsChoice& o) const { return nw == o.nw && upt == o.upt && stages == o.stages && grid == o.grid; }
+};
+
+// Instantiated (consumer warps, units per thread) pairs: columns of up to NW * 32 * UPT * 4 rows.
+const void* gs_kernel(int nw, int upt) {
+    using namespace asyflexa;
+    if (nw == 7) {
+        switch (upt) {
+            case 2: return reinterpret_cast<const void*>(batch_gs_kernel<7, 2>);
+            case 3: return reinterpret_cast<const void*>(batch_gs_kernel<7, 3>);
+            case 5: return reinterpret_cast<const void*>(batch_gs_kernel<7, 5>);
+            case 6: return reinterpret_cast<const void*>(batch_gs_kernel<7, 6>);
+            default: return nullptr;
+        }
+    }
+    if (nw == 15) {
+        switch (upt) {
+            case 1: return reinterpret_cast<const void*>(batch_gs_kernel<15, 1>);
+            case 2: return reinterpret_cast<const void*>(batch_gs_kernel<15, 2>);
+            case 3: return reinterpret_cast<const void*>(batch_gs_kernel<15, 3>);
+            case 5: return reinterpret_cast<const void*>(batch_gs_kernel<15, 5>);
+            default: return nullptr;
+        }
+    }
+    return nullptr;
+}
+
+int gs_upt_for(int nw, int64_t units) {
+    const int64_t t = static_cast<int64_t>(nw) * 32;
+    const int64_t need = (units + t - 1) / t;
+    static const int k7[] = {2, 3, 5, 6};
+    static const int k15[] = {1, 2, 3, 5};
+    const int* c = nw == 7 ? k7 : k15;
+    for (int i = 0; i < 4; ++i)
+        if (c[i] >= need) return c[i];
+    return 0;
+}
+
+constexpr int64_t kGsMaxRows = 8192;   // the Gauss-Seidel form's column limit
+
+// Autotuned launch shapes, per batch shape, for the life of the process.
+std::mutex g_tune_mu;
+std::map<std::string, GsChoice> g_gs_tuned;
+std::map<std::string, int> g_w_tuned;
+
 }  // namespace
 
 struct asyflexa_batch_s {
@@ -110,6 +171,19 @@ struct asyflexa_batch_s {
     int grid = 0;          // CTAs of the next sweep launch
     int graph_grid = 0;    // CTAs of the captured round
     long long launches = 0;
+    // Gauss-Seidel form
+    int form = 0;                       // ASYFLEXA_BATCH_FORM_ASYNC or ASYFLEXA_BATCH_FORM_GS
+    int64_t max_units = 0;              // 16-byte units of the longest column
+    std::vector<asyflexa::GsInst> h_gs;
+    asyflexa::GsInst* d_gs = nullptr;
+    int* d_order = nullptr;
+    int* d_queue = nullptr;
+    GsChoice gs{};                      // launch shape (nw == 0: not chosen yet)
+    cudaGraph_t gs_graph = nullptr;
+    cudaGraphExec_t gs_exec = nullptr;
+    GsChoice gs_graph_cfg{};
+    int smem_per_sm = 0;
+    std::string shape_key;
 };
 
 namespace {
@@ -257,6 +331,430 @@ int enqueue_round(asyflexa_batch_s& B, void* const* xs) {
     return ASYFLEXA_OK;
 }
 
+
+// ------------------------------------------------------------------ Gauss-Seidel form
+
+// The launch shape for nw consumer warps: units per thread for the longest column, the ring
+// depth that fits the shared memory of the CTAs an SM holds, and the grid.
+int gs_shape(asyflexa_batch_s& B, int nw, GsChoice* out) {
+    GsChoice c;
+    c.nw = nw;
+    c.upt = gs_upt_for(nw, B.max_units);
+    c.kernel = c.upt ? gs_kernel(nw, c.upt) : nullptr;
+    if (!c.kernel) return ASYFLEXA_EUNSUPPORTED;
+    const int want_per_sm = nw < 8 ? 2 : 1;
+    const size_t slot_bytes = static_cast<size_t>((B.max_units * 16 + 127) / 128 * 128);
+    const asyflexa::GsLayout L0 = asyflexa::make_gs_layout(nw, slot_bytes, 0);
+    const size_t budget = std::min<size_t>(B.smem_optin, static_cast<size_t>(B.smem_per_sm) / want_per_sm - 1024);
+    if (L0.total + 2 * (L0.slot_bytes + sizeof(asyflexa::GsSlot) + 16) > budget) return ASYFLEXA_EUNSUPPORTED;
+    int stages = static_cast<int>((budget - L0.total - 256) / (L0.slot_bytes + sizeof(asyflexa::GsSlot) + 16));
+    stages = std::max(2, std::min(16, stages));
+    while (stages > 2 && asyflexa::make_gs_layout(nw, slot_bytes, stages).total > budget) --stages;
+    c.stages = stages;
+    c.slot_bytes = static_cast<int64_t>(slot_bytes);
+    c.smem = asyflexa::make_gs_layout(nw, slot_bytes, stages).total;
+    BCK(cudaFuncSetAttribute(c.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(c.smem)),
+        "GS kernel shared-memory attribute");
+    int per_sm = 0;
+    BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c.kernel, (nw + 1) * 32, c.smem), "GS occupancy");
+    if (per_sm < 1) return ASYFLEXA_EUNSUPPORTED;
+    c.ctas_per_sm = per_sm;
+    long long g = static_cast<long long>(per_sm) * B.sm_count;
+    if (B.opts.num_ctas > 0) g = std::min<long long>(g, B.opts.num_ctas);
+    c.grid = static_cast<int>(std::max<long long>(1, std::min<long long>(g, B.count)));
+    *out = c;
+    return ASYFLEXA_OK;
+}
+
+// One launch of the Gauss-Seidel kernel over the whole batch (the queue reset first).
+int gs_enqueue(asyflexa_batch_s& B, const GsChoice& c, int sweeps_only, int max_sweeps) {
+    asyflexa::GsParams p{};
+    p.inst = B.d_gs;
+    p.order = B.d_order;
+    p.count = B.count;
+    p.queue = B.d_queue;
+    p.gamma = B.opts.gamma;
+    p.tol_gap = B.opts.tol_gap;
+    p.tol_stat = B.opts.tol_stat;
+    p.check_every = B.opts.check_every;
+    p.max_sweeps = max_sweeps;
+    p.stages = c.stages;
+    p.slot_bytes = c.slot_bytes;
+    p.sweeps_only = sweeps_only;
+    p.keep_a_in_l2 = (B.flags & ASYFLEXA_BATCH_SHARED_A) ? 1 : 0;
+    p.err = B.err;
+    BCK(cudaMemsetAsync(B.d_queue, 0, sizeof(int), B.stream), "reset queue");
+    void* args[] = {&p};
+    const cudaError_t e = cudaLaunchKernel(c.kernel, dim3(c.grid), dim3((c.nw + 1) * 32), args, c.smem, B.stream);
+    ++B.launches;
+    BCK(e, "GS batch launch");
+    return ASYFLEXA_OK;
+}
+
+// The launch shape of the Gauss-Seidel form: cached for this batch shape, else the faster of
+// 7 and 15 consumer warps per CTA over one real sweep of every problem (tuning sweeps are
+// added to *tuned_sweeps).
+int gs_choose(asyflexa_batch_s& B, long long* tuned_sweeps) {
+    if (B.gs.nw) return ASYFLEXA_OK;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto itc = g_gs_tuned.find(B.shape_key);
+        if (itc != g_gs_tuned.end()) {
+            const int rc = gs_shape(B, itc->second.nw, &B.gs);
+            if (rc == ASYFLEXA_OK) return ASYFLEXA_OK;
+        }
+    }
+    std::vector<GsChoice> cands;
+    for (int nw : {7, 15}) {
+        GsChoice c;
+        if (gs_shape(B, nw, &c) == ASYFLEXA_OK) cands.push_back(c);
+    }
+    if (cands.empty()) return bfail("batched problems: no Gauss-Seidel launch shape fits", ASYFLEXA_EUNSUPPORTED);
+    if (cands.size() == 1) {
+        B.gs = cands[0];
+    } else {
+        cudaEvent_t a0, a1;
+        BCK(cudaEventCreate(&a0), "event");
+        BCK(cudaEventCreate(&a1), "event");
+        float best = 0.f;
+        for (const GsChoice& c : cands) {
+            BCK(cudaEventRecord(a0, B.stream), "event record");
+            int rc = gs_enqueue(B, c, 1, 1);
+            if (rc) return rc;
+            BCK(cudaEventRecord(a1, B.stream), "event record");
+            BCK(cudaEventSynchronize(a1), "event sync");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a0, a1);
+            if (best == 0.f || ms < best) {
+                best = ms;
+                B.gs = c;
+            }
+            ++*tuned_sweeps;
+        }
+        cudaEventDestroy(a0);
+        cudaEventDestroy(a1);
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_gs_tuned[B.shape_key] = B.gs;
+    return ASYFLEXA_OK;
+}
+
+int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflexa_stats* per, asyflexa_stats* total) {
+    const int count = B.count;
+    for (int k = 0; k < count; ++k) {
+        asyflexa::GsInst& g = B.h_gs[k];
+        g.x = static_cast<float*>(xs[k]);
+        g.f_star = f_star ? f_star[k] : NAN;
+        g.F = g.stat = g.xmax = NAN;
+        g.sweeps = g.nnz = 0;
+        g.status = ASYFLEXA_ENOTCONV;
+        g.checks = 0;
+    }
+    BCK(cudaMemcpyAsync(B.d_gs, B.h_gs.data(), count * sizeof(asyflexa::GsInst), cudaMemcpyHostToDevice, B.stream),
+        "upload problem table");
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0), "event");
+    BCK(cudaEventCreate(&e1), "event");
+    BCK(cudaEventRecord(e0, B.stream), "event record");
+    long long tuned = 0;
+    int rc = gs_choose(B, &tuned);
+    if (rc) return rc;
+    const int budget = static_cast<int>(std::max<long long>(0, B.opts.max_sweeps - tuned));
+    // the solve launch as a CUDA graph (re-captured when the launch shape or budget changes)
+    GsChoice key = B.gs;
+    key.stages = B.gs.stages * 100000 + budget;  // the budget is a kernel argument
+    if (!B.gs_exec || !(B.gs_graph_cfg == key)) {
+        if (B.gs_exec) cudaGraphExecDestroy(B.gs_exec);
+        if (B.gs_graph) cudaGraphDestroy(B.gs_graph);
+        B.gs_exec = nullptr;
+        B.gs_graph = nullptr;
+        BCK(cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const int erc = gs_enqueue(B, B.gs, 0, budget);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(B.stream, &g);
+        if (erc) return erc;
+        BCK(ce, "end capture");
+        B.gs_graph = g;
+        BCK(cudaGraphInstantiate(&B.gs_exec, g, 0), "instantiate graph");
+        B.gs_graph_cfg = key;
+    }
+    BCK(cudaGraphLaunch(B.gs_exec, B.stream), "graph launch");
+    BCK(cudaEventRecord(e1, B.stream), "event record");
+    BCK(cudaEventSynchronize(e1), "event sync");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int errw = 0;
+    BCK(cudaMemcpy(&errw, B.err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+    if (errw) return bfail("a bounded device-side wait expired", ASYFLEXA_ETIMEOUT);
+    BCK(cudaMemcpy(B.h_gs.data(), B.d_gs, count * sizeof(asyflexa::GsInst), cudaMemcpyDeviceToHost),
+        "read problem table");
+    long long bu = 0, max_sweeps = 0;
+    int worst = ASYFLEXA_OK;
+    for (int k = 0; k < count; ++k) {
+        const asyflexa::GsInst& g = B.h_gs[k];
+        const long long sw = g.sweeps + tuned;
+        bu += sw * g.n;
+        max_sweeps = std::max(max_sweeps, sw);
+        const int st = g.status;
+        if (st != ASYFLEXA_OK && (worst == ASYFLEXA_OK || st < 0)) worst = st;
+        if (per) {
+            asyflexa_stats s;
+            std::memset(&s, 0, sizeof s);
+            s.F = g.F;
+            s.rel_gap = std::isfinite(g.f_star) ? (g.F - g.f_star) / std::fabs(g.f_star) : NAN;
+            s.stat_xhat = g.stat;
+            s.stat_mf = NAN;
+            s.kkt_viol = NAN;
+            s.dual_gap = NAN;
+            s.nnz = g.nnz;
+            s.sweeps = sw;
+            s.block_updates = sw * g.n;
+            s.status = st;
+            s.checked = g.checks > 0 ? 1 : 0;
+            s.block_w = 1;
+            s.batch_form = ASYFLEXA_BATCH_FORM_GS;
+            s.ctas_per_sm = B.gs.ctas_per_sm;
+            per[k] = s;
+        }
+    }
+    if (total) {
+        std::memset(total, 0, sizeof *total);
+        total->sweeps = max_sweeps;
+        total->block_updates = bu;
+        total->seconds = ms * 1e-3;
+        total->status = worst;
+        total->kernel_launches = B.launches;
+        total->block_w = 1;
+        total->batch_form = ASYFLEXA_BATCH_FORM_GS;
+        total->ctas_per_sm = B.gs.ctas_per_sm;
+        total->kernel_variant = B.gs.nw;
+    }
+    return worst;
+}
+
+int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star, asyflexa_stats* per,
+                 asyflexa_stats* total) {
+    const int count = B->count;
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0), "event");
+    BCK(cudaEventCreate(&e1), "event");
+    BCK(cudaEventRecord(e0, B->stream), "event record");
+    // reset problem states for these iterates
+    for (int k = 0; k < count; ++k) {
+        B->h_inst[k].x = xs[k];
+        B->h_inst[k].active = 1;
+        ConvState& c = B->h_conv[k];
+        c.f_star = f_star ? f_star[k] : NAN;
+        c.F = c.F_prev = NAN;
+        c.conv_round = -2;
+    }
+    B->grid = 0;  // every problem active again: full grid until the first deactivation
+    int rc = upload_table(*B);
+    if (rc) return rc;
+    BCK(cudaMemcpyAsync(B->d_conv, B->h_conv.data(), count * sizeof(ConvState), cudaMemcpyHostToDevice, B->stream),
+        "upload convergence state");
+    BCK(cudaMemsetAsync(B->d_round, 0, sizeof(int), B->stream), "clear round");
+    for (int k = 0; k < count; ++k) {
+        BCK(Launcher<float>::refresh(*B->h[k], xs[k]), "initial refresh");
+        B->launches += 4;
+    }
+    long long sweeps = 0;
+    // autotuner: time one sweep per candidate block width (these are real sweeps); the choice
+    // is cached per batch shape
+    if (B->opts.block_w == 0 && B->graph_w == 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto itw = g_w_tuned.find(B->shape_key);
+        if (itw != g_w_tuned.end()) {
+            rc = build_blocks(*B, itw->second);
+            if (!rc) rc = upload_table(*B);
+            if (rc) return rc;
+            B->graph_w = itw->second;
+        }
+    }
+    if (B->opts.block_w == 0 && B->graph_w == 0) {
+        float best = 0.f;
+        int best_w = 32;
+        cudaEvent_t a0, a1;
+        BCK(cudaEventCreate(&a0), "event");
+        BCK(cudaEventCreate(&a1), "event");
+        for (int w : kCandidates) {
+            rc = build_blocks(*B, w);
+            if (!rc) rc = upload_table(*B);
+            if (rc) return rc;
+            BCK(cudaEventRecord(a0, B->stream), "event record");
+            rc = launch_batched(*B, 1);
+            if (rc) return rc;
+            BCK(cudaEventRecord(a1, B->stream), "event record");
+            BCK(cudaEventSynchronize(a1), "event sync");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a0, a1);
+            if (best == 0.f || ms < best) {
+                best = ms;
+                best_w = w;
+            }
+            ++sweeps;
+        }
+        rc = build_blocks(*B, best_w);
+        if (!rc) rc = upload_table(*B);
+        if (rc) return rc;
+        for (int k = 0; k < count; ++k) {
+            BCK(Launcher<float>::refresh(*B->h[k], xs[k]), "refresh after autotune");
+            B->launches += 4;
+        }
+        B->graph_w = best_w;
+        cudaEventDestroy(a0);
+        cudaEventDestroy(a1);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_w_tuned[B->shape_key] = best_w;
+    }
+    // one round as a CUDA graph, re-captured when the iterates, the width or the grid change
+    std::vector<void*> xv(xs, xs + count);
+    auto capture = [&]() -> int {
+        if (B->exec) cudaGraphExecDestroy(B->exec);
+        if (B->graph) cudaGraphDestroy(B->graph);
+        B->exec = nullptr;
+        B->graph = nullptr;
+        BCK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        const int erc = enqueue_round(*B, xs);
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(B->stream, &g);
+        if (erc) return erc;
+        BCK(ce, "end capture");
+        B->graph = g;
+        BCK(cudaGraphInstantiate(&B->exec, g, 0), "instantiate graph");
+        B->graph_x = xv;
+        B->graph_w = B->w;
+        B->graph_grid = B->grid;
+        return ASYFLEXA_OK;
+    };
+    B->grid = active_grid(*B);
+    if (!B->exec || B->graph_x != xv || B->graph_w != B->w || B->graph_grid != B->grid) {
+        rc = capture();
+        if (rc) return rc;
+    }
+    const int per_round = B->opts.refresh_every;
+    int n_active = count, last_active = count;
+    // exact check of each problem at its returned x: computed when it leaves the rounds
+    std::vector<asyflexa_stats> checked(count);
+    std::vector<char> have(count, 0);
+    for (;;) {
+        while (sweeps < B->opts.max_sweeps && n_active > 0) {
+            BCK(cudaGraphLaunch(B->exec, B->stream), "graph launch");
+            sweeps += per_round;
+            BCK(cudaMemcpyAsync(&n_active, B->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, B->stream),
+                "read count");
+            BCK(cudaStreamSynchronize(B->stream), "synchronize");
+            int errw = 0;
+            BCK(cudaMemcpy(&errw, B->err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+            if (errw) return bfail("a bounded device-side wait expired", ASYFLEXA_ETIMEOUT);
+            if (n_active > 0 && n_active < last_active) {
+                // problems were deactivated on the device: shrink the grid to the active ones
+                last_active = n_active;
+                BCK(cudaMemcpy(B->h_inst.data(), B->d_inst, count * sizeof(BatchInst), cudaMemcpyDeviceToHost),
+                    "read problem table");
+                const int g = active_grid(*B);
+                if (g < B->graph_grid) {
+                    B->grid = g;
+                    rc = capture();
+                    if (rc) return rc;
+                }
+            }
+        }
+        // the problems that left the rounds: exact stationarity check; those above tol_stat
+        // rejoin the rounds
+        BCK(cudaMemcpy(B->h_conv.data(), B->d_conv, count * sizeof(ConvState), cudaMemcpyDeviceToHost),
+            "read state");
+        BCK(cudaMemcpy(B->h_inst.data(), B->d_inst, count * sizeof(BatchInst), cudaMemcpyDeviceToHost),
+            "read problem table");
+        int back = 0;
+        for (int k = 0; k < count; ++k) {
+            ConvState& c = B->h_conv[k];
+            if (c.conv_round < 0 || have[k]) continue;
+            asyflexa_stats st;
+            std::memset(&st, 0, sizeof st);
+            B->h[k]->opts.f_star = c.f_star;
+            const int crc = asyflexa_check(B->h[k], xs[k], &st);
+            B->launches += 8;
+            st.status = crc;
+            if (!crc && !(st.stat_xhat <= B->opts.tol_stat) && sweeps < B->opts.max_sweeps) {
+                c.conv_round = -2;
+                c.F_prev = NAN;
+                B->h_inst[k].active = 1;
+                ++back;
+            } else {
+                checked[k] = st;
+                have[k] = 1;
+            }
+        }
+        if (back == 0) break;
+        BCK(cudaMemcpyAsync(B->d_conv, B->h_conv.data(), count * sizeof(ConvState), cudaMemcpyHostToDevice,
+                            B->stream),
+            "upload convergence state");
+        rc = upload_table(*B);
+        if (rc) return rc;
+        n_active = back;
+        last_active = back;
+        B->grid = active_grid(*B);
+        rc = capture();
+        if (rc) return rc;
+    }
+    BCK(cudaEventRecord(e1, B->stream), "event record");
+    BCK(cudaEventSynchronize(e1), "event sync");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    long long bu = 0, max_k = 0;
+    int worst = ASYFLEXA_OK;
+    for (int k = 0; k < count; ++k) {
+        const ConvState& c = B->h_conv[k];
+        const long long nb = (B->h[k]->prob.n + B->w - 1) / B->w;
+        const long long ksweeps = c.conv_round >= 0 ? static_cast<long long>(c.conv_round + 1) * per_round : sweeps;
+        bu += nb * ksweeps;
+        max_k = std::max(max_k, ksweeps);
+        int st = c.conv_round >= 0 ? ASYFLEXA_OK : (c.conv_round == -1 ? ASYFLEXA_ENONFINITE : ASYFLEXA_ENOTCONV);
+        if (have[k] && checked[k].status) st = checked[k].status;
+        if (have[k] && !checked[k].status && !(checked[k].stat_xhat <= B->opts.tol_stat)) st = ASYFLEXA_ENOTCONV;
+        if (per) {
+            asyflexa_stats s;
+            std::memset(&s, 0, sizeof s);
+            if (have[k]) {
+                s = checked[k];
+            } else {
+                B->h[k]->opts.f_star = c.f_star;
+                const int crc = asyflexa_check(B->h[k], xs[k], &s);
+                if (crc) st = crc;
+            }
+            s.sweeps = ksweeps;
+            s.block_updates = nb * ksweeps;
+            s.status = st;
+            s.block_w = B->w;
+            s.batch_form = ASYFLEXA_BATCH_FORM_ASYNC;
+            per[k] = s;
+        }
+        if (st != ASYFLEXA_OK && (worst == ASYFLEXA_OK || st < 0)) worst = st;
+    }
+    if (total) {
+        std::memset(total, 0, sizeof *total);
+        total->sweeps = sweeps;
+        total->block_updates = bu;
+        total->seconds = ms * 1e-3;
+        total->status = worst;
+        total->kernel_launches = B->launches;
+        total->block_w = B->w;
+        total->batch_form = ASYFLEXA_BATCH_FORM_ASYNC;
+    }
+    return worst;
+}
+
+
+int rounds_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflexa_stats* per,
+                 asyflexa_stats* total) {
+    return rounds_solve_impl(&B, xs, f_star, per, total);
+}
+
 }  // namespace
 
 extern "C" {
@@ -309,7 +807,29 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
     }
     B->sm_count = B->h[0]->sm_count;
     B->smem_optin = B->h[0]->smem_optin;
+    {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, B->h[0]->device);
+        B->smem_per_sm = v > 0 ? v : static_cast<int>(B->smem_optin);
+    }
     const int64_t units = B->max_mcopy / 4;
+    B->max_units = units;
+    // the form: forced by the flags, else the Gauss-Seidel form when every problem fits it and
+    // there are enough problems to occupy a good part of the GPU one CTA each
+    {
+        const bool gs_fits = B->max_mcopy <= kGsMaxRows;  // (15 warps x 5 units x 4 rows = 9600)
+        if ((flags & ASYFLEXA_BATCH_FORM_GS) && (flags & ASYFLEXA_BATCH_FORM_ASYNC))
+            return fail(bfail("at most one of ASYFLEXA_BATCH_FORM_GS and ASYFLEXA_BATCH_FORM_ASYNC"));
+        if (flags & ASYFLEXA_BATCH_FORM_GS) {
+            if (!gs_fits)
+                return fail(bfail("the Gauss-Seidel form needs m <= 8192 for every problem", ASYFLEXA_EUNSUPPORTED));
+            B->form = ASYFLEXA_BATCH_FORM_GS;
+        } else if (flags & ASYFLEXA_BATCH_FORM_ASYNC) {
+            B->form = ASYFLEXA_BATCH_FORM_ASYNC;
+        } else {
+            B->form = (gs_fits && count * 4 >= B->sm_count) ? ASYFLEXA_BATCH_FORM_GS : ASYFLEXA_BATCH_FORM_ASYNC;
+        }
+    }
     B->cpc = static_cast<int>((units + asyflexa::kRegStageUnits - 1) / asyflexa::kRegStageUnits);
     B->kernel = batched_kernel(B->cpc);
     if (!B->kernel) return fail(bfail("batched problems need m <= 24576", ASYFLEXA_EUNSUPPORTED));
@@ -368,6 +888,50 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
     if (e != cudaSuccess) return fail(bfail(std::string("batch allocation: ") + cudaGetErrorString(e), ASYFLEXA_ENOMEM));
     const int rc = build_blocks(*B, opts->block_w > 0 ? opts->block_w : 32);
     if (rc) return fail(rc);
+    {
+        // Gauss-Seidel form: the problem table and the queue order (largest m * n first)
+        B->h_gs.resize(count);
+        std::vector<int> order(count);
+        double total_mn = 0.0;
+        int64_t max_n = 0;
+        for (int k = 0; k < count; ++k) {
+            const asyflexa_s& hk = *B->h[k];
+            asyflexa::GsInst& g = B->h_gs[k];
+            std::memset(&g, 0, sizeof g);
+            g.A = static_cast<const float*>(hk.prob.A);
+            g.lda = hk.prob.lda;
+            g.m = hk.prob.m;
+            g.n = hk.prob.n;
+            g.b = static_cast<const float*>(hk.prob.b);
+            g.lo = static_cast<const float*>(hk.prob.lo);
+            g.hi = static_cast<const float*>(hk.prob.hi);
+            g.lin = static_cast<const float*>(hk.prob.lin);
+            g.dw = hk.dw;
+            g.lam = hk.prob.lambda;
+            const bool lasso = hk.prob.loss == ASYFLEXA_LOSS_LASSO;
+            g.s_loss = lasso ? 1.0 : 2.0;
+            g.c2 = lasso ? 0.0 : 2.0 * hk.prob.c;
+            g.c = lasso ? 0.0 : hk.prob.c;
+            g.loss = hk.prob.loss;
+            g.f_star = NAN;
+            order[k] = k;
+            total_mn += static_cast<double>(hk.prob.m) * static_cast<double>(hk.prob.n);
+            max_n = std::max<int64_t>(max_n, hk.prob.n);
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return static_cast<double>(B->h_gs[a].m) * B->h_gs[a].n > static_cast<double>(B->h_gs[b].m) * B->h_gs[b].n;
+        });
+        e = cudaMalloc(&B->d_gs, count * sizeof(asyflexa::GsInst));
+        if (e == cudaSuccess) e = cudaMalloc(&B->d_order, count * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&B->d_queue, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(B->d_order, order.data(), count * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(bfail(std::string("batch allocation: ") + cudaGetErrorString(e), ASYFLEXA_ENOMEM));
+        char key[160];
+        std::snprintf(key, sizeof key, "count=%d mn=%.0f max_m=%lld max_n=%lld flags=%d nctas=%d sms=%d", count, total_mn,
+                      static_cast<long long>(B->max_mcopy), static_cast<long long>(max_n), flags, opts->num_ctas,
+                      B->sm_count);
+        B->shape_key = key;
+    }
     // the caller's stream continues after the set-up work
     e = cudaEventRecord(B->ev_out, B->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(B->user_stream, B->ev_out, 0);
@@ -384,12 +948,14 @@ int asyflexa_batch_destroy(asyflexa_batch_t B) {
     if (B->stream) cudaStreamSynchronize(B->stream);
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
+    if (B->gs_exec) cudaGraphExecDestroy(B->gs_exec);
+    if (B->gs_graph) cudaGraphDestroy(B->gs_graph);
     for (auto hk : B->h) asyflexa_destroy(hk);
     if (B->ev_in) cudaEventDestroy(B->ev_in);
     if (B->ev_out) cudaEventDestroy(B->ev_out);
     if (B->stream) cudaStreamDestroy(B->stream);
     void* ptrs[] = {B->d_inst, B->d_blk_inst, B->d_blk_local, B->d_conv, B->d_round, B->d_nactive,
-                    B->counters, B->hist, B->err};
+                    B->counters, B->hist, B->err, B->d_gs, B->d_order, B->d_queue};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete B;
@@ -399,157 +965,37 @@ int asyflexa_batch_destroy(asyflexa_batch_t B) {
 int asyflexa_batch_solve(asyflexa_batch_t B, void* const* xs, const double* f_star, asyflexa_stats* per,
                          asyflexa_stats* total) {
     if (!B || !xs) return bfail("batch or xs is NULL");
-    const int count = B->count;
     // the batch's stream starts after the caller's prior work (the iterates may come from it)
     BCK(cudaEventRecord(B->ev_in, B->user_stream), "event record");
     BCK(cudaStreamWaitEvent(B->stream, B->ev_in, 0), "stream wait");
-    cudaEvent_t e0, e1;
-    BCK(cudaEventCreate(&e0), "event");
-    BCK(cudaEventCreate(&e1), "event");
-    BCK(cudaEventRecord(e0, B->stream), "event record");
-    // reset problem states for these iterates
-    for (int k = 0; k < count; ++k) {
-        B->h_inst[k].x = xs[k];
-        B->h_inst[k].active = 1;
-        ConvState& c = B->h_conv[k];
-        c.f_star = f_star ? f_star[k] : NAN;
-        c.F = c.F_prev = NAN;
-        c.conv_round = -2;
-    }
-    B->grid = 0;  // every problem active again: full grid until the first deactivation
-    int rc = upload_table(*B);
-    if (rc) return rc;
-    BCK(cudaMemcpyAsync(B->d_conv, B->h_conv.data(), count * sizeof(ConvState), cudaMemcpyHostToDevice, B->stream),
-        "upload convergence state");
-    BCK(cudaMemsetAsync(B->d_round, 0, sizeof(int), B->stream), "clear round");
-    for (int k = 0; k < count; ++k) {
-        BCK(Launcher<float>::refresh(*B->h[k], xs[k]), "initial refresh");
-        B->launches += 4;
-    }
-    long long sweeps = 0;
-    // autotuner: time one sweep per candidate block width (these are real sweeps)
-    if (B->opts.block_w == 0 && B->graph_w == 0) {
-        float best = 0.f;
-        int best_w = 32;
-        cudaEvent_t a0, a1;
-        BCK(cudaEventCreate(&a0), "event");
-        BCK(cudaEventCreate(&a1), "event");
-        for (int w : kCandidates) {
-            rc = build_blocks(*B, w);
-            if (!rc) rc = upload_table(*B);
-            if (rc) return rc;
-            BCK(cudaEventRecord(a0, B->stream), "event record");
-            rc = launch_batched(*B, 1);
-            if (rc) return rc;
-            BCK(cudaEventRecord(a1, B->stream), "event record");
-            BCK(cudaEventSynchronize(a1), "event sync");
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, a0, a1);
-            if (best == 0.f || ms < best) {
-                best = ms;
-                best_w = w;
-            }
-            ++sweeps;
+    const int rc = B->form == ASYFLEXA_BATCH_FORM_GS ? gs_solve(*B, xs, f_star, per, total)
+                                                     : rounds_solve(*B, xs, f_star, per, total);
+    // the caller's stream continues after the batch's work
+    cudaEventRecord(B->ev_out, B->stream);
+    cudaStreamWaitEvent(B->user_stream, B->ev_out, 0);
+    return rc;
+}
+
+int asyflexa_batch_check(asyflexa_batch_t B, void* const* xs, const double* f_star, asyflexa_stats* per) {
+    if (!B || !xs || !per) return bfail("batch, xs or per is NULL");
+    BCK(cudaEventRecord(B->ev_in, B->user_stream), "event record");
+    BCK(cudaStreamWaitEvent(B->stream, B->ev_in, 0), "stream wait");
+    int first = ASYFLEXA_OK;
+    for (int k = 0; k < B->count; ++k) {
+        asyflexa_stats s;
+        std::memset(&s, 0, sizeof s);
+        B->h[k]->opts.f_star = f_star ? f_star[k] : NAN;
+        const int crc = asyflexa_check(B->h[k], xs[k], &s);
+        if (crc && first == ASYFLEXA_OK) {
+            first = crc;
+            asyflexa_internal::set_thread_error("problem " + std::to_string(k) + ": " + asyflexa_last_error(B->h[k]));
         }
-        rc = build_blocks(*B, best_w);
-        if (!rc) rc = upload_table(*B);
-        if (rc) return rc;
-        for (int k = 0; k < count; ++k) {
-            BCK(Launcher<float>::refresh(*B->h[k], xs[k]), "refresh after autotune");
-            B->launches += 4;
-        }
-        B->graph_w = best_w;
-        cudaEventDestroy(a0);
-        cudaEventDestroy(a1);
+        s.status = crc;
+        per[k] = s;
     }
-    // one round as a CUDA graph, re-captured when the iterates, the width or the grid change
-    std::vector<void*> xv(xs, xs + count);
-    auto capture = [&]() -> int {
-        if (B->exec) cudaGraphExecDestroy(B->exec);
-        if (B->graph) cudaGraphDestroy(B->graph);
-        B->exec = nullptr;
-        B->graph = nullptr;
-        BCK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        const int erc = enqueue_round(*B, xs);
-        cudaGraph_t g = nullptr;
-        const cudaError_t ce = cudaStreamEndCapture(B->stream, &g);
-        if (erc) return erc;
-        BCK(ce, "end capture");
-        B->graph = g;
-        BCK(cudaGraphInstantiate(&B->exec, g, 0), "instantiate graph");
-        B->graph_x = xv;
-        B->graph_w = B->w;
-        B->graph_grid = B->grid;
-        return ASYFLEXA_OK;
-    };
-    B->grid = active_grid(*B);
-    if (!B->exec || B->graph_x != xv || B->graph_w != B->w || B->graph_grid != B->grid) {
-        rc = capture();
-        if (rc) return rc;
-    }
-    const int per_round = B->opts.refresh_every;
-    int n_active = count, last_active = count;
-    while (sweeps < B->opts.max_sweeps && n_active > 0) {
-        BCK(cudaGraphLaunch(B->exec, B->stream), "graph launch");
-        sweeps += per_round;
-        BCK(cudaMemcpyAsync(&n_active, B->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, B->stream), "read count");
-        BCK(cudaStreamSynchronize(B->stream), "synchronize");
-        int errw = 0;
-        BCK(cudaMemcpy(&errw, B->err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
-        if (errw) return bfail("a bounded device-side wait expired", ASYFLEXA_ETIMEOUT);
-        if (n_active > 0 && n_active < last_active) {
-            // problems were deactivated on the device: shrink the grid to the active ones
-            last_active = n_active;
-            BCK(cudaMemcpy(B->h_inst.data(), B->d_inst, count * sizeof(BatchInst), cudaMemcpyDeviceToHost),
-                "read problem table");
-            const int g = active_grid(*B);
-            if (g < B->graph_grid) {
-                B->grid = g;
-                rc = capture();
-                if (rc) return rc;
-            }
-        }
-    }
-    BCK(cudaEventRecord(e1, B->stream), "event record");
-    BCK(cudaEventSynchronize(e1), "event sync");
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    BCK(cudaMemcpy(B->h_conv.data(), B->d_conv, count * sizeof(ConvState), cudaMemcpyDeviceToHost), "read state");
-    long long bu = 0;
-    int worst = ASYFLEXA_OK;
-    for (int k = 0; k < count; ++k) {
-        const ConvState& c = B->h_conv[k];
-        const long long nb = (B->h[k]->prob.n + B->w - 1) / B->w;
-        const long long ksweeps = c.conv_round >= 0 ? static_cast<long long>(c.conv_round + 1) * per_round : sweeps;
-        bu += nb * ksweeps;
-        int st = c.conv_round >= 0 ? ASYFLEXA_OK : (c.conv_round == -1 ? ASYFLEXA_ENONFINITE : ASYFLEXA_ENOTCONV);
-        if (per) {
-            asyflexa_stats s;
-            std::memset(&s, 0, sizeof s);
-            B->h[k]->opts.f_star = c.f_star;
-            const int crc = asyflexa_check(B->h[k], xs[k], &s);
-            if (crc) st = crc;
-            s.sweeps = ksweeps;
-            s.block_updates = nb * ksweeps;
-            s.status = st;
-            per[k] = s;
-        }
-        if (st != ASYFLEXA_OK && (worst == ASYFLEXA_OK || st < 0)) worst = st;
-    }
-    BCK(cudaEventRecord(B->ev_out, B->stream), "event record");
-    BCK(cudaStreamWaitEvent(B->user_stream, B->ev_out, 0), "stream wait");
-    if (total) {
-        std::memset(total, 0, sizeof *total);
-        total->sweeps = sweeps;
-        total->block_updates = bu;
-        total->seconds = ms * 1e-3;
-        total->status = worst;
-        total->kernel_launches = B->launches;
-        total->block_w = B->w;
-    }
-    return worst;
+    cudaEventRecord(B->ev_out, B->stream);
+    cudaStreamWaitEvent(B->user_stream, B->ev_out, 0);
+    return first;
 }
 
 }  // extern "C"

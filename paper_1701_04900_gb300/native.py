@@ -60,7 +60,7 @@ class Stats(C.Structure):
         ("status", C.c_int32), ("checked", C.c_int32),
         ("polish_sweeps", C.c_int64), ("polish_seconds", C.c_double),
         ("block_w", C.c_int32), ("kernel_variant", C.c_int32), ("dual_gap", C.c_double),
-        ("tau_extra", C.c_double),
+        ("tau_extra", C.c_double), ("batch_form", C.c_int32), ("ctas_per_sm", C.c_int32),
     ]
 
     def as_dict(self) -> dict:
@@ -75,11 +75,13 @@ EXPORTS = [
     "asyflexa_destroy", "asyflexa_residual_refresh", "asyflexa_step", "asyflexa_solve", "asyflexa_check",
     "asyflexa_read_counters", "asyflexa_reset_counters", "asyflexa_get_residual", "asyflexa_get_weights",
     "asyflexa_last_error", "asyflexa_residual_noalloc", "asyflexa_quantize", "asyflexa_gather_columns",
-    "asyflexa_batch_create", "asyflexa_batch_solve", "asyflexa_batch_destroy",
+    "asyflexa_batch_create", "asyflexa_batch_solve", "asyflexa_batch_check", "asyflexa_batch_destroy",
     "asyflexa_multi_create", "asyflexa_multi_solve", "asyflexa_multi_destroy",
-    "asyflexa_convert_check", "asyflexa_wait_check",
+    "asyflexa_convert_check", "asyflexa_wait_check", "asyflexa_adjoint",
 ]
 BATCH_SHARED_A = 1
+BATCH_FORM_ASYNC = 2
+BATCH_FORM_GS = 4
 
 
 def lib(path: str | None = None):
@@ -132,6 +134,8 @@ def lib(path: str | None = None):
     L.asyflexa_batch_create.argtypes = [C.POINTER(vp), C.POINTER(Problem), i32, C.POINTER(Opts), i32, vp]
     L.asyflexa_batch_solve.restype = C.c_int
     L.asyflexa_batch_solve.argtypes = [vp, C.POINTER(vp), vp, C.POINTER(Stats), C.POINTER(Stats)]
+    L.asyflexa_batch_check.restype = C.c_int
+    L.asyflexa_batch_check.argtypes = [vp, C.POINTER(vp), vp, C.POINTER(Stats)]
     L.asyflexa_batch_destroy.restype = C.c_int
     L.asyflexa_batch_destroy.argtypes = [vp]
     L.asyflexa_multi_create.restype = C.c_int
@@ -142,6 +146,9 @@ def lib(path: str | None = None):
     L.asyflexa_multi_destroy.argtypes = [vp]
     L.asyflexa_gather_columns.restype = C.c_int
     L.asyflexa_gather_columns.argtypes = [vp, C.c_int64, i32, C.c_int64, vp, C.c_int64, vp, C.c_int64, vp]
+    L.asyflexa_adjoint.restype = C.c_int
+    L.asyflexa_adjoint.argtypes = [vp, C.c_int64, i32, C.c_int64, C.c_int64, vp, vp, dbl, C.POINTER(Opts),
+                                   C.POINTER(dbl), vp, C.POINTER(C.c_int64), C.POINTER(Stats), vp]
     del dbl
     if path is None:
         _lib = L
@@ -170,6 +177,25 @@ def _dtype_code(t) -> int:
 def default_opts() -> Opts:
     o = Opts()
     lib().asyflexa_opts_default(C.byref(o))
+    return o
+
+
+def make_opts(block_w=32, mode="sync", gamma=0.9, tau=0.0, tau_rel=0.0, refresh_every=10, check_every=10,
+              max_sweeps=1000, num_ctas=0, tol_gap=1e-6, tol_stat=1e-6, f_star=math.nan, profile=False, variant=0,
+              switch_tol=1e-7, gamma_mu=0.0, tau_adapt=False, exact_grad=0) -> Opts:
+    """asyflexa_opts from keyword arguments (the library's defaults, then these values)."""
+    o = default_opts()
+    o.block_w, o.mode = int(block_w), (ASYNC if mode == "async" else SYNC)
+    o.gamma, o.tau, o.tau_rel = float(gamma), float(tau), float(tau_rel)
+    o.refresh_every, o.check_every, o.max_sweeps = int(refresh_every), int(check_every), int(max_sweeps)
+    o.num_ctas = int(num_ctas)
+    o.tol_gap, o.tol_stat, o.f_star = float(tol_gap), float(tol_stat), float(f_star)
+    o.profile = 1 if profile else 0
+    o.variant = int(variant)
+    o.switch_tol = float(switch_tol)
+    o.gamma_mu = float(gamma_mu)
+    o.tau_adapt = 1 if tau_adapt else 0
+    o.exact_grad = int(exact_grad)
     return o
 
 
@@ -217,18 +243,10 @@ class Solver:
             if A_master.dtype != torch.float32 or not A_master.is_contiguous() or A_master.shape[0] != n:
                 raise ValueError("A_master must be a contiguous float32 (n, lda_master) CUDA tensor")
             p.A_master, p.lda_master = A_master.data_ptr(), A_master.shape[1]
-        o = default_opts()
-        o.block_w, o.mode = int(block_w), (ASYNC if mode == "async" else SYNC)
-        o.gamma, o.tau, o.tau_rel = float(gamma), float(tau), float(tau_rel)
-        o.refresh_every, o.check_every, o.max_sweeps = int(refresh_every), int(check_every), int(max_sweeps)
-        o.num_ctas = int(num_ctas)
-        o.tol_gap, o.tol_stat, o.f_star = float(tol_gap), float(tol_stat), float(f_star)
-        o.profile = 1 if profile else 0
-        o.variant = int(variant)
-        o.switch_tol = float(switch_tol)
-        o.gamma_mu = float(gamma_mu)
-        o.tau_adapt = 1 if tau_adapt else 0
-        o.exact_grad = int(exact_grad)
+        o = make_opts(block_w=block_w, mode=mode, gamma=gamma, tau=tau, tau_rel=tau_rel, refresh_every=refresh_every,
+                      check_every=check_every, max_sweeps=max_sweeps, num_ctas=num_ctas, tol_gap=tol_gap,
+                      tol_stat=tol_stat, f_star=f_star, profile=profile, variant=variant, switch_tol=switch_tol,
+                      gamma_mu=gamma_mu, tau_adapt=tau_adapt, exact_grad=exact_grad)
         self.problem, self.opts = p, o
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream

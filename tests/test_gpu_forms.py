@@ -142,3 +142,33 @@ def test_autograd_gradient_matches_oracle_adjoint_and_finite_differences():
     h = 1e-4
     fd = (L(1.0 + h) - L(1.0 - h)) / (2 * h)
     assert abs(float(lam.grad) - fd) <= 2e-2 * abs(fd)
+
+
+@pytest.mark.parametrize("store", [np.float64, np.float32])
+def test_adjoint_entry_point_matches_oracle_cholesky(store):
+    """asyflexa_adjoint at the planted solution of a Nesterov LASSO (200 x 1000, 50 nonzeros):
+    the support, dL/dlam = -s^T w and dL/db = A_S w against the oracle's FP64 Cholesky solve of
+    (A_S^T A_S) w = v_S for a random v.  FP64 storage: 1e-9 relative; FP32 (FP32 arithmetic in
+    the support solve): 1e-4."""
+    import torch
+    from paper_1701_04900_gb300.autograd import adjoint
+    d = nesterov_lasso(200, 1000, 50, lam=1.0, seed=43, store_dtype=store)
+    p = O.Problem.from_data(d)
+    tdt = torch.float64 if store == np.float64 else torch.float32
+    At = torch.from_numpy(d["At"]).cuda()
+    xs = d["x_star"].astype(store)
+    v = np.random.default_rng(44).standard_normal(d["n"]).astype(store)
+    x_t = torch.from_numpy(xs).cuda()
+    v_t = torch.from_numpy(v).cuda()
+    tol = 1e-9 if store == np.float64 else 1e-4
+    kw = dict(tol_stat=1e-13, max_sweeps=20000) if store == np.float64 else dict(tol_stat=1e-6, max_sweeps=4000)
+    dlam, db, k, st = adjoint(At, d["m"], x_t, v_t, **kw)
+    dlam_o, db_o, _, S = O.lasso_adjoint_gradient(p.A, xs.astype(np.float64), v.astype(np.float64))
+    assert k == len(S) == 50
+    assert st["status"] == 0, st
+    assert abs(dlam - dlam_o) <= tol * abs(dlam_o)
+    dbg = db.cpu().numpy()
+    assert np.abs(dbg - db_o).max() <= tol * np.abs(db_o).max()
+    # empty support: the solution does not move with (lam, b)
+    dlam0, db0, k0, _ = adjoint(At, d["m"], torch.zeros(d["n"], dtype=tdt, device="cuda"), v_t)
+    assert k0 == 0 and dlam0 == 0.0 and float(db0.abs().max()) == 0.0

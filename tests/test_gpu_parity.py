@@ -376,21 +376,44 @@ def test_degenerate_shapes_and_bounds():
     assert rel_inf(x.cpu().numpy(), ref[-1]) < TOL64
 
 
-def test_async_divergence_is_reported():
-    """Too many blocks in flight for the step (every block of a small problem at once, no
-    proximal weight) can make the asynchronous iteration diverge; the library must report
-    it (ENONFINITE) instead of returning garbage."""
+@pytest.mark.parametrize("store", [np.float64, np.float32])
+def test_async_divergence_is_reported(store):
+    """A step that overshoots by construction: 64 x 4096 with nearly identical columns (all
+    ones plus 1e-3 U[-1, 1]) and blocks of 8 columns.  The 8 columns of a block see the same
+    residual and each one alone would remove its whole projection, so even one block update
+    multiplies that part of r by about 1 - 8 * 0.9 = -6.2 (the FP64 oracle's Jacobi sweep grows
+    ||r||_inf by about 3e3 per sweep).  The iterates overflow within the first check interval,
+    and the library must report ENONFINITE instead of returning a number."""
     import torch
     from paper_1701_04900_gb300 import AsyflexaError
-    d = nesterov_lasso(2000, 10000, 100, lam=1.0, seed=11, store_dtype=np.float64)
-    s = make_solver(d, block_w=32, mode="async", gamma=0.9, max_sweeps=400, check_every=10)
-    x = xzeros(d, torch.float64)
-    try:
-        st = s.solve(x)
-    except AsyflexaError as e:
-        assert e.code == -5
-    else:
-        assert np.isfinite(st["F"])
+    rng = np.random.default_rng(4)
+    m, n = 64, 4096
+    A = (1.0 + 1e-3 * rng.uniform(-1, 1, (m, n))).astype(store)
+    d = dict(At=np.ascontiguousarray(A.T), b=rng.standard_normal(m).astype(store), lam=1e-3, m=m, n=n)
+    s = make_solver(d, block_w=8, mode="async", gamma=0.9, max_sweeps=400, check_every=10)
+    x = xzeros(d, torch.float64 if store == np.float64 else torch.float32)
+    with pytest.raises(AsyflexaError) as ei:
+        s.solve(x)
+    assert ei.value.code == -5
+    s.close()
+
+
+@pytest.mark.parametrize("store", [np.float64, np.float32])
+def test_nan_in_b_is_reported(store):
+    """Host-side fault injection: a NaN in b makes the residual, and with it F, non-finite.
+    The solve must stop with ENONFINITE (no kernel faults or waits on the value)."""
+    import torch
+    from paper_1701_04900_gb300 import AsyflexaError
+    d = random_lasso(300, 500, seed=21, lam=0.1, store_dtype=store)
+    d["b"] = d["b"].copy()
+    d["b"][17] = np.nan
+    for mode in ("async", "sync"):
+        s = make_solver(d, block_w=32, mode=mode, max_sweeps=50, check_every=5)
+        x = xzeros(d, torch.float64 if store == np.float64 else torch.float32)
+        with pytest.raises(AsyflexaError) as ei:
+            s.solve(x)
+        assert ei.value.code == -5
+        s.close()
 
 
 def test_invalid_inputs_are_rejected():
