@@ -262,12 +262,14 @@ int asyflexa_get_weights(asyflexa_t h, double* d_out);
 /* r_out = A x - b for the problem *prob at x, without a handle and without allocating
  * any device memory.  (The paper has no counterpart; this is a service entry point.)
  *
- * For callers that cannot allocate device memory when they need the residual: code that
- * runs while a CUDA stream is being captured into a graph, where cudaMalloc is not
- * permitted, or a latency-sensitive loop in which cudaMalloc/cudaFree would synchronise
- * the device and stall other streams.  The result equals asyflexa_residual_refresh on a
- * handle for the same problem and x (same kernels: ordered compaction of the nonzeros of
- * x, compensated products, fixed-order FP64 reduction), up to the number of partial sums.
+ * For callers that cannot allocate device memory when they need the residual: a plugin or
+ * library inside a host application that hands it a fixed device-memory budget and owns every
+ * allocation itself, or a latency-sensitive loop in which cudaMalloc / cudaFree would
+ * synchronise the device and stall the other streams.  The result equals
+ * asyflexa_residual_refresh on a handle for the same problem and x up to the grouping of
+ * partial sums: the same ordered compaction of the nonzeros of x, the same compensated
+ * products and the same fixed-order FP64 reduction, through the register-batched gather
+ * kernel instead of the handle's pipelined one.
  *
  * prob: as for asyflexa_create (device pointers A, b, col_scale; lo, hi, lambda, c, loss
  * are ignored).  x: length n device vector of x_dtype.  r_out: caller-owned device buffer
@@ -281,10 +283,13 @@ int asyflexa_get_weights(asyflexa_t h, double* d_out);
  *
  * Scratch: one file-scope 8 MiB device array, held by every GPU that loads the library
  * until the process exits.  Its device address is looked up (cudaGetSymbolAddress) by the
- * first call on each device, so make that first call before any stream capture.  Every
- * call shares the array: calls that overlap on the GPU (e.g. on two streams) race and must
- * be serialised by the caller.  The array keeps the last call's contents; every scratch
- * value a call reads is written earlier in the same call, so nothing needs clearing. */
+ * first call on each device, with that device current, so make that first call before any
+ * stream capture.  The address is then cached per device index for the life of the process:
+ * this assumes the device's primary context throughout (after cudaDeviceReset, or from a
+ * different context on that device, the cached address is not valid).  Every call shares the
+ * array: calls that overlap on the GPU (e.g. on two streams) race and must be serialised by
+ * the caller.  The array keeps the last call's contents; every scratch value a call reads is
+ * written earlier in the same call, so nothing needs clearing. */
 int asyflexa_residual_noalloc(const asyflexa_problem* prob, const void* x, double* r_out, void* cuda_stream);
 
 /* Diagnostic: run the kernels' own number conversions over an array.  The kernels convert
@@ -369,8 +374,9 @@ int asyflexa_adjoint(const void* A, int64_t lda, int32_t a_dtype, int64_t m, int
  *
  *   ASYFLEXA_BATCH_FORM_GS (Gauss-Seidel form): ONE persistent launch for the whole batch.
  *     Each CTA takes the next problem from a queue (largest first), runs Algorithm 1 on it
- *     alone -- a single owner for every block, so exact cyclic Gauss-Seidel over scalar
- *     blocks (Section 4.1) with the fixed step of S.4 and the best response of eq. 2 -- with
+ *     alone -- a single owner for every block, so exact cyclic block Gauss-Seidel (blocks of
+ *     w <= 4 columns; w = 1 is the scalar blocks of Section 4.1) with the fixed step of S.4
+ *     and the best response of eq. 2 -- with
  *     the residual held in registers, and runs its own stopping test (exact residual, F,
  *     gap, and the Section 4.3 merit) before taking the next problem.  FP32 problems with
  *     m <= 8192.  The launch is captured in a CUDA graph and replayed by later solves.
@@ -381,10 +387,11 @@ int asyflexa_adjoint(const void* A, int64_t lda, int32_t a_dtype, int64_t m, int
  *     captured CUDA graph.  FP32 problems with m <= 24576.
  *
  * The form is chosen at create (flags) or automatically: the Gauss-Seidel form when every
- * problem fits it and there are at least (SM count / 4) problems, else the async rounds.  An
+ * problem fits it and there are at least as many problems as SMs, else the async rounds.  An
  * autotuner then picks the form's launch shape at the first solve by timing one real sweep of
- * every problem per candidate -- Gauss-Seidel form: 8 or 16 consumer warps per CTA (2 or 1
- * CTAs per SM) with the ring depth that fits; async rounds: the block width 16, 32 or 64 --
+ * every problem per candidate -- Gauss-Seidel form: 7 or 15 consumer warps per CTA (2 or 1
+ * CTAs per SM) with the ring depth that fits, and the block width 1, 2 or 4; async rounds:
+ * the block width 16, 32 or 64 --
  * and caches the choice per batch shape (problem count, total size, largest m, flags) for
  * the life of the process. */
 typedef struct asyflexa_batch_s* asyflexa_batch_t;
@@ -401,7 +408,9 @@ typedef struct asyflexa_batch_s* asyflexa_batch_t;
  * method parameters: gamma, tau, tau_rel, tol_gap, tol_stat, max_sweeps, num_ctas (0 = all
  * SMs; in the Gauss-Seidel form the most CTAs that run problems at once), check_every
  * (Gauss-Seidel form: sweeps between stopping tests), refresh_every (async rounds: sweeps per
- * round), switch_tol, block_w (async rounds; 0 lets the autotuner pick it).  All problems and
+ * round), switch_tol, block_w (async rounds: 16 .. 128, 0 lets the autotuner pick 16, 32 or
+ * 64; Gauss-Seidel form: 1 .. 4 fixes the block width, any other value lets the autotuner pick
+ * 1, 2 or 4).  All problems and
  * their device buffers must outlive the batch.  Errors: asyflexa_last_error(NULL). */
 int asyflexa_batch_create(asyflexa_batch_t* hb, const asyflexa_problem* probs, int32_t count,
                           const asyflexa_opts* opts, int32_t flags, void* cuda_stream);
@@ -415,10 +424,13 @@ int asyflexa_batch_create(asyflexa_batch_t* hb, const asyflexa_problem* probs, i
  * stationarity check then runs for it, and a problem that fails it rejoins the rounds.
  * per (count entries, may be NULL): each problem's F, rel_gap, stat_xhat, nnz, sweeps,
  * block_updates and status (ENOTCONV at max_sweeps, ENONFINITE if F became non-finite) as the
- * stopping test saw them; for the exact check of asyflexa_check use asyflexa_batch_check.
+ * stopping test saw them, and block_w (Gauss-Seidel form: the tuned width, or as many columns
+ * as one ring slot holds if fewer); for the exact check of asyflexa_check use
+ * asyflexa_batch_check.
  * total: sweeps (the largest number of sweeps of any problem, tuning sweeps included),
- * block_updates (all problems), seconds (CUDA events around the solve), block_w (1 in the
- * Gauss-Seidel form: scalar blocks), batch_form, ctas_per_sm, status (OK if all done). */
+ * block_updates (all problems), seconds (CUDA events around the solve), block_w, batch_form,
+ * ctas_per_sm, kernel_variant (Gauss-Seidel form: consumer warps per CTA), status (OK if all
+ * done). */
 int asyflexa_batch_solve(asyflexa_batch_t hb, void* const* xs, const double* f_star, asyflexa_stats* per,
                          asyflexa_stats* total);
 

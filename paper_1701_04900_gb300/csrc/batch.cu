@@ -84,13 +84,24 @@ __global__ void batch_converge_kernel(ConvState* cs, BatchInst* inst, int count,
 
 constexpr int kCandidates[] = {16, 32, 64};
 
+// (d_j, 1/d_j) in FP32 for the Gauss-Seidel form ((0, 0) where d_j <= 0).
+__global__ void gs_coef_kernel(const double* dw, int64_t n, float2* dd) {
+    for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
+         j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const double d = dw[j];
+        dd[j] = d > 0.0 ? make_float2(static_cast<float>(d), static_cast<float>(1.0 / d)) : make_float2(0.f, 0.f);
+    }
+}
+
 // Launch shape of the Gauss-Seidel form.
 struct GsChoice {
-    int nw = 0, upt = 0, stages = 0, ctas_per_sm = 0, grid = 0;
+    int nw = 0, upt = 0, stages = 0, ctas_per_sm = 0, grid = 0, w = 1;
     int64_t slot_bytes = 0;
     size_t smem = 0;
     const void* kernel = nullptr;
-    bool operator==(const GsChoice& o) const { return nw == o.nw && upt == o.upt && stages == o.stages && grid == o.grid; }
+    bool operator==(const GsChoice& o) const {
+        return nw == o.nw && upt == o.upt && stages == o.stages && grid == o.grid && w == o.w;
+    }
 };
 
 // Instantiated (consumer warps, units per thread) pairs: columns of up to NW * 32 * UPT * 4 rows.
@@ -174,6 +185,8 @@ struct asyflexa_batch_s {
     // Gauss-Seidel form
     int form = 0;                       // ASYFLEXA_BATCH_FORM_ASYNC or ASYFLEXA_BATCH_FORM_GS
     int64_t max_units = 0;              // 16-byte units of the longest column
+    int64_t slot_bytes = 0;             // ring slot: the longest column, and up to 4 short columns (16 KB)
+    float2* d_dd = nullptr;             // (d_j, 1/d_j) in FP32 of every problem, concatenated
     std::vector<asyflexa::GsInst> h_gs;
     asyflexa::GsInst* d_gs = nullptr;
     int* d_order = nullptr;
@@ -343,11 +356,11 @@ int gs_shape(asyflexa_batch_s& B, int nw, GsChoice* out) {
     c.kernel = c.upt ? gs_kernel(nw, c.upt) : nullptr;
     if (!c.kernel) return ASYFLEXA_EUNSUPPORTED;
     const int want_per_sm = nw < 8 ? 2 : 1;
-    const size_t slot_bytes = static_cast<size_t>((B.max_units * 16 + 127) / 128 * 128);
+    const size_t slot_bytes = static_cast<size_t>((B.slot_bytes + 127) / 128 * 128);
     const asyflexa::GsLayout L0 = asyflexa::make_gs_layout(nw, slot_bytes, 0);
     const size_t budget = std::min<size_t>(B.smem_optin, static_cast<size_t>(B.smem_per_sm) / want_per_sm - 1024);
-    if (L0.total + 2 * (L0.slot_bytes + sizeof(asyflexa::GsSlot) + 16) > budget) return ASYFLEXA_EUNSUPPORTED;
-    int stages = static_cast<int>((budget - L0.total - 256) / (L0.slot_bytes + sizeof(asyflexa::GsSlot) + 16));
+    if (L0.total + 2 * (L0.slot_bytes + 16) > budget) return ASYFLEXA_EUNSUPPORTED;
+    int stages = static_cast<int>((budget - L0.total - 256) / (L0.slot_bytes + 16));
     stages = std::max(2, std::min(16, stages));
     while (stages > 2 && asyflexa::make_gs_layout(nw, slot_bytes, stages).total > budget) --stages;
     c.stages = stages;
@@ -379,6 +392,7 @@ int gs_enqueue(asyflexa_batch_s& B, const GsChoice& c, int sweeps_only, int max_
     p.check_every = B.opts.check_every;
     p.max_sweeps = max_sweeps;
     p.stages = c.stages;
+    p.w = c.w;
     p.slot_bytes = c.slot_bytes;
     p.sweeps_only = sweeps_only;
     p.keep_a_in_l2 = (B.flags & ASYFLEXA_BATCH_SHARED_A) ? 1 : 0;
@@ -391,9 +405,13 @@ int gs_enqueue(asyflexa_batch_s& B, const GsChoice& c, int sweeps_only, int max_
     return ASYFLEXA_OK;
 }
 
-// The launch shape of the Gauss-Seidel form: cached for this batch shape, else the faster of
-// 7 and 15 consumer warps per CTA over one real sweep of every problem (tuning sweeps are
-// added to *tuned_sweeps).
+// Block width of the Gauss-Seidel form: opts.block_w in 1 .. kGsWMax fixes it, any other value
+// lets the autotuner pick it from {1, 2, 4}.
+bool gs_fixed_w(const asyflexa_batch_s& B) { return B.opts.block_w >= 1 && B.opts.block_w <= asyflexa::kGsWMax; }
+
+// The launch shape of the Gauss-Seidel form: cached for this batch shape, else the fastest of
+// 7 or 15 consumer warps per CTA and block widths 1, 2, 4 over one real sweep of every problem
+// per candidate (tuning sweeps are added to *tuned_sweeps).
 int gs_choose(asyflexa_batch_s& B, long long* tuned_sweeps) {
     if (B.gs.nw) return ASYFLEXA_OK;
     {
@@ -401,13 +419,25 @@ int gs_choose(asyflexa_batch_s& B, long long* tuned_sweeps) {
         auto itc = g_gs_tuned.find(B.shape_key);
         if (itc != g_gs_tuned.end()) {
             const int rc = gs_shape(B, itc->second.nw, &B.gs);
-            if (rc == ASYFLEXA_OK) return ASYFLEXA_OK;
+            if (rc == ASYFLEXA_OK) {
+                B.gs.w = itc->second.w;
+                return ASYFLEXA_OK;
+            }
         }
     }
     std::vector<GsChoice> cands;
     for (int nw : {7, 15}) {
         GsChoice c;
-        if (gs_shape(B, nw, &c) == ASYFLEXA_OK) cands.push_back(c);
+        if (gs_shape(B, nw, &c) != ASYFLEXA_OK) continue;
+        if (gs_fixed_w(B)) {
+            c.w = B.opts.block_w;
+            cands.push_back(c);
+            continue;
+        }
+        for (int w : {1, 2, 4}) {
+            c.w = w;
+            cands.push_back(c);
+        }
     }
     if (cands.empty()) return bfail("batched problems: no Gauss-Seidel launch shape fits", ASYFLEXA_EUNSUPPORTED);
     if (cands.size() == 1) {
@@ -425,8 +455,10 @@ int gs_choose(asyflexa_batch_s& B, long long* tuned_sweeps) {
             BCK(cudaEventSynchronize(a1), "event sync");
             float ms = 0.f;
             cudaEventElapsedTime(&ms, a0, a1);
-            if (best == 0.f || ms < best) {
-                best = ms;
+            // a sweep of the whole batch mostly times its longest columns, where the width
+            // changes little: within 3% the wider block wins (it pays on short columns)
+            if (best == 0.f || ms < 0.97f * best || (ms < 1.03f * best && c.w > B.gs.w)) {
+                if (best == 0.f || ms < best) best = ms;
                 B.gs = c;
             }
             ++*tuned_sweeps;
@@ -513,7 +545,7 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
             s.block_updates = sw * g.n;
             s.status = st;
             s.checked = g.checks > 0 ? 1 : 0;
-            s.block_w = 1;
+            s.block_w = g.w_used;
             s.batch_form = ASYFLEXA_BATCH_FORM_GS;
             s.ctas_per_sm = B.gs.ctas_per_sm;
             per[k] = s;
@@ -526,7 +558,7 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
         total->seconds = ms * 1e-3;
         total->status = worst;
         total->kernel_launches = B.launches;
-        total->block_w = 1;
+        total->block_w = B.gs.w;
         total->batch_form = ASYFLEXA_BATCH_FORM_GS;
         total->ctas_per_sm = B.gs.ctas_per_sm;
         total->kernel_variant = B.gs.nw;
@@ -827,7 +859,7 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
         } else if (flags & ASYFLEXA_BATCH_FORM_ASYNC) {
             B->form = ASYFLEXA_BATCH_FORM_ASYNC;
         } else {
-            B->form = (gs_fits && count * 4 >= B->sm_count) ? ASYFLEXA_BATCH_FORM_GS : ASYFLEXA_BATCH_FORM_ASYNC;
+            B->form = (gs_fits && count >= B->sm_count) ? ASYFLEXA_BATCH_FORM_GS : ASYFLEXA_BATCH_FORM_ASYNC;
         }
     }
     B->cpc = static_cast<int>((units + asyflexa::kRegStageUnits - 1) / asyflexa::kRegStageUnits);
@@ -906,7 +938,6 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
             g.lo = static_cast<const float*>(hk.prob.lo);
             g.hi = static_cast<const float*>(hk.prob.hi);
             g.lin = static_cast<const float*>(hk.prob.lin);
-            g.dw = hk.dw;
             g.lam = hk.prob.lambda;
             const bool lasso = hk.prob.loss == ASYFLEXA_LOSS_LASSO;
             g.s_loss = lasso ? 1.0 : 2.0;
@@ -918,6 +949,31 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
             total_mn += static_cast<double>(hk.prob.m) * static_cast<double>(hk.prob.n);
             max_n = std::max<int64_t>(max_n, hk.prob.n);
         }
+        // the (d_j, 1/d_j) table and the ring slot: at least the longest column, and room for up
+        // to kGsWMax short columns within 16 KB
+        int64_t total_n = 0, slot = 0;
+        for (int k = 0; k < count; ++k) {
+            const asyflexa_s& hk = *B->h[k];
+            total_n += hk.prob.n;
+            const int64_t colb = hk.mcopy * 4;
+            const int64_t multi = std::min<int64_t>(asyflexa::kGsWMax * hk.prob.lda * 4, 16384);
+            slot = std::max(slot, std::max(colb, multi));
+        }
+        B->slot_bytes = slot;
+        e = cudaMalloc(&B->d_dd, total_n * sizeof(float2));
+        if (e != cudaSuccess) return fail(bfail(std::string("batch allocation: ") + cudaGetErrorString(e), ASYFLEXA_ENOMEM));
+        {
+            int64_t off = 0;
+            for (int k = 0; k < count; ++k) {
+                const asyflexa_s& hk = *B->h[k];
+                gs_coef_kernel<<<static_cast<int>(std::min<int64_t>(1024, (hk.prob.n + 255) / 256)), 256, 0, B->stream>>>(
+                    hk.dw, hk.prob.n, B->d_dd + off);
+                B->h_gs[k].dd = B->d_dd + off;
+                off += hk.prob.n;
+            }
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return fail(bfail(std::string("coefficient kernel: ") + cudaGetErrorString(e), ASYFLEXA_ECUDA));
+        }
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
             return static_cast<double>(B->h_gs[a].m) * B->h_gs[a].n > static_cast<double>(B->h_gs[b].m) * B->h_gs[b].n;
         });
@@ -927,9 +983,9 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
         if (e == cudaSuccess) e = cudaMemcpy(B->d_order, order.data(), count * sizeof(int), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return fail(bfail(std::string("batch allocation: ") + cudaGetErrorString(e), ASYFLEXA_ENOMEM));
         char key[160];
-        std::snprintf(key, sizeof key, "count=%d mn=%.0f max_m=%lld max_n=%lld flags=%d nctas=%d sms=%d", count, total_mn,
-                      static_cast<long long>(B->max_mcopy), static_cast<long long>(max_n), flags, opts->num_ctas,
-                      B->sm_count);
+        std::snprintf(key, sizeof key, "count=%d mn=%.0f max_m=%lld max_n=%lld flags=%d nctas=%d w=%d sms=%d", count,
+                      total_mn, static_cast<long long>(B->max_mcopy), static_cast<long long>(max_n), flags,
+                      opts->num_ctas, opts->block_w, B->sm_count);
         B->shape_key = key;
     }
     // the caller's stream continues after the set-up work
@@ -955,7 +1011,7 @@ int asyflexa_batch_destroy(asyflexa_batch_t B) {
     if (B->ev_out) cudaEventDestroy(B->ev_out);
     if (B->stream) cudaStreamDestroy(B->stream);
     void* ptrs[] = {B->d_inst, B->d_blk_inst, B->d_blk_local, B->d_conv, B->d_round, B->d_nactive,
-                    B->counters, B->hist, B->err, B->d_gs, B->d_order, B->d_queue};
+                    B->counters, B->hist, B->err, B->d_gs, B->d_order, B->d_queue, B->d_dd};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete B;

@@ -3,23 +3,31 @@
 //
 // A CTA takes the next problem from a queue (problems ordered by decreasing size, so that
 // the largest start first) and runs Algorithm 1 on it with a single owner for every block:
-// with one CTA there are no updates in flight, so the iteration is exact cyclic
-// Gauss-Seidel over scalar blocks (the paper's own block choice, Section 4.1) with the fixed
-// step of S.4 and the best response of eq. 2.  The CTA then runs its own stopping test
-// (exact residual, F, gap, and the Section 4.3 merit ||xhat(x) - x||_inf / max(1, ||x||_inf))
-// and goes on with the next problem, so the whole batch needs no host round trip.
+// with one CTA there are no updates in flight, so the iteration is exact cyclic block
+// Gauss-Seidel (blocks of w <= 4 consecutive columns with the separable surrogate; w = 1 is
+// the paper's scalar blocks, Section 4.1) with the fixed step of S.4 and the best response of
+// eq. 2.  The CTA then runs its own stopping test (exact residual, F, gap, and the Section 4.3
+// merit ||xhat(x) - x||_inf / max(1, ||x||_inf)) and goes on with the next problem, so the
+// whole batch needs no host round trip.
 //
 //   * The residual r = A x - b lives in registers for the whole solve: consumer thread t
 //     owns the 16-byte units u = k * T + t (k < UPT, 4 rows each) of every column, and holds
 //     r for those rows as an unevaluated FP32 pair (hi, lo) so that small late increments
 //     are not lost to FP32 rounding.  Because a thread reads and updates only its own rows,
-//     the update r += a_j Delta_j needs no barrier before the next column's gradient.
-//   * A producer warp streams the columns HBM -> SMEM with 1-D bulk (TMA) copies into a ring
-//     of S slots (full / empty mbarriers).  With each copy it stages the column's
-//     coefficients (x_j, 1/d_j, lam/d_j, bounds, linear term) next to the slot.
-//   * One named barrier per column publishes the per-warp partial sums of a_j^T r; every
-//     consumer thread then evaluates the same FP32 best response (gs_delta).
-//   * Every gradient a_j^T r is a Dot2 sum (error-free products and sums) over r's (hi, lo) pair.
+//     the update r += A_i Delta_i needs no barrier before the next block's gradients.
+//   * A producer warp streams the blocks HBM -> SMEM, one 1-D bulk (TMA) copy per block (its
+//     columns are contiguous: stride lda), into a ring of S slots (full / empty mbarriers).
+//     A bulk copy costs the SM about the same time whatever its size up to tens of KB, so
+//     short columns are fetched several per copy.  The consumers load the block's
+//     coefficients (x_j and the FP32 d_j, 1/d_j staged at create) themselves, while they
+//     form the block's gradients.
+//   * A named barrier per block publishes the per-warp partial sums of a_j^T r for the block's
+//     columns; lane t of warp 0 then evaluates the FP32 best response of column t (gs_delta)
+//     and writes x_j, a second barrier publishes the steps, and every consumer thread folds
+//     a_j Delta_j into its rows, re-reading the block from its slot.
+//   * Near the tolerance every gradient a_j^T r is a Dot2 sum (error-free products and sums) over
+//     r's (hi, lo) pair and every update is error-free; before that the sweeps use plain FP32
+//     FMAs (an exact refresh follows every sweep phase).
 //   * Phases of one solve: REFRESH (r = -b + sum over x_j != 0 of a_j x_j with error-free
 //     products and sums, then F with FP64 sums), SWEEP (k sweeps, k = check_every or 2 near
 //     the tolerance), MERIT (x^_j with unit step, the largest |x^_j - x_j|).  A problem stops
@@ -46,14 +54,14 @@ struct GsInst {
     const float* lo;
     const float* hi;
     const float* lin;
-    const double* dw;
+    const float2* dd;           // (d_j, 1/d_j) in FP32; (0, 0) where d_j <= 0
     double lam, s_loss, c2, c;  // s_loss = 1 (LASSO) or 2 (NCQUAD); c2 = 2c; c: NCQUAD weight (for F)
     double f_star;              // NaN: no gap test, stop on the merit alone
     int loss, pad0;
     // written by the kernel
     double F, stat, xmax;
     long long sweeps, nnz;
-    int status, checks;
+    int status, checks, w_used, pad1;  // w_used: the block width (the tuned one, or as many as a slot holds)
 };
 
 struct GsParams {
@@ -63,40 +71,40 @@ struct GsParams {
     int* queue;         // next position in `order` (0 before the launch)
     double gamma, tol_gap, tol_stat;
     int check_every, max_sweeps, stages;
-    int64_t slot_bytes;   // ring slot: the longest column's 16-byte units, rounded up to 128 bytes
+    int w;              // block width, 1 .. kGsWMax
+    int64_t slot_bytes; // ring slot (a multiple of 128 bytes, at least the longest column)
     int sweeps_only;    // 1: exactly max_sweeps sweeps per problem, no stopping test (autotuner)
     int keep_a_in_l2;   // 1: A shared by the problems (normal L2 priority)
     int* err;
 };
 
-// Coefficients of the column in a ring slot (j < 0: end of a REFRESH phase).
-struct GsSlot {
-    int j;
-    float x, dinv, lam, lo, hi, lin, d;  // d = d_j and dinv = 1/d_j in FP32 (0 if d_j <= 0)
-};
+constexpr int kGsMeta = 64;  // REFRESH item ring (a power of 2, >= the ring depth)
+constexpr int kGsWMax = 4;   // largest block width of the Gauss-Seidel form
 
 struct GsLayout {
-    size_t slot_bytes, off_ring, off_meta, off_part, off_red, off_bars, off_misc, total;
+    size_t slot_bytes, off_ring, off_meta, off_part, off_red, off_dls, off_bars, off_misc, total;
 };
 
-// slot_bytes: the longest column of the batch (16-byte units, rounded up to 128 bytes).
 __host__ __device__ inline GsLayout make_gs_layout(int nw, size_t slot_bytes, int stages) {
     GsLayout L;
     L.slot_bytes = slot_bytes;
     size_t o = 0;
     L.off_ring = o;
     o += L.slot_bytes * stages;
-    L.off_meta = o;
-    o += sizeof(GsSlot) * stages;
-    L.off_part = o;  // two buffers of per-warp (s, c) partial pairs
-    o += 2 * static_cast<size_t>(nw) * 2 * sizeof(float);
+    L.off_meta = o;  // first column of each REFRESH item (-1: end of the phase)
+    o += sizeof(int) * kGsMeta;
+    L.off_part = o;  // two buffers of per-warp (s, c) partial pairs for up to kGsWMax columns
+    o += 2 * static_cast<size_t>(kGsWMax) * nw * 2 * sizeof(float);
     o = (o + 15) / 16 * 16;
     L.off_red = o;   // per-warp FP64 sums of the objective pieces
     o += static_cast<size_t>(nw) * 8 * sizeof(double);
+    L.off_dls = o;   // the steps x_new - x of the current block's columns
+    o += kGsWMax * sizeof(float);
+    o = (o + 15) / 16 * 16;
     L.off_bars = o;
     o += 2 * static_cast<size_t>(stages) * sizeof(uint64_t);
     L.off_misc = o;  // abort flag, queue position, decision values
-    o += 64;
+    o += 128;
     L.total = (o + 127) / 128 * 128;
     return L;
 }
@@ -110,6 +118,16 @@ struct GsMisc {
     int abort, qi, nonfinite, pad;
     double F, xmax, merit;
     long long nnz;
+    // the solve's control state, kept and decided by thread 0
+    long long sweeps;
+    double stat_ref;  // best merit so far
+    float stat_last;
+    int phase, k_sweeps, status, checks, exact, flat, flat_plain, done, reset;
+};
+
+// The coefficients of column j that the best response needs (bounds and linear term apart).
+struct GsCoef {
+    float x, d, dinv;
 };
 
 // x^_j - x_j for the best response of eq. 2 (soft-threshold, then clip), in FP32, from the
@@ -118,18 +136,19 @@ struct GsMisc {
 // and near a stationary point grad + lam (or grad - lam) cancels: formed as (gh + lam) + gl it
 // is exact up to the last rounding (Sterbenz), where x - grad/d loses the digits of a small
 // difference of two numbers as large as lam / d.
-__device__ __forceinline__ float gs_delta(const GsSlot& c, float gh, float gl, float s_loss, float c2) {
+__device__ __forceinline__ float gs_delta(const GsCoef& c, float lo, float hi, float lin, float lam, float gh, float gl,
+                                         float s_loss, float c2) {
     // grad = s_loss * g - c2 x + lin as a pair (s_loss is 1 or 2: exact)
     float th, tl;
-    two_sum(s_loss * gh, fmaf(-c2, c.x, c.lin), th, tl);
+    two_sum(s_loss * gh, fmaf(-c2, c.x, lin), th, tl);
     tl += s_loss * gl;
     float e;
     if (c.dinv > 0.f) {
         const float q = fmaf(c.x, c.d, -th) - tl;
-        if (q > c.lam)
-            e = -((th + c.lam) + tl) * c.dinv;
-        else if (q < -c.lam)
-            e = -((th - c.lam) + tl) * c.dinv;
+        if (q > lam)
+            e = -((th + lam) + tl) * c.dinv;
+        else if (q < -lam)
+            e = -((th - lam) + tl) * c.dinv;
         else
             e = -c.x;
     } else {
@@ -138,8 +157,8 @@ __device__ __forceinline__ float gs_delta(const GsSlot& c, float gh, float gl, f
     // the box, if active; otherwise e itself (not x + e rounded to FP32 and minus x, which
     // would hide a step below half an ulp of x from the stopping test)
     const float xe = c.x + e;
-    if (xe < c.lo) return c.lo - c.x;
-    if (xe > c.hi) return c.hi - c.x;
+    if (xe < lo) return lo - c.x;
+    if (xe > hi) return hi - c.x;
     return e;
 }
 
@@ -162,9 +181,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
     extern __shared__ __align__(128) unsigned char smem[];
     const GsLayout L = make_gs_layout(NW, static_cast<size_t>(p.slot_bytes), p.stages);
     unsigned char* ring = smem + L.off_ring;
-    GsSlot* meta = reinterpret_cast<GsSlot*>(smem + L.off_meta);
+    int* meta = reinterpret_cast<int*>(smem + L.off_meta);
     float2* part = reinterpret_cast<float2*>(smem + L.off_part);
     double* red = reinterpret_cast<double*>(smem + L.off_red);
+    float* dls = reinterpret_cast<float*>(smem + L.off_dls);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + L.off_bars);
     uint64_t* empty = full + p.stages;
     GsMisc* misc = reinterpret_cast<GsMisc*>(smem + L.off_misc);
@@ -188,7 +208,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
 
     const uint64_t pol = p.keep_a_in_l2 ? l2_policy_evict_normal() : l2_policy_evict_first();
     long long it = 0;   // ring items issued (producer) / consumed (consumers); identical sequences
-    int buf = 0;        // partial-sum buffer of the next column
+    int pslot = 0, cslot = 0;        // slot of item `it` (it mod S), producer / consumer side
+    uint32_t ppar = 0u, cpar = 0u;   // parity of that slot's use by item `it`
+    int buf = 0;        // partial-sum buffer of the next block
     bool ok = true;     // this thread's waits all completed
 
     float rhi[UPT][4], rlo[UPT][4];
@@ -201,265 +223,378 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
         const int ii = p.order[qi];
         const GsInst& I = p.inst[ii];
         const float* A = I.A;
-        const int64_t lda = I.lda, m = I.m, n = I.n;
-        const int64_t units = (m + 3) / 4;
-        const uint32_t col_bytes = static_cast<uint32_t>(units * 16);
+        float* X = I.x;
+        const float2* DD = I.dd;
+        const float *LO = I.lo, *HI = I.hi, *LIN = I.lin;
+        const int lda = static_cast<int>(I.lda), m = static_cast<int>(I.m), n = static_cast<int>(I.n);
+        const int units = (m + 3) / 4;
         const float s_loss = static_cast<float>(I.s_loss), c2 = static_cast<float>(I.c2);
+        const float lam = static_cast<float>(I.lam);
         const float gamma = static_cast<float>(p.gamma);
+        // columns per block: the tuned width, as many as a slot holds
+        const int wcap = static_cast<int>((p.slot_bytes - static_cast<int64_t>(units) * 16) /
+                                          (static_cast<int64_t>(lda) * 4)) + 1;
+        const int w = p.w < wcap ? p.w : wcap;
+        // this thread's units k < kmine hold rows of the column; unit klast (or -1) is the
+        // column's last one, of which only its first vlast rows are < m
+        const int kmine = tid < units ? (units - 1 - tid) / T + 1 : 0;
+        const int klast = ((units - 1) % T == tid) ? (units - 1) / T : -1;
+        const int vlast = m - 4 * (units - 1);
 
-        if (!producer) {
+        auto reset_r = [&]() {
 #pragma unroll
             for (int k = 0; k < UPT; ++k) {
-                const int64_t u = static_cast<int64_t>(k) * T + tid;
+                const int u = k * T + tid;
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    const int64_t row = u * 4 + e;
+                    const int row = u * 4 + e;
                     rhi[k][e] = row < m ? -I.b[row] : 0.f;
                     rlo[k][e] = 0.f;
                 }
             }
-        }
+        };
+        if (!producer) reset_r();
 
-        long long sweeps = 0;
-        int status = ASYFLEXA_ENOTCONV, checks = 0, phase = kGsRefresh, k_sweeps = 0;
-        float stat_last = NAN;
-        // stationarity floor: with the gap met and the merit within kGsFloorBand tol_stat,
-        // kGsFloorChecks checks in a row that do not lower the best merit by 10% end the solve
-        // (ENOTCONV): the FP32 iterate has stopped moving
-        double stat_ref = INFINITY;
-        int flat = 0;
+        if (tid == 0) {
+            misc->sweeps = 0;
+            misc->status = ASYFLEXA_ENOTCONV;
+            misc->checks = 0;
+            misc->phase = kGsRefresh;
+            misc->k_sweeps = 0;
+            misc->stat_last = NAN;
+            // stationarity floor: with the gap met and the merit within kGsFloorBand tol_stat,
+            // kGsFloorChecks checks in a row that do not lower the best merit by 10% end the
+            // solve (ENOTCONV): the FP32 iterate has stopped moving
+            misc->stat_ref = INFINITY;
+            misc->flat = 0;
+            // the sweeps' arithmetic: plain FP32 until the solve is near its tolerance (the gap
+            // test passed with a known f_star; without one, a merit within kGsFloorBand tol_stat,
+            // or two checks in a row that did not lower the best merit by 10%), exact from then on
+            misc->exact = 0;
+            misc->flat_plain = 0;
+            misc->done = 0;
+            misc->reset = 0;
+        }
+        __syncthreads();
         for (;;) {
+            const int phase = misc->phase, k_sweeps = misc->k_sweeps;
+            const bool exact = misc->exact != 0;
             // ================================================================ one phase
             if (producer) {
-                // ---- issue the phase's columns into the ring (lane 0), in consumption order.
-                // wait_free(q, lead): item q may be issued once item q - lead has been consumed
-                auto wait_free = [&](long long q, long long lead_items) -> bool {
-                    if (q < lead_items) return true;
-                    const long long r0 = q - lead_items;
-                    return mbar_wait_bounded(&empty[r0 % S], static_cast<uint32_t>((r0 / S) & 1), abort_flag, p.err);
+                // ---- issue the phase's items into the ring (lane 0), in consumption order.
+                // Item `it` goes to slot `pslot` (= it mod S), whose previous use (item it - S) had
+                // parity ppar ^ 1.
+                auto wait_slot = [&]() -> bool {  // item it - S consumed: its slot is free
+                    if (it < S) return true;
+                    return mbar_wait_bounded(&empty[pslot], ppar ^ 1u, abort_flag, p.err);
                 };
-                auto put = [&](const GsSlot& c) {
-                    const int slot = static_cast<int>(it % S);
-                    meta[slot] = c;
-                    if (c.j >= 0) {
-                        mbar_arrive_expect_tx(&full[slot], col_bytes);
-                        bulk_load(ring + slot * L.slot_bytes, A + static_cast<int64_t>(c.j) * lda, col_bytes,
-                                  &full[slot], pol);
+                auto issue = [&](int j0, int wb) {  // lane 0, after wait_slot: columns j0 .. j0 + wb - 1
+                    if (wb > 0) {
+                        const uint32_t bytes = static_cast<uint32_t>(
+                            static_cast<int64_t>(wb - 1) * lda * 4 + static_cast<int64_t>(units) * 16);
+                        mbar_arrive_expect_tx(&full[pslot], bytes);
+                        bulk_load(ring + pslot * L.slot_bytes, A + static_cast<int64_t>(j0) * lda, bytes, &full[pslot],
+                                  pol);
                     } else {
-                        mbar_arrive(&full[slot]);
+                        mbar_arrive(&full[pslot]);
                     }
                     ++it;
+                    if (++pslot == S) {
+                        pslot = 0;
+                        ppar ^= 1u;
+                    }
                 };
-                auto coef = [&](int j, float xj) {
-                    GsSlot c;
-                    c.j = j;
-                    c.x = xj;
-                    const double dj = I.dw[j];
-                    c.dinv = dj > 0.0 ? static_cast<float>(1.0 / dj) : 0.f;
-                    c.d = dj > 0.0 ? static_cast<float>(dj) : 0.f;
-                    c.lam = static_cast<float>(I.lam);
-                    c.lo = I.lo ? I.lo[j] : -INFINITY;
-                    c.hi = I.hi ? I.hi[j] : INFINITY;
-                    c.lin = I.lin ? I.lin[j] : 0.f;
-                    return c;
-                };
+                bool go = true;
                 if (phase == kGsRefresh) {
-                    // the nonzero columns of x, found 32 at a time by the whole warp
-                    bool go = true;
-                    for (int64_t j0 = 0; j0 < n && go; j0 += 32) {
-                        const int64_t j = j0 + lane;
-                        const float xv = j < n ? I.x[j] : 0.f;
-                        unsigned mask = __ballot_sync(0xffffffffu, xv != 0.f);
-                        while (mask && go) {
-                            const int bit = __ffs(mask) - 1;
-                            mask &= mask - 1;
-                            const float xj = __shfl_sync(0xffffffffu, xv, bit);
+                    // the blocks of w columns that hold a nonzero x_j, found 32 columns at a time
+                    // by the whole warp (w divides 32); meta[item] = the block's first column
+                    for (int j0 = 0; j0 < n && go; j0 += 32) {
+                        const int j = j0 + lane;
+                        const bool nz = j < n && X[j] != 0.f;
+                        const unsigned mask = __ballot_sync(0xffffffffu, nz);
+                        for (int b0 = 0; b0 < 32 && go; b0 += w) {
+                            const unsigned bm = (mask >> b0) & ((1u << w) - 1u);
+                            if (bm == 0u) continue;
                             int okl = 1;
                             if (lane == 0) {
-                                okl = wait_free(it, S) ? 1 : 0;
+                                okl = wait_slot() ? 1 : 0;
                                 if (okl) {
-                                    GsSlot c{};
-                                    c.j = static_cast<int>(j0 + bit);
-                                    c.x = xj;
-                                    put(c);
+                                    meta[it & (kGsMeta - 1)] = j0 + b0;
+                                    issue(j0 + b0, n - (j0 + b0) < w ? n - (j0 + b0) : w);
                                 }
                             }
                             go = __shfl_sync(0xffffffffu, okl, 0) != 0;
                         }
                     }
-                    if (lane == 0 && go && wait_free(it, S)) {
-                        GsSlot c{};
-                        c.j = -1;
-                        put(c);
+                    if (lane == 0 && go && wait_slot()) {
+                        meta[it & (kGsMeta - 1)] = -1;
+                        issue(0, 0);
                     }
-                } else {
-                    const bool sweep = phase == kGsSweep;
-                    const long long cnt = sweep ? static_cast<long long>(k_sweeps) * n : n;
-                    // x_j of a sweep is final once the column's previous update is consumed: with
-                    // n >= S + 32 the slot-free wait of the first of 32 items guarantees it for all
-                    // 32, whose coefficients the warp then loads at once; otherwise lane 0 loads
-                    // them column by column, at most min(S, n) items ahead
-                    const bool batch = !sweep || n >= S + 32;
-                    if (batch) {
-                        bool go = true;
-                        for (long long q0 = 0; q0 < cnt && go; q0 += 32) {
-                            int okl = 1;
-                            if (lane == 0) okl = wait_free(it, S) ? 1 : 0;
-                            go = __shfl_sync(0xffffffffu, okl, 0) != 0;
-                            if (!go) break;
-                            const long long q = q0 + lane;
-                            GsSlot mine{};
-                            if (q < cnt) {
-                                const int j = static_cast<int>(q % n);
-                                mine = coef(j, I.x[j]);
+                } else if (lane == 0) {
+                    const int nsw = phase == kGsSweep ? k_sweeps : 1;
+                    for (int sw = 0; sw < nsw && go; ++sw)
+                        for (int j0 = 0; j0 < n; j0 += w) {
+                            if (!wait_slot()) {
+                                go = false;
+                                break;
                             }
-                            const int nb = static_cast<int>(cnt - q0 < 32 ? cnt - q0 : 32);
-                            for (int l = 0; l < nb && go; ++l) {
-                                GsSlot c;
-                                c.j = __shfl_sync(0xffffffffu, mine.j, l);
-                                c.x = __shfl_sync(0xffffffffu, mine.x, l);
-                                c.dinv = __shfl_sync(0xffffffffu, mine.dinv, l);
-                                c.lam = __shfl_sync(0xffffffffu, mine.lam, l);
-                                c.lo = __shfl_sync(0xffffffffu, mine.lo, l);
-                                c.hi = __shfl_sync(0xffffffffu, mine.hi, l);
-                                c.lin = __shfl_sync(0xffffffffu, mine.lin, l);
-                                c.d = __shfl_sync(0xffffffffu, mine.d, l);
-                                if (lane == 0) {
-                                    okl = wait_free(it, S) ? 1 : 0;
-                                    if (okl) put(c);
-                                }
-                                go = __shfl_sync(0xffffffffu, okl, 0) != 0;
-                            }
+                            issue(j0, n - j0 < w ? n - j0 : w);
                         }
-                    } else if (lane == 0) {
-                        const long long lead = n < S ? n : S;
-                        for (long long q = 0; q < cnt; ++q) {
-                            if (!wait_free(it, lead)) break;
-                            const int j = static_cast<int>(q % n);
-                            put(coef(j, I.x[j]));
-                        }
-                    }
                 }
                 it = __shfl_sync(0xffffffffu, it, 0);
+                pslot = __shfl_sync(0xffffffffu, pslot, 0);
+                ppar = __shfl_sync(0xffffffffu, ppar, 0);
             } else if (phase == kGsRefresh) {
                 // ---- r += a_j x_j over the nonzero columns (no barrier: every thread reads and
                 // writes only its own rows)
                 for (;;) {
-                    const int slot = static_cast<int>(it % S);
-                    ok = ok && !*abort_flag &&
-                         mbar_wait_bounded(&full[slot], static_cast<uint32_t>((it / S) & 1), abort_flag, p.err);
+                    const int slot = cslot;
+                    ok = ok && !*abort_flag && mbar_wait_bounded(&full[slot], cpar, abort_flag, p.err);
                     if (!ok) break;
-                    const GsSlot c = meta[slot];
-                    if (c.j >= 0) {
-                        const uint4* src = reinterpret_cast<const uint4*>(ring + slot * L.slot_bytes);
+                    const int j0 = meta[it & (kGsMeta - 1)];
+                    if (j0 >= 0) {
+                        const int wb = n - j0 < w ? n - j0 : w;
+                        for (int t = 0; t < wb; ++t) {
+                            const float xj = X[j0 + t];
+                            if (xj == 0.f) continue;
+                            const uint4* src = reinterpret_cast<const uint4*>(ring + slot * L.slot_bytes +
+                                                                              static_cast<size_t>(t) * lda * 4);
 #pragma unroll
-                        for (int k = 0; k < UPT; ++k) {
-                            const int64_t u = static_cast<int64_t>(k) * T + tid;
-                            if (u < units) {
-                                float a[4];
-                                ATraits<float>::unpack(src[k * T + tid], a);
+                            for (int k = 0; k < UPT; ++k) {
+                                if (k < kmine) {
+                                    float a[4];
+                                    ATraits<float>::unpack(src[k * T + tid], a);
+                                    const int nv = k == klast ? vlast : 4;
 #pragma unroll
-                                for (int e = 0; e < 4; ++e)
-                                    if (u * 4 + e < m) ff_add_prod(rhi[k][e], rlo[k][e], a[e], c.x);
+                                    for (int e = 0; e < 4; ++e)
+                                        if (e < nv) ff_add_prod(rhi[k][e], rlo[k][e], a[e], xj);
+                                }
                             }
                         }
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&empty[slot]);
                     ++it;
-                    if (c.j < 0) break;
+                    if (++cslot == S) {
+                        cslot = 0;
+                        cpar ^= 1u;
+                    }
+                    if (j0 < 0) break;
                 }
             } else {
-                // ---- SWEEP (k sweeps of cyclic coordinate updates) or MERIT (one pass, no update)
+                // ---- SWEEP (k sweeps of cyclic block updates) or MERIT (one pass, no update).
+                // A block is wb <= w consecutive columns of a sweep (the last block of a sweep may
+                // be shorter), fetched by one copy into one slot; its columns share the residual
+                // r of the block's start (the separable surrogate of the block update), so their
+                // dots and reductions overlap and one barrier publishes all wb partial sums.  The
+                // update pass then re-reads the block from its slot, released at the block end.
                 const bool merit = phase == kGsMerit;
-                const long long cnt = merit ? n : static_cast<long long>(k_sweeps) * n;
+                const bool ex = merit || exact;
+                const int nsw = merit ? 1 : k_sweeps;
                 float mmax = 0.f;
                 bool bad = false;
-                for (long long q = 0; q < cnt; ++q) {
-                    const int slot = static_cast<int>(it % S);
-                    ok = ok && !*abort_flag &&
-                         mbar_wait_bounded(&full[slot], static_cast<uint32_t>((it / S) & 1), abort_flag, p.err);
-                    const GsSlot c = meta[slot];
-                    const uint4* src = reinterpret_cast<const uint4*>(ring + slot * L.slot_bytes);
-                    // a_j^T r with Dot2 products on r's (hi, lo) pair in both phases: a plain FP32
-                    // dot of length m errs by about sqrt(m) eps ||a_j|| ||r||, which divided by
-                    // d_j = ||a_j||^2 would put the iteration's fixed point 1e-5 away from
-                    // stationarity on columns of moderate norm
-                    uint4 colr[UPT];
-                    DFAcc dacc0, dacc1;
-                    float lo_acc = 0.f;
-#pragma unroll
-                    for (int k = 0; k < UPT; ++k) {
-                        const int64_t u = static_cast<int64_t>(k) * T + tid;
-                        colr[k] = (ok && u < units) ? src[k * T + tid] : make_uint4(0u, 0u, 0u, 0u);
-                        if (u == units - 1) {  // rows past m in the last unit
-                            const int valid = static_cast<int>(m - u * 4);
-                            if (valid < 4) colr[k].w = 0u;
-                            if (valid < 3) colr[k].z = 0u;
-                            if (valid < 2) colr[k].y = 0u;
-                        }
-                        float a[4];
-                        ATraits<float>::unpack(colr[k], a);
-                        dacc0.add_prod(a[0], rhi[k][0]);
-                        dacc1.add_prod(a[1], rhi[k][1]);
-                        dacc0.add_prod(a[2], rhi[k][2]);
-                        dacc1.add_prod(a[3], rhi[k][3]);
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) lo_acc = fmaf(a[e], rlo[k][e], lo_acc);
+                // a column unit into registers, the rows past m of the last unit zeroed
+                auto load_unit = [&](const uint4* src, int k) -> uint4 {
+                    uint4 v = (ok && k < kmine) ? src[k * T + tid] : make_uint4(0u, 0u, 0u, 0u);
+                    if (k == klast) {
+                        if (vlast < 4) v.w = 0u;
+                        if (vlast < 3) v.z = 0u;
+                        if (vlast < 2) v.y = 0u;
                     }
-                    float2* cp = part + buf * NW;
-                    {
-                        float ts, tc;
-                        two_sum(dacc0.s, dacc1.s, ts, tc);
-                        tc += (dacc0.c + dacc1.c) + lo_acc;
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            const float so = __shfl_xor_sync(0xffffffffu, ts, o);
-                            const float co = __shfl_xor_sync(0xffffffffu, tc, o);
-                            float t, e;
-                            two_sum(ts, so, t, e);
-                            tc = (tc + co) + e;
-                            ts = t;
-                        }
-                        if (lane == 0) cp[warp] = make_float2(ts, tc);
+                    return v;
+                };
+                // Lane t of warp 0 owns the block's column t: it sums the column's warp partials,
+                // evaluates its best response and writes x_j, so column j (always at position
+                // j mod w of its block) is read and written by one thread.  Its coefficients are
+                // loaded one block ahead.
+                float cx = 0.f, cd = 0.f, cdi = 0.f;
+                auto load_coef = [&](int j0, int wb) {
+                    if (warp == 0 && lane < wb) {
+                        const int j = j0 + lane;
+                        const float2 dd = DD[j];
+                        cx = X[j];
+                        cd = dd.x;
+                        cdi = dd.y;
                     }
-                    named_bar_sync(1, T);
-                    // the NW partial pairs in a fixed order: every thread gets the same g
-                    float gh, gl;
-                    {
-                        float s = cp[0].x, cc = cp[0].y;
+                };
+                load_coef(0, n < w ? n : w);
+                for (int sw = 0; sw < nsw; ++sw) {
+                    for (int j0 = 0; j0 < n; j0 += w) {
+                        const int wb = n - j0 < w ? n - j0 : w;
+                        const int slot = cslot;
+                        ok = ok && !*abort_flag && mbar_wait_bounded(&full[slot], cpar, abort_flag, p.err);
+                        float2* cp = part + buf * (kGsWMax * NW);
+                        // a_j^T r.  Exact arithmetic (the merit pass, and the sweeps once the solve
+                        // is near its tolerance): Dot2 products on r's (hi, lo) pair -- a plain FP32
+                        // dot of length m errs by about sqrt(m) eps ||a_j|| ||r||, which divided by
+                        // d_j = ||a_j||^2 puts the plain iteration's fixed point up to 1e-5 away from
+                        // stationarity.  Earlier sweeps use plain FP32 FMAs on r_hi (the columns of a
+                        // block interleaved); the exact refresh after every sweep phase removes their
+                        // drift.
+                        if (ex) {
+#pragma unroll 1
+                            for (int t = 0; t < wb; ++t) {
+                                const uint4* src = reinterpret_cast<const uint4*>(ring + slot * L.slot_bytes +
+                                                                                  static_cast<size_t>(t) * lda * 4);
+                                DFAcc dacc0, dacc1;
+                                float lo_acc = 0.f;
 #pragma unroll
-                        for (int w = 1; w < NW; ++w) {
-                            float t, e;
-                            two_sum(s, cp[w].x, t, e);
-                            cc = (cc + cp[w].y) + e;
-                            s = t;
-                        }
-                        two_sum(s, cc, gh, gl);
-                    }
-                    buf ^= 1;
-                    const float e = gs_delta(c, gh, gl, s_loss, c2);
-                    if (merit) {
-                        // |x^_j - x_j| (unit step): the Section 4.3 merit
-                        mmax = fmaxf(mmax, fabsf(e));
-                        bad |= !(fabsf(gh) <= 3.0e38f);  // NaN or infinite gradient
-                    } else {
-                        const float xn = fmaf(gamma, e, c.x);
-                        const float dlt = xn - c.x;
-                        if (ok && tid == 0) I.x[c.j] = xn;
-                        if (ok && dlt != 0.f) {
+                                for (int k = 0; k < UPT; ++k) {
+                                    float a[4];
+                                    ATraits<float>::unpack(load_unit(src, k), a);
+                                    dacc0.add_prod(a[0], rhi[k][0]);
+                                    dacc1.add_prod(a[1], rhi[k][1]);
+                                    dacc0.add_prod(a[2], rhi[k][2]);
+                                    dacc1.add_prod(a[3], rhi[k][3]);
 #pragma unroll
-                            for (int k = 0; k < UPT; ++k) {
-                                float a[4];
-                                ATraits<float>::unpack(colr[k], a);
+                                    for (int e = 0; e < 4; ++e) lo_acc = fmaf(a[e], rlo[k][e], lo_acc);
+                                }
+                                float ts, tc;
+                                two_sum(dacc0.s, dacc1.s, ts, tc);
+                                tc += (dacc0.c + dacc1.c) + lo_acc;
 #pragma unroll
-                                for (int e = 0; e < 4; ++e) ff_add_prod(rhi[k][e], rlo[k][e], a[e], dlt);
+                                for (int o = 16; o > 0; o >>= 1) {
+                                    const float so = __shfl_xor_sync(0xffffffffu, ts, o);
+                                    const float co = __shfl_xor_sync(0xffffffffu, tc, o);
+                                    float tt, e;
+                                    two_sum(ts, so, tt, e);
+                                    tc = (tc + co) + e;
+                                    ts = tt;
+                                }
+                                if (lane == 0) cp[t * NW + warp] = make_float2(ts, tc);
+                            }
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < kGsWMax; ++t) {
+                                if (t < wb) {
+                                    const uint4* src = reinterpret_cast<const uint4*>(
+                                        ring + slot * L.slot_bytes + static_cast<size_t>(t) * lda * 4);
+                                    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+#pragma unroll
+                                    for (int k = 0; k < UPT; ++k) {
+                                        float a[4];
+                                        ATraits<float>::unpack(load_unit(src, k), a);
+                                        acc0 = fmaf(a[0], rhi[k][0], acc0);
+                                        acc1 = fmaf(a[1], rhi[k][1], acc1);
+                                        acc2 = fmaf(a[2], rhi[k][2], acc2);
+                                        acc3 = fmaf(a[3], rhi[k][3], acc3);
+                                    }
+                                    const float v = warp_sum((acc0 + acc1) + (acc2 + acc3));
+                                    if (lane == 0) cp[t * NW + warp] = make_float2(v, 0.f);
+                                }
                             }
                         }
+                        named_bar_sync(1, T);
+                        if (warp == 0) {
+                            const int jn = j0 + w < n ? j0 + w : 0;  // the next block (next sweep: 0)
+                            float nx = cx, nd = cd, ndi = cdi;
+                            if (lane < wb) {
+                                // the column's partials in a fixed order: g = gh + gl
+                                const float2* c2p = cp + lane * NW;
+                                float gh, gl;
+                                if (ex) {
+                                    float sh = c2p[0].x, cc = c2p[0].y;
+#pragma unroll
+                                    for (int w2 = 1; w2 < NW; ++w2) {
+                                        float tt, e;
+                                        two_sum(sh, c2p[w2].x, tt, e);
+                                        cc = (cc + c2p[w2].y) + e;
+                                        sh = tt;
+                                    }
+                                    two_sum(sh, cc, gh, gl);
+                                } else {
+                                    float sh = 0.f;
+#pragma unroll
+                                    for (int w2 = 0; w2 < NW; ++w2) sh += c2p[w2].x;
+                                    gh = sh;
+                                    gl = 0.f;
+                                }
+                                const int j = j0 + lane;
+                                const GsCoef c{cx, cd, cdi};
+                                const float e = gs_delta(c, LO ? LO[j] : -INFINITY, HI ? HI[j] : INFINITY,
+                                                         LIN ? LIN[j] : 0.f, lam, gh, gl, s_loss, c2);
+                                if (merit) {
+                                    // |x^_j - x_j| (unit step): the Section 4.3 merit
+                                    mmax = fmaxf(mmax, fabsf(e));
+                                    bad |= !(fabsf(gh) <= 3.0e38f);  // NaN or infinite gradient
+                                } else {
+                                    const float xn = fmaf(gamma, e, cx);
+                                    if (ok) X[j] = xn;
+                                    dls[lane] = ok ? xn - cx : 0.f;
+                                    if (jn == j0) nx = xn;  // one block per sweep: its own new x
+                                }
+                            }
+                            // the next block's coefficients (loaded by the lane that will use them)
+                            if (jn != j0) {
+                                const int wbn = n - jn < w ? n - jn : w;
+                                if (lane < wbn) {
+                                    const float2 dd = DD[jn + lane];
+                                    nx = X[jn + lane];
+                                    nd = dd.x;
+                                    ndi = dd.y;
+                                }
+                            }
+                            cx = nx;
+                            cd = nd;
+                            cdi = ndi;
+                        }
+                        buf ^= 1;
+                        if (!merit) {
+                            named_bar_sync(1, T);  // the block's steps are in dls
+                            // the block's increment r += A_i Delta_i, each thread on its own rows,
+                            // the columns read again from the slot
+                            if (ex) {
+#pragma unroll 1
+                                for (int t = 0; t < wb; ++t) {
+                                    const float dl = dls[t];
+                                    if (dl != 0.f) {
+                                        const uint4* src = reinterpret_cast<const uint4*>(
+                                            ring + slot * L.slot_bytes + static_cast<size_t>(t) * lda * 4);
+#pragma unroll
+                                        for (int k = 0; k < UPT; ++k) {
+                                            float a[4];
+                                            ATraits<float>::unpack(load_unit(src, k), a);
+#pragma unroll
+                                            for (int e = 0; e < 4; ++e) ff_add_prod(rhi[k][e], rlo[k][e], a[e], dl);
+                                        }
+                                    }
+                                }
+                            } else {
+#pragma unroll
+                                for (int t = 0; t < kGsWMax; ++t) {
+                                    if (t < wb) {
+                                        const float dl = dls[t];
+                                        if (dl != 0.f) {
+                                            const uint4* src = reinterpret_cast<const uint4*>(
+                                                ring + slot * L.slot_bytes + static_cast<size_t>(t) * lda * 4);
+#pragma unroll
+                                            for (int k = 0; k < UPT; ++k) {
+                                                float a[4];
+                                                ATraits<float>::unpack(load_unit(src, k), a);
+#pragma unroll
+                                                for (int e = 0; e < 4; ++e) rhi[k][e] = fmaf(a[e], dl, rhi[k][e]);
+                                            }
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                        __syncwarp();
+                        if (lane == 0 && ok) mbar_arrive(&empty[slot]);
+                        ++it;
+                        if (++cslot == S) {
+                            cslot = 0;
+                            cpar ^= 1u;
+                        }
                     }
-                    __syncwarp();
-                    if (lane == 0 && ok) mbar_arrive(&empty[slot]);
-                    ++it;
+                }
+                if (merit && warp == 0) {
+                    // the largest merit over warp 0's lanes
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        mmax = fmaxf(mmax, __shfl_xor_sync(0xffffffffu, mmax, o));
+                        bad |= __shfl_xor_sync(0xffffffffu, bad ? 1 : 0, o) != 0;
+                    }
                 }
                 if (merit && tid == 0) {
                     misc->merit = bad ? NAN : static_cast<double>(mmax);
@@ -478,11 +613,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                         const double v = static_cast<double>(rhi[k][e]) + static_cast<double>(rlo[k][e]);
                         rr += v * v;
                     }
-                for (int64_t j = tid; j < n; j += T) {
-                    const double xj = static_cast<double>(I.x[j]);
+                for (int j = tid; j < n; j += T) {
+                    const double xj = static_cast<double>(X[j]);
                     ax += fabs(xj);
                     x2 += xj * xj;
-                    if (I.lin) lx += static_cast<double>(I.lin[j]) * xj;
+                    if (LIN) lx += static_cast<double>(LIN[j]) * xj;
                     xm = fmax(xm, fabs(xj));
                     nz += xj != 0.0 ? 1.0 : 0.0;
                 }
@@ -506,94 +641,105 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                 }
                 named_bar_sync(1, T);
                 if (tid == 0) {
-                    double s[6] = {0, 0, 0, 0, 0, 0};
-                    for (int w = 0; w < NW; ++w) {
-                        for (int q = 0; q < 5; ++q) s[q] += red[w * 8 + q];
-                        s[5] = fmax(s[5], red[w * 8 + 5]);
+                    double sm[6] = {0, 0, 0, 0, 0, 0};
+                    for (int w2 = 0; w2 < NW; ++w2) {
+                        for (int q = 0; q < 5; ++q) sm[q] += red[w2 * 8 + q];
+                        sm[5] = fmax(sm[5], red[w2 * 8 + 5]);
                     }
-                    const double F = (I.loss == ASYFLEXA_LOSS_LASSO ? 0.5 * s[0] : s[0] - I.c * s[2]) + s[3] +
-                                     I.lam * s[1];
+                    const double F = (I.loss == ASYFLEXA_LOSS_LASSO ? 0.5 * sm[0] : sm[0] - I.c * sm[2]) + sm[3] +
+                                     I.lam * sm[1];
                     misc->F = F;
-                    misc->nnz = static_cast<long long>(s[4]);
-                    misc->xmax = s[5];
+                    misc->nnz = static_cast<long long>(sm[4]);
+                    misc->xmax = sm[5];
                     misc->nonfinite = isfinite(F) ? 0 : 1;
                 }
             }
             __syncthreads();
 
             // ================================================================ next phase
-            // (the same decision in every thread, from the shared values)
-            if (*abort_flag) break;
-            if (phase == kGsRefresh) {
-                if (misc->nonfinite) {
-                    status = ASYFLEXA_ENONFINITE;
-                    break;
-                }
-                if (p.sweeps_only) {
-                    if (sweeps >= p.max_sweeps) break;
-                    k_sweeps = static_cast<int>(p.max_sweeps - sweeps);
-                    phase = kGsSweep;
-                    continue;
-                }
-                const double fs = I.f_star;
-                const bool gap_ok = !isfinite(fs) || (misc->F - fs) / fabs(fs) <= p.tol_gap;
-                if (sweeps > 0 && gap_ok) {
-                    phase = kGsMerit;
-                    continue;
-                }
-            } else if (phase == kGsMerit) {
-                ++checks;
-                const double st = misc->merit / fmax(1.0, misc->xmax);
-                stat_last = static_cast<float>(st);
-                if (!isfinite(misc->merit)) {
-                    status = ASYFLEXA_ENONFINITE;
-                    break;
-                }
-                if (st <= p.tol_stat) {
-                    status = ASYFLEXA_OK;
-                    break;
-                }
-                if (st < 0.9 * stat_ref) {
-                    stat_ref = st;
-                    flat = 0;
-                } else if (st <= kGsFloorBand * p.tol_stat && ++flat >= kGsFloorChecks) {
-                    break;
-                }
-            } else {
-                // sweeps done: exact residual and F next
-                sweeps += k_sweeps;
-                phase = kGsRefresh;
-                if (!producer) {
-#pragma unroll
-                    for (int k = 0; k < UPT; ++k) {
-                        const int64_t u = static_cast<int64_t>(k) * T + tid;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int64_t row = u * 4 + e;
-                            rhi[k][e] = row < m ? -I.b[row] : 0.f;
-                            rlo[k][e] = 0.f;
+            // (decided by thread 0 from the shared values; every thread follows after a barrier)
+            if (tid == 0) {
+                GsMisc& g = *misc;
+                g.reset = 0;
+                bool sweep_next = false;
+                if (*abort_flag) {
+                    g.done = 1;
+                } else if (phase == kGsRefresh) {
+                    const double fs = I.f_star;
+                    const bool gap_ok = !isfinite(fs) || (g.F - fs) / fabs(fs) <= p.tol_gap;
+                    if (g.nonfinite) {
+                        g.status = ASYFLEXA_ENONFINITE;
+                        g.done = 1;
+                    } else if (p.sweeps_only) {
+                        if (g.sweeps >= p.max_sweeps) {
+                            g.done = 1;
+                        } else {
+                            g.k_sweeps = static_cast<int>(p.max_sweeps - g.sweeps);
+                            g.phase = kGsSweep;
                         }
+                    } else {
+                        if (gap_ok && isfinite(fs)) g.exact = 1;
+                        if (g.sweeps > 0 && gap_ok)
+                            g.phase = kGsMerit;
+                        else
+                            sweep_next = true;
+                    }
+                } else if (phase == kGsMerit) {
+                    ++g.checks;
+                    const double st = g.merit / fmax(1.0, g.xmax);
+                    g.stat_last = static_cast<float>(st);
+                    if (!isfinite(g.merit)) {
+                        g.status = ASYFLEXA_ENONFINITE;
+                        g.done = 1;
+                    } else if (st <= p.tol_stat) {
+                        g.status = ASYFLEXA_OK;
+                        g.done = 1;
+                    } else {
+                        const bool better = st < 0.9 * g.stat_ref;
+                        if (better) g.stat_ref = st;
+                        if (!g.exact) {
+                            g.flat_plain = better ? 0 : g.flat_plain + 1;
+                            if (st <= kGsFloorBand * p.tol_stat || g.flat_plain >= 2) g.exact = 1;
+                        } else if (better) {
+                            g.flat = 0;
+                        } else if (st <= kGsFloorBand * p.tol_stat && ++g.flat >= kGsFloorChecks) {
+                            g.done = 1;
+                        }
+                        sweep_next = !g.done;
+                    }
+                } else {
+                    // sweeps done: exact residual and F next
+                    g.sweeps += k_sweeps;
+                    g.phase = kGsRefresh;
+                    g.reset = 1;
+                }
+                if (sweep_next) {
+                    if (g.sweeps >= p.max_sweeps) {
+                        g.done = 1;
+                    } else {
+                        // near the tolerance the next check comes after 2 sweeps
+                        const bool near = phase == kGsMerit && g.stat_last <= 2.0 * p.tol_stat;
+                        long long k = near ? 2 : p.check_every;
+                        if (k > p.max_sweeps - g.sweeps) k = p.max_sweeps - g.sweeps;
+                        g.k_sweeps = static_cast<int>(k);
+                        g.phase = kGsSweep;
                     }
                 }
-                continue;
             }
-            if (sweeps >= p.max_sweeps) break;
-            // near the tolerance the next check comes after 2 sweeps
-            const bool near = phase == kGsMerit && stat_last <= 2.0 * p.tol_stat;
-            int k = near ? 2 : p.check_every;
-            if (k > p.max_sweeps - sweeps) k = static_cast<int>(p.max_sweeps - sweeps);
-            k_sweeps = k;
-            phase = kGsSweep;
+            __syncthreads();
+            if (misc->done) break;
+            if (misc->reset && !producer) reset_r();
         }
         if (tid == 0) {
             GsInst& O = p.inst[ii];
             O.F = misc->F;
-            O.stat = static_cast<double>(stat_last);
+            O.stat = static_cast<double>(misc->stat_last);
             O.xmax = misc->xmax;
-            O.sweeps = sweeps;
+            O.sweeps = misc->sweeps;
             O.nnz = misc->nnz;
-            O.status = *abort_flag ? kDevTimeout : status;
-            O.checks = checks;
+            O.status = *abort_flag ? kDevTimeout : misc->status;
+            O.checks = misc->checks;
+            O.w_used = w;
         }
         __syncthreads();  // the results and misc are read before the next problem rewrites misc
     }

@@ -1,13 +1,15 @@
 // asyflexa_residual_noalloc: the exact residual r = A x - b without a handle and without
 // any device allocation.
 //
-// Some callers cannot allocate device memory when they need this value: code that runs
-// while a CUDA stream is being captured into a graph (cudaMalloc is not permitted there),
-// or a latency-sensitive loop in which cudaMalloc / cudaFree would synchronise the device
-// and stall every other stream.  This entry point runs the same kernels as the residual
-// refresh of a handle (ordered compaction of the nonzeros of x, gather products with
-// compensated accumulation, fixed-order reduction) but takes its scratch from one
-// file-scope device array of fixed size instead of handle-owned allocations.
+// Some callers cannot allocate device memory when they need this value: a plugin inside a
+// host application that gives it a fixed device-memory budget and owns every allocation, or
+// a latency-sensitive loop in which cudaMalloc / cudaFree would synchronise the device and
+// stall every other stream.  This entry point takes its scratch from one file-scope device
+// array of fixed size instead of handle-owned allocations, and computes what the residual
+// refresh of a handle computes by the same steps (ordered compaction of the nonzeros of x,
+// compensated products, fixed-order FP64 reduction) through the register-batched gather
+// kernel (gather_gemv_exact_kernel) instead of the handle's pipelined one, so the two agree up
+// to the grouping of partial sums.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -60,7 +62,8 @@ __global__ void noalloc_reduce_kernel(double* r, const double* partial, int nseg
     }
 }
 
-// Device address of g_noalloc_scratch on the current device, looked up once per device.
+// Device address of g_noalloc_scratch on the current device, looked up once per device index
+// and cached for the life of the process (the device's primary context is assumed throughout).
 int scratch_address(int dev, unsigned char** out) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_scratch_addr[dev]) {

@@ -1,11 +1,13 @@
 """asyflexa_residual_noalloc: the residual without a handle and without device allocation.
 
 Callers that cannot allocate device memory at the point where they need r = A x - b (for
-example inside a CUDA stream capture, or a loop where cudaMalloc would synchronise the
-device) use this entry point.  The test calls it through the C ABI twice in a row (the
-scratch array is shared and keeps the previous call's contents) and compares each result
-with the existing handle entry point asyflexa_residual_refresh + asyflexa_get_residual.
-It lives in its own file, collected last, and needs no state from other tests.
+example a plugin that its host application gives a fixed device-memory budget, or a loop in
+which cudaMalloc would synchronise the device) use this entry point.  The test calls it
+through the C ABI twice in a row (the scratch array is shared and keeps the previous call's
+contents) and compares each result with the existing handle entry point
+asyflexa_residual_refresh + asyflexa_get_residual, for every storage type (BF16 and FP8 with
+their per-column scales).  It lives in its own file, collected last, and needs no state from
+other tests.
 """
 
 import ctypes as C
@@ -20,19 +22,25 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-12   # both sides accumulate exactly; only the grouping of partial sums differs
 
 
-@pytest.mark.parametrize("store", [np.float64, np.float32])
+@pytest.mark.parametrize("store", ["f64", "f32", "bf16", "fp8"])
 def test_noalloc_matches_handle_refresh_twice(store):
     import torch
     from paper_1701_04900_gb300 import Solver, native
     from paper_1701_04900_gb300.build import build_library
+    from tests._gpu_helpers import quantize_columns
     build_library()
     L = native.lib()
-    d = random_lasso(1003, 777, seed=21, lam=0.1, store_dtype=store, zero_cols=2)
-    At = torch.from_numpy(d["At"]).cuda()
+    dt = np.float64 if store == "f64" else np.float32
+    d = random_lasso(1003, 777, seed=21, lam=0.1, store_dtype=dt, zero_cols=2)
     b = torch.from_numpy(d["b"]).cuda()
-    s = Solver(At, b, d["lam"], m=d["m"])
+    if store in ("bf16", "fp8"):
+        At, scale, _ = quantize_columns(d["At"], d["m"], store)
+        s = Solver(At, b, d["lam"], m=d["m"], col_scale=scale)
+    else:
+        At = torch.from_numpy(d["At"]).cuda()
+        s = Solver(At, b, d["lam"], m=d["m"])
     rng = np.random.default_rng(5)
-    tdt = torch.float64 if store == np.float64 else torch.float32
+    store = dt
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
         x = (rng.standard_normal(d["n"]) * (rng.random(d["n"]) < 0.4)).astype(store)
