@@ -406,22 +406,18 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                 // Lane t of warp 0 owns the block's column t: it sums the column's warp partials,
                 // evaluates its best response and writes x_j, so column j (always at position
                 // j mod w of its block) is read and written by one thread.  Its coefficients are
-                // loaded one block ahead.
+                // loaded at the block's start and used after the block's first barrier.
                 float cx = 0.f, cd = 0.f, cdi = 0.f;
-                auto load_coef = [&](int j0, int wb) {
-                    if (warp == 0 && lane < wb) {
-                        const int j = j0 + lane;
-                        const float2 dd = DD[j];
-                        cx = X[j];
-                        cd = dd.x;
-                        cdi = dd.y;
-                    }
-                };
-                load_coef(0, n < w ? n : w);
                 for (int sw = 0; sw < nsw; ++sw) {
                     for (int j0 = 0; j0 < n; j0 += w) {
                         const int wb = n - j0 < w ? n - j0 : w;
                         const int slot = cslot;
+                        if (warp == 0 && lane < wb) {
+                            const float2 dd = DD[j0 + lane];
+                            cx = X[j0 + lane];
+                            cd = dd.x;
+                            cdi = dd.y;
+                        }
                         ok = ok && !*abort_flag && mbar_wait_bounded(&full[slot], cpar, abort_flag, p.err);
                         float2* cp = part + buf * (kGsWMax * NW);
                         // a_j^T r.  Exact arithmetic (the merit pass, and the sweeps once the solve
@@ -463,31 +459,52 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                                 }
                                 if (lane == 0) cp[t * NW + warp] = make_float2(ts, tc);
                             }
+                        } else if (w == 1) {
+                            const uint4* src = reinterpret_cast<const uint4*>(ring + slot * L.slot_bytes);
+                            float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+#pragma unroll
+                            for (int k = 0; k < UPT; ++k) {
+                                float a[4];
+                                ATraits<float>::unpack(load_unit(src, k), a);
+                                acc0 = fmaf(a[0], rhi[k][0], acc0);
+                                acc1 = fmaf(a[1], rhi[k][1], acc1);
+                                acc2 = fmaf(a[2], rhi[k][2], acc2);
+                                acc3 = fmaf(a[3], rhi[k][3], acc3);
+                            }
+                            const float v = warp_sum((acc0 + acc1) + (acc2 + acc3));
+                            if (lane == 0) cp[warp] = make_float2(v, 0.f);
                         } else {
+                            // all kGsWMax columns without branches, so that their load, FMA and
+                            // shuffle chains interleave: a column past the block's end reads the
+                            // block's first column and its result is not used
+                            float acc[kGsWMax];
 #pragma unroll
                             for (int t = 0; t < kGsWMax; ++t) {
-                                if (t < wb) {
-                                    const uint4* src = reinterpret_cast<const uint4*>(
-                                        ring + slot * L.slot_bytes + static_cast<size_t>(t) * lda * 4);
-                                    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+                                const uint4* src = reinterpret_cast<const uint4*>(
+                                    ring + slot * L.slot_bytes + static_cast<size_t>(t < wb ? t : 0) * lda * 4);
+                                float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-                                    for (int k = 0; k < UPT; ++k) {
-                                        float a[4];
-                                        ATraits<float>::unpack(load_unit(src, k), a);
-                                        acc0 = fmaf(a[0], rhi[k][0], acc0);
-                                        acc1 = fmaf(a[1], rhi[k][1], acc1);
-                                        acc2 = fmaf(a[2], rhi[k][2], acc2);
-                                        acc3 = fmaf(a[3], rhi[k][3], acc3);
-                                    }
-                                    const float v = warp_sum((acc0 + acc1) + (acc2 + acc3));
-                                    if (lane == 0) cp[t * NW + warp] = make_float2(v, 0.f);
+                                for (int k = 0; k < UPT; ++k) {
+                                    float a[4];
+                                    ATraits<float>::unpack(load_unit(src, k), a);
+                                    a0 = fmaf(a[0], rhi[k][0], a0);
+                                    a1 = fmaf(a[1], rhi[k][1], a1);
+                                    a0 = fmaf(a[2], rhi[k][2], a0);
+                                    a1 = fmaf(a[3], rhi[k][3], a1);
                                 }
+                                acc[t] = a0 + a1;
+                            }
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                                for (int t = 0; t < kGsWMax; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+                            if (lane == 0) {
+#pragma unroll
+                                for (int t = 0; t < kGsWMax; ++t) cp[t * NW + warp] = make_float2(acc[t], 0.f);
                             }
                         }
                         named_bar_sync(1, T);
                         if (warp == 0) {
-                            const int jn = j0 + w < n ? j0 + w : 0;  // the next block (next sweep: 0)
-                            float nx = cx, nd = cd, ndi = cdi;
                             if (lane < wb) {
                                 // the column's partials in a fixed order: g = gh + gl
                                 const float2* c2p = cp + lane * NW;
@@ -521,22 +538,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                                     const float xn = fmaf(gamma, e, cx);
                                     if (ok) X[j] = xn;
                                     dls[lane] = ok ? xn - cx : 0.f;
-                                    if (jn == j0) nx = xn;  // one block per sweep: its own new x
                                 }
+                            } else if (lane < kGsWMax && !merit) {
+                                dls[lane] = 0.f;  // no column at this position
                             }
-                            // the next block's coefficients (loaded by the lane that will use them)
-                            if (jn != j0) {
-                                const int wbn = n - jn < w ? n - jn : w;
-                                if (lane < wbn) {
-                                    const float2 dd = DD[jn + lane];
-                                    nx = X[jn + lane];
-                                    nd = dd.x;
-                                    ndi = dd.y;
-                                }
-                            }
-                            cx = nx;
-                            cd = nd;
-                            cdi = ndi;
                         }
                         buf ^= 1;
                         if (!merit) {
@@ -560,20 +565,26 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                                     }
                                 }
                             } else {
+                                // dls[t] = 0 for t >= wb (and for columns that did not move); the
+                                // columns past the block's end read the block's first column
+                                float dl[kGsWMax];
+                                bool any = false;
 #pragma unroll
                                 for (int t = 0; t < kGsWMax; ++t) {
-                                    if (t < wb) {
-                                        const float dl = dls[t];
-                                        if (dl != 0.f) {
+                                    dl[t] = dls[t];
+                                    any |= dl[t] != 0.f;
+                                }
+                                if (any) {
+#pragma unroll
+                                    for (int k = 0; k < UPT; ++k) {
+#pragma unroll
+                                        for (int t = 0; t < kGsWMax; ++t) {
                                             const uint4* src = reinterpret_cast<const uint4*>(
-                                                ring + slot * L.slot_bytes + static_cast<size_t>(t) * lda * 4);
+                                                ring + slot * L.slot_bytes + static_cast<size_t>(t < wb ? t : 0) * lda * 4);
+                                            float a[4];
+                                            ATraits<float>::unpack(load_unit(src, k), a);
 #pragma unroll
-                                            for (int k = 0; k < UPT; ++k) {
-                                                float a[4];
-                                                ATraits<float>::unpack(load_unit(src, k), a);
-#pragma unroll
-                                                for (int e = 0; e < 4; ++e) rhi[k][e] = fmaf(a[e], dl, rhi[k][e]);
-                                            }
+                                            for (int e = 0; e < 4; ++e) rhi[k][e] = fmaf(a[e], dl[t], rhi[k][e]);
                                         }
                                     }
                                 }
@@ -604,40 +615,57 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
 
             // ================================================================ after the phase
             if (phase == kGsRefresh && !producer) {
-                // F(x) from the exact residual: FP64 sums in a fixed order
-                double rr = 0.0, ax = 0.0, x2 = 0.0, lx = 0.0, xm = 0.0, nz = 0.0;
+                // F(x) from the exact residual: FP64 sums in a fixed order, one quantity at a
+                // time (few registers live beside the residual)
+                auto warp_put = [&](double v, int q) {
 #pragma unroll
-                for (int k = 0; k < UPT; ++k)
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0) red[warp * 8 + q] = v;
+                };
+                {
+                    double rr = 0.0;
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const double v = static_cast<double>(rhi[k][e]) + static_cast<double>(rlo[k][e]);
-                        rr += v * v;
+                    for (int k = 0; k < UPT; ++k)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const double v = static_cast<double>(rhi[k][e]) + static_cast<double>(rlo[k][e]);
+                            rr += v * v;
+                        }
+                    warp_put(rr, 0);
+                }
+                {
+                    double ax = 0.0, x2 = 0.0;
+                    for (int j = tid; j < n; j += T) {
+                        const double xj = static_cast<double>(X[j]);
+                        ax += fabs(xj);
+                        x2 += xj * xj;
                     }
-                for (int j = tid; j < n; j += T) {
-                    const double xj = static_cast<double>(X[j]);
-                    ax += fabs(xj);
-                    x2 += xj * xj;
-                    if (LIN) lx += static_cast<double>(LIN[j]) * xj;
-                    xm = fmax(xm, fabs(xj));
-                    nz += xj != 0.0 ? 1.0 : 0.0;
+                    warp_put(ax, 1);
+                    warp_put(x2, 2);
                 }
+                {
+                    double lx = 0.0;
+                    if (LIN)
+                        for (int j = tid; j < n; j += T) lx += static_cast<double>(LIN[j]) * static_cast<double>(X[j]);
+                    warp_put(lx, 3);
+                }
+                {
+                    int nz = 0;
+                    float xm = 0.f;
+                    for (int j = tid; j < n; j += T) {
+                        const float xj = X[j];
+                        nz += xj != 0.f ? 1 : 0;
+                        xm = fmaxf(xm, fabsf(xj));
+                    }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    rr += __shfl_xor_sync(0xffffffffu, rr, o);
-                    ax += __shfl_xor_sync(0xffffffffu, ax, o);
-                    x2 += __shfl_xor_sync(0xffffffffu, x2, o);
-                    lx += __shfl_xor_sync(0xffffffffu, lx, o);
-                    nz += __shfl_xor_sync(0xffffffffu, nz, o);
-                    xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
-                }
-                if (lane == 0) {
-                    double* rw = red + warp * 8;
-                    rw[0] = rr;
-                    rw[1] = ax;
-                    rw[2] = x2;
-                    rw[3] = lx;
-                    rw[4] = nz;
-                    rw[5] = xm;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        nz += __shfl_xor_sync(0xffffffffu, nz, o);
+                        xm = fmaxf(xm, __shfl_xor_sync(0xffffffffu, xm, o));
+                    }
+                    if (lane == 0) {
+                        red[warp * 8 + 4] = static_cast<double>(nz);
+                        red[warp * 8 + 5] = static_cast<double>(xm);
+                    }
                 }
                 named_bar_sync(1, T);
                 if (tid == 0) {
