@@ -202,20 +202,21 @@ def planted_f_ref(gen):
     return 0.5 * float(r @ r) + LAM * float(np.abs(xs).sum())
 
 
-def run_cpu_core_study(args):
+def run_cpu_core_study(args, m=20000, n=40000, k=400):
     """Section 4.2's core-count study: time to a relative error of F below 1e-4 on the
-    Nesterov LASSO the paper uses for it (20000 x 40000, lambda = 1, 1 % nonzero), for the
-    multi-core CPU oracle on c = 1, 2, 4, ... host threads (variables partitioned among the
-    threads, lock-free) in both of its forms, next to the GPU's async solve to the same error.
-    The Gram form precomputes A^T A and A^T b (as the paper's experiments do; the precompute is
-    timed apart); the residual form shares r = Ax - b as the GPU does.  The CPU times leave the
-    per-sweep check out; the GPU time is the whole solve, checks included."""
+    Nesterov LASSO the paper uses for it (20000 x 40000, lambda = 1, 1 % nonzero; a smaller
+    instance of the same recipe by default), for the multi-core CPU oracle on c = 1, 2, 4, ...
+    host threads (variables partitioned among the threads, lock-free) in both of its forms,
+    next to the GPU's async solve to the same error.  The Gram form precomputes A^T A and A^T b
+    (as the paper's experiments do; the precompute is timed apart); the residual form shares
+    r = Ax - b as the GPU does.  The CPU times leave the per-sweep check out; the GPU time is the
+    whole solve, checks included."""
     import numpy as np
     import torch
     from paper_1701_04900_gb300 import Solver
     from inputs import nesterov_lasso_torch
     from oracle import cores as oc
-    m, n, k, tol = 20000, 40000, 400, 1e-4
+    tol = 1e-4
     gen = nesterov_lasso_torch(m, n, k, lam=LAM, seed=0, device="cuda")
     sup = gen["support"]
     r = gen["At"][sup, :m].double().T @ gen["x_star"][sup] - gen["b"].double()
@@ -250,6 +251,142 @@ def run_cpu_core_study(args):
             rr["speedup"] = runs[0]["seconds"] / rr["seconds"]
             rr["gpu_speedup_vs_this"] = rr["seconds"] / t
         out[form] = runs
+    return out
+
+
+# ---------------------------------------------------------------------- cpu_baseline leg
+# Besides --impl reference, the one place where bench.py runs the oracle: it times the oracle on
+# a bounded sample of the headline instance, runs the core-count study, and evaluates the system
+# forms' returned iterates with the oracle (on sampled columns where an instance is large).  No
+# value computed here feeds a GPU run.
+
+def _host_residual(At, b64, x, m, chunk=8192):
+    """r = A x - b in FP64 on the host from the nonzero columns of x, in column chunks."""
+    import numpy as np
+    import torch
+    nz = np.nonzero(x)[0]
+    r = -b64.copy()
+    for c0 in range(0, nz.size, chunk):
+        cols = nz[c0:c0 + chunk]
+        Ac = At[torch.as_tensor(cols, device=At.device, dtype=torch.long), :m].double().cpu().numpy()
+        r += Ac.T @ x[cols].astype(np.float64)
+    return r
+
+
+def oracle_check_iterate(At, b, m, x, lam, loss="lasso", c=0.0, lo=None, hi=None, sample=4096, seed=0):
+    """The oracle's view of an iterate x of a large instance: F(x) from the exact FP64 residual of
+    the nonzero columns, and the merit ||xhat(x) - x||_inf / max(1, ||x||_inf) (Section 4.3) on the
+    support (|x_j| > 1e-5 max(1, ||x||_inf)) and `sample` random other columns, evaluated by the
+    oracle on the sub-problem of those columns whose residual is r."""
+    import numpy as np
+    import torch
+    import oracle as O
+    x64 = x.astype(np.float64)
+    r = _host_residual(At, b.double().cpu().numpy(), x, m)
+    xabs = np.abs(x64)
+    if loss == "lasso":
+        F = 0.5 * float(r @ r) + lam * float(xabs.sum())
+    else:
+        F = float(r @ r) - c * float(x64 @ x64) + lam * float(xabs.sum())
+    rng = np.random.default_rng(seed)
+    cols = np.union1d(O.lasso_support(x64), rng.choice(x.size, size=min(sample, x.size), replace=False))
+    Ac = At[torch.as_tensor(cols, device=At.device, dtype=torch.long), :m].double().cpu().numpy().T
+    xs = x64[cols]
+    p = O.Problem(A=Ac, b=Ac @ xs - r, lam=lam, loss=loss, c=c,
+                  lo=None if lo is None else lo.double().cpu().numpy()[cols],
+                  hi=None if hi is None else hi.double().cpu().numpy()[cols])
+    merit = float(np.abs(O.xhat_merit(p, xs, O.surrogate_weights(p))).max()) / max(1.0, float(xabs.max()))
+    return {"F": F, "merit": merit, "merit_columns": int(cols.size)}
+
+
+def cpu_form_checks(ctx):
+    """The oracle on the forms' outputs (each part reported on its own, errors included)."""
+    import numpy as np
+    import oracle as O
+    out = {}
+    fr = ctx.get("form_results", {})
+    mp = fr.get("mixed_precision", {})
+    try:
+        res = {}
+        if "lasso" in mp and ctx.get("gen") is not None:
+            g = ctx["gen"]
+            for name, x in mp["lasso"]["x"].items():
+                q = oracle_check_iterate(g["At"], g["b"], M, x, LAM)
+                q["rel_gap_vs_planted"] = (q["F"] - ctx["f_ref"]) / abs(ctx["f_ref"])
+                res[name] = q
+            for name in ("bf16", "fp8"):
+                if name in res:
+                    res[name]["rel_F_diff_vs_fp32"] = (res[name]["F"] - res["fp32"]["F"]) / abs(res["fp32"]["F"])
+            out["mixed_precision_lasso"] = res
+        if "ncquad" in mp:
+            q = mp["ncquad"]
+            res = {}
+            for name, x in q["x"].items():
+                res[name] = oracle_check_iterate(q["At"], q["b"], q["m"], x, q["lam"], loss="ncquad", c=q["c"],
+                                                 lo=q["lo"], hi=q["hi"])
+            for name in ("bf16", "fp8"):
+                if name in res:
+                    res[name]["rel_F_diff_vs_fp32"] = (res[name]["F"] - res["fp32"]["F"]) / abs(res["fp32"]["F"])
+            out["mixed_precision_ncquad"] = res
+    except Exception as exc:
+        out["mixed_precision_error"] = f"{type(exc).__name__}: {exc}"[:300]
+    try:
+        gr = fr.get("gradient")
+        if gr:
+            AS, xs, AvS, bv = gr["AS"], gr["x_star_S"], gr["AvS"], gr["bv"]
+            v = 2.0 * AvS.T @ (AvS @ xs - bv)          # dL/dx_S of L = ||A_val x - b_val||^2 at x*
+            dlam_o, _, _, S = O.lasso_adjoint_gradient(AS, xs, v)
+            out["gradient"] = {"oracle_dL_dlam_at_planted_optimum": dlam_o, "library_dL_dlam": gr["dL_dlam"],
+                               "rel_diff_vs_oracle": abs(gr["dL_dlam"] - dlam_o) / abs(dlam_o),
+                               "support": int(len(S)), "oracle": "FP64 Cholesky on the planted support"}
+    except Exception as exc:
+        out["gradient_error"] = f"{type(exc).__name__}: {exc}"[:300]
+    try:
+        bt = fr.get("batched_256")
+        if bt:
+            rows = []
+            for (A, b), x, f in zip(bt["probs"], bt["x"], bt["f_ref"]):
+                p = O.Problem(A=A.astype(np.float64), b=b.astype(np.float64), lam=1.0)
+                x64 = x.astype(np.float64)
+                rows.append({"rel_gap": (O.objective(p, x64) - f) / abs(f),
+                             "merit": O.stationarity(O.xhat_merit(p, x64, O.surrogate_weights(p)), x64)})
+            out["batched_first_8_instances"] = {"max_rel_gap": max(r["rel_gap"] for r in rows),
+                                                "max_merit": max(r["merit"] for r in rows)}
+    except Exception as exc:
+        out["batched_error"] = f"{type(exc).__name__}: {exc}"[:300]
+    try:
+        ml = fr.get("multi_lane")
+        if ml:
+            A = ml["A"].astype(np.float64).T
+            merits = []
+            for x, lam in zip(ml["X"], ml["lams"]):
+                p = O.Problem(A=A, b=ml["b"].astype(np.float64), lam=lam)
+                x64 = x.astype(np.float64)
+                merits.append(O.stationarity(O.xhat_merit(p, x64, O.surrogate_weights(p)), x64))
+            out["multi_lane_lanes_0_31_63"] = {"merits": merits, "max_merit": max(merits)}
+    except Exception as exc:
+        out["multi_lane_error"] = f"{type(exc).__name__}: {exc}"[:300]
+    return out
+
+
+def cpu_baseline_leg(args, sample, ctx):
+    """The oracle timed on the host cores on a bounded sample of the headline instance, the
+    core-count study (a 4000 x 8000 instance of the paper's recipe; the paper's 20000 x 40000
+    with --cpu-speedup), and the oracle checks of the forms."""
+    cores = os.cpu_count() or 1
+    At_s, b_s, ncols = sample
+    r = cpu_oracle_sample(At_s, b_s, LAM, args.cpu_seconds, cores)
+    out = {"value": r["block_updates"] / r["seconds"], "unit": "block-updates/s", "cores": cores, "kind": "oracle",
+           "sample": f"FP64 numpy cyclic Gauss-Seidel sweeps (w={W_BLOCK}) over the first {ncols} columns "
+                     f"({ncols // W_BLOCK} blocks) of this {M}x{N} instance for {r['seconds']:.1f} s "
+                     f"({r['sweeps']} sweeps)"}
+    try:
+        out["core_study"] = run_cpu_core_study(args) if args.cpu_speedup else \
+            run_cpu_core_study(args, m=4000, n=8000, k=80)
+    except Exception as exc:  # reported, the headline line still prints
+        out["core_study"] = {"error": f"{type(exc).__name__}: {exc}"[:400]}
+    if ctx:
+        out["form_checks"] = cpu_form_checks(ctx)
     return out
 
 
@@ -379,30 +516,28 @@ def run_ours(args):
               "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,
               "staleness_hist": ctr["staleness_hist"]}
 
+    # support recovery of the returned x: entries above 1e-5 max(1, ||x||_inf) (the fixed step
+    # leaves geometric tails on coordinates that are zero at the optimum) against the planted
+    # support
+    sel = x.abs() > 1e-5 * max(1.0, float(x.abs().max()))
+    planted = torch.zeros(N, dtype=torch.bool, device="cuda")
+    planted[gen["support"]] = True
+    hits = int((sel & planted).sum())
+    result["support_recovery"] = {"nnz": int((x != 0).sum()), "nnz_rel_1e-5": int(sel.sum()),
+                                  "planted": int(planted.sum()), "precision": hits / max(1, int(sel.sum())),
+                                  "recall": hits / max(1, int(planted.sum()))}
     if rank == 0 and not args.no_sync:
         result["sync"] = run_sync(gen, f_ref, args)
     if rank == 0 and not args.no_e2e:
         result["e2e"] = run_e2e(gen, f_ref, args, refresh_every, check_every)
+    cpu_sample = None
     if rank == 0 and not args.no_cpu:
-        cores = os.cpu_count() or 1
         ncols = 3200
-        At_s = At[:ncols].cpu().numpy()
-        b_s = b.cpu().numpy()
-        r = cpu_oracle_sample(At_s, b_s, LAM, args.cpu_seconds, cores)
-        result["cpu_baseline"] = {
-            "value": r["block_updates"] / r["seconds"], "unit": "block-updates/s", "cores": cores, "kind": "oracle",
-            "sample": f"FP64 numpy cyclic Gauss-Seidel sweeps (w={W_BLOCK}) over the first {ncols} columns "
-                      f"({ncols // W_BLOCK} blocks) of this {M}x{N} instance for {r['seconds']:.1f} s "
-                      f"({r['sweeps']} sweeps)"}
-        if args.cpu_speedup:
-            try:
-                result["cpu_baseline"]["core_study"] = run_cpu_core_study(args)
-            except Exception as exc:  # reported, the headline line still prints
-                result["cpu_baseline"]["core_study"] = {"error": f"{type(exc).__name__}: {exc}"[:400]}
+        cpu_sample = (At[:ncols].cpu().numpy(), b.cpu().numpy(), ncols)
     s.close()
+    ctx = {"gen": gen, "f_ref": f_ref}
+    del At, b
     if rank == 0 and not args.no_forms:
-        ctx = {"gen": gen, "f_ref": f_ref}
-        del gen, At, b
         result["forms"] = {}
         for name, fn in (("stepsize", run_form_stepsize), ("mixed_precision", run_form_mixed_precision),
                          ("gradient", run_form_gradient), ("batched", run_form_batched),
@@ -412,7 +547,10 @@ def run_ours(args):
             except Exception as exc:  # a failing form is reported, the headline line still prints
                 result["forms"][name] = {"error": f"{type(exc).__name__}: {exc}"[:400]}
             torch.cuda.empty_cache()
-        ctx.clear()
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline_leg(args, cpu_sample, ctx if not args.no_forms else None)
+    ctx.clear()
+    del gen
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -505,7 +643,7 @@ def run_e2e(gen, f_ref, args, refresh_every, check_every):
             "steps": steps, "seconds_per_step": el / steps}
 
 
-def _time_solves(make_solver, n, repeats=2):
+def _time_solves(make_solver, n, repeats=2, return_x=False):
     """Warm-up solve, then the best of `repeats` timed solves from x = 0 (same work each)."""
     import torch
     s = make_solver()
@@ -521,7 +659,7 @@ def _time_solves(make_solver, n, repeats=2):
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
     s.close()
-    return min(times), st
+    return (min(times), st, x) if return_x else (min(times), st)
 
 
 def run_form_stepsize(args, ctx):
@@ -557,34 +695,41 @@ def run_form_mixed_precision(args, ctx):
     kinds = {"fp32": None, "bf16": "bf16", "fp8": "fp8"}
     elt = {"fp32": 4, "bf16": 2, "fp8": 1}
 
-    def run_all(At, b, lam, m, n, common):
+    def run_all(At, b, lam, m, n, common, keep):
         res = {}
         for name, kind in kinds.items():
             if kind is None:
-                t, st = _time_solves(lambda: Solver(At, b, lam, m=m, **common), n)
+                t, st, x = _time_solves(lambda: Solver(At, b, lam, m=m, **common), n, return_x=True)
             else:
                 Q, sc = quantize(At, m, kind)
-                t, st = _time_solves(lambda: Solver(Q, b, lam, m=m, col_scale=sc, A_master=At, **common), n)
+                t, st, x = _time_solves(lambda: Solver(Q, b, lam, m=m, col_scale=sc, A_master=At, **common), n,
+                                        return_x=True)
                 del Q, sc
             res[name] = {"seconds": t, "sweeps": st["sweeps"], "polish_sweeps": st["polish_sweeps"],
                          "rel_gap": st["rel_gap"], "stat_xhat": st["stat_xhat"], "F": st["F"], "nnz": st["nnz"],
                          "status": st["status"], "A_bytes_per_sweep": n * m * elt[name]}
+            keep[name] = x.cpu().numpy()
         for name in ("bf16", "fp8"):
             res[name]["speedup_vs_fp32"] = res["fp32"]["seconds"] / res[name]["seconds"]
         return res
 
+    keep = ctx.setdefault("form_results", {}).setdefault("mixed_precision", {})
     gen = ctx.get("gen")
     if gen is not None:
         common = dict(block_w=W_BLOCK, mode="async", gamma=GAMMA, max_sweeps=2000, check_every=10,
                       refresh_every=10, tol_stat=1e-6, f_star=ctx["f_ref"])
-        out["lasso"] = dict(workload=f"lasso_nesterov_{M}x{N}", **run_all(gen["At"], gen["b"], LAM, M, N, common))
+        kl = keep.setdefault("lasso", {"x": {}})
+        out["lasso"] = dict(workload=f"lasso_nesterov_{M}x{N}",
+                            **run_all(gen["At"], gen["b"], LAM, M, N, common, kl["x"]))
         del gen
     m, n = 10000, 50000
     g = ncquad_problem_torch(m, n, seed=0, device="cuda")
     common = dict(loss="ncquad", c=g["c"], lo=g["lo"], hi=g["hi"], block_w=W_BLOCK, mode="async", gamma=GAMMA,
                   max_sweeps=4000, check_every=10, refresh_every=10, tol_stat=1e-6)
+    kq = keep.setdefault("ncquad", {"x": {}})
     out["ncquad"] = dict(workload=f"ncquad_{m}x{n}_box1", c=g["c"], lam=g["lam"],
-                         **run_all(g["At"], g["b"], g["lam"], m, n, common))
+                         **run_all(g["At"], g["b"], g["lam"], m, n, common, kq["x"]))
+    kq.update(At=g["At"], b=g["b"], lam=g["lam"], c=g["c"], lo=g["lo"], hi=g["hi"], m=m, n=n)
     return out
 
 
@@ -617,7 +762,7 @@ def run_form_gradient(args, ctx=None):
         loss.backward()
         torch.cuda.synchronize()
         t2 = time.perf_counter()
-        return float(loss), float(lam.grad), t1 - t0, t2 - t1, int((x != 0).sum())
+        return float(loss.detach()), float(lam.grad), t1 - t0, t2 - t1, int((x != 0).sum())
 
     def loss_only(lam_v):
         with torch.no_grad():
@@ -649,24 +794,61 @@ def run_form_gradient(args, ctx=None):
         else:
             step *= 0.5
     t_tune = time.perf_counter() - t0
+    if ctx is not None:
+        sup = gen["support"]
+        ctx.setdefault("form_results", {})["gradient"] = {
+            "AS": At[sup, :m].double().T.cpu().numpy(), "x_star_S": gen["x_star"][sup].cpu().numpy(),
+            "AvS": val["At"][sup, :2000].double().T.cpu().numpy(), "bv": bv.double().cpu().numpy(), "dL_dlam": g0}
     return {"workload": f"lasso_train_{m}x{n}_val_2000", "loss_at_lam1": L0, "dL_dlam": g0, "fd_dL_dlam": fd,
             "rel_diff_vs_fd": abs(g0 - fd) / max(abs(fd), 1e-30), "forward_s": t_fwd, "backward_s": t_bwd,
             "fd_two_solves_s": t_fd, "backward_speedup_vs_fd": t_fd / max(t_bwd, 1e-12), "nnz": nnz,
             "tune_20_steps_s": t_tune, "lambda_final": math.exp(log_best), "loss_at_start": L0, "loss_final": L_best}
 
 
+def _batch_solve_timed(make, xs, f_star=None):
+    """Warm-up solve (the autotuner runs on the first solve of a batch shape), then one timed
+    solve from x = 0 (wall clock around the call; synchronised on both sides), then the
+    library's exact check of every problem (outside the timed region)."""
+    import torch
+    bs = make()
+    bs.solve(xs, f_star=f_star)
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    per, tot = bs.solve(xs, f_star=f_star)
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    exact = bs.check(xs, f_star=f_star)
+    bs.close()
+    return t, per, tot, exact
+
+
+def _status_counts(stats):
+    out = {}
+    for st in stats:
+        k = {0: "ok", 1: "not_converged", -5: "nonfinite"}.get(st["status"], str(st["status"]))
+        out[k] = out.get(k, 0) + 1
+    return out
+
+
 def run_form_batched(args, ctx=None):
-    """System form (2).  (a) 256 LASSO instances of uneven sizes (m ~ U[500, 4000],
-    n ~ U[2000, 20000], 2% planted, FP32) solved together: one sweep launch per round,
-    CUDA-graph rounds, autotuned block width; time until every instance has a 1e-6 relative
-    gap, against sequential single-problem solves of the first 32 instances (scaled to 256).
-    (b) A 64-point geometric lambda path on one 5000 x 20000 instance (lambda_max = ||A^T b||_inf
-    down to the planted lambda = 1): the 64 problems share A and run in one batch (blocks
-    interleaved for L2 reuse, stall criterion), against 64 sequential warm-started solves."""
+    """System form (2).
+    (a) 256 LASSO instances of uneven sizes (m ~ U[500, 4000], n ~ U[2000, 20000], 2% planted,
+        FP32) solved together in ONE persistent launch (the Gauss-Seidel form: one CTA per
+        instance at a time from a largest-first queue, in-kernel stopping tests, launch
+        captured in a CUDA graph, launch shape autotuned and cached), until every instance
+        has a 1e-6 relative gap and ||xhat(x) - x||_inf / max(1, ||x||_inf) <= 1e-6; against
+        measured sequential solves of all 256 instances with the plain async form to the same
+        gap and stationarity.
+    (b) A 64-point geometric lambda path on one 5000 x 20000 instance (lambda_max =
+        ||A^T b||_inf down to the planted lambda = 1), every lane to stationarity <= 1e-6:
+        the Gauss-Seidel form, the async rounds form, the multi-lane tensor-core form, and 64
+        sequential warm-started (and cold) plain solves."""
     import numpy as np
     import torch
     from paper_1701_04900_gb300 import Solver
-    from paper_1701_04900_gb300.batch import BatchSolver
+    from paper_1701_04900_gb300.batch import BatchSolver, MultiLaneSolver
     from inputs import nesterov_lasso_torch
     rng = np.random.default_rng(0)
     probs, f_ref, gens = [], [], []
@@ -680,38 +862,55 @@ def run_form_batched(args, ctx=None):
         probs.append(dict(At=g["At"], b=g["b"], lam=1.0, m=m))
         gens.append((m, n))
     total_bytes = sum(m * n * 4 for m, n in gens)
-    bs = BatchSolver(probs, block_w=0, refresh_every=10, max_sweeps=3000)
     xs = [torch.zeros(p["At"].shape[0], dtype=torch.float32, device="cuda") for p in probs]
-    bs.solve(xs, f_star=f_ref)                       # warm-up (includes the autotuner)
-    for x in xs:
-        x.zero_()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    per, tot = bs.solve(xs, f_star=f_ref)
-    torch.cuda.synchronize()
-    t_batch = time.perf_counter() - t0
-    bs.close()
-    seq_n = 32
-    t_seq = 0.0
-    for i in range(seq_n):
-        p = probs[i]
-        # the same cap on updates in flight as the batched form: max(1, m / (4 w)) CTAs
-        wb = tot["block_w"]
-        s = Solver(p["At"], p["b"], 1.0, m=p["m"], block_w=wb, mode="async", refresh_every=10,
-                   check_every=10, max_sweeps=3000, f_star=f_ref[i], num_ctas=max(1, min(152, p["m"] // (4 * wb))))
+    t_batch, per, tot, exact = _batch_solve_timed(
+        lambda: BatchSolver(probs, max_sweeps=3000, check_every=10, tol_stat=1e-6), xs, f_ref)
+    swept = sum(st["sweeps"] * m * n * 4 for st, (m, n) in zip(per, gens))
+    # sequential: the plain asynchronous form, one instance after another, with at most
+    # about m/4 columns in flight (max(1, m / (4 w)) CTAs of w = 32 columns)
+    t_seq, seq_stats, seq_times = 0.0, [], []
+    for i, p in enumerate(probs):
+        s = Solver(p["At"], p["b"], 1.0, m=p["m"], block_w=W_BLOCK, mode="async", refresh_every=10,
+                   check_every=10, max_sweeps=3000, f_star=f_ref[i], tol_stat=1e-6,
+                   num_ctas=max(1, min(152, p["m"] // (4 * W_BLOCK))))
         x = torch.zeros(p["At"].shape[0], dtype=torch.float32, device="cuda")
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        s.solve(x)
+        seq_stats.append(s.solve(x))
         torch.cuda.synchronize()
-        t_seq += time.perf_counter() - t1
+        seq_times.append(time.perf_counter() - t1)
+        t_seq += seq_times[-1]
         s.close()
-    batched = {"instances": 256, "A_bytes": total_bytes, "seconds_to_all_1e-6": t_batch, "status": tot["status"],
-               "sweeps": tot["sweeps"], "block_w_autotuned": tot["block_w"],
-               "block_updates_per_s": tot["block_updates"] / t_batch,
-               "max_rel_gap": max(s["rel_gap"] for s in per), "max_stat_xhat": max(s["stat_xhat"] for s in per),
-               "sequential_seconds_32": t_seq, "sequential_seconds_est_256": t_seq * 256 / seq_n,
-               "speedup_vs_sequential": t_seq * 256 / seq_n / t_batch}
+    # the Gauss-Seidel form's per-problem CTA times: their sum over the SMs bounds what a perfect
+    # packing would take; the longest is the problem that holds the batch
+    cta = [st["seconds"] for st in per]
+    budget_bound = [i for i, st in enumerate(per) if st["status"] == 1]
+    batched = {"instances": 256, "A_bytes": total_bytes, "form": "gs" if tot["batch_form"] == 4 else "async",
+               "ctas_per_sm": tot["ctas_per_sm"], "consumer_warps": tot["kernel_variant"],
+               "seconds_to_all_converged": t_batch, "status": tot["status"], "per_instance_status": _status_counts(per),
+               "max_sweeps": tot["sweeps"], "mean_sweeps": sum(st["sweeps"] for st in per) / len(per),
+               "block_w": tot["block_w"], "block_updates_per_s": tot["block_updates"] / t_batch,
+               "sweep_A_bytes_per_s": swept / t_batch,
+               "problems_in_later_launches": tot["handed_over"],
+               "cta_seconds_sum": sum(cta), "cta_seconds_max": max(cta),
+               "cta_seconds_sum_over_sms": sum(cta) / torch.cuda.get_device_properties(0).multi_processor_count,
+               "not_converged_instances": [{"index": i, "m": gens[i][0], "n": gens[i][1], "sweeps": per[i]["sweeps"],
+                                            "rel_gap": per[i]["rel_gap"], "cta_seconds": per[i]["seconds"],
+                                            "sequential_seconds": seq_times[i],
+                                            "sequential_status": seq_stats[i]["status"]} for i in budget_bound],
+               "max_rel_gap": max(st["rel_gap"] for st in per),
+               "max_stat_xhat": max(st["stat_xhat"] for st in per),
+               "max_stat_xhat_exact_check": max(st["stat_xhat"] for st in exact),
+               "max_rel_gap_exact_check": max(st["rel_gap"] for st in exact),
+               "sequential_seconds_all_256": t_seq, "sequential_status": _status_counts(seq_stats),
+               "sequential_max_stat_xhat": max(st["stat_xhat"] for st in seq_stats),
+               "sequential_block_w": W_BLOCK,
+               "speedup_vs_sequential": t_seq / t_batch}
+    if ctx is not None:
+        ctx.setdefault("form_results", {})["batched_256"] = {
+            "x": [x.cpu().numpy() for x in xs[:8]], "probs": [(p["At"][:, :p["m"]].cpu().numpy().T,
+                                                               p["b"].cpu().numpy()) for p in probs[:8]],
+            "f_ref": f_ref[:8]}
     del probs, xs, gens
     torch.cuda.empty_cache()
 
@@ -720,30 +919,32 @@ def run_form_batched(args, ctx=None):
     At, b = g["At"], g["b"]
     lam_max = float((At[:, :m].double() @ b.double()).abs().max())
     lams = [lam_max * (1.0 / lam_max) ** (k / 63) for k in range(64)]
+    sup = g["support"]
+    r = At[sup, :m].double().T @ g["x_star"][sup] - b.double()
+    f1 = 0.5 * float(r @ r) + float(g["x_star"].abs().sum())
     base = dict(At=At, b=b, m=m)
-    bs = BatchSolver([dict(base, lam=l) for l in lams], block_w=32, refresh_every=10, max_sweeps=3000,
-                     switch_tol=1e-9, shared_a=True)
-    xs = [torch.zeros(n, dtype=torch.float32, device="cuda") for _ in lams]
-    bs.solve(xs)
-    for x in xs:
-        x.zero_()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    per, tot = bs.solve(xs)
-    torch.cuda.synchronize()
-    t_path = time.perf_counter() - t0
-    bs.close()
-    # sequential warm-started path (same stopping rule: stall of F between checks)
+    path = {"lambdas": 64, "lambda_max": lam_max, "tol_stat": 1e-6}
+    for name, kw in (("gs", dict(form="gs", shared_a=True, check_every=10)),
+                     ("async_rounds", dict(form="async", shared_a=True, block_w=32, refresh_every=10,
+                                           switch_tol=1e-9))):
+        xs = [torch.zeros(n, dtype=torch.float32, device="cuda") for _ in lams]
+        t, per, tot, exact = _batch_solve_timed(
+            lambda: BatchSolver([dict(base, lam=l) for l in lams], max_sweeps=3000, tol_stat=1e-6, **kw), xs)
+        path[name] = {"seconds": t, "status": tot["status"], "per_lane_status": _status_counts(per),
+                      "max_sweeps": tot["sweeps"], "max_stat_xhat_exact_check": max(q["stat_xhat"] for q in exact),
+                      "last_lane_rel_gap_vs_planted": (exact[-1]["F"] - f1) / f1}
+        del xs
+    # sequential warm-started path (each solve to the same stationarity)
     x = torch.zeros(n, dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    seq_sweeps = 0
-    seq_last = None
+    seq_sweeps, seq_stat = 0, 0.0
     for l in lams:
         s = Solver(At, b, l, m=m, block_w=32, mode="async", refresh_every=10, check_every=10, max_sweeps=3000,
                    tol_stat=1e-6)
-        seq_last = s.solve(x)
-        seq_sweeps += seq_last["sweeps"]
+        st = s.solve(x)
+        seq_sweeps += st["sweeps"]
+        seq_stat = max(seq_stat, st["stat_xhat"])
         s.close()
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
@@ -759,7 +960,6 @@ def run_form_batched(args, ctx=None):
     torch.cuda.synchronize()
     t_cold = time.perf_counter() - t0
     # the multi-lane form: every block update for all 64 lanes at once on the tensor cores
-    from paper_1701_04900_gb300.batch import MultiLaneSolver
     Bm = b.reshape(1, -1).expand(64, -1).contiguous()
     ml = MultiLaneSolver(At, Bm, lams, m, refresh_every=10, check_every=10, max_sweeps=3000, tol_stat=1e-6)
     Xm = torch.zeros((64, n), dtype=torch.float32, device="cuda")
@@ -771,22 +971,18 @@ def run_form_batched(args, ctx=None):
     torch.cuda.synchronize()
     t_multi = time.perf_counter() - t0
     ml.close()
-    multi = {"seconds": t_multi, "sweeps": mtot["sweeps"], "status": mtot["status"],
-             "max_stat_xhat": max(q["stat_xhat"] for q in mper),
-             "last_lane_rel_gap_vs_planted": None, "speedup_vs_sequential_warm": t_seq / t_multi,
-             "speedup_vs_batched": t_path / t_multi}
-    path = {"lambdas": 64, "lambda_max": lam_max, "seconds_batched": t_path, "status": tot["status"],
-            "sweeps_batched": tot["sweeps"], "seconds_sequential_warm": t_seq, "sweeps_sequential": seq_sweeps,
-            "speedup_vs_sequential": t_seq / t_path, "seconds_sequential_cold": t_cold,
-            "sweeps_sequential_cold": cold_sweeps, "speedup_vs_sequential_cold": t_cold / t_path,
-            "last_lane_stat_xhat": per[-1]["stat_xhat"],
-            "last_lane_rel_gap_vs_planted": None, "sequential_last_stat_xhat": seq_last["stat_xhat"]}
-    sup = g["support"]
-    r = At[sup, :m].double().T @ g["x_star"][sup] - b.double()
-    f1 = 0.5 * float(r @ r) + float(g["x_star"].abs().sum())
-    path["last_lane_rel_gap_vs_planted"] = (per[-1]["F"] - f1) / f1
-    multi["last_lane_rel_gap_vs_planted"] = (mper[-1]["F"] - f1) / f1
-    path["multi_lane"] = multi
+    path["multi_lane"] = {"seconds": t_multi, "sweeps": mtot["sweeps"], "status": mtot["status"],
+                          "max_stat_xhat": max(q["stat_xhat"] for q in mper),
+                          "last_lane_rel_gap_vs_planted": (mper[-1]["F"] - f1) / f1}
+    path["sequential_warm"] = {"seconds": t_seq, "sweeps": seq_sweeps, "max_stat_xhat": seq_stat}
+    path["sequential_cold"] = {"seconds": t_cold, "sweeps": cold_sweeps}
+    for name in ("gs", "async_rounds", "multi_lane"):
+        path[name]["speedup_vs_sequential_warm"] = t_seq / path[name]["seconds"]
+        path[name]["speedup_vs_sequential_cold"] = t_cold / path[name]["seconds"]
+    if ctx is not None:
+        ctx.setdefault("form_results", {})["multi_lane"] = {
+            "X": Xm[[0, 31, 63]].cpu().numpy(), "lams": [lams[0], lams[31], lams[63]],
+            "A": At[:, :m].cpu().numpy(), "b": b.cpu().numpy()}
     return {"batched": batched, "lambda_path": path}
 
 
@@ -918,7 +1114,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--cpu-speedup", action="store_true",
-                    help="add the core-count study of the CPU oracle (a few minutes of host time)")
+                    help="run the core-count study on the paper's 20000 x 40000 instance (a few minutes of host "
+                         "time) instead of the default 4000 x 8000 one")
     ap.add_argument("--cpu-speedup-only", action="store_true",
                     help="run only the core-count study and print it as one JSON line")
     args = ap.parse_args()

@@ -190,6 +190,10 @@ typedef struct {
     double tau_extra;           /* solve with tau_adapt: the proximal weight added at the end */
     int32_t batch_form;         /* batched solve: ASYFLEXA_BATCH_FORM_ASYNC or ASYFLEXA_BATCH_FORM_GS */
     int32_t ctas_per_sm;        /* batched solve, Gauss-Seidel form: CTAs resident per SM (autotuned) */
+    int32_t handed_over;        /* batched solve, Gauss-Seidel form: problems that ran in more than
+                                   one launch (total), or the further launches it ran in (per
+                                   problem) */
+    int32_t reserved1;
 } asyflexa_stats;
 
 /* Library version (ASYFLEXA_ABI_VERSION).  Never fails. */
@@ -386,14 +390,23 @@ int asyflexa_adjoint(const void* A, int64_t lda, int32_t a_dtype, int64_t m, int
  *     refreshes, objectives and a device-side convergence test, the round replayed as a
  *     captured CUDA graph.  FP32 problems with m <= 24576.
  *
+ * A problem the Gauss-Seidel form has not finished after 300 sweeps leaves the launch and
+ * continues, from its current iterate, in a further Gauss-Seidel launch over the problems left
+ * (its own launch shape, tuned on them for the longest per-problem time), which hands its own
+ * unfinished problems on after 600 sweeps, and so on with the handoff doubling: the first
+ * launch ends with the bulk of the batch, and the last few problems run under a shape of
+ * their own.
+ *
  * The form is chosen at create (flags) or automatically: the Gauss-Seidel form when every
  * problem fits it and there are at least as many problems as SMs, else the async rounds.  An
- * autotuner then picks the form's launch shape at the first solve by timing one real sweep of
+ * autotuner then picks the form's launch shape at the first solve by timing one sweep of
  * every problem per candidate -- Gauss-Seidel form: 7 or 15 consumer warps per CTA (2 or 1
- * CTAs per SM) with the ring depth that fits, and the block width 1, 2 or 4; async rounds:
- * the block width 16, 32 or 64 --
- * and caches the choice per batch shape (problem count, total size, largest m, flags) for
- * the life of the process. */
+ * CTAs per SM), the block width and ring slot -- 1, 2 or 4 columns with 16 KB slots, 4 or 8
+ * with 32 KB slots (a slot holds up to 8 columns; a problem whose columns do not fit w to a
+ * slot takes as many as fit) -- and the ring depth that fits; the tuning sweeps are undone (the iterates are saved and restored), so
+ * they count neither as sweeps nor against max_sweeps; async rounds: the block width 16, 32
+ * or 64 (real sweeps, counted) -- and caches the choice per batch shape (problem count, total
+ * size, largest m, flags) for the life of the process. */
 typedef struct asyflexa_batch_s* asyflexa_batch_t;
 
 /* flags for asyflexa_batch_create */
@@ -409,8 +422,8 @@ typedef struct asyflexa_batch_s* asyflexa_batch_t;
  * SMs; in the Gauss-Seidel form the most CTAs that run problems at once), check_every
  * (Gauss-Seidel form: sweeps between stopping tests), refresh_every (async rounds: sweeps per
  * round), switch_tol, block_w (async rounds: 16 .. 128, 0 lets the autotuner pick 16, 32 or
- * 64; Gauss-Seidel form: 1 .. 4 fixes the block width, any other value lets the autotuner pick
- * 1, 2 or 4).  All problems and
+ * 64; Gauss-Seidel form: 1 .. 8 fixes the block width, any other value lets the autotuner pick
+ * 1, 2, 4 or 8).  All problems and
  * their device buffers must outlive the batch.  Errors: asyflexa_last_error(NULL). */
 int asyflexa_batch_create(asyflexa_batch_t* hb, const asyflexa_problem* probs, int32_t count,
                           const asyflexa_opts* opts, int32_t flags, void* cuda_stream);
@@ -425,9 +438,11 @@ int asyflexa_batch_create(asyflexa_batch_t* hb, const asyflexa_problem* probs, i
  * per (count entries, may be NULL): each problem's F, rel_gap, stat_xhat, nnz, sweeps,
  * block_updates and status (ENOTCONV at max_sweeps, ENONFINITE if F became non-finite) as the
  * stopping test saw them, and block_w (Gauss-Seidel form: the tuned width, or as many columns
- * as one ring slot holds if fewer); for the exact check of asyflexa_check use
- * asyflexa_batch_check.
- * total: sweeps (the largest number of sweeps of any problem, tuning sweeps included),
+ * as one ring slot holds if fewer); Gauss-Seidel form also: seconds (the time its CTA worked
+ * on it, global timer), kernel_variant and ctas_per_sm (of the launch that finished it) and
+ * handed_over; for the exact check of asyflexa_check use asyflexa_batch_check.
+ * total: sweeps (the largest number of sweeps of any problem; async rounds: tuning sweeps
+ * included),
  * block_updates (all problems), seconds (CUDA events around the solve), block_w, batch_form,
  * ctas_per_sm, kernel_variant (Gauss-Seidel form: consumer warps per CTA), status (OK if all
  * done). */

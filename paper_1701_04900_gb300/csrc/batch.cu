@@ -85,6 +85,22 @@ __global__ void batch_converge_kernel(ConvState* cs, BatchInst* inst, int count,
 constexpr int kCandidates[] = {16, 32, 64};
 
 // (d_j, 1/d_j) in FP32 for the Gauss-Seidel form ((0, 0) where d_j <= 0).
+// Saves (to_save = 1) or restores the iterates of the problems order[0 .. cnt) to / from save,
+// problem k at the offset of its (d_j, 1/d_j) table: the autotuner's sweeps leave x as it was.
+__global__ void gs_copy_x_kernel(const asyflexa::GsInst* inst, const int* order, int cnt, const float2* dd_base,
+                                 float* save, int to_save) {
+    for (int q = blockIdx.x; q < cnt; q += gridDim.x) {
+        const asyflexa::GsInst& g = inst[order[q]];
+        float* sv = save + (g.dd - dd_base);
+        for (int64_t j = threadIdx.x; j < g.n; j += blockDim.x) {
+            if (to_save)
+                sv[j] = g.x[j];
+            else
+                g.x[j] = sv[j];
+        }
+    }
+}
+
 __global__ void gs_coef_kernel(const double* dw, int64_t n, float2* dd) {
     for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
          j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -96,11 +112,12 @@ __global__ void gs_coef_kernel(const double* dw, int64_t n, float2* dd) {
 // Launch shape of the Gauss-Seidel form.
 struct GsChoice {
     int nw = 0, upt = 0, stages = 0, ctas_per_sm = 0, grid = 0, w = 1;
-    int64_t slot_bytes = 0;
+    int64_t slot_cap = 0, slot_bytes = 0;
     size_t smem = 0;
     const void* kernel = nullptr;
     bool operator==(const GsChoice& o) const {
-        return nw == o.nw && upt == o.upt && stages == o.stages && grid == o.grid && w == o.w;
+        return nw == o.nw && upt == o.upt && stages == o.stages && grid == o.grid && w == o.w &&
+               slot_bytes == o.slot_bytes;
     }
 };
 
@@ -143,7 +160,11 @@ constexpr int64_t kGsMaxRows = 8192;   // the Gauss-Seidel form's column limit
 
 // Autotuned launch shapes, per batch shape, for the life of the process.
 std::mutex g_tune_mu;
-std::map<std::string, GsChoice> g_gs_tuned;
+struct GsTuned {
+    GsChoice shape;
+    std::vector<int> wpick;  // block width of each problem tuned (in the order of the members)
+};
+std::map<std::string, GsTuned> g_gs_tuned;
 std::map<std::string, int> g_w_tuned;
 
 }  // namespace
@@ -185,11 +206,15 @@ struct asyflexa_batch_s {
     // Gauss-Seidel form
     int form = 0;                       // ASYFLEXA_BATCH_FORM_ASYNC or ASYFLEXA_BATCH_FORM_GS
     int64_t max_units = 0;              // 16-byte units of the longest column
-    int64_t slot_bytes = 0;             // ring slot: the longest column, and up to 4 short columns (16 KB)
+    int64_t max_colbytes = 0;           // bytes of the longest column (its 16-byte units)
+    int64_t max_multi = 0;              // bytes of kGsWMax columns of the problem with the largest lda
     float2* d_dd = nullptr;             // (d_j, 1/d_j) in FP32 of every problem, concatenated
+    float* d_xsave = nullptr;           // the iterates, saved across the autotuner's sweeps
     std::vector<asyflexa::GsInst> h_gs;
     asyflexa::GsInst* d_gs = nullptr;
-    int* d_order = nullptr;
+    int* d_order = nullptr;             // problems, largest m * n first
+    int* d_order2 = nullptr;            // the problems of the second Gauss-Seidel launch
+    std::vector<int> h_order;
     int* d_queue = nullptr;
     GsChoice gs{};                      // launch shape (nw == 0: not chosen yet)
     cudaGraph_t gs_graph = nullptr;
@@ -347,16 +372,27 @@ int enqueue_round(asyflexa_batch_s& B, void* const* xs) {
 
 // ------------------------------------------------------------------ Gauss-Seidel form
 
-// The launch shape for nw consumer warps: units per thread for the longest column, the ring
-// depth that fits the shared memory of the CTAs an SM holds, and the grid.
-int gs_shape(asyflexa_batch_s& B, int nw, GsChoice* out) {
+// A problem the Gauss-Seidel launch has not finished after this many sweeps leaves it and is
+// finished, from its current iterate, by a second Gauss-Seidel launch over such problems only:
+// they then run side by side, under a launch shape tuned for them.
+constexpr int kGsHandoffSweeps = 300;
+
+// The launch shape for nw consumer warps and ring slots of at least the longest column, with room
+// for up to kGsWMax columns within slot_cap bytes: units per thread for the longest column, the
+// ring depth that fits the shared memory of the CTAs an SM holds, and the grid.
+int64_t gs_slot(const asyflexa_batch_s& B, int64_t slot_cap) {
+    const int64_t s = std::max(B.max_colbytes, std::min(B.max_multi, slot_cap));
+    return (s + 127) / 128 * 128;
+}
+
+int gs_shape(asyflexa_batch_s& B, int nw, int64_t slot_cap, GsChoice* out) {
     GsChoice c;
     c.nw = nw;
     c.upt = gs_upt_for(nw, B.max_units);
     c.kernel = c.upt ? gs_kernel(nw, c.upt) : nullptr;
     if (!c.kernel) return ASYFLEXA_EUNSUPPORTED;
     const int want_per_sm = nw < 8 ? 2 : 1;
-    const size_t slot_bytes = static_cast<size_t>((B.slot_bytes + 127) / 128 * 128);
+    const size_t slot_bytes = static_cast<size_t>(gs_slot(B, slot_cap));
     const asyflexa::GsLayout L0 = asyflexa::make_gs_layout(nw, slot_bytes, 0);
     const size_t budget = std::min<size_t>(B.smem_optin, static_cast<size_t>(B.smem_per_sm) / want_per_sm - 1024);
     if (L0.total + 2 * (L0.slot_bytes + 16) > budget) return ASYFLEXA_EUNSUPPORTED;
@@ -364,9 +400,11 @@ int gs_shape(asyflexa_batch_s& B, int nw, GsChoice* out) {
     stages = std::max(2, std::min(16, stages));
     while (stages > 2 && asyflexa::make_gs_layout(nw, slot_bytes, stages).total > budget) --stages;
     c.stages = stages;
+    c.slot_cap = slot_cap;
     c.slot_bytes = static_cast<int64_t>(slot_bytes);
     c.smem = asyflexa::make_gs_layout(nw, slot_bytes, stages).total;
-    BCK(cudaFuncSetAttribute(c.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(c.smem)),
+    // the opt-in maximum: launch shapes of one kernel differ in their shared memory
+    BCK(cudaFuncSetAttribute(c.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(B.smem_optin)),
         "GS kernel shared-memory attribute");
     int per_sm = 0;
     BCK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c.kernel, (nw + 1) * 32, c.smem), "GS occupancy");
@@ -379,12 +417,14 @@ int gs_shape(asyflexa_batch_s& B, int nw, GsChoice* out) {
     return ASYFLEXA_OK;
 }
 
-// One launch of the Gauss-Seidel kernel over the whole batch (the queue reset first).
-int gs_enqueue(asyflexa_batch_s& B, const GsChoice& c, int sweeps_only, int max_sweeps) {
+// One launch of the Gauss-Seidel kernel over the problems order[0 .. cnt) (device array; the
+// queue is reset first).
+int gs_enqueue(asyflexa_batch_s& B, const GsChoice& c, int sweeps_only, int max_sweeps, int handoff,
+               const int* order, int cnt) {
     asyflexa::GsParams p{};
     p.inst = B.d_gs;
-    p.order = B.d_order;
-    p.count = B.count;
+    p.order = order;
+    p.count = cnt;
     p.queue = B.d_queue;
     p.gamma = B.opts.gamma;
     p.tol_gap = B.opts.tol_gap;
@@ -395,79 +435,124 @@ int gs_enqueue(asyflexa_batch_s& B, const GsChoice& c, int sweeps_only, int max_
     p.w = c.w;
     p.slot_bytes = c.slot_bytes;
     p.sweeps_only = sweeps_only;
+    p.handoff_sweeps = handoff;
     p.keep_a_in_l2 = (B.flags & ASYFLEXA_BATCH_SHARED_A) ? 1 : 0;
     p.err = B.err;
     BCK(cudaMemsetAsync(B.d_queue, 0, sizeof(int), B.stream), "reset queue");
     void* args[] = {&p};
-    const cudaError_t e = cudaLaunchKernel(c.kernel, dim3(c.grid), dim3((c.nw + 1) * 32), args, c.smem, B.stream);
+    const int grid = std::max(1, std::min(c.grid, cnt));
+    const cudaError_t e = cudaLaunchKernel(c.kernel, dim3(grid), dim3((c.nw + 1) * 32), args, c.smem, B.stream);
     ++B.launches;
     BCK(e, "GS batch launch");
     return ASYFLEXA_OK;
 }
 
 // Block width of the Gauss-Seidel form: opts.block_w in 1 .. kGsWMax fixes it, any other value
-// lets the autotuner pick it from {1, 2, 4}.
+// lets the autotuner pick it from {1, 2, 4, 8}.  Ring slots hold up to kGsWMax columns within
+// 16 KB, or (wider blocks of the longer columns, fewer stages) within 32 KB.
 bool gs_fixed_w(const asyflexa_batch_s& B) { return B.opts.block_w >= 1 && B.opts.block_w <= asyflexa::kGsWMax; }
 
-// The launch shape of the Gauss-Seidel form: cached for this batch shape, else the fastest of
-// 7 or 15 consumer warps per CTA and block widths 1, 2, 4 over one real sweep of every problem
-// per candidate (tuning sweeps are added to *tuned_sweeps).
-int gs_choose(asyflexa_batch_s& B, long long* tuned_sweeps) {
-    if (B.gs.nw) return ASYFLEXA_OK;
+// The launch shape of the Gauss-Seidel form for the problems order[0 .. cnt) (members: their
+// indices), and each member's block width (B.h_gs[k].wpick; the caller uploads the table):
+// cached under `key`, else tuned.  Launch shapes: 7 or 15 consumer warps per CTA with 16 KB ring
+// slots (widths 1, 2, 4) or 32 KB slots (widths 4, 8); opts.block_w in 1 .. kGsWMax fixes the
+// width.  Every (shape, width) pair is timed over one sweep of the members, from their iterates,
+// which are restored after each; every CTA times its problem.  Each member takes its fastest
+// width under a shape, and the shape chosen minimises the summed times of the members (use_max
+// = false: the GPU time the sweeps take, for a whole batch) or the largest one (use_max = true:
+// for a few problems left over, which run side by side).  The device table must hold wpick = 0
+// for the members.
+int gs_choose(asyflexa_batch_s& B, const int* order, int cnt, const std::vector<int>& members, const std::string& key,
+              bool use_max, GsChoice* out) {
+    const size_t nm = members.size();
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto itc = g_gs_tuned.find(B.shape_key);
-        if (itc != g_gs_tuned.end()) {
-            const int rc = gs_shape(B, itc->second.nw, &B.gs);
+        auto itc = g_gs_tuned.find(key);
+        if (itc != g_gs_tuned.end() && itc->second.wpick.size() == nm) {
+            const int rc = gs_shape(B, itc->second.shape.nw, itc->second.shape.slot_cap, out);
             if (rc == ASYFLEXA_OK) {
-                B.gs.w = itc->second.w;
+                out->w = itc->second.shape.w;
+                for (size_t i = 0; i < nm; ++i) B.h_gs[members[i]].wpick = itc->second.wpick[i];
                 return ASYFLEXA_OK;
             }
         }
     }
-    std::vector<GsChoice> cands;
-    for (int nw : {7, 15}) {
+    struct Shape {
         GsChoice c;
-        if (gs_shape(B, nw, &c) != ASYFLEXA_OK) continue;
-        if (gs_fixed_w(B)) {
-            c.w = B.opts.block_w;
-            cands.push_back(c);
-            continue;
+        std::vector<int> widths;
+    };
+    std::vector<Shape> shapes;
+    size_t ncand = 0;
+    for (int nw : {7, 15})
+        for (int64_t cap : {int64_t{16384}, int64_t{32768}}) {
+            Shape sh;
+            if (cap > 16384 && gs_slot(B, cap) == gs_slot(B, 16384)) continue;  // the same slots
+            if (gs_shape(B, nw, cap, &sh.c) != ASYFLEXA_OK) continue;
+            if (gs_fixed_w(B))
+                sh.widths = {B.opts.block_w};
+            else if (cap > 16384)
+                sh.widths = {4, 8};
+            else
+                sh.widths = {1, 2, 4};
+            ncand += sh.widths.size();
+            shapes.push_back(sh);
         }
-        for (int w : {1, 2, 4}) {
-            c.w = w;
-            cands.push_back(c);
-        }
-    }
-    if (cands.empty()) return bfail("batched problems: no Gauss-Seidel launch shape fits", ASYFLEXA_EUNSUPPORTED);
-    if (cands.size() == 1) {
-        B.gs = cands[0];
-    } else {
-        cudaEvent_t a0, a1;
-        BCK(cudaEventCreate(&a0), "event");
-        BCK(cudaEventCreate(&a1), "event");
-        float best = 0.f;
-        for (const GsChoice& c : cands) {
-            BCK(cudaEventRecord(a0, B.stream), "event record");
-            int rc = gs_enqueue(B, c, 1, 1);
-            if (rc) return rc;
-            BCK(cudaEventRecord(a1, B.stream), "event record");
-            BCK(cudaEventSynchronize(a1), "event sync");
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, a0, a1);
-            // a sweep of the whole batch mostly times its longest columns, where the width
-            // changes little: within 3% the wider block wins (it pays on short columns)
-            if (best == 0.f || ms < 0.97f * best || (ms < 1.03f * best && c.w > B.gs.w)) {
-                if (best == 0.f || ms < best) best = ms;
-                B.gs = c;
+    if (shapes.empty()) return bfail("batched problems: no Gauss-Seidel launch shape fits", ASYFLEXA_EUNSUPPORTED);
+    std::vector<int> pick(nm, shapes[0].widths[0]);
+    *out = shapes[0].c;
+    out->w = shapes[0].widths[0];
+    if (ncand > 1) {
+        double best = 0.0;
+        std::vector<asyflexa::GsInst> tmp(B.count);
+        const int cgrid = std::max(1, std::min(cnt, 4 * B.sm_count));
+        gs_copy_x_kernel<<<cgrid, 256, 0, B.stream>>>(B.d_gs, order, cnt, B.d_dd, B.d_xsave, 1);
+        ++B.launches;
+        BCK(cudaGetLastError(), "save iterates");
+        for (Shape& sh : shapes) {
+            std::vector<double> fastest(nm, 0.0);
+            std::vector<int> wbest(nm, sh.widths[0]);
+            for (int w : sh.widths) {
+                GsChoice c = sh.c;
+                c.w = w;
+                int rc = gs_enqueue(B, c, 1, 1, 0, order, cnt);
+                if (rc) return rc;
+                gs_copy_x_kernel<<<cgrid, 256, 0, B.stream>>>(B.d_gs, order, cnt, B.d_dd, B.d_xsave, 0);
+                ++B.launches;
+                BCK(cudaGetLastError(), "restore iterates");
+                BCK(cudaMemcpyAsync(tmp.data(), B.d_gs, B.count * sizeof(asyflexa::GsInst), cudaMemcpyDeviceToHost,
+                                    B.stream),
+                    "read problem table");
+                BCK(cudaStreamSynchronize(B.stream), "synchronize");
+                for (size_t i = 0; i < nm; ++i) {
+                    const double t = static_cast<double>(tmp[members[i]].ns);
+                    if (fastest[i] == 0.0 || t < fastest[i]) {
+                        fastest[i] = t;
+                        wbest[i] = w;
+                    }
+                }
             }
-            ++*tuned_sweeps;
+            double obj = 0.0;
+            for (size_t i = 0; i < nm; ++i) obj = use_max ? std::max(obj, fastest[i]) : obj + fastest[i];
+            if (best == 0.0 || obj < best) {
+                best = obj;
+                *out = sh.c;
+                pick = wbest;
+            }
         }
-        cudaEventDestroy(a0);
-        cudaEventDestroy(a1);
+        // the launch's own width: the one most members take
+        int most = 0, nmost = -1;
+        for (int w = 1; w <= asyflexa::kGsWMax; ++w) {
+            const int c = static_cast<int>(std::count(pick.begin(), pick.end(), w));
+            if (c > nmost) {
+                nmost = c;
+                most = w;
+            }
+        }
+        out->w = most;
     }
+    for (size_t i = 0; i < nm; ++i) B.h_gs[members[i]].wpick = pick[i];
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_gs_tuned[B.shape_key] = B.gs;
+    g_gs_tuned[key] = GsTuned{*out, pick};
     return ASYFLEXA_OK;
 }
 
@@ -481,27 +566,38 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
         g.sweeps = g.nnz = 0;
         g.status = ASYFLEXA_ENOTCONV;
         g.checks = 0;
+        g.wpick = 0;
     }
-    BCK(cudaMemcpyAsync(B.d_gs, B.h_gs.data(), count * sizeof(asyflexa::GsInst), cudaMemcpyHostToDevice, B.stream),
-        "upload problem table");
+    auto upload = [&]() -> int {
+        BCK(cudaMemcpyAsync(B.d_gs, B.h_gs.data(), count * sizeof(asyflexa::GsInst), cudaMemcpyHostToDevice,
+                            B.stream),
+            "upload problem table");
+        return ASYFLEXA_OK;
+    };
+    int rc = upload();
+    if (rc) return rc;
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0), "event");
     BCK(cudaEventCreate(&e1), "event");
     BCK(cudaEventRecord(e0, B.stream), "event record");
-    long long tuned = 0;
-    int rc = gs_choose(B, &tuned);
+    std::vector<int> all(count);
+    for (int k = 0; k < count; ++k) all[k] = k;
+    rc = gs_choose(B, B.d_order, count, all, B.shape_key, false, &B.gs);
+    if (!rc) rc = upload();  // the widths picked
     if (rc) return rc;
-    const int budget = static_cast<int>(std::max<long long>(0, B.opts.max_sweeps - tuned));
-    // the solve launch as a CUDA graph (re-captured when the launch shape or budget changes)
+    const int budget = B.opts.max_sweeps;
+    const int handoff = budget > 2 * kGsHandoffSweeps ? kGsHandoffSweeps : 0;
+    // the first launch as a CUDA graph (re-captured when the launch shape or budget changes)
     GsChoice key = B.gs;
     key.stages = B.gs.stages * 100000 + budget;  // the budget is a kernel argument
+    key.grid = B.gs.grid * 1000 + handoff;
     if (!B.gs_exec || !(B.gs_graph_cfg == key)) {
         if (B.gs_exec) cudaGraphExecDestroy(B.gs_exec);
         if (B.gs_graph) cudaGraphDestroy(B.gs_graph);
         B.gs_exec = nullptr;
         B.gs_graph = nullptr;
         BCK(cudaStreamBeginCapture(B.stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-        const int erc = gs_enqueue(B, B.gs, 0, budget);
+        const int erc = gs_enqueue(B, B.gs, 0, budget, handoff, B.d_order, count);
         cudaGraph_t g = nullptr;
         const cudaError_t ce = cudaStreamEndCapture(B.stream, &g);
         if (erc) return erc;
@@ -511,22 +607,75 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
         B.gs_graph_cfg = key;
     }
     BCK(cudaGraphLaunch(B.gs_exec, B.stream), "graph launch");
+    BCK(cudaMemcpyAsync(B.h_gs.data(), B.d_gs, count * sizeof(asyflexa::GsInst), cudaMemcpyDeviceToHost, B.stream),
+        "read problem table");
+    BCK(cudaStreamSynchronize(B.stream), "synchronize");
+    int errw = 0;
+    BCK(cudaMemcpy(&errw, B.err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+    if (errw) return bfail("a bounded device-side wait expired", ASYFLEXA_ETIMEOUT);
+    // Problems still short of their tolerances after a launch's handoff sweeps continue from their
+    // iterates in a further launch over them alone, under a launch shape tuned for them, with
+    // twice the handoff sweeps (so that the last few problems end up with a shape of their own).
+    std::vector<long long> done_sw(count), done_ns(count);
+    std::vector<int> extra(count, 0);               // further launches each problem ran in
+    std::vector<GsChoice> shape_of(count, B.gs);   // the launch that finished it
+    for (int k = 0; k < count; ++k) {
+        done_sw[k] = B.h_gs[k].sweeps;
+        done_ns[k] = B.h_gs[k].ns;
+    }
+    int hand = handoff;
+    for (int round = 1;; ++round) {
+        std::vector<int> rest;
+        long long done_max = 0;
+        for (int k : B.h_order)
+            if (B.h_gs[k].status == asyflexa::kGsHandoff) {
+                rest.push_back(k);
+                done_max = std::max(done_max, done_sw[k]);
+            }
+        if (rest.empty()) break;
+        const int nrest = static_cast<int>(rest.size());
+        const int budget2 = static_cast<int>(std::max<long long>(0, budget - done_max));
+        hand *= 2;
+        const int handoff2 = budget2 > 2 * hand ? hand : 0;
+        BCK(cudaMemcpyAsync(B.d_order2, rest.data(), nrest * sizeof(int), cudaMemcpyHostToDevice, B.stream),
+            "upload order");
+        std::string key2 = B.shape_key + " round=" + std::to_string(round) + " of";
+        for (int k : rest) key2 += " " + std::to_string(k);
+        for (int k : rest) B.h_gs[k].wpick = 0;
+        GsChoice c2;
+        rc = upload();
+        if (!rc) rc = gs_choose(B, B.d_order2, nrest, rest, key2, true, &c2);
+        if (!rc) rc = upload();
+        if (!rc) rc = gs_enqueue(B, c2, 0, budget2, handoff2, B.d_order2, nrest);
+        if (rc) return rc;
+        std::vector<asyflexa::GsInst> tmp(count);
+        BCK(cudaMemcpyAsync(tmp.data(), B.d_gs, count * sizeof(asyflexa::GsInst), cudaMemcpyDeviceToHost, B.stream),
+            "read problem table");
+        BCK(cudaStreamSynchronize(B.stream), "synchronize");
+        errw = 0;
+        BCK(cudaMemcpy(&errw, B.err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
+        if (errw) return bfail("a bounded device-side wait expired", ASYFLEXA_ETIMEOUT);
+        for (int k : rest) {
+            B.h_gs[k] = tmp[k];
+            done_sw[k] += tmp[k].sweeps;
+            done_ns[k] += tmp[k].ns;
+            ++extra[k];
+            shape_of[k] = c2;
+        }
+    }
     BCK(cudaEventRecord(e1, B.stream), "event record");
     BCK(cudaEventSynchronize(e1), "event sync");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int errw = 0;
-    BCK(cudaMemcpy(&errw, B.err, sizeof(int), cudaMemcpyDeviceToHost), "read error word");
-    if (errw) return bfail("a bounded device-side wait expired", ASYFLEXA_ETIMEOUT);
-    BCK(cudaMemcpy(B.h_gs.data(), B.d_gs, count * sizeof(asyflexa::GsInst), cudaMemcpyDeviceToHost),
-        "read problem table");
     long long bu = 0, max_sweeps = 0;
+    int nhanded = 0;
     int worst = ASYFLEXA_OK;
     for (int k = 0; k < count; ++k) {
         const asyflexa::GsInst& g = B.h_gs[k];
-        const long long sw = g.sweeps + tuned;
+        const long long sw = done_sw[k];  // over every launch the problem ran in
+        nhanded += extra[k] > 0 ? 1 : 0;
         bu += sw * g.n;
         max_sweeps = std::max(max_sweeps, sw);
         const int st = g.status;
@@ -546,8 +695,11 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
             s.status = st;
             s.checked = g.checks > 0 ? 1 : 0;
             s.block_w = g.w_used;
+            s.seconds = 1e-9 * static_cast<double>(done_ns[k]);
             s.batch_form = ASYFLEXA_BATCH_FORM_GS;
-            s.ctas_per_sm = B.gs.ctas_per_sm;
+            s.ctas_per_sm = shape_of[k].ctas_per_sm;
+            s.kernel_variant = shape_of[k].nw;
+            s.handed_over = extra[k];
             per[k] = s;
         }
     }
@@ -559,6 +711,7 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
         total->status = worst;
         total->kernel_launches = B.launches;
         total->block_w = B.gs.w;
+        total->handed_over = nhanded;
         total->batch_form = ASYFLEXA_BATCH_FORM_GS;
         total->ctas_per_sm = B.gs.ctas_per_sm;
         total->kernel_variant = B.gs.nw;
@@ -566,21 +719,23 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
     return worst;
 }
 
+
 int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star, asyflexa_stats* per,
-                 asyflexa_stats* total) {
+                      asyflexa_stats* total, const std::vector<char>* mask, long long budget) {
     const int count = B->count;
+    auto in = [&](int k) { return !mask || (*mask)[k] != 0; };
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0), "event");
     BCK(cudaEventCreate(&e1), "event");
     BCK(cudaEventRecord(e0, B->stream), "event record");
-    // reset problem states for these iterates
+    // reset problem states for these iterates (problems outside the mask: inactive)
     for (int k = 0; k < count; ++k) {
         B->h_inst[k].x = xs[k];
-        B->h_inst[k].active = 1;
+        B->h_inst[k].active = in(k) ? 1 : 0;
         ConvState& c = B->h_conv[k];
         c.f_star = f_star ? f_star[k] : NAN;
         c.F = c.F_prev = NAN;
-        c.conv_round = -2;
+        c.conv_round = in(k) ? -2 : 0;
     }
     B->grid = 0;  // every problem active again: full grid until the first deactivation
     int rc = upload_table(*B);
@@ -589,6 +744,7 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
         "upload convergence state");
     BCK(cudaMemsetAsync(B->d_round, 0, sizeof(int), B->stream), "clear round");
     for (int k = 0; k < count; ++k) {
+        if (!in(k)) continue;
         BCK(Launcher<float>::refresh(*B->h[k], xs[k]), "initial refresh");
         B->launches += 4;
     }
@@ -632,6 +788,7 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
         if (!rc) rc = upload_table(*B);
         if (rc) return rc;
         for (int k = 0; k < count; ++k) {
+            if (!in(k)) continue;
             BCK(Launcher<float>::refresh(*B->h[k], xs[k]), "refresh after autotune");
             B->launches += 4;
         }
@@ -667,12 +824,14 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
         if (rc) return rc;
     }
     const int per_round = B->opts.refresh_every;
-    int n_active = count, last_active = count;
+    int n_active = 0;
+    for (int k = 0; k < count; ++k) n_active += in(k) ? 1 : 0;
+    int last_active = n_active;
     // exact check of each problem at its returned x: computed when it leaves the rounds
     std::vector<asyflexa_stats> checked(count);
     std::vector<char> have(count, 0);
     for (;;) {
-        while (sweeps < B->opts.max_sweeps && n_active > 0) {
+        while (sweeps < budget && n_active > 0) {
             BCK(cudaGraphLaunch(B->exec, B->stream), "graph launch");
             sweeps += per_round;
             BCK(cudaMemcpyAsync(&n_active, B->d_nactive, sizeof(int), cudaMemcpyDeviceToHost, B->stream),
@@ -703,14 +862,14 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
         int back = 0;
         for (int k = 0; k < count; ++k) {
             ConvState& c = B->h_conv[k];
-            if (c.conv_round < 0 || have[k]) continue;
+            if (!in(k) || c.conv_round < 0 || have[k]) continue;
             asyflexa_stats st;
             std::memset(&st, 0, sizeof st);
             B->h[k]->opts.f_star = c.f_star;
             const int crc = asyflexa_check(B->h[k], xs[k], &st);
             B->launches += 8;
             st.status = crc;
-            if (!crc && !(st.stat_xhat <= B->opts.tol_stat) && sweeps < B->opts.max_sweeps) {
+            if (!crc && !(st.stat_xhat <= B->opts.tol_stat) && sweeps < budget) {
                 c.conv_round = -2;
                 c.F_prev = NAN;
                 B->h_inst[k].active = 1;
@@ -741,6 +900,7 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
     long long bu = 0, max_k = 0;
     int worst = ASYFLEXA_OK;
     for (int k = 0; k < count; ++k) {
+        if (!in(k)) continue;
         const ConvState& c = B->h_conv[k];
         const long long nb = (B->h[k]->prob.n + B->w - 1) / B->w;
         const long long ksweeps = c.conv_round >= 0 ? static_cast<long long>(c.conv_round + 1) * per_round : sweeps;
@@ -784,7 +944,7 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
 
 int rounds_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflexa_stats* per,
                  asyflexa_stats* total) {
-    return rounds_solve_impl(&B, xs, f_star, per, total);
+    return rounds_solve_impl(&B, xs, f_star, per, total, nullptr, B.opts.max_sweeps);
 }
 
 }  // namespace
@@ -918,7 +1078,10 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
     if (e == cudaSuccess) e = cudaMemset(B->hist, 0, 32 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(B->err, 0, sizeof(int));
     if (e != cudaSuccess) return fail(bfail(std::string("batch allocation: ") + cudaGetErrorString(e), ASYFLEXA_ENOMEM));
-    const int rc = build_blocks(*B, opts->block_w > 0 ? opts->block_w : 32);
+    // the async rounds' block width (for a Gauss-Seidel batch, whose block_w 1..4 is the
+    // Gauss-Seidel width, 32 for the problems it hands over)
+    const bool gs_w = B->form == ASYFLEXA_BATCH_FORM_GS && opts->block_w <= asyflexa::kGsWMax;
+    const int rc = build_blocks(*B, opts->block_w > 0 && !gs_w ? opts->block_w : 32);
     if (rc) return fail(rc);
     {
         // Gauss-Seidel form: the problem table and the queue order (largest m * n first)
@@ -949,18 +1112,16 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
             total_mn += static_cast<double>(hk.prob.m) * static_cast<double>(hk.prob.n);
             max_n = std::max<int64_t>(max_n, hk.prob.n);
         }
-        // the (d_j, 1/d_j) table and the ring slot: at least the longest column, and room for up
-        // to kGsWMax short columns within 16 KB
-        int64_t total_n = 0, slot = 0;
+        // the (d_j, 1/d_j) table, and the sizes the ring slot is chosen from
+        int64_t total_n = 0;
         for (int k = 0; k < count; ++k) {
             const asyflexa_s& hk = *B->h[k];
             total_n += hk.prob.n;
-            const int64_t colb = hk.mcopy * 4;
-            const int64_t multi = std::min<int64_t>(asyflexa::kGsWMax * hk.prob.lda * 4, 16384);
-            slot = std::max(slot, std::max(colb, multi));
+            B->max_colbytes = std::max<int64_t>(B->max_colbytes, hk.mcopy * 4);
+            B->max_multi = std::max<int64_t>(B->max_multi, asyflexa::kGsWMax * hk.prob.lda * 4);
         }
-        B->slot_bytes = slot;
         e = cudaMalloc(&B->d_dd, total_n * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc(&B->d_xsave, total_n * sizeof(float));
         if (e != cudaSuccess) return fail(bfail(std::string("batch allocation: ") + cudaGetErrorString(e), ASYFLEXA_ENOMEM));
         {
             int64_t off = 0;
@@ -979,8 +1140,10 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
         });
         e = cudaMalloc(&B->d_gs, count * sizeof(asyflexa::GsInst));
         if (e == cudaSuccess) e = cudaMalloc(&B->d_order, count * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&B->d_order2, count * sizeof(int));
         if (e == cudaSuccess) e = cudaMalloc(&B->d_queue, sizeof(int));
         if (e == cudaSuccess) e = cudaMemcpy(B->d_order, order.data(), count * sizeof(int), cudaMemcpyHostToDevice);
+        B->h_order = order;
         if (e != cudaSuccess) return fail(bfail(std::string("batch allocation: ") + cudaGetErrorString(e), ASYFLEXA_ENOMEM));
         char key[160];
         std::snprintf(key, sizeof key, "count=%d mn=%.0f max_m=%lld max_n=%lld flags=%d nctas=%d w=%d sms=%d", count,
@@ -1011,7 +1174,7 @@ int asyflexa_batch_destroy(asyflexa_batch_t B) {
     if (B->ev_out) cudaEventDestroy(B->ev_out);
     if (B->stream) cudaStreamDestroy(B->stream);
     void* ptrs[] = {B->d_inst, B->d_blk_inst, B->d_blk_local, B->d_conv, B->d_round, B->d_nactive,
-                    B->counters, B->hist, B->err, B->d_gs, B->d_order, B->d_queue, B->d_dd};
+                    B->counters, B->hist, B->err, B->d_gs, B->d_order, B->d_order2, B->d_queue, B->d_dd, B->d_xsave};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete B;

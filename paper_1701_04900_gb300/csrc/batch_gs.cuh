@@ -38,6 +38,7 @@
 #pragma once
 
 #include <cmath>
+#include <type_traits>
 
 #include "ptx.cuh"
 #include "sweep.cuh"
@@ -57,11 +58,12 @@ struct GsInst {
     const float2* dd;           // (d_j, 1/d_j) in FP32; (0, 0) where d_j <= 0
     double lam, s_loss, c2, c;  // s_loss = 1 (LASSO) or 2 (NCQUAD); c2 = 2c; c: NCQUAD weight (for F)
     double f_star;              // NaN: no gap test, stop on the merit alone
-    int loss, pad0;
+    int loss, wpick;            // wpick: this problem's block width (0: the launch's)
     // written by the kernel
     double F, stat, xmax;
     long long sweeps, nnz;
     int status, checks, w_used, pad1;  // w_used: the block width (the tuned one, or as many as a slot holds)
+    long long ns;                      // the problem's solve time on its CTA (global timer)
 };
 
 struct GsParams {
@@ -71,15 +73,17 @@ struct GsParams {
     int* queue;         // next position in `order` (0 before the launch)
     double gamma, tol_gap, tol_stat;
     int check_every, max_sweeps, stages;
-    int w;              // block width, 1 .. kGsWMax
+    int w;              // block width, 1 .. kGsWMax, of the problems with wpick = 0
     int64_t slot_bytes; // ring slot (a multiple of 128 bytes, at least the longest column)
     int sweeps_only;    // 1: exactly max_sweeps sweeps per problem, no stopping test (autotuner)
+    int handoff_sweeps; // > 0: a problem still short of its tolerances after this many sweeps stops
+                        // with kGsHandoff (the host finishes it with a second launch)
     int keep_a_in_l2;   // 1: A shared by the problems (normal L2 priority)
     int* err;
 };
 
 constexpr int kGsMeta = 64;  // REFRESH item ring (a power of 2, >= the ring depth)
-constexpr int kGsWMax = 4;   // largest block width of the Gauss-Seidel form
+constexpr int kGsWMax = 8;   // largest block width of the Gauss-Seidel form
 
 struct GsLayout {
     size_t slot_bytes, off_ring, off_meta, off_part, off_red, off_dls, off_bars, off_misc, total;
@@ -110,6 +114,7 @@ __host__ __device__ inline GsLayout make_gs_layout(int nw, size_t slot_bytes, in
 }
 
 constexpr int kGsRefresh = 0, kGsSweep = 1, kGsMerit = 2;
+constexpr int kGsHandoff = 2;  // status: left for the second launch (not an asyflexa_status)
 constexpr int kGsFloorChecks = 5;
 constexpr double kGsFloorBand = 100.0;  // the floor rule applies within 100 tol_stat
 
@@ -234,7 +239,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
         // columns per block: the tuned width, as many as a slot holds
         const int wcap = static_cast<int>((p.slot_bytes - static_cast<int64_t>(units) * 16) /
                                           (static_cast<int64_t>(lda) * 4)) + 1;
-        const int w = p.w < wcap ? p.w : wcap;
+        const int wsel = I.wpick > 0 ? I.wpick : p.w;
+        const int w = wsel < wcap ? wsel : wcap;
         // this thread's units k < kmine hold rows of the column; unit klast (or -1) is the
         // column's last one, of which only its first vlast rows are < m
         const int kmine = tid < units ? (units - 1 - tid) / T + 1 : 0;
@@ -255,6 +261,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
         };
         if (!producer) reset_r();
 
+        const uint64_t t_start = global_timer_ns();
         if (tid == 0) {
             misc->sweeps = 0;
             misc->status = ASYFLEXA_ENOTCONV;
@@ -306,21 +313,24 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                 };
                 bool go = true;
                 if (phase == kGsRefresh) {
-                    // the blocks of w columns that hold a nonzero x_j, found 32 columns at a time
-                    // by the whole warp (w divides 32); meta[item] = the block's first column
+                    // the blocks of up to w columns that hold a nonzero x_j, found 32 columns at a
+                    // time by the whole warp; no block crosses a group of 32 (w need not divide
+                    // 32).  meta[item] = (the block's first column) * 16 + its width
                     for (int j0 = 0; j0 < n && go; j0 += 32) {
                         const int j = j0 + lane;
                         const bool nz = j < n && X[j] != 0.f;
                         const unsigned mask = __ballot_sync(0xffffffffu, nz);
-                        for (int b0 = 0; b0 < 32 && go; b0 += w) {
-                            const unsigned bm = (mask >> b0) & ((1u << w) - 1u);
+                        for (int b0 = 0; b0 < 32 && j0 + b0 < n && go; b0 += w) {
+                            int wb = 32 - b0 < w ? 32 - b0 : w;
+                            if (n - (j0 + b0) < wb) wb = n - (j0 + b0);
+                            const unsigned bm = (mask >> b0) & ((1u << wb) - 1u);
                             if (bm == 0u) continue;
                             int okl = 1;
                             if (lane == 0) {
                                 okl = wait_slot() ? 1 : 0;
                                 if (okl) {
-                                    meta[it & (kGsMeta - 1)] = j0 + b0;
-                                    issue(j0 + b0, n - (j0 + b0) < w ? n - (j0 + b0) : w);
+                                    meta[it & (kGsMeta - 1)] = (j0 + b0) * 16 + wb;
+                                    issue(j0 + b0, wb);
                                 }
                             }
                             go = __shfl_sync(0xffffffffu, okl, 0) != 0;
@@ -351,9 +361,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                     const int slot = cslot;
                     ok = ok && !*abort_flag && mbar_wait_bounded(&full[slot], cpar, abort_flag, p.err);
                     if (!ok) break;
-                    const int j0 = meta[it & (kGsMeta - 1)];
-                    if (j0 >= 0) {
-                        const int wb = n - j0 < w ? n - j0 : w;
+                    const int code = meta[it & (kGsMeta - 1)];
+                    const int j0 = code >> 4;  // -1: the end of the refresh
+                    if (code >= 0) {
+                        const int wb = code & 15;
                         for (int t = 0; t < wb; ++t) {
                             const float xj = X[j0 + t];
                             if (xj == 0.f) continue;
@@ -406,17 +417,31 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                 // Lane t of warp 0 owns the block's column t: it sums the column's warp partials,
                 // evaluates its best response and writes x_j, so column j (always at position
                 // j mod w of its block) is read and written by one thread.  Its coefficients are
-                // loaded at the block's start and used after the block's first barrier.
-                float cx = 0.f, cd = 0.f, cdi = 0.f;
+                // loaded one block ahead (x_j was last written by this thread a sweep earlier, or,
+                // when a sweep is a single block, in the block just done: then the new value).
+                float cx = 0.f, cd = 0.f, cdi = 0.f;  // this block's column
+                float nx = 0.f, nd = 0.f, ndi = 0.f;  // the next block's
+                if (warp == 0 && lane < w && lane < n) {
+                    const float2 dd = DD[lane];
+                    nx = X[lane];
+                    nd = dd.x;
+                    ndi = dd.y;
+                }
                 for (int sw = 0; sw < nsw; ++sw) {
                     for (int j0 = 0; j0 < n; j0 += w) {
                         const int wb = n - j0 < w ? n - j0 : w;
                         const int slot = cslot;
-                        if (warp == 0 && lane < wb) {
-                            const float2 dd = DD[j0 + lane];
-                            cx = X[j0 + lane];
-                            cd = dd.x;
-                            cdi = dd.y;
+                        const int jn = j0 + w < n ? j0 + w : 0;  // the next block (of this or the next sweep)
+                        if (warp == 0) {
+                            cx = nx;
+                            cd = nd;
+                            cdi = ndi;
+                            if (lane < w && jn + lane < n) {
+                                const float2 dd = DD[jn + lane];
+                                nx = X[jn + lane];
+                                nd = dd.x;
+                                ndi = dd.y;
+                            }
                         }
                         ok = ok && !*abort_flag && mbar_wait_bounded(&full[slot], cpar, abort_flag, p.err);
                         float2* cp = part + buf * (kGsWMax * NW);
@@ -474,34 +499,43 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                             const float v = warp_sum((acc0 + acc1) + (acc2 + acc3));
                             if (lane == 0) cp[warp] = make_float2(v, 0.f);
                         } else {
-                            // all kGsWMax columns without branches, so that their load, FMA and
+                            // WB >= w columns without branches, so that their load, FMA and
                             // shuffle chains interleave: a column past the block's end reads the
                             // block's first column and its result is not used
-                            float acc[kGsWMax];
+                            auto dots = [&](auto wbc) {
+                                constexpr int WB = decltype(wbc)::value;
+                                float acc[WB];
 #pragma unroll
-                            for (int t = 0; t < kGsWMax; ++t) {
-                                const uint4* src = reinterpret_cast<const uint4*>(
-                                    ring + slot * L.slot_bytes + static_cast<size_t>(t < wb ? t : 0) * lda * 4);
-                                float a0 = 0.f, a1 = 0.f;
+                                for (int t = 0; t < WB; ++t) {
+                                    const uint4* src = reinterpret_cast<const uint4*>(
+                                        ring + slot * L.slot_bytes + static_cast<size_t>(t < wb ? t : 0) * lda * 4);
+                                    float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-                                for (int k = 0; k < UPT; ++k) {
-                                    float a[4];
-                                    ATraits<float>::unpack(load_unit(src, k), a);
-                                    a0 = fmaf(a[0], rhi[k][0], a0);
-                                    a1 = fmaf(a[1], rhi[k][1], a1);
-                                    a0 = fmaf(a[2], rhi[k][2], a0);
-                                    a1 = fmaf(a[3], rhi[k][3], a1);
+                                    for (int k = 0; k < UPT; ++k) {
+                                        float a[4];
+                                        ATraits<float>::unpack(load_unit(src, k), a);
+                                        a0 = fmaf(a[0], rhi[k][0], a0);
+                                        a1 = fmaf(a[1], rhi[k][1], a1);
+                                        a0 = fmaf(a[2], rhi[k][2], a0);
+                                        a1 = fmaf(a[3], rhi[k][3], a1);
+                                    }
+                                    acc[t] = a0 + a1;
                                 }
-                                acc[t] = a0 + a1;
-                            }
 #pragma unroll
-                            for (int o = 16; o > 0; o >>= 1)
+                                for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-                                for (int t = 0; t < kGsWMax; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-                            if (lane == 0) {
+                                    for (int t = 0; t < WB; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+                                if (lane == 0) {
 #pragma unroll
-                                for (int t = 0; t < kGsWMax; ++t) cp[t * NW + warp] = make_float2(acc[t], 0.f);
-                            }
+                                    for (int t = 0; t < WB; ++t) cp[t * NW + warp] = make_float2(acc[t], 0.f);
+                                }
+                            };
+                            if (w <= 2)
+                                dots(std::integral_constant<int, 2>{});
+                            else if (w <= 4)
+                                dots(std::integral_constant<int, 4>{});
+                            else
+                                dots(std::integral_constant<int, 8>{});
                         }
                         named_bar_sync(1, T);
                         if (warp == 0) {
@@ -537,6 +571,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                                 } else {
                                     const float xn = fmaf(gamma, e, cx);
                                     if (ok) X[j] = xn;
+                                    if (jn == j0) nx = xn;  // the sweep is this one block
                                     dls[lane] = ok ? xn - cx : 0.f;
                                 }
                             } else if (lane < kGsWMax && !merit) {
@@ -567,27 +602,37 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                             } else {
                                 // dls[t] = 0 for t >= wb (and for columns that did not move); the
                                 // columns past the block's end read the block's first column
-                                float dl[kGsWMax];
-                                bool any = false;
+                                auto update = [&](auto wbc) {
+                                    constexpr int WB = decltype(wbc)::value;
+                                    float dl[WB];
+                                    bool any = false;
 #pragma unroll
-                                for (int t = 0; t < kGsWMax; ++t) {
-                                    dl[t] = dls[t];
-                                    any |= dl[t] != 0.f;
-                                }
-                                if (any) {
+                                    for (int t = 0; t < WB; ++t) {
+                                        dl[t] = dls[t];
+                                        any |= dl[t] != 0.f;
+                                    }
+                                    if (any) {
 #pragma unroll
-                                    for (int k = 0; k < UPT; ++k) {
+                                        for (int k = 0; k < UPT; ++k) {
 #pragma unroll
-                                        for (int t = 0; t < kGsWMax; ++t) {
-                                            const uint4* src = reinterpret_cast<const uint4*>(
-                                                ring + slot * L.slot_bytes + static_cast<size_t>(t < wb ? t : 0) * lda * 4);
-                                            float a[4];
-                                            ATraits<float>::unpack(load_unit(src, k), a);
+                                            for (int t = 0; t < WB; ++t) {
+                                                const uint4* src = reinterpret_cast<const uint4*>(
+                                                    ring + slot * L.slot_bytes +
+                                                    static_cast<size_t>(t < wb ? t : 0) * lda * 4);
+                                                float a[4];
+                                                ATraits<float>::unpack(load_unit(src, k), a);
 #pragma unroll
-                                            for (int e = 0; e < 4; ++e) rhi[k][e] = fmaf(a[e], dl[t], rhi[k][e]);
+                                                for (int e = 0; e < 4; ++e) rhi[k][e] = fmaf(a[e], dl[t], rhi[k][e]);
+                                            }
                                         }
                                     }
-                                }
+                                };
+                                if (w <= 2)
+                                    update(std::integral_constant<int, 2>{});
+                                else if (w <= 4)
+                                    update(std::integral_constant<int, 4>{});
+                                else
+                                    update(std::integral_constant<int, 8>{});
                             }
                         }
                         __syncwarp();
@@ -744,6 +789,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                 if (sweep_next) {
                     if (g.sweeps >= p.max_sweeps) {
                         g.done = 1;
+                    } else if (p.handoff_sweeps > 0 && g.sweeps >= p.handoff_sweeps) {
+                        g.status = kGsHandoff;
+                        g.done = 1;
                     } else {
                         // near the tolerance the next check comes after 2 sweeps
                         const bool near = phase == kGsMerit && g.stat_last <= 2.0 * p.tol_stat;
@@ -768,6 +816,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
             O.status = *abort_flag ? kDevTimeout : misc->status;
             O.checks = misc->checks;
             O.w_used = w;
+            O.ns = static_cast<long long>(global_timer_ns() - t_start);
         }
         __syncthreads();  // the results and misc are read before the next problem rewrites misc
     }

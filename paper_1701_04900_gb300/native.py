@@ -61,6 +61,7 @@ class Stats(C.Structure):
         ("polish_sweeps", C.c_int64), ("polish_seconds", C.c_double),
         ("block_w", C.c_int32), ("kernel_variant", C.c_int32), ("dual_gap", C.c_double),
         ("tau_extra", C.c_double), ("batch_form", C.c_int32), ("ctas_per_sm", C.c_int32),
+        ("handed_over", C.c_int32), ("reserved1", C.c_int32),
     ]
 
     def as_dict(self) -> dict:

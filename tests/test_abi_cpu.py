@@ -61,7 +61,7 @@ int main(void) {
   P(asyflexa_opts, exact_grad)
   P(asyflexa_stats, staleness_hist) P(asyflexa_stats, kernel_launches) P(asyflexa_stats, checked)
   P(asyflexa_stats, kernel_variant) P(asyflexa_stats, dual_gap) P(asyflexa_stats, tau_extra)
-  P(asyflexa_stats, batch_form) P(asyflexa_stats, ctas_per_sm)
+  P(asyflexa_stats, batch_form) P(asyflexa_stats, ctas_per_sm) P(asyflexa_stats, handed_over)
   return 0;
 }
 """

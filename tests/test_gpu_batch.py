@@ -106,16 +106,17 @@ def test_batch_shared_matrix_lambda_path_with_autotuned_width():
 
 # ----------------------------------------------------------------------------- Gauss-Seidel form
 
-def _gs_oracle_sweeps(d, sweeps, gamma=0.9, w=1):
+def _gs_oracle_sweeps(d, sweeps, gamma=0.9, w=1, x0=None):
     p = O.Problem.from_data(d)
     dw = O.surrogate_weights(p)
-    x, r = np.zeros(p.n), O.residual(p, np.zeros(p.n))
+    x = np.zeros(p.n) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
+    r = O.residual(p, x)
     for _ in range(sweeps):
         x, r = O.gauss_seidel_sweep(p, x, r, dw, gamma, w=w)
     return x
 
 
-@pytest.mark.parametrize("w", [1, 4])
+@pytest.mark.parametrize("w", [1, 4, 8])
 def test_batch_gs_form_iterates_are_block_gauss_seidel(w):
     """No stopping possible (tol_stat = 0, 2 sweeps in all): each problem's x equals two
     cyclic block Gauss-Seidel sweeps (blocks of w columns, w = 1: scalar blocks) of the oracle.
@@ -138,6 +139,37 @@ def test_batch_gs_form_iterates_are_block_gauss_seidel(w):
         assert st["sweeps"] == 2 and st["status"] == native.ENOTCONV
         assert rel_inf(x.cpu().numpy(), _gs_oracle_sweeps(d, 2, w=st["block_w"])) < TOL32
     assert any(st["block_w"] == w for st in per)
+    bs.close()
+
+
+@pytest.mark.parametrize("w", [2, 4, 8])
+def test_batch_gs_form_warm_start_with_a_refresh_every_sweep(w):
+    """From a nonzero x0 (every third coordinate nonzero) with a check after every sweep, the
+    residual the kernel starts each sweep from is rebuilt from x over the blocks that hold a
+    nonzero: x after 3 sweeps equals 3 oracle block Gauss-Seidel sweeps from x0.  Columns of
+    m = 1200 and 1700 (3 and 2 to a 16 KB ring slot) and 2400 and 3000 (3 and 2 to a 32 KB
+    slot) give blocks narrower than w whichever slot the autotuner takes, so the rebuild's
+    blocks do not line up with its groups of 32 columns."""
+    import torch
+    from paper_1701_04900_gb300.batch import BatchSolver
+    from paper_1701_04900_gb300 import native
+    shapes = [(1200, 100), (1700, 70), (2400, 50), (3000, 40), (301, 121), (4000, 45), (64, 33)]
+    ds = [random_lasso(m, n, seed=120 + i, lam=0.2, store_dtype=np.float32) for i, (m, n) in enumerate(shapes)]
+    x0s = []
+    for i, d in enumerate(ds):
+        v = np.random.default_rng(300 + i).uniform(-0.5, 0.5, d["n"]).astype(np.float32)
+        v[np.arange(d["n"]) % 3 != 0] = 0.0
+        x0s.append(v)
+    bs = BatchSolver([_cuda(d) for d in ds], form="gs", block_w=w, max_sweeps=3, check_every=1, tol_stat=0.0)
+    xs = [torch.from_numpy(v.copy()).cuda() for v in x0s]
+    per, _ = bs.solve(xs)
+    for d, v, x, st in zip(ds, x0s, xs, per):
+        assert st["sweeps"] == 3 and st["status"] == native.ENOTCONV
+        ref = _gs_oracle_sweeps(d, 3, w=st["block_w"], x0=v)
+        assert rel_inf(x.cpu().numpy(), ref) < TOL32, (d["m"], d["n"], st["block_w"])
+    widths = {st["block_w"] for st in per[:4]}
+    # a width that does not divide 32 (3 or 6)
+    assert any(32 % wb for wb in widths) if w > 2 else widths <= {1, 2}
     bs.close()
 
 
