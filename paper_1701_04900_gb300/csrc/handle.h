@@ -75,6 +75,8 @@ struct asyflexa_s {
     // the column-in-registers form of the register kernel exists for this problem, and whether
     // the form with a producer warp was asked for instead (asyflexa_opts.variant 3)
     bool reg_rc_ok = false, reg_rc_off = false;
+    int reg_g = 1;           // column-in-registers form: columns per barrier
+    size_t rc_smem = 0;      // its shared memory
 
 
     int check_ctas = 0;

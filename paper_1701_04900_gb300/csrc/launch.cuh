@@ -91,11 +91,41 @@ const void* rc_inst() {
         return nullptr;
 }
 
+// Columns per barrier of the column-in-registers form by storage type: BF16 and FP8 columns
+// are short in bytes but not in rows, so their per-column barrier, warp sums and residual reads
+// are shared by 2 and 4 columns; FP32 keeps 1.
 template <typename TA>
-const void* rc_kernel(int cpc, int upt) {
+constexpr int rc_group() {
+    if constexpr (std::is_same<TA, __nv_bfloat16>::value) return 2;
+    if constexpr (std::is_same<TA, __nv_fp8_e4m3>::value) return 4;
+    return 1;
+}
+
+// The instance of the column-in-registers form for cpc stages, upt units per thread and g
+// columns per barrier (g = 1, or rc_group<TA>() and its half for the short-column types, at
+// the column lengths the automatic choice gives them: more than 16384 rows), or nullptr.
+template <typename TA>
+const void* rc_kernel(int cpc, int upt, int g = 1) {
     if constexpr (sizeof(typename ATraits<TA>::TC) != 4) {
         return nullptr;
     } else {
+        if (g != 1) {
+            constexpr int G = rc_group<TA>();
+            if constexpr (G >= 2) {
+                if constexpr (std::is_same<TA, __nv_bfloat16>::value) {
+                    if (g == 2 && cpc == 2 && upt == 4) return reinterpret_cast<const void*>(sweep_async_rc_kernel<TA, 2, 0, 2>);
+                    if (g == 2 && cpc == 3 && upt == 6) return reinterpret_cast<const void*>(sweep_async_rc_kernel<TA, 3, 0, 2>);
+                    if (g == 2 && cpc == 3 && upt == 5) return reinterpret_cast<const void*>(sweep_async_rc_kernel<TA, 3, 5, 2>);
+                }
+                if constexpr (std::is_same<TA, __nv_fp8_e4m3>::value) {
+                    if (cpc == 2 && upt == 3) {
+                        if (g == 4) return reinterpret_cast<const void*>(sweep_async_rc_kernel<TA, 2, 3, 4>);
+                        if (g == 2) return reinterpret_cast<const void*>(sweep_async_rc_kernel<TA, 2, 3, 2>);
+                    }
+                }
+            }
+            return nullptr;
+        }
         if (upt != kRegKpc * cpc) {
             if constexpr (std::is_same<TA, __nv_fp8_e4m3>::value)
                 if (cpc == 2 && upt == 3) return reinterpret_cast<const void*>(sweep_async_rc_kernel<TA, 2, 3>);
@@ -150,10 +180,20 @@ int Launcher<TA>::choose_reg(asyflexa_s& h) {
         e = cudaFuncSetAttribute(fx, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.reg_smem));
         if (e != cudaSuccess) return -static_cast<int>(e);
     }
-    const void* fr = rc_kernel<TA>(cpc, upt);
+    // the column-in-registers form: the most columns per barrier whose stages fit the ring with
+    // one column's stages to spare for the prefetch (and one refilling warp per stage)
+    h.reg_g = 1;
+    for (int g = rc_group<TA>(); g > 1; g /= 2) {
+        if (g * cpc + cpc > stages || g * cpc > kRegConsWarps) continue;
+        if (make_reg_layout(rt_rows, stages, g).total > h.smem_optin || !rc_kernel<TA>(cpc, upt, g)) continue;
+        h.reg_g = g;
+        break;
+    }
+    h.rc_smem = make_reg_layout(rt_rows, stages, h.reg_g).total;
+    const void* fr = rc_kernel<TA>(cpc, upt, h.reg_g);
     h.reg_rc_ok = fr != nullptr;
     if (fr) {
-        e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.reg_smem));
+        e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.rc_smem));
         if (e != cudaSuccess) return -static_cast<int>(e);
     }
     return 1;
@@ -260,8 +300,8 @@ cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
         void* args[] = {&p};
         const bool exact = h.reg_exact_ok && h.opts.exact_grad == 1;
         if (!exact && h.reg_rc_ok && !h.reg_rc_off) {  // the column-in-registers form
-            const cudaError_t e = cudaLaunchKernel(rc_kernel<TA>(h.reg_cpc, h.reg_upt), dim3(h.sweep_ctas),
-                                                   dim3(kRcThreads), args, h.reg_smem, h.stream);
+            const cudaError_t e = cudaLaunchKernel(rc_kernel<TA>(h.reg_cpc, h.reg_upt, h.reg_g), dim3(h.sweep_ctas),
+                                                   dim3(kRcThreads), args, h.rc_smem, h.stream);
             ++h.launches;
             return e != cudaSuccess ? e : cudaGetLastError();
         }

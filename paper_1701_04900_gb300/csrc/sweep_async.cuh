@@ -42,6 +42,7 @@ constexpr int kRegThreads = kRegConsThreads + 32;
 constexpr int kRegKpc = 2;                                   // units per thread per stage
 constexpr int kRegStageUnits = kRegKpc * kRegConsThreads;    // 1024 units = 16 KB
 constexpr int kRegMaxRowsPerThread = 48;
+constexpr int kRcGMax = 4;  // columns per barrier of the column-in-registers form
 
 struct RegLayout {
     int stages;
@@ -55,7 +56,8 @@ struct ColCoef {
     float lin, pad0;                    // linear term of f (0 if none)
 };
 
-__host__ __device__ inline RegLayout make_reg_layout(int rt_rows, int stages) {
+// g: columns whose partial sums one barrier publishes (1 for the other register kernels).
+__host__ __device__ inline RegLayout make_reg_layout(int rt_rows, int stages, int g = 1) {
     RegLayout L;
     L.stages = stages;
     L.stage_bytes = static_cast<size_t>(kRegStageUnits) * 16;
@@ -64,8 +66,9 @@ __host__ __device__ inline RegLayout make_reg_layout(int rt_rows, int stages) {
     o += L.stage_bytes * stages;
     L.off_rt = o;
     o = align_up_sz(o + static_cast<size_t>(rt_rows) * sizeof(float), 16);
-    L.off_colpart = o;  // two buffers of per-warp partial sums (FP32 pairs in the compensated form)
-    o = align_up_sz(o + 2 * kRegConsWarps * 2 * sizeof(float), 16);
+    L.off_colpart = o;  // two buffers of per-warp partial sums (FP32 pairs in the compensated form,
+                        // or the partials of g columns)
+    o = align_up_sz(o + 2 * kRegConsWarps * (g > 2 ? g : 2) * sizeof(float), 16);
     L.off_coef = o;
     o = align_up_sz(o + kWMax * sizeof(ColCoef), 16);
     L.off_bars = o;
@@ -672,7 +675,7 @@ __device__ __forceinline__ void rc_issue(const SweepParams& p, const RcPos& q, i
     bulk_load(ring + st * stage_bytes, col + u0 * V, nbytes, &full[st], l2_policy_evict_first());
 }
 
-template <typename TA, int CPC, int UPTX = 0>
+template <typename TA, int CPC, int UPTX = 0, int G = 1>
 __global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const SweepParams p) {
     using TC = typename ATraits<TA>::TC;
     static_assert(sizeof(TC) == 4, "register kernel computes in FP32");
@@ -682,9 +685,10 @@ __global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const Swe
     constexpr int UPT = UPTX > 0 ? UPTX : kRegKpc * CPC;
     static_assert(UPT <= kRegKpc * CPC, "units beyond the column's stages");
     static_assert(UPT * V <= kRegMaxRowsPerThread, "too many rows per thread");
+    static_assert(G >= 1 && G <= kRcGMax, "columns per barrier");
 
     extern __shared__ __align__(128) unsigned char smem[];
-    const RegLayout L = make_reg_layout(p.tile_rows, p.stages);
+    const RegLayout L = make_reg_layout(p.tile_rows, p.stages, G);
     unsigned char* ring = smem + L.off_ring;
     float* rt = reinterpret_cast<float*>(smem + L.off_rt);
     float* colpart = reinterpret_cast<float*>(smem + L.off_colpart);
@@ -750,93 +754,152 @@ __global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const Swe
             named_bar_sync(1, kRcThreads);
             const float gamma = *s_gamma;
 
-            for (int jl = 0; jl < bv.wb; ++jl) {
-                // ---- dot a_j^T r~ over this thread's rows; the units stay in registers
-                float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
-                uint4 colr[UPT];
+            // groups of G columns (the block's last group may be shorter): their stages are
+            // consecutive ring items, so G * nchunks <= S slots hold a whole group; each
+            // thread reads its residual units once per group for all G dots, and one barrier
+            // publishes the group's G partial sums
+            for (int j0 = 0; j0 < bv.wb; j0 += G) {
+                const int gn = G == 1 ? 1 : (bv.wb - j0 < G ? bv.wb - j0 : G);
+                // ---- dots a_j^T r~ over this thread's rows; the units stay in registers
+                constexpr int NACC = G == 1 ? 4 : 2;  // independent FMA chains per column
+                float acc[G][NACC];
+                uint4 colr[G][UPT];
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+#pragma unroll
+                    for (int q = 0; q < NACC; ++q) acc[g][q] = 0.f;
                 bool ok = !*abort_flag;
-                const uint32_t st0 = stage;  // slot of the column's first stage
+                const uint32_t st0 = stage, ph0 = phase;  // slot and parity of the group's first stage
 #pragma unroll
                 for (int c = 0; c < CPC; ++c) {
                     if (c < nchunks) {
-                        if (ok) ok = mbar_wait_bounded(&full[stage], phase, abort_flag, p.err);
-                        const uint4* src = reinterpret_cast<const uint4*>(ring + stage * L.stage_bytes);
+                        const uint4* src[G];
+#pragma unroll
+                        for (int g = 0; g < G; ++g) {
+                            src[g] = nullptr;
+                            if (g < gn) {
+                                uint32_t sl = st0 + static_cast<uint32_t>(g * nchunks + c), ph = ph0;
+                                if (sl >= static_cast<uint32_t>(S)) {
+                                    sl -= static_cast<uint32_t>(S);
+                                    ph ^= 1u;
+                                }
+                                if (ok) ok = mbar_wait_bounded(&full[sl], ph, abort_flag, p.err);
+                                src[g] = reinterpret_cast<const uint4*>(ring + sl * L.stage_bytes);
+                            }
+                        }
                         const bool whole = static_cast<int64_t>(c + 1) * kRegStageUnits <= units_full;
 #pragma unroll
                         for (int kk = 0; kk < kRegKpc; ++kk) {
                             const int k = c * kRegKpc + kk;
                             if (k < UPT) {
                                 const int64_t u = static_cast<int64_t>(k) * kRcThreads + tid;
-                                colr[k] = (ok && (whole || u < units)) ? src[kk * kRcThreads + tid]
-                                                                       : make_uint4(0u, 0u, 0u, 0u);
-                                float a[V];
-                                ATraits<TA>::unpack(colr[k], a);
                                 const float* rv = rt + u * V;
-                                if (whole || u < units_full) {
+                                const bool full_unit = whole || u < units_full;
+                                float r[V];
+                                if (full_unit) {
 #pragma unroll
                                     for (int e = 0; e < V; e += 4) {
                                         const float4 r4 = *reinterpret_cast<const float4*>(rv + e);
-                                        acc0 = fmaf(a[e], r4.x, acc0);
-                                        acc1 = fmaf(a[e + 1], r4.y, acc1);
-                                        acc2 = fmaf(a[e + 2], r4.z, acc2);
-                                        acc3 = fmaf(a[e + 3], r4.w, acc3);
+                                        r[e] = r4.x;
+                                        r[e + 1] = r4.y;
+                                        r[e + 2] = r4.z;
+                                        r[e + 3] = r4.w;
                                     }
-                                } else if (u < units) {
-                                    const int valid = static_cast<int>(bv.m - u * V);
+                                } else {
+                                    const int valid = u < units ? static_cast<int>(bv.m - u * V) : 0;
 #pragma unroll
-                                    for (int e = 0; e < V; ++e)
-                                        if (e < valid) acc0 = fmaf(a[e], rv[e], acc0);
+                                    for (int e = 0; e < V; ++e) r[e] = e < valid ? rv[e] : 0.f;
+                                }
+#pragma unroll
+                                for (int g = 0; g < G; ++g) {
+                                    colr[g][k] = (g < gn && ok && (whole || u < units)) ? src[g][kk * kRcThreads + tid]
+                                                                                       : make_uint4(0u, 0u, 0u, 0u);
+                                    float a[V];
+                                    ATraits<TA>::unpack(colr[g][k], a);
+#pragma unroll
+                                    for (int e = 0; e < V; ++e) acc[g][e % NACC] = fmaf(a[e], r[e], acc[g][e % NACC]);
                                 }
                             }
-                        }
-                        if (++stage == static_cast<uint32_t>(S)) {
-                            stage = 0;
-                            phase ^= 1u;
                         }
                     } else {
 #pragma unroll
                         for (int kk = 0; kk < kRegKpc; ++kk)
-                            if (c * kRegKpc + kk < UPT) colr[c * kRegKpc + kk] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                            for (int g = 0; g < G; ++g)
+                                if (c * kRegKpc + kk < UPT) colr[g][c * kRegKpc + kk] = make_uint4(0u, 0u, 0u, 0u);
                     }
                 }
-                static_assert(kRegConsWarps == 16, "the sums below read 16 warp partials");
-                float* cp = colpart + buf * kRegConsWarps;
                 {
-                    const float v = warp_sum((acc0 + acc1) + (acc2 + acc3));
-                    if (lane == 0) cp[warp] = v;
+                    uint32_t nx = st0 + static_cast<uint32_t>(gn * nchunks);
+                    phase = ph0;
+                    if (nx >= static_cast<uint32_t>(S)) {
+                        nx -= static_cast<uint32_t>(S);
+                        phase ^= 1u;
+                    }
+                    stage = nx;
                 }
-                const ColCoef cf = coef[jl];
+                static_assert(kRegConsWarps == 16, "the sums below read 16 warp partials");
+                float* cp = colpart + buf * (kRegConsWarps * G);
+                {
+                    float v[G];
+#pragma unroll
+                    for (int g = 0; g < G; ++g)
+                        v[g] = NACC == 4 ? (acc[g][0] + acc[g][1]) + (acc[g][NACC - 2] + acc[g][NACC - 1])
+                                         : acc[g][0] + acc[g][1];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                        for (int g = 0; g < G; ++g) v[g] += __shfl_xor_sync(0xffffffffu, v[g], o);
+                    if (lane == 0) {
+#pragma unroll
+                        for (int g = 0; g < G; ++g)
+                            if (g < gn) cp[g * kRegConsWarps + warp] = v[g];
+                    }
+                }
+                ColCoef cf[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (g < gn) cf[g] = coef[j0 + g];
                 named_bar_sync(1, kRcThreads);
-                // every warp has read the column's stages: warp c refills the slot of stage c
-                // with the item S further on
-                if (warp < nchunks && lane == 0 && !*abort_flag) {
-                    RcPos q{s, b, jl, 0};
+                // every warp has read the group's stages: warp c refills the slot of the group's
+                // stage c with the item S further on
+                if (warp < gn * nchunks && lane == 0 && !*abort_flag) {
+                    RcPos q{s, b, j0, 0};
                     if (rc_next(q, S + warp, p, nchunks)) {
                         uint32_t st = st0 + static_cast<uint32_t>(warp);
                         if (st >= static_cast<uint32_t>(S)) st -= static_cast<uint32_t>(S);
                         rc_issue<TA>(p, q, static_cast<int>(st), ring, L.stage_bytes, full, fills, units);
                     }
                 }
-                // ---- best response (eq. 2) + fixed step (S.4), identical in every thread
-                const float g = sum_partials_16(cp);
-                buf ^= 1;
-                const float xn = best_response_step(bv, cf, g, gamma);
-                const float dlt = xn - cf.x;
-                float dj = 0.f;
-                if (!*abort_flag) {
-                    if (tid == 0) bv.x[bv.c0 + jl] = static_cast<TX>(xn);
-                    dj = dlt * cf.scale;
-                    any |= dlt != 0.f;
+                // ---- best responses (eq. 2) + fixed step (S.4), identical in every thread
+                float dj[G];
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    dj[g] = 0.f;
+                    if (g < gn) {
+                        const float gs = sum_partials_16(cp + g * kRegConsWarps);
+                        const float xn = best_response_step(bv, cf[g], gs, gamma);
+                        const float dlt = xn - cf[g].x;
+                        if (!*abort_flag) {
+                            if (tid == 0) bv.x[bv.c0 + j0 + g] = static_cast<TX>(xn);
+                            dj[g] = dlt * cf[g].scale;
+                            any |= dlt != 0.f;
+                        }
+                    }
                 }
+                buf ^= 1;
                 // ---- fold a_j * Delta_j into the register increment (units past the column
                 // hold zeros)
-                if (dj != 0.f) {
 #pragma unroll
-                    for (int k = 0; k < UPT; ++k) {
-                        float a[V];
-                        ATraits<TA>::unpack(colr[k], a);
+                for (int g = 0; g < G; ++g) {
+                    if (dj[g] != 0.f) {
 #pragma unroll
-                        for (int e = 0; e < V; ++e) inc[k][e] = fmaf(a[e], dj, inc[k][e]);
+                        for (int k = 0; k < UPT; ++k) {
+                            float a[V];
+                            ATraits<TA>::unpack(colr[g][k], a);
+#pragma unroll
+                            for (int e = 0; e < V; ++e) inc[k][e] = fmaf(a[e], dj[g], inc[k][e]);
+                        }
                     }
                 }
             }
