@@ -176,7 +176,8 @@ typedef struct {
     int64_t sweep_kernel_sweeps;   /* profile=1: sweeps performed by those launches */
     int32_t status;             /* asyflexa_status of the last solve/check */
     int32_t checked;            /* 1 if the stat_* / kkt fields were evaluated */
-    int64_t polish_sweeps;      /* with A_master: sweeps of the last solve run on the FP32 copy */
+    int64_t polish_sweeps;      /* with A_master: sweeps of the last solve run on the FP32 copy;
+                                   multi-lane form: sweeps of the single-lane finish of a lane */
     double polish_seconds;      /* with A_master: device time of that FP32 phase */
     int32_t block_w;            /* batched solve: block width used (given or autotuned) */
     int32_t kernel_variant;     /* async sweep kernel this handle launches (1, 2 or 3, see
@@ -479,7 +480,13 @@ int asyflexa_multi_create(asyflexa_multi_t* h, const asyflexa_problem* prob, int
 /* Solve all lanes from the iterates in X (device FP32, lane l's x at X + l * ldx, ldx >= n),
  * written back in place.  A lane is done when (F - f_star[l]) / |f_star[l]| <= tol_gap (or,
  * with f_star NULL or NaN, when a check interval lowers F by <= switch_tol |F|) and its
- * ||xhat(x) - x||_inf / max(1, ||x||_inf) <= tol_stat.  per (k entries) and total may be NULL.
+ * ||xhat(x) - x||_inf / max(1, ||x||_inf) <= tol_stat.  The in-loop test uses the tensor-core
+ * gradients; when every lane has passed it, each lane is confirmed by the exact check of
+ * asyflexa_check at its returned iterate (FP64 residual, exact gradient), and a lane that fails
+ * it is finished from its iterate by the single-lane solver (FP32 products, exact checks;
+ * per[l].polish_sweeps counts its sweeps) within the sweeps left.  per (k entries; F, gap,
+ * stationarity, KKT measures and nnz of the exact check) and total may be NULL.  B (the
+ * data vectors, lane l's b at B + l * ldb) must stay valid for the life of the handle.
  * Returns OK when every lane is done, ENOTCONV at max_sweeps, or an error. */
 int asyflexa_multi_solve(asyflexa_multi_t h, void* X, int64_t ldx, const double* f_star, asyflexa_stats* per,
                          asyflexa_stats* total);

@@ -46,10 +46,14 @@ struct asyflexa_multi_s {
     cudaStream_t stream = nullptr;
     std::vector<double> lam;
     double* lam_d = nullptr;
+    const float* B = nullptr;  // the caller's k x ldb data vectors (lane l at B + l ldb)
+    int64_t ldb = 0;
     double* Bm = nullptr;     // m x kp: -b of every lane (initial residual)
     double* R = nullptr;      // m x kp
     float* X = nullptr;       // n x kp
     float* G = nullptr;       // n x kp (checks)
+    float* dinv = nullptr;    // n: 1/d_j (FP32)
+    float* thr = nullptr;     // n x kp: lam_l / d_j (FP32)
     double* norms = nullptr;  // 3 kp
     unsigned long long* meas = nullptr;  // 2 kp
     unsigned long long* counters = nullptr;
@@ -71,6 +75,8 @@ int launch_multi(asyflexa_multi_s& H, int mode, int sweeps) {
     p.X = H.X;
     p.dw = H.base->dw;
     p.lam = H.lam_d;
+    p.dinv = H.dinv;
+    p.thr = H.thr;
     p.gamma = H.opts.gamma;
     p.kp = H.kp;
     p.nblocks = static_cast<int>((H.n + asyflexa::kMW - 1) / asyflexa::kMW);
@@ -158,6 +164,47 @@ int multi_stationarity(asyflexa_multi_s& H, std::vector<double>& stat) {
     return ASYFLEXA_OK;
 }
 
+// The exact check of asyflexa_check (FP64 residual from the nonzero columns, F, the gap with
+// f_star_l, ||xhat(x) - x||_inf / max(1, ||x||_inf) from an exact gradient) for lane l at its
+// iterate x_l (the caller's layout): the lane-0 handle is pointed at lane l's b and lambda for
+// the call, then back at lane 0.
+int multi_lane_check(asyflexa_multi_s& H, int l, const float* x_l, double f_star_l, asyflexa_stats* st) {
+    asyflexa_s& b = *H.base;
+    b.prob.b = H.B + static_cast<int64_t>(l) * H.ldb;
+    b.prob.lambda = H.lam[l];
+    b.opts.f_star = f_star_l;
+    b.r_valid = false;
+    std::memset(st, 0, sizeof *st);
+    const int rc = asyflexa_check(H.base, x_l, st);
+    b.prob.b = H.B;
+    b.prob.lambda = H.lam[0];
+    b.opts.f_star = NAN;
+    b.r_valid = false;
+    if (rc) return mfail(std::string("lane check: ") + asyflexa_last_error(H.base), rc);
+    return ASYFLEXA_OK;
+}
+
+// Finishes lane l from its iterate x_l (the caller's layout) with the single-lane solver (FP32
+// products, exact checks), at most max_sweeps sweeps: for a lane whose tensor-core iterate the
+// exact check rejects.  st: the solve's statistics.
+int multi_lane_polish(asyflexa_multi_s& H, int l, float* x_l, double f_star_l, int max_sweeps, asyflexa_stats* st) {
+    asyflexa_s& b = *H.base;
+    b.prob.b = H.B + static_cast<int64_t>(l) * H.ldb;
+    b.prob.lambda = H.lam[l];
+    b.opts.f_star = f_star_l;
+    b.opts.max_sweeps = max_sweeps;
+    b.r_valid = false;
+    std::memset(st, 0, sizeof *st);
+    const int rc = asyflexa_solve(H.base, x_l, st);
+    b.prob.b = H.B;
+    b.prob.lambda = H.lam[0];
+    b.opts.f_star = NAN;
+    b.opts.max_sweeps = H.opts.max_sweeps;
+    b.r_valid = false;
+    if (rc < 0) return mfail(std::string("lane polish: ") + asyflexa_last_error(H.base), rc);
+    return ASYFLEXA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -165,7 +212,7 @@ extern "C" {
 int asyflexa_multi_destroy(asyflexa_multi_t H) {
     if (!H) return ASYFLEXA_OK;
     if (H->stream) cudaStreamSynchronize(H->stream);
-    void* ptrs[] = {H->lam_d, H->Bm, H->R, H->X, H->G, H->norms, H->meas, H->counters, H->hist};
+    void* ptrs[] = {H->lam_d, H->Bm, H->R, H->X, H->G, H->norms, H->meas, H->counters, H->hist, H->dinv, H->thr};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (H->base) asyflexa_destroy(H->base);
@@ -206,6 +253,8 @@ int asyflexa_multi_create(asyflexa_multi_t* out, const asyflexa_problem* prob, i
     if (rc) return fail(mfail(std::string("lane 0: ") + asyflexa_last_error(nullptr), rc));
     H->opts = o;
     H->stream = static_cast<cudaStream_t>(stream);
+    H->B = static_cast<const float*>(B);
+    H->ldb = ldb;
     H->k = k;
     H->kp = k <= 8 ? 8 : k <= 16 ? 16 : k <= 32 ? 32 : 64;
     H->m = prob->m;
@@ -224,6 +273,8 @@ int asyflexa_multi_create(asyflexa_multi_t* out, const asyflexa_problem* prob, i
     if (e == cudaSuccess) e = cudaMalloc(&H->R, H->m * H->kp * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&H->X, H->n * H->kp * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&H->G, H->n * H->kp * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&H->dinv, H->n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&H->thr, H->n * H->kp * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&H->norms, 3 * H->kp * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&H->meas, 2 * H->kp * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&H->counters, 4 * sizeof(unsigned long long));
@@ -247,6 +298,18 @@ int asyflexa_multi_create(asyflexa_multi_t* out, const asyflexa_problem* prob, i
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return fail(mfail(std::string("multi set-up: ") + cudaGetErrorString(e), ASYFLEXA_ECUDA));
+    }
+    // the elementwise step's coefficient tables
+    {
+        const int grid = H->base->sm_count * 4;
+        switch (H->kp) {
+            case 8: asyflexa::multi_coef_kernel<8><<<grid, 256, 0, H->stream>>>(H->base->dw, H->lam_d, H->n, H->dinv, H->thr); break;
+            case 16: asyflexa::multi_coef_kernel<16><<<grid, 256, 0, H->stream>>>(H->base->dw, H->lam_d, H->n, H->dinv, H->thr); break;
+            case 32: asyflexa::multi_coef_kernel<32><<<grid, 256, 0, H->stream>>>(H->base->dw, H->lam_d, H->n, H->dinv, H->thr); break;
+            default: asyflexa::multi_coef_kernel<64><<<grid, 256, 0, H->stream>>>(H->base->dw, H->lam_d, H->n, H->dinv, H->thr); break;
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(mfail(std::string("multi set-up: ") + cudaGetErrorString(e), ASYFLEXA_ECUDA));
     }
     // Bm = -B laid out m x kp
     asyflexa::multi_transpose_kernel<float, double><<<H->base->sm_count * 2, 256, 0, H->stream>>>(
@@ -277,6 +340,12 @@ int asyflexa_multi_solve(asyflexa_multi_t H, void* X, int64_t ldx, const double*
     long long sweeps = 0;
     int since_refresh = 0;
     const int step = std::max(1, std::min(H->opts.check_every, H->opts.refresh_every));
+    // A lane that the in-loop test (tensor-core gradients) passes is confirmed by the exact check
+    // at its returned iterate.  The split-TF32 products put the multi-lane fixed point up to
+    // about 1e-6 away in that measure, so a lane the exact check rejects is finished by the
+    // single-lane solver from its iterate (its FP32 products and exact checks).
+    std::vector<asyflexa_stats> exact(k);
+    std::vector<long long> polish(k, 0);
     while (sweeps < H->opts.max_sweeps) {
         const int ks = static_cast<int>(std::min<long long>(step, H->opts.max_sweeps - sweeps));
         rc = launch_multi(*H, 0, ks);
@@ -296,7 +365,8 @@ int asyflexa_multi_solve(asyflexa_multi_t H, void* X, int64_t ldx, const double*
             if (done[l]) continue;
             const bool known = f_star && std::isfinite(f_star[l]);
             const bool gap_ok = known ? (F[l] - f_star[l]) / std::fabs(f_star[l]) <= H->opts.tol_gap
-                                      : std::isfinite(Fprev[l]) && Fprev[l] - F[l] <= H->opts.switch_tol * std::fabs(F[l]);
+                                      : std::isfinite(Fprev[l]) &&
+                                            Fprev[l] - F[l] <= H->opts.switch_tol * std::fabs(F[l]);
             if (gap_ok) need_stat = true;
             Fprev[l] = F[l];
         }
@@ -316,14 +386,28 @@ int asyflexa_multi_solve(asyflexa_multi_t H, void* X, int64_t ldx, const double*
         }
         if (std::all_of(done.begin(), done.end(), [](int d) { return d != 0; })) break;
     }
-    // final evaluation at the returned iterates (exact residual, objective, stationarity)
-    rc = multi_refresh(*H);
-    if (!rc) rc = multi_objective(*H, F, nnz);
-    if (!rc) rc = multi_stationarity(*H, stat);
-    if (rc) return rc;
     asyflexa::multi_transpose_kernel<float, float><<<H->base->sm_count * 2, 256, 0, H->stream>>>(
         H->X, 0, static_cast<float*>(X), ldx, H->n, H->k, H->kp, 1, 1.0);
     MCK(cudaGetLastError(), "scatter iterates");
+    for (int l = 0; l < k; ++l) {
+        const double fsl = f_star ? f_star[l] : NAN;
+        float* xl = static_cast<float*>(X) + static_cast<int64_t>(l) * ldx;
+        rc = multi_lane_check(*H, l, xl, fsl, &exact[l]);
+        if (rc) return rc;
+        const bool gap_ok = !std::isfinite(fsl) || exact[l].rel_gap <= H->opts.tol_gap;
+        if (!done[l] || (gap_ok && exact[l].stat_xhat <= H->opts.tol_stat)) continue;
+        const long long left = H->opts.max_sweeps - sweeps;
+        asyflexa_stats ps;
+        if (left <= 0) {
+            done[l] = 0;
+            continue;
+        }
+        rc = multi_lane_polish(*H, l, xl, fsl, static_cast<int>(left), &ps);
+        if (rc) return rc;
+        polish[l] = ps.sweeps;
+        exact[l] = ps;
+        done[l] = ps.status == ASYFLEXA_OK ? 1 : 0;
+    }
     MCK(cudaEventRecord(e1, H->stream), "event record");
     MCK(cudaEventSynchronize(e1), "event sync");
     float ms = 0.f;
@@ -338,16 +422,11 @@ int asyflexa_multi_solve(asyflexa_multi_t H, void* X, int64_t ldx, const double*
         if (per) {
             asyflexa_stats s;
             std::memset(&s, 0, sizeof s);
-            s.sweeps = done[l] ? conv_sweeps[l] : sweeps;
+            s = exact[l];  // F, gap, stationarity, KKT measures and nnz of the exact check
+            s.sweeps = (conv_sweeps[l] >= 0 ? conv_sweeps[l] : sweeps) + polish[l];
+            s.polish_sweeps = polish[l];
             s.block_updates = s.sweeps * nblocks;
-            s.F = F[l];
-            const bool known = f_star && std::isfinite(f_star[l]);
-            s.rel_gap = known ? (F[l] - f_star[l]) / std::fabs(f_star[l]) : NAN;
-            s.stat_xhat = stat[l];
-            s.stat_mf = NAN;
-            s.kkt_viol = NAN;
-            s.dual_gap = NAN;
-            s.nnz = static_cast<long long>(nnz[l]);
+            s.seconds = 0.0;
             s.status = st;
             s.checked = 1;
             s.block_w = asyflexa::kMW;

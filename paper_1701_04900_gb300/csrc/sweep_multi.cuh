@@ -18,6 +18,7 @@
 // Delta, added to R with FP64 atomics).
 #pragma once
 
+#include "convert.cuh"
 #include "ptx.cuh"
 #include "sweep.cuh"
 #include "types.cuh"
@@ -38,6 +39,8 @@ struct MultiParams {
     float* X;             // n x kp (row-major)
     const double* dw;     // n surrogate weights (shared by the lanes)
     const double* lam;    // kp (padding lanes: +inf)
+    const float* dinv;    // n: 1/d_j rounded to FP32 (0 where d_j <= 0)
+    const float* thr;     // n x kp: lam_l / d_j rounded to FP32 (0 where d_j <= 0)
     double gamma;
     int kp, nblocks, sweeps;
     int mode;             // 0: sweep; 1: refresh (R += A X, no step); 2: gradient only (G out)
@@ -116,7 +119,7 @@ __device__ __forceinline__ void fetch_r_tile(const MultiParams& p, int64_t row0,
     for (int q = 0; q < kMT * KP / kMThreads; ++q) {
         const int i = threadIdx.x + kMThreads * q;
         const int64_t row = row0 + i / KP;
-        v[q] = row < p.m ? static_cast<float>(__ldcg(p.R + row * KP + i % KP)) : 0.f;
+        v[q] = row < p.m ? f64_to_f32(__ldcg(p.R + row * KP + i % KP)) : 0.f;  // integer pipes
     }
 }
 
@@ -239,12 +242,13 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
                     } else if (p.mode == 2) {
                         p.G[jj * KP + l] = s.g[j * kMRS + l];
                     } else {
-                        const double d = p.dw[jj];
+                        // the FP32 coefficients 1/d_j and lam_l/d_j come from tables made once per
+                        // handle (FP64 divisions are slow on GB300's narrow FP64 pipe)
+                        const float dinv = p.dinv[jj];
                         const float x = p.X[jj * KP + l];
                         float xh = 0.f;
-                        if (d > 0.0) {
-                            const float dinv = static_cast<float>(1.0 / d);
-                            const float thr = static_cast<float>(p.lam[l] / d);  // +inf for padding lanes
+                        if (dinv > 0.f) {
+                            const float thr = p.thr[jj * KP + l];  // +inf for padding lanes
                             const float v = fmaf(-s.g[j * kMRS + l], dinv, x);
                             const float av = fabsf(v) - thr;
                             xh = av > 0.f ? copysignf(av, v) : 0.f;
@@ -303,13 +307,14 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
                             for (int e = 0; e < 4; ++e) c[e] = c_hh[e] + (c_ab[e] + c_ba[e]);
                             const int l0 = nt * 8 + 2 * tig;
                             const int64_t r0 = row0 + t0, r1 = row0 + t0 + 8;
+                            // (the FP32 -> FP64 widening on the integer pipes: the FP64 pipe is narrow)
                             if (r0 < p.m) {
-                                if (c[0] != 0.f) red_add_f64(p.R + r0 * KP + l0, static_cast<double>(c[0]));
-                                if (c[1] != 0.f) red_add_f64(p.R + r0 * KP + l0 + 1, static_cast<double>(c[1]));
+                                if (c[0] != 0.f) red_add_f64(p.R + r0 * KP + l0, f32_to_f64(c[0]));
+                                if (c[1] != 0.f) red_add_f64(p.R + r0 * KP + l0 + 1, f32_to_f64(c[1]));
                             }
                             if (r1 < p.m) {
-                                if (c[2] != 0.f) red_add_f64(p.R + r1 * KP + l0, static_cast<double>(c[2]));
-                                if (c[3] != 0.f) red_add_f64(p.R + r1 * KP + l0 + 1, static_cast<double>(c[3]));
+                                if (c[2] != 0.f) red_add_f64(p.R + r1 * KP + l0, f32_to_f64(c[2]));
+                                if (c[3] != 0.f) red_add_f64(p.R + r1 * KP + l0 + 1, f32_to_f64(c[3]));
                             }
                         }
                     }
@@ -329,6 +334,20 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
                 atomicAdd(&p.counters[1], 1ull);
             }
         }
+    }
+}
+
+// The elementwise step's FP32 coefficients: dinv[j] = 1/d_j and thr[j KP + l] = lam_l / d_j,
+// each the FP64 quotient rounded to FP32 (0 where d_j <= 0).
+template <int KP>
+__global__ void multi_coef_kernel(const double* dw, const double* lam, int64_t n, float* dinv, float* thr) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n * KP;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t j = i / KP;
+        const int l = static_cast<int>(i % KP);
+        const double d = dw[j];
+        thr[i] = d > 0.0 ? static_cast<float>(lam[l] / d) : 0.f;
+        if (l == 0) dinv[j] = d > 0.0 ? static_cast<float>(1.0 / d) : 0.f;
     }
 }
 

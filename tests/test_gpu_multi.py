@@ -53,9 +53,9 @@ def test_multi_single_cta_is_gauss_seidel_per_lane(m, n, k):
 
 def test_multi_lambda_path_reaches_the_optimum():
     """A lambda path on a planted instance: every lane stops at stationarity <= 1e-6 as the
-    library measures it, the FP64 oracle confirms it to 5e-6 (the multi-lane residual and
-    gradients come from FP32-grade products: TF32 hi/lo splits, FP64 sums across blocks),
-    and the lambda = 1 lane reaches the planted optimum."""
+    library's exact check measures it (the tensor-core gradients only decide when to check),
+    the FP64 oracle confirms it (1.5e-6 allows for the FP32 iterate; the library's figure
+    agrees with the oracle's to 2e-8), and the lambda = 1 lane reaches the planted optimum."""
     import torch
     from paper_1701_04900_gb300.batch import MultiLaneSolver
     d = nesterov_lasso(1000, 4000, 40, lam=1.0, seed=70, store_dtype=np.float32)
@@ -73,8 +73,10 @@ def test_multi_lambda_path_reaches_the_optimum():
         p.lam = lam
         x = X[l].cpu().numpy().astype(np.float64)
         merit = O.stationarity(O.xhat_merit(p, x, O.surrogate_weights(p)), x)
-        assert merit <= 5e-6, (lam, merit)
-        assert O.objective(p, x) == pytest.approx(per[l]["F"], rel=1e-7)
+        assert merit <= 1.5e-6, (lam, merit)
+        assert per[l]["stat_xhat"] <= 1e-6
+        assert abs(per[l]["stat_xhat"] - merit) <= 2e-8, (lam, per[l]["stat_xhat"], merit)
+        assert O.objective(p, x) == pytest.approx(per[l]["F"], rel=1e-9)
     assert (per[-1]["F"] - f1) / f1 <= 1e-6
     ms.close()
 
@@ -89,6 +91,12 @@ def test_multi_many_lanes_padded_to_64():
     X = torch.zeros((40, d["n"]), dtype=torch.float32, device="cuda")
     per, tot = ms.solve(X)
     assert tot["status"] == 0
+    assert all(st["stat_xhat"] <= 1e-6 for st in per)
+    for l in (0, 20, 39):
+        q = O.Problem.from_data(d)
+        q.lam = lams[l]
+        xl = X[l].cpu().numpy().astype(np.float64)
+        assert O.stationarity(O.xhat_merit(q, xl, O.surrogate_weights(q)), xl) <= 1.5e-6, l
     p = O.Problem.from_data(d)
     x = X[-1].cpu().numpy().astype(np.float64)
     f1 = O.objective(p, d["x_star"])
