@@ -481,11 +481,12 @@ int asyflexa_multi_create(asyflexa_multi_t* h, const asyflexa_problem* prob, int
  * written back in place.  A lane is done when (F - f_star[l]) / |f_star[l]| <= tol_gap (or,
  * with f_star NULL or NaN, when a check interval lowers F by <= switch_tol |F|) and its
  * ||xhat(x) - x||_inf / max(1, ||x||_inf) <= tol_stat.  The in-loop test uses the tensor-core
- * gradients; when every lane has passed it, each lane is confirmed by the exact check of
- * asyflexa_check at its returned iterate (FP64 residual, exact gradient), and a lane that fails
- * it is finished from its iterate by the single-lane solver (FP32 products, exact checks;
- * per[l].polish_sweeps counts its sweeps) within the sweeps left.  per (k entries; F, gap,
- * stationarity, KKT measures and nnz of the exact check) and total may be NULL.  B (the
+ * gradients; when every lane has passed it, every lane is checked exactly at its returned
+ * iterate (r = A x - b and A^T r of all lanes with error-free FP32 products and sums, as
+ * accurate as FP64 accumulation), and a lane that fails that check is finished from its
+ * iterate by the single-lane solver (FP32 products, exact checks; per[l].polish_sweeps counts
+ * its sweeps) within the sweeps left.  per (k entries; F, gap, stationarity and nnz of the
+ * exact check, or the finishing solve's statistics) and total may be NULL.  B (the
  * data vectors, lane l's b at B + l * ldb) must stay valid for the life of the handle.
  * Returns OK when every lane is done, ENOTCONV at max_sweeps, or an error. */
 int asyflexa_multi_solve(asyflexa_multi_t h, void* X, int64_t ldx, const double* f_star, asyflexa_stats* per,

@@ -52,6 +52,9 @@ struct asyflexa_multi_s {
     double* R = nullptr;      // m x kp
     float* X = nullptr;       // n x kp
     float* G = nullptr;       // n x kp (checks)
+    double* Rx = nullptr;     // m x kp: exact residuals (checks)
+    float2* Rhl = nullptr;    // m x kp: the same as FP32 (hi, lo) pairs
+    double* Gx = nullptr;     // n x kp: exact gradients (checks)
     float* dinv = nullptr;    // n: 1/d_j (FP32)
     float* thr = nullptr;     // n x kp: lam_l / d_j (FP32)
     double* norms = nullptr;  // 3 kp
@@ -104,18 +107,20 @@ int multi_refresh(asyflexa_multi_s& H) {
 }
 
 template <int KP>
-void launch_norms(asyflexa_multi_s& H) {
-    asyflexa::multi_norms_kernel<KP><<<H.base->sm_count * 2, 256, 0, H.stream>>>(H.R, H.m, H.X, H.n, H.norms);
+void launch_norms(asyflexa_multi_s& H, const double* R) {
+    asyflexa::multi_norms_kernel<KP><<<H.base->sm_count * 2, 256, 0, H.stream>>>(R, H.m, H.X, H.n, H.norms);
 }
 
-// Per-lane F = 0.5 ||r||^2 + lam ||x||_1 and nnz.  Synchronises.
-int multi_objective(asyflexa_multi_s& H, std::vector<double>& F, std::vector<double>& nnz) {
+// Per-lane F = 0.5 ||r||^2 + lam ||x||_1 and nnz from the residuals R (the sweeps' by default).
+// Synchronises.
+int multi_objective(asyflexa_multi_s& H, std::vector<double>& F, std::vector<double>& nnz, const double* R = nullptr) {
+    if (!R) R = H.R;
     MCK(cudaMemsetAsync(H.norms, 0, 3 * H.kp * sizeof(double), H.stream), "clear norms");
     switch (H.kp) {
-        case 8: launch_norms<8>(H); break;
-        case 16: launch_norms<16>(H); break;
-        case 32: launch_norms<32>(H); break;
-        default: launch_norms<64>(H); break;
+        case 8: launch_norms<8>(H, R); break;
+        case 16: launch_norms<16>(H, R); break;
+        case 32: launch_norms<32>(H, R); break;
+        default: launch_norms<64>(H, R); break;
     }
     ++H.launches;
     MCK(cudaGetLastError(), "norms launch");
@@ -164,23 +169,45 @@ int multi_stationarity(asyflexa_multi_s& H, std::vector<double>& stat) {
     return ASYFLEXA_OK;
 }
 
-// The exact check of asyflexa_check (FP64 residual from the nonzero columns, F, the gap with
-// f_star_l, ||xhat(x) - x||_inf / max(1, ||x||_inf) from an exact gradient) for lane l at its
-// iterate x_l (the caller's layout): the lane-0 handle is pointed at lane l's b and lambda for
-// the call, then back at lane 0.
-int multi_lane_check(asyflexa_multi_s& H, int l, const float* x_l, double f_star_l, asyflexa_stats* st) {
-    asyflexa_s& b = *H.base;
-    b.prob.b = H.B + static_cast<int64_t>(l) * H.ldb;
-    b.prob.lambda = H.lam[l];
-    b.opts.f_star = f_star_l;
-    b.r_valid = false;
-    std::memset(st, 0, sizeof *st);
-    const int rc = asyflexa_check(H.base, x_l, st);
-    b.prob.b = H.B;
-    b.prob.lambda = H.lam[0];
-    b.opts.f_star = NAN;
-    b.r_valid = false;
-    if (rc) return mfail(std::string("lane check: ") + asyflexa_last_error(H.base), rc);
+template <int KP>
+void launch_exact(asyflexa_multi_s& H) {
+    const int gr = static_cast<int>((H.m + asyflexa::kXT - 1) / asyflexa::kXT);
+    const int gg = static_cast<int>((H.n + asyflexa::kXT - 1) / asyflexa::kXT);
+    const float* A = static_cast<const float*>(H.base->prob.A);
+    asyflexa::multi_exact_residual_kernel<KP><<<gr, 256, 0, H.stream>>>(A, H.base->prob.lda, H.m, H.n, H.X, H.B,
+                                                                        H.ldb, H.k, H.Rx, H.Rhl);
+    asyflexa::multi_exact_grad_kernel<KP><<<gg, 256, 0, H.stream>>>(A, H.base->prob.lda, H.m, H.n, H.Rhl, H.Gx);
+    asyflexa::multi_stat64_kernel<KP><<<H.base->sm_count * 4, 256, 0, H.stream>>>(H.Gx, H.X, H.base->dw, H.lam_d,
+                                                                                   H.n, H.meas);
+}
+
+// The exact check of every lane at the current iterates: R = A X - B and G = A^T R with
+// error-free FP32 products and sums (FP64-grade), then per lane F, nnz and
+// ||xhat(x) - x||_inf / max(1, ||x||_inf).  Synchronises.
+int multi_exact_check(asyflexa_multi_s& H, std::vector<double>& F, std::vector<double>& nnz,
+                      std::vector<double>& stat) {
+    MCK(cudaMemsetAsync(H.meas, 0, 2 * H.kp * sizeof(unsigned long long), H.stream), "clear measures");
+    switch (H.kp) {
+        case 8: launch_exact<8>(H); break;
+        case 16: launch_exact<16>(H); break;
+        case 32: launch_exact<32>(H); break;
+        default: launch_exact<64>(H); break;
+    }
+    H.launches += 3;
+    MCK(cudaGetLastError(), "exact check launch");
+    int rc = multi_objective(H, F, nnz, H.Rx);
+    if (rc) return rc;
+    std::vector<unsigned long long> v(2 * H.kp);
+    MCK(cudaMemcpyAsync(v.data(), H.meas, v.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, H.stream),
+        "read measures");
+    MCK(cudaStreamSynchronize(H.stream), "synchronize");
+    stat.assign(H.k, 0.0);
+    for (int l = 0; l < H.k; ++l) {
+        double dx, ax;
+        std::memcpy(&dx, &v[l], sizeof dx);
+        std::memcpy(&ax, &v[H.kp + l], sizeof ax);
+        stat[l] = dx / std::max(1.0, ax);
+    }
     return ASYFLEXA_OK;
 }
 
@@ -212,7 +239,7 @@ extern "C" {
 int asyflexa_multi_destroy(asyflexa_multi_t H) {
     if (!H) return ASYFLEXA_OK;
     if (H->stream) cudaStreamSynchronize(H->stream);
-    void* ptrs[] = {H->lam_d, H->Bm, H->R, H->X, H->G, H->norms, H->meas, H->counters, H->hist, H->dinv, H->thr};
+    void* ptrs[] = {H->lam_d, H->Bm, H->R, H->X, H->G, H->norms, H->meas, H->counters, H->hist, H->dinv, H->thr, H->Rx, H->Rhl, H->Gx};
     for (void* q : ptrs)
         if (q) cudaFree(q);
     if (H->base) asyflexa_destroy(H->base);
@@ -274,6 +301,9 @@ int asyflexa_multi_create(asyflexa_multi_t* out, const asyflexa_problem* prob, i
     if (e == cudaSuccess) e = cudaMalloc(&H->X, H->n * H->kp * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&H->G, H->n * H->kp * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&H->dinv, H->n * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&H->Rx, H->m * H->kp * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&H->Rhl, H->m * H->kp * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&H->Gx, H->n * H->kp * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&H->thr, H->n * H->kp * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&H->norms, 3 * H->kp * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&H->meas, 2 * H->kp * sizeof(unsigned long long));
@@ -386,26 +416,37 @@ int asyflexa_multi_solve(asyflexa_multi_t H, void* X, int64_t ldx, const double*
         }
         if (std::all_of(done.begin(), done.end(), [](int d) { return d != 0; })) break;
     }
+    // the exact check of every lane at its iterate; a lane the in-loop test passed but the exact
+    // check rejects is finished by the single-lane solver
+    std::vector<double> Fx, nnzx, statx;
+    rc = multi_exact_check(*H, Fx, nnzx, statx);
+    if (rc) return rc;
     asyflexa::multi_transpose_kernel<float, float><<<H->base->sm_count * 2, 256, 0, H->stream>>>(
         H->X, 0, static_cast<float*>(X), ldx, H->n, H->k, H->kp, 1, 1.0);
     MCK(cudaGetLastError(), "scatter iterates");
     for (int l = 0; l < k; ++l) {
         const double fsl = f_star ? f_star[l] : NAN;
-        float* xl = static_cast<float*>(X) + static_cast<int64_t>(l) * ldx;
-        rc = multi_lane_check(*H, l, xl, fsl, &exact[l]);
-        if (rc) return rc;
-        const bool gap_ok = !std::isfinite(fsl) || exact[l].rel_gap <= H->opts.tol_gap;
-        if (!done[l] || (gap_ok && exact[l].stat_xhat <= H->opts.tol_stat)) continue;
+        asyflexa_stats& q = exact[l];
+        std::memset(&q, 0, sizeof q);
+        q.F = Fx[l];
+        q.rel_gap = std::isfinite(fsl) ? (Fx[l] - fsl) / std::fabs(fsl) : NAN;
+        q.stat_xhat = statx[l];
+        q.stat_mf = q.kkt_viol = q.dual_gap = NAN;
+        q.nnz = static_cast<long long>(nnzx[l]);
+        q.checked = 1;
+        const bool gap_ok = !std::isfinite(fsl) || q.rel_gap <= H->opts.tol_gap;
+        if (!done[l] || (gap_ok && q.stat_xhat <= H->opts.tol_stat)) continue;
         const long long left = H->opts.max_sweeps - sweeps;
-        asyflexa_stats ps;
         if (left <= 0) {
             done[l] = 0;
             continue;
         }
+        asyflexa_stats ps;
+        float* xl = static_cast<float*>(X) + static_cast<int64_t>(l) * ldx;
         rc = multi_lane_polish(*H, l, xl, fsl, static_cast<int>(left), &ps);
         if (rc) return rc;
         polish[l] = ps.sweeps;
-        exact[l] = ps;
+        q = ps;
         done[l] = ps.status == ASYFLEXA_OK ? 1 : 0;
     }
     MCK(cudaEventRecord(e1, H->stream), "event record");

@@ -28,6 +28,8 @@ namespace asyflexa {
 constexpr int kMW = 32;               // block width (columns)
 constexpr int kMT = 64;               // rows per tile
 constexpr int kMThreads = 256;        // 8 warps
+constexpr int kMWarps = kMThreads / 32;
+constexpr int kMAR = kMW * kMT / kMThreads;  // rows of an A tile column per thread
 constexpr int kMKMax = 64;            // lanes (padded) per launch
 constexpr int kMAS = kMT + 4;         // A tile stride (floats): conflict-free fragment loads
 constexpr int kMRS = kMKMax + 8;      // R tile / Delta stride (floats)
@@ -88,23 +90,25 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const float (&a)[4], con
 }
 
 // The A tile rows [row0, row0 + kMT) of columns c0 .. c0 + wb - 1 (zeros elsewhere): thread t
-// holds 8 consecutive rows of column t / 8.  fetch loads them into registers (the next tile's
-// loads overlap the current tile's MMAs); store splits them into TF32 hi / lo in shared memory.
-__device__ __forceinline__ void fetch_a_tile(const MultiParams& p, int64_t c0, int wb, int64_t row0, float (&v)[8]) {
-    const int j = threadIdx.x >> 3;
-    const int t0 = (threadIdx.x & 7) * 8;
+// holds kMAR consecutive rows of column t / (kMT / kMAR).  fetch loads them into registers (the
+// next tile's loads overlap the current tile's MMAs); store splits them into TF32 hi / lo in
+// shared memory.
+__device__ __forceinline__ void fetch_a_tile(const MultiParams& p, int64_t c0, int wb, int64_t row0,
+                                             float (&v)[kMAR]) {
+    const int j = threadIdx.x / (kMT / kMAR);
+    const int t0 = (threadIdx.x % (kMT / kMAR)) * kMAR;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < kMAR; ++e) {
         const int64_t row = row0 + t0 + e;
         v[e] = (j < wb && row < p.m) ? __ldg(p.A + (c0 + j) * p.lda + row) : 0.f;
     }
 }
 
-__device__ __forceinline__ void store_a_tile(MultiSmem& s, const float (&v)[8]) {
-    const int j = threadIdx.x >> 3;
-    const int t0 = (threadIdx.x & 7) * 8;
+__device__ __forceinline__ void store_a_tile(MultiSmem& s, const float (&v)[kMAR]) {
+    const int j = threadIdx.x / (kMT / kMAR);
+    const int t0 = (threadIdx.x % (kMT / kMAR)) * kMAR;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
+    for (int e = 0; e < kMAR; ++e) {
         float hi, lo;
         split_tf32(v[e], hi, lo);
         s.a_hi[j * kMAS + t0 + e] = hi;
@@ -119,7 +123,7 @@ __device__ __forceinline__ void fetch_r_tile(const MultiParams& p, int64_t row0,
     for (int q = 0; q < kMT * KP / kMThreads; ++q) {
         const int i = threadIdx.x + kMThreads * q;
         const int64_t row = row0 + i / KP;
-        v[q] = row < p.m ? f64_to_f32(__ldcg(p.R + row * KP + i % KP)) : 0.f;  // integer pipes
+        v[q] = row < p.m ? static_cast<float>(__ldcg(p.R + row * KP + i % KP)) : 0.f;
     }
 }
 
@@ -147,9 +151,9 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
     const int tig = lane & 3;   // thread in group
     constexpr int kNT = KP / 8;                 // n tiles (lanes)
     constexpr int kP1 = 2 * kNT;                // gradient pass: (m tile, n tile) pairs over j
-    constexpr int kP1W = (kP1 + 7) / 8;         // pairs per warp
+    constexpr int kP1W = (kP1 + kMWarps - 1) / kMWarps;  // pairs per warp
     constexpr int kP2 = (kMT / 16) * kNT;       // scatter pass: pairs over rows
-    constexpr int kP2W = (kP2 + 7) / 8;
+    constexpr int kP2W = (kP2 + kMWarps - 1) / kMWarps;
     __shared__ int s_any;
     __shared__ unsigned long long s_uread;
 
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc_hi[q][e] = acc_lo[q][e] = 0.f;
             if (p.mode != 1) {
-                float av[8], rv[kMT * KP / kMThreads];
+                float av[kMAR], rv[kMT * KP / kMThreads];
                 fetch_a_tile(p, c0, wb, 0, av);
                 fetch_r_tile<KP>(p, 0, rv);
                 for (int64_t row0 = 0; row0 < p.m; row0 += kMT) {
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
                     __syncthreads();
 #pragma unroll
                     for (int q = 0; q < kP1W; ++q) {
-                        const int pr = warp + 8 * q;
+                        const int pr = warp + kMWarps * q;
                         if (pr < kP1) {
                             const int mt = pr / kNT, nt = pr % kNT;
                             const int j0 = mt * 16 + grp;
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
             // G to shared memory (fragment rows = columns j, fragment columns = lanes)
 #pragma unroll
             for (int q = 0; q < kP1W; ++q) {
-                const int pr = warp + 8 * q;
+                const int pr = warp + kMWarps * q;
                 if (pr < kP1) {
                     const int mt = pr / kNT, nt = pr % kNT;
                     const int j0 = mt * 16 + grp, l0 = nt * 8 + 2 * tig;
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
             __syncthreads();
             // ---- scatter pass: R += A_i Delta (FP64 atomics; rows >= m skipped)
             if (s_any && p.mode != 2) {
-                float av[8];
+                float av[kMAR];
                 fetch_a_tile(p, c0, wb, 0, av);
                 for (int64_t row0 = 0; row0 < p.m; row0 += kMT) {
                     store_a_tile(s, av);
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
                     if (row0 + kMT < p.m) fetch_a_tile(p, c0, wb, row0 + kMT, av);
 #pragma unroll
                     for (int q = 0; q < kP2W; ++q) {
-                        const int pr = warp + 8 * q;
+                        const int pr = warp + kMWarps * q;
                         if (pr < kP2) {
                             const int mt = pr / kNT, nt = pr % kNT;
                             const int t0 = mt * 16 + grp;
@@ -307,14 +311,13 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
                             for (int e = 0; e < 4; ++e) c[e] = c_hh[e] + (c_ab[e] + c_ba[e]);
                             const int l0 = nt * 8 + 2 * tig;
                             const int64_t r0 = row0 + t0, r1 = row0 + t0 + 8;
-                            // (the FP32 -> FP64 widening on the integer pipes: the FP64 pipe is narrow)
                             if (r0 < p.m) {
-                                if (c[0] != 0.f) red_add_f64(p.R + r0 * KP + l0, f32_to_f64(c[0]));
-                                if (c[1] != 0.f) red_add_f64(p.R + r0 * KP + l0 + 1, f32_to_f64(c[1]));
+                                if (c[0] != 0.f) red_add_f64(p.R + r0 * KP + l0, static_cast<double>(c[0]));
+                                if (c[1] != 0.f) red_add_f64(p.R + r0 * KP + l0 + 1, static_cast<double>(c[1]));
                             }
                             if (r1 < p.m) {
-                                if (c[2] != 0.f) red_add_f64(p.R + r1 * KP + l0, f32_to_f64(c[2]));
-                                if (c[3] != 0.f) red_add_f64(p.R + r1 * KP + l0 + 1, f32_to_f64(c[3]));
+                                if (c[2] != 0.f) red_add_f64(p.R + r1 * KP + l0, static_cast<double>(c[2]));
+                                if (c[3] != 0.f) red_add_f64(p.R + r1 * KP + l0 + 1, static_cast<double>(c[3]));
                             }
                         }
                     }
@@ -401,6 +404,137 @@ __global__ void __launch_bounds__(256) multi_transpose_kernel(const TS* src, int
 template <int KP>
 __global__ void __launch_bounds__(256) multi_stat_kernel(const float* G, const float* X, const double* dw,
                                                          const double* lam, int64_t n, unsigned long long* out) {
+    const int64_t total = n * KP;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t j = i / KP;
+        const int l = static_cast<int>(i % KP);
+        const double x = X[i], d = dw[j], g = G[i];
+        double xh = 0.0;
+        if (d > 0.0) {
+            const double v = x - g / d;
+            const double av = fabs(v) - lam[l] / d;
+            xh = av > 0.0 ? copysign(av, v) : 0.0;
+        }
+        const double dx = fabs(xh - x), ax = fabs(x);
+        if (dx > 0.0) atomicMax(&out[l], static_cast<unsigned long long>(__double_as_longlong(dx)));
+        if (ax > 0.0) atomicMax(&out[KP + l], static_cast<unsigned long long>(__double_as_longlong(ax)));
+    }
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Exact checks of all lanes at once (CUDA cores, error-free FP32 products and sums: Dot2 of
+// Ogita, Rump and Oishi), as accurate as FP64 accumulation: the multi-lane sweeps' split-TF32
+// products are FP32-grade, which puts their stationarity measure up to ~1e-6 off.
+// ---------------------------------------------------------------------------------------
+
+constexpr int kXT = 32;  // rows (residual) or columns (gradient) per CTA of the exact checks
+
+// R = A X - B for every lane: a CTA owns kXT rows and every lane (thread t: row t mod 32, lanes
+// t/32 + 8 q); the columns whose lanes are all zero are skipped.  B: the caller's k x ldb data
+// vectors (lanes >= k: 0).  R: m x KP, FP64; Rhl: the same as FP32 (hi, lo) pairs, R = hi + lo
+// to about 2^-48 relative, for the gradient kernel.
+template <int KP>
+__global__ void __launch_bounds__(256) multi_exact_residual_kernel(const float* A, int64_t lda, int64_t m, int64_t n,
+                                                                   const float* X, const float* B, int64_t ldb, int k,
+                                                                   double* R, float2* Rhl) {
+    constexpr int LPT = KP / 8;  // lanes per thread
+    __shared__ float sA[kXT][kXT + 1];   // [column][row]
+    __shared__ float sX[kXT][KP];        // [column][lane]
+    __shared__ int sNz[kXT];
+    const int tid = threadIdx.x;
+    const int rl = tid & 31, lg = tid >> 5;
+    const int64_t row0 = static_cast<int64_t>(blockIdx.x) * kXT;
+    DFAcc acc[LPT];
+    for (int64_t j0 = 0; j0 < n; j0 += kXT) {
+        __syncthreads();  // previous chunk consumed
+        for (int i = tid; i < kXT * KP; i += 256) {
+            const int jc = i / KP, l = i % KP;
+            sX[jc][l] = j0 + jc < n ? X[(j0 + jc) * KP + l] : 0.f;
+        }
+        for (int i = tid; i < kXT * kXT; i += 256) {
+            const int jc = i / kXT, r = i % kXT;
+            sA[jc][r] = (j0 + jc < n && row0 + r < m) ? A[(j0 + jc) * lda + row0 + r] : 0.f;
+        }
+        __syncthreads();
+        if (tid < kXT) {
+            int nz = 0;
+            for (int l = 0; l < KP; ++l) nz |= sX[tid][l] != 0.f;
+            sNz[tid] = nz;
+        }
+        __syncthreads();
+        for (int jc = 0; jc < kXT; ++jc) {
+            if (!sNz[jc]) continue;
+            const float a = sA[jc][rl];
+#pragma unroll
+            for (int q = 0; q < LPT; ++q) acc[q].add_prod(a, sX[jc][lg + 8 * q]);
+        }
+    }
+    const int64_t row = row0 + rl;
+    if (row < m) {
+#pragma unroll
+        for (int q = 0; q < LPT; ++q) {
+            const int l = lg + 8 * q;
+            const double b = l < k ? static_cast<double>(B[static_cast<int64_t>(l) * ldb + row]) : 0.0;
+            const double v = acc[q].value() - b;
+            const float h = f64_to_f32(v);
+            R[row * KP + l] = v;
+            Rhl[row * KP + l] = make_float2(h, f64_to_f32(v - f32_to_f64(h)));
+        }
+    }
+}
+
+// G = A^T R for every lane: a CTA owns kXT columns (thread t: column t mod 32, lanes t/32 + 8 q)
+// and walks the rows in tiles of 64, with R as its FP32 (hi, lo) pairs (a r = a r_hi + a r_lo,
+// the first product error-free).  G: n x KP, FP64.
+template <int KP>
+__global__ void __launch_bounds__(256) multi_exact_grad_kernel(const float* A, int64_t lda, int64_t m, int64_t n,
+                                                               const float2* Rhl, double* G) {
+    constexpr int LPT = KP / 8;
+    constexpr int RT = 64;
+    __shared__ float sA[kXT][RT + 1];    // [column][row]
+    __shared__ float sRh[RT][KP], sRl[RT][KP];
+    const int tid = threadIdx.x;
+    const int cl = tid & 31, lg = tid >> 5;
+    const int64_t j0 = static_cast<int64_t>(blockIdx.x) * kXT;
+    DFAcc acc[LPT];
+    float lo_acc[LPT];
+#pragma unroll
+    for (int q = 0; q < LPT; ++q) lo_acc[q] = 0.f;
+    for (int64_t r0 = 0; r0 < m; r0 += RT) {
+        __syncthreads();
+        for (int i = tid; i < kXT * RT; i += 256) {
+            const int jc = i / RT, r = i % RT;
+            sA[jc][r] = (j0 + jc < n && r0 + r < m) ? A[(j0 + jc) * lda + r0 + r] : 0.f;
+        }
+        for (int i = tid; i < RT * KP; i += 256) {
+            const int r = i / KP, l = i % KP;
+            const float2 v = r0 + r < m ? Rhl[(r0 + r) * KP + l] : make_float2(0.f, 0.f);
+            sRh[r][l] = v.x;
+            sRl[r][l] = v.y;
+        }
+        __syncthreads();
+        for (int r = 0; r < RT; ++r) {
+            const float a = sA[cl][r];
+#pragma unroll
+            for (int q = 0; q < LPT; ++q) {
+                acc[q].add_prod(a, sRh[r][lg + 8 * q]);
+                lo_acc[q] = fmaf(a, sRl[r][lg + 8 * q], lo_acc[q]);
+            }
+        }
+    }
+    const int64_t j = j0 + cl;
+    if (j < n) {
+#pragma unroll
+        for (int q = 0; q < LPT; ++q) G[j * KP + lg + 8 * q] = acc[q].value() + static_cast<double>(lo_acc[q]);
+    }
+}
+
+// Per-lane ||xhat(x) - x||_inf and ||x||_inf from FP64 gradients (same as multi_stat_kernel).
+template <int KP>
+__global__ void __launch_bounds__(256) multi_stat64_kernel(const double* G, const float* X, const double* dw,
+                                                           const double* lam, int64_t n, unsigned long long* out) {
     const int64_t total = n * KP;
     for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < total;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
