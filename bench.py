@@ -1065,10 +1065,40 @@ def run_ncu_case_multi():
     ml.close()
 
 
+def run_ncu_case_batch():
+    """ncu case of the batched Gauss-Seidel kernel: 152 planted Nesterov instances, m ~ U[500,
+    2000], n ~ U[2000, 6000] (about 3 GB in all, larger than L2), 20 sweeps.  The first solve
+    runs the autotuner (one-sweep launches) and its launch; the second reuses the cached shape:
+    its single launch is the one summarised."""
+    import numpy as np
+    import torch
+    from paper_1701_04900_gb300.batch import BatchSolver
+    from inputs import nesterov_lasso_torch
+    rng = np.random.default_rng(3)
+    probs = []
+    for i in range(152):
+        m = int(rng.integers(500, 2001))
+        n = int(rng.integers(2000, 6001))
+        g = nesterov_lasso_torch(m, n, max(1, int(0.02 * n)), lam=1.0, seed=5000 + i, device="cuda")
+        probs.append(dict(At=g["At"], b=g["b"], lam=1.0, m=m))
+    bs = BatchSolver(probs, form="gs", max_sweeps=20, check_every=10, tol_stat=1e-6)
+    xs = [torch.zeros(p["At"].shape[0], dtype=torch.float32, device="cuda") for p in probs]
+    bs.solve(xs)
+    for x in xs:
+        x.zero_()
+    per, tot = bs.solve(xs)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": True, "mode": "batch", "problems": len(probs), "sweeps": tot["sweeps"],
+                      "block_w": tot["block_w"], "consumer_warps": tot["kernel_variant"],
+                      "A_bytes": sum(p["m"] * p["At"].shape[0] * 4 for p in probs)}))
+    bs.close()
+
+
 def run_ncu_case(args):
     """Small case for ncu captures: the same generator with n = 12800 (A = 1 GB, larger
     than L2), one refresh, then `--ncu-launches` async sweep launches of 10 sweeps each
-    (or Jacobi sweeps with --ncu-mode sync; --ncu-mode multi: the multi-lane case).  Used by
+    (or Jacobi sweeps with --ncu-mode sync; --ncu-mode multi: the multi-lane case; --ncu-mode
+    batch: the batched Gauss-Seidel case).  Used by
     the commands in profiles/."""
     import torch
     from paper_1701_04900_gb300.build import build_library
@@ -1078,6 +1108,9 @@ def run_ncu_case(args):
     torch.cuda.set_device(0)
     if args.ncu_mode == "multi":
         run_ncu_case_multi()
+        return
+    if args.ncu_mode == "batch":
+        run_ncu_case_batch()
         return
     n = 12800
     gen = nesterov_lasso_torch(M, n, K_PLANT * n // N, lam=LAM, seed=0, device="cuda")
@@ -1096,7 +1129,7 @@ def run_ncu_case(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--ncu-case", action="store_true", help="small profiling case (see run_ncu_case)")
-    ap.add_argument("--ncu-mode", default="async", choices=["async", "sync", "multi"])
+    ap.add_argument("--ncu-mode", default="async", choices=["async", "sync", "multi", "batch"])
     ap.add_argument("--ncu-launches", type=int, default=3)
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2],
                     help="async sweep kernel (asyflexa_opts.variant; 0 = automatic)")
