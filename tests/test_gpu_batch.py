@@ -219,6 +219,39 @@ def test_batch_gs_form_uneven_instances_reach_gap_and_stationarity():
     bs.close()
 
 
+def test_batch_gs_form_hands_slow_problems_to_further_launches():
+    """Problems still short of their tolerances after 300 sweeps leave the first launch and
+    continue from their iterates in further launches (their own tuned shape): they report
+    the sweeps of every launch, the handoff count, and, when they stop with OK, the gap and
+    the stationarity the oracle confirms; the quick problems finish in the first launch."""
+    import torch
+    from paper_1701_04900_gb300.batch import BatchSolver
+    ds = [nesterov_lasso(1200, 3000, 60, lam=1.0, seed=140 + i, store_dtype=np.float32) for i in range(3)]
+    ds += [nesterov_lasso(300, 7000, 150, lam=1.0, seed=150 + i, store_dtype=np.float32) for i in range(3)]
+    f_ref = [O.objective(O.Problem.from_data(d), d["x_star"]) for d in ds]
+    bs = BatchSolver([_cuda(d) for d in ds], form="gs", max_sweeps=3000, check_every=10)
+    xs = [torch.zeros(d["n"], dtype=torch.float32, device="cuda") for d in ds]
+    per, tot = bs.solve(xs, f_star=f_ref)
+    handed = [i for i, st in enumerate(per) if st["handed_over"] > 0]
+    assert tot["handed_over"] == len(handed) >= 1, [st["sweeps"] for st in per]
+    for i, st in enumerate(per):
+        assert st["status"] in (0, 1)
+        if i in handed:
+            assert st["sweeps"] > 300
+        else:
+            assert st["sweeps"] <= 310
+        if st["status"] == 1:
+            continue
+        p = O.Problem.from_data(ds[i])
+        xi = xs[i].cpu().numpy().astype(np.float64)
+        F = O.objective(p, xi)
+        assert (F - f_ref[i]) / f_ref[i] <= 1.5e-6
+        assert abs(F - st["F"]) <= 1e-9 * F
+        assert O.stationarity(O.xhat_merit(p, xi, O.surrogate_weights(p)), xi) <= 1.5e-6, i
+    assert any(per[i]["status"] == 0 for i in handed)
+    bs.close()
+
+
 def test_batch_gs_form_shared_matrix_lambda_path_and_cached_shape():
     """A lambda path on one matrix (f_star unknown: the problems stop on the merit alone);
     every lane is stationary to 1e-6 by the oracle, and the lambda = 1 lane reaches the
