@@ -464,8 +464,10 @@ int asyflexa_batch_destroy(asyflexa_batch_t hb);
  * several data vectors -- solved together: every block update of Algorithm 1 is done for all
  * lanes at once, its two products G = A_i^T R~ (w x k) and R += A_i Delta_i (m x k) on the
  * tensor cores (TF32 with a hi/lo split, FP32-grade products, FP64 residuals), so each byte of
- * A serves k lanes.  Blocks of w = 32 columns; async mode; at most max(1, m / 32) CTAs (2 per
- * SM) by default, i.e. at most m columns of each lane in flight (opts.num_ctas overrides).
+ * A serves k lanes.  Blocks of w = 32 columns; async mode.  By default every solve starts with
+ * max(1, 2m / 32) CTAs (at most 2 per SM), i.e. up to 2m columns of each lane in flight, and
+ * halves the grid whenever a check interval raises some lane's F (too many updates in flight);
+ * opts.num_ctas > 0 fixes the grid.
  *
  * prob:    FP32 A (m x n, lda) and FP32 vectors; LASSO loss; no box, linear term or master
  *          copy (EUNSUPPORTED otherwise).  prob->b and prob->lambda are ignored.

@@ -41,6 +41,8 @@ const void* multi_kernel() { return reinterpret_cast<const void*>(asyflexa::swee
 struct asyflexa_multi_s {
     asyflexa_t base = nullptr;  // single-lane handle on lane 0: weights d_j, geometry, stream
     int k = 0, kp = 0, grid = 0;
+    int grid_start = 0;     // the grid every solve starts from
+    bool grid_auto = false; // num_ctas 0: the grid halves when a check interval raises some lane's F
     int64_t m = 0, n = 0;
     asyflexa_opts opts{};
     cudaStream_t stream = nullptr;
@@ -288,11 +290,15 @@ int asyflexa_multi_create(asyflexa_multi_t* out, const asyflexa_problem* prob, i
     H->n = prob->n;
     H->lam.assign(lambdas, lambdas + k);
     const int nblocks = static_cast<int>((H->n + asyflexa::kMW - 1) / asyflexa::kMW);
-    // updates in flight: every lane has grid * w columns in flight; the default keeps that at
-    // most m (a lambda path stayed stable up to about 2 m, a single problem diverged at 2.4 m)
-    const int cap = static_cast<int>(std::max<int64_t>(1, H->m / asyflexa::kMW));
+    // updates in flight: every lane has grid * w columns in flight.  The default starts at up to
+    // 2 m (2 CTAs per SM at most: a lambda path converged as fast in sweeps as with m, a single
+    // problem diverged at 2.4 m) and halves the grid whenever a check interval raises some
+    // lane's F, the sign of too many updates in flight
+    const int cap = static_cast<int>(std::max<int64_t>(1, 2 * H->m / asyflexa::kMW));
+    H->grid_auto = opts->num_ctas <= 0;
     H->grid = opts->num_ctas > 0 ? opts->num_ctas : std::min(cap, H->base->sm_count * 2);
     H->grid = std::max(1, std::min(H->grid, nblocks));
+    H->grid_start = H->grid;
     std::vector<double> lp(H->kp, INFINITY);
     for (int l = 0; l < k; ++l) lp[l] = lambdas[l];
     cudaError_t e = cudaMalloc(&H->lam_d, H->kp * sizeof(double));
@@ -370,6 +376,8 @@ int asyflexa_multi_solve(asyflexa_multi_t H, void* X, int64_t ldx, const double*
     long long sweeps = 0;
     int since_refresh = 0;
     const int step = std::max(1, std::min(H->opts.check_every, H->opts.refresh_every));
+    H->grid = H->grid_start;
+    std::vector<double> Flast(k, NAN);  // every lane's F at the previous check (grid control)
     // A lane that the in-loop test (tensor-core gradients) passes is confirmed by the exact check
     // at its returned iterate.  The split-TF32 products put the multi-lane fixed point up to
     // about 1e-6 away in that measure, so a lane the exact check rejects is finished by the
@@ -389,6 +397,13 @@ int asyflexa_multi_solve(asyflexa_multi_t H, void* X, int64_t ldx, const double*
         }
         rc = multi_objective(*H, F, nnz);
         if (rc) return rc;
+        if (H->grid_auto && H->grid > 1) {
+            bool rose = false;
+            for (int l = 0; l < k; ++l)
+                rose |= std::isfinite(Flast[l]) && F[l] > Flast[l] + 1e-12 * std::fabs(Flast[l]);
+            if (rose) H->grid = std::max(1, H->grid / 2);
+        }
+        Flast = F;
         bool need_stat = false;
         for (int l = 0; l < k; ++l) {
             if (!std::isfinite(F[l])) return mfail("objective is not finite", ASYFLEXA_ENONFINITE);

@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kMThreads) sweep_multi_kernel(const MultiParam
     const int grp = lane >> 2;  // groupID of the mma fragments
     const int tig = lane & 3;   // thread in group
     constexpr int kNT = KP / 8;                 // n tiles (lanes)
-    constexpr int kP1 = 2 * kNT;                // gradient pass: (m tile, n tile) pairs over j
+    constexpr int kP1 = (kMW / 16) * kNT;       // gradient pass: (m tile, n tile) pairs over j
     constexpr int kP1W = (kP1 + kMWarps - 1) / kMWarps;  // pairs per warp
     constexpr int kP2 = (kMT / 16) * kNT;       // scatter pass: pairs over rows
     constexpr int kP2W = (kP2 + kMWarps - 1) / kMWarps;
