@@ -843,7 +843,8 @@ def run_form_batched(args, ctx=None):
         gap and stationarity.
     (b) A 64-point geometric lambda path on one 5000 x 20000 instance (lambda_max =
         ||A^T b||_inf down to the planted lambda = 1), every lane to stationarity <= 1e-6:
-        the Gauss-Seidel form, the async rounds form, the multi-lane tensor-core form, and 64
+        the batch API's automatic choice (shared A: the multi-lane form), the Gauss-Seidel
+        form, the async rounds form, the multi-lane tensor-core form called directly, and 64
         sequential warm-started (and cold) plain solves."""
     import numpy as np
     import torch
@@ -924,13 +925,15 @@ def run_form_batched(args, ctx=None):
     f1 = 0.5 * float(r @ r) + float(g["x_star"].abs().sum())
     base = dict(At=At, b=b, m=m)
     path = {"lambdas": 64, "lambda_max": lam_max, "tol_stat": 1e-6}
-    for name, kw in (("gs", dict(form="gs", shared_a=True, check_every=10)),
+    for name, kw in (("batched_auto", dict(shared_a=True, check_every=10, refresh_every=10)),
+                     ("gs", dict(form="gs", shared_a=True, check_every=10)),
                      ("async_rounds", dict(form="async", shared_a=True, block_w=32, refresh_every=10,
                                            switch_tol=1e-9))):
         xs = [torch.zeros(n, dtype=torch.float32, device="cuda") for _ in lams]
         t, per, tot, exact = _batch_solve_timed(
             lambda: BatchSolver([dict(base, lam=l) for l in lams], max_sweeps=3000, tol_stat=1e-6, **kw), xs)
         path[name] = {"seconds": t, "status": tot["status"], "per_lane_status": _status_counts(per),
+                      "form": {2: "async", 4: "gs", 8: "multi"}.get(tot["batch_form"], "?"),
                       "max_sweeps": tot["sweeps"], "max_stat_xhat_exact_check": max(q["stat_xhat"] for q in exact),
                       "last_lane_rel_gap_vs_planted": (exact[-1]["F"] - f1) / f1}
         del xs
@@ -976,7 +979,7 @@ def run_form_batched(args, ctx=None):
                           "last_lane_rel_gap_vs_planted": (mper[-1]["F"] - f1) / f1}
     path["sequential_warm"] = {"seconds": t_seq, "sweeps": seq_sweeps, "max_stat_xhat": seq_stat}
     path["sequential_cold"] = {"seconds": t_cold, "sweeps": cold_sweeps}
-    for name in ("gs", "async_rounds", "multi_lane"):
+    for name in ("batched_auto", "gs", "async_rounds", "multi_lane"):
         path[name]["speedup_vs_sequential_warm"] = t_seq / path[name]["seconds"]
         path[name]["speedup_vs_sequential_cold"] = t_cold / path[name]["seconds"]
     if ctx is not None:

@@ -189,7 +189,7 @@ typedef struct {
                                    stopping test: with FP32 iterates ||A^T r||_inf carries the
                                    rounding of the heaviest column, which loosens the bound. */
     double tau_extra;           /* solve with tau_adapt: the proximal weight added at the end */
-    int32_t batch_form;         /* batched solve: ASYFLEXA_BATCH_FORM_ASYNC or ASYFLEXA_BATCH_FORM_GS */
+    int32_t batch_form;         /* batched solve: ASYFLEXA_BATCH_FORM_ASYNC, _GS or _MULTI */
     int32_t ctas_per_sm;        /* batched solve, Gauss-Seidel form: CTAs resident per SM (autotuned) */
     int32_t handed_over;        /* batched solve, Gauss-Seidel form: problems that ran in more than
                                    one launch (total), or the further launches it ran in (per
@@ -398,14 +398,21 @@ int asyflexa_adjoint(const void* A, int64_t lda, int32_t a_dtype, int64_t m, int
  * launch ends with the bulk of the batch, and the last few problems run under a shape of
  * their own.
  *
- * The form is chosen at create (flags) or automatically: the Gauss-Seidel form when every
- * problem fits it and there are at least as many problems as SMs, else the async rounds.  An
+ *   ASYFLEXA_BATCH_FORM_MULTI (multi-lane form): problems that share A (a lambda path or
+ *     several data vectors; LASSO, no box or linear term, at most 64) are the lanes of one
+ *     multi-lane handle (asyflexa_multi_*): every block update is done for all of them at once
+ *     on the tensor cores, and every lane is confirmed by an exact check.
+ *
+ * The form is chosen at create (flags) or automatically: the multi-lane form when the problems
+ * fit it and ASYFLEXA_BATCH_SHARED_A is set, else the Gauss-Seidel form when every problem fits
+ * it and there are at least as many problems as SMs, else the async rounds.  An
  * autotuner then picks the form's launch shape at the first solve by timing one sweep of
  * every problem per candidate -- Gauss-Seidel form: 7 or 15 consumer warps per CTA (2 or 1
  * CTAs per SM), the block width and ring slot -- 1, 2 or 4 columns with 16 KB slots, 4 or 8
  * with 32 KB slots (a slot holds up to 8 columns; a problem whose columns do not fit w to a
- * slot takes as many as fit) -- and the ring depth that fits; the tuning sweeps are undone (the iterates are saved and restored), so
- * they count neither as sweeps nor against max_sweeps; async rounds: the block width 16, 32
+ * slot takes as many as fit) -- and the ring depth that fits; the tuning sweeps are undone
+ * (the iterates are saved and restored), so they count neither as sweeps nor against
+ * max_sweeps; async rounds: the block width 16, 32
  * or 64 (real sweeps, counted) -- and caches the choice per batch shape (problem count, total
  * size, largest m, flags) for the life of the process. */
 typedef struct asyflexa_batch_s* asyflexa_batch_t;
@@ -417,6 +424,8 @@ typedef struct asyflexa_batch_s* asyflexa_batch_t;
 #define ASYFLEXA_BATCH_FORM_ASYNC 2   /* force the async rounds form */
 #define ASYFLEXA_BATCH_FORM_GS 4      /* force the Gauss-Seidel form (EUNSUPPORTED if a problem
                                          does not fit it) */
+#define ASYFLEXA_BATCH_FORM_MULTI 8   /* force the multi-lane form (EUNSUPPORTED if the problems
+                                         do not fit it) */
 
 /* probs: count FP32 problems (as for asyflexa_create; LASSO or NCQUAD loss).  opts: shared
  * method parameters: gamma, tau, tau_rel, tol_gap, tol_stat, max_sweeps, num_ctas (0 = all

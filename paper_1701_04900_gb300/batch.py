@@ -9,7 +9,7 @@ from . import native
 from .native import AsyflexaError, Problem, Stats, default_opts, lib
 
 
-FORMS = {"auto": 0, "async": native.BATCH_FORM_ASYNC, "gs": native.BATCH_FORM_GS}
+FORMS = {"auto": 0, "async": native.BATCH_FORM_ASYNC, "gs": native.BATCH_FORM_GS, "multi": native.BATCH_FORM_MULTI}
 
 
 class BatchSolver:

@@ -222,6 +222,10 @@ struct asyflexa_batch_s {
     GsChoice gs_graph_cfg{};
     int smem_per_sm = 0;
     std::string shape_key;
+    // multi-lane form: one problem per lane of a multi-lane handle (shared A)
+    asyflexa_multi_t multi = nullptr;
+    float* d_bmat = nullptr;  // count x m: the problems' b, one lane per row
+    float* d_xmat = nullptr;  // count x n: the iterates, gathered for a solve
 };
 
 namespace {
@@ -720,22 +724,43 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
 }
 
 
-int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star, asyflexa_stats* per,
-                      asyflexa_stats* total, const std::vector<char>* mask, long long budget) {
+// The multi-lane form: the problems' iterates gathered into the lanes of the multi-lane handle,
+// solved, and scattered back.
+int multi_form_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflexa_stats* per,
+                     asyflexa_stats* total) {
+    const int64_t n = B.h[0]->prob.n;
+    for (int k = 0; k < B.count; ++k)
+        BCK(cudaMemcpyAsync(B.d_xmat + k * n, xs[k], n * sizeof(float), cudaMemcpyDeviceToDevice, B.stream),
+            "gather iterates");
+    const int rc = asyflexa_multi_solve(B.multi, B.d_xmat, n, f_star, per, total);
+    if (rc < 0) return rc;
+    for (int k = 0; k < B.count; ++k)
+        BCK(cudaMemcpyAsync(xs[k], B.d_xmat + k * n, n * sizeof(float), cudaMemcpyDeviceToDevice, B.stream),
+            "scatter iterates");
+    BCK(cudaStreamSynchronize(B.stream), "synchronize");
+    if (per)
+        for (int k = 0; k < B.count; ++k) per[k].batch_form = ASYFLEXA_BATCH_FORM_MULTI;
+    if (total) total->batch_form = ASYFLEXA_BATCH_FORM_MULTI;
+    return rc;
+}
+
+int rounds_solve(asyflexa_batch_s& Bref, void* const* xs, const double* f_star, asyflexa_stats* per,
+                 asyflexa_stats* total) {
+    asyflexa_batch_s* B = &Bref;
+    const long long budget = B->opts.max_sweeps;
     const int count = B->count;
-    auto in = [&](int k) { return !mask || (*mask)[k] != 0; };
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0), "event");
     BCK(cudaEventCreate(&e1), "event");
     BCK(cudaEventRecord(e0, B->stream), "event record");
-    // reset problem states for these iterates (problems outside the mask: inactive)
+    // reset problem states for these iterates
     for (int k = 0; k < count; ++k) {
         B->h_inst[k].x = xs[k];
-        B->h_inst[k].active = in(k) ? 1 : 0;
+        B->h_inst[k].active = 1;
         ConvState& c = B->h_conv[k];
         c.f_star = f_star ? f_star[k] : NAN;
         c.F = c.F_prev = NAN;
-        c.conv_round = in(k) ? -2 : 0;
+        c.conv_round = -2;
     }
     B->grid = 0;  // every problem active again: full grid until the first deactivation
     int rc = upload_table(*B);
@@ -744,7 +769,6 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
         "upload convergence state");
     BCK(cudaMemsetAsync(B->d_round, 0, sizeof(int), B->stream), "clear round");
     for (int k = 0; k < count; ++k) {
-        if (!in(k)) continue;
         BCK(Launcher<float>::refresh(*B->h[k], xs[k]), "initial refresh");
         B->launches += 4;
     }
@@ -788,8 +812,7 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
         if (!rc) rc = upload_table(*B);
         if (rc) return rc;
         for (int k = 0; k < count; ++k) {
-            if (!in(k)) continue;
-            BCK(Launcher<float>::refresh(*B->h[k], xs[k]), "refresh after autotune");
+                BCK(Launcher<float>::refresh(*B->h[k], xs[k]), "refresh after autotune");
             B->launches += 4;
         }
         B->graph_w = best_w;
@@ -825,7 +848,7 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
     }
     const int per_round = B->opts.refresh_every;
     int n_active = 0;
-    for (int k = 0; k < count; ++k) n_active += in(k) ? 1 : 0;
+    n_active = count;
     int last_active = n_active;
     // exact check of each problem at its returned x: computed when it leaves the rounds
     std::vector<asyflexa_stats> checked(count);
@@ -862,7 +885,7 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
         int back = 0;
         for (int k = 0; k < count; ++k) {
             ConvState& c = B->h_conv[k];
-            if (!in(k) || c.conv_round < 0 || have[k]) continue;
+            if (c.conv_round < 0 || have[k]) continue;
             asyflexa_stats st;
             std::memset(&st, 0, sizeof st);
             B->h[k]->opts.f_star = c.f_star;
@@ -900,7 +923,6 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
     long long bu = 0, max_k = 0;
     int worst = ASYFLEXA_OK;
     for (int k = 0; k < count; ++k) {
-        if (!in(k)) continue;
         const ConvState& c = B->h_conv[k];
         const long long nb = (B->h[k]->prob.n + B->w - 1) / B->w;
         const long long ksweeps = c.conv_round >= 0 ? static_cast<long long>(c.conv_round + 1) * per_round : sweeps;
@@ -942,10 +964,6 @@ int rounds_solve_impl(asyflexa_batch_s* B, void* const* xs, const double* f_star
 }
 
 
-int rounds_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflexa_stats* per,
-                 asyflexa_stats* total) {
-    return rounds_solve_impl(&B, xs, f_star, per, total, nullptr, B.opts.max_sweeps);
-}
 
 }  // namespace
 
@@ -1010,17 +1028,55 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
     // there are enough problems to occupy a good part of the GPU one CTA each
     {
         const bool gs_fits = B->max_mcopy <= kGsMaxRows;  // (15 warps x 5 units x 4 rows = 9600)
-        if ((flags & ASYFLEXA_BATCH_FORM_GS) && (flags & ASYFLEXA_BATCH_FORM_ASYNC))
-            return fail(bfail("at most one of ASYFLEXA_BATCH_FORM_GS and ASYFLEXA_BATCH_FORM_ASYNC"));
-        if (flags & ASYFLEXA_BATCH_FORM_GS) {
+        const int forms = ((flags & ASYFLEXA_BATCH_FORM_GS) ? 1 : 0) + ((flags & ASYFLEXA_BATCH_FORM_ASYNC) ? 1 : 0) +
+                          ((flags & ASYFLEXA_BATCH_FORM_MULTI) ? 1 : 0);
+        if (forms > 1) return fail(bfail("at most one ASYFLEXA_BATCH_FORM_* flag"));
+        // the multi-lane form fits a lambda path or several data vectors: shared A, LASSO, no
+        // box or linear term, at most 64 problems
+        bool multi_fits = count <= 64;
+        for (int k = 0; k < count && multi_fits; ++k) {
+            const asyflexa_problem& q = probs[k];
+            multi_fits = q.A == probs[0].A && q.lda == probs[0].lda && q.m == probs[0].m && q.n == probs[0].n &&
+                         q.loss == ASYFLEXA_LOSS_LASSO && q.x_dtype == ASYFLEXA_F32 && !q.lo && !q.hi && !q.lin;
+        }
+        if (flags & ASYFLEXA_BATCH_FORM_MULTI) {
+            if (!multi_fits)
+                return fail(bfail("the multi-lane form needs at most 64 LASSO problems sharing A, without box or "
+                                  "linear term", ASYFLEXA_EUNSUPPORTED));
+            B->form = ASYFLEXA_BATCH_FORM_MULTI;
+        } else if (flags & ASYFLEXA_BATCH_FORM_GS) {
             if (!gs_fits)
                 return fail(bfail("the Gauss-Seidel form needs m <= 8192 for every problem", ASYFLEXA_EUNSUPPORTED));
             B->form = ASYFLEXA_BATCH_FORM_GS;
         } else if (flags & ASYFLEXA_BATCH_FORM_ASYNC) {
             B->form = ASYFLEXA_BATCH_FORM_ASYNC;
+        } else if (multi_fits && (flags & ASYFLEXA_BATCH_SHARED_A) && count > 1) {
+            B->form = ASYFLEXA_BATCH_FORM_MULTI;
         } else {
             B->form = (gs_fits && count >= B->sm_count) ? ASYFLEXA_BATCH_FORM_GS : ASYFLEXA_BATCH_FORM_ASYNC;
         }
+    }
+    if (B->form == ASYFLEXA_BATCH_FORM_MULTI) {
+        const int64_t m = probs[0].m, n = probs[0].n;
+        cudaError_t e = cudaMalloc(&B->d_bmat, static_cast<size_t>(count) * m * sizeof(float));
+        if (e == cudaSuccess) e = cudaMalloc(&B->d_xmat, static_cast<size_t>(count) * n * sizeof(float));
+        for (int k = 0; k < count && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(B->d_bmat + k * m, probs[k].b, m * sizeof(float), cudaMemcpyDeviceToDevice, B->stream);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(bfail(std::string("batch allocation: ") + cudaGetErrorString(e), ASYFLEXA_ENOMEM));
+        }
+        std::vector<double> lams(count);
+        for (int k = 0; k < count; ++k) lams[k] = probs[k].lambda;
+        asyflexa_problem p0 = probs[0];
+        p0.b = B->d_bmat;
+        const int rc = asyflexa_multi_create(&B->multi, &p0, count, B->d_bmat, m, lams.data(), opts, B->stream);
+        if (rc) return fail(rc);
+        e = cudaEventRecord(B->ev_out, B->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(B->user_stream, B->ev_out, 0);
+        if (e != cudaSuccess) return fail(bfail(std::string("batch set-up: ") + cudaGetErrorString(e), ASYFLEXA_ECUDA));
+        *out = B;
+        return ASYFLEXA_OK;
     }
     B->cpc = static_cast<int>((units + asyflexa::kRegStageUnits - 1) / asyflexa::kRegStageUnits);
     B->kernel = batched_kernel(B->cpc);
@@ -1173,7 +1229,8 @@ int asyflexa_batch_destroy(asyflexa_batch_t B) {
     if (B->ev_in) cudaEventDestroy(B->ev_in);
     if (B->ev_out) cudaEventDestroy(B->ev_out);
     if (B->stream) cudaStreamDestroy(B->stream);
-    void* ptrs[] = {B->d_inst, B->d_blk_inst, B->d_blk_local, B->d_conv, B->d_round, B->d_nactive,
+    if (B->multi) asyflexa_multi_destroy(B->multi);
+    void* ptrs[] = {B->d_bmat, B->d_xmat, B->d_inst, B->d_blk_inst, B->d_blk_local, B->d_conv, B->d_round, B->d_nactive,
                     B->counters, B->hist, B->err, B->d_gs, B->d_order, B->d_order2, B->d_queue, B->d_dd, B->d_xsave};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1187,8 +1244,9 @@ int asyflexa_batch_solve(asyflexa_batch_t B, void* const* xs, const double* f_st
     // the batch's stream starts after the caller's prior work (the iterates may come from it)
     BCK(cudaEventRecord(B->ev_in, B->user_stream), "event record");
     BCK(cudaStreamWaitEvent(B->stream, B->ev_in, 0), "stream wait");
-    const int rc = B->form == ASYFLEXA_BATCH_FORM_GS ? gs_solve(*B, xs, f_star, per, total)
-                                                     : rounds_solve(*B, xs, f_star, per, total);
+    const int rc = B->form == ASYFLEXA_BATCH_FORM_GS      ? gs_solve(*B, xs, f_star, per, total)
+                   : B->form == ASYFLEXA_BATCH_FORM_MULTI ? multi_form_solve(*B, xs, f_star, per, total)
+                                                          : rounds_solve(*B, xs, f_star, per, total);
     // the caller's stream continues after the batch's work
     cudaEventRecord(B->ev_out, B->stream);
     cudaStreamWaitEvent(B->user_stream, B->ev_out, 0);

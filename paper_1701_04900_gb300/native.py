@@ -83,6 +83,7 @@ EXPORTS = [
 BATCH_SHARED_A = 1
 BATCH_FORM_ASYNC = 2
 BATCH_FORM_GS = 4
+BATCH_FORM_MULTI = 8
 
 
 def lib(path: str | None = None):

@@ -252,6 +252,33 @@ def test_batch_gs_form_hands_slow_problems_to_further_launches():
     bs.close()
 
 
+def test_batch_shared_matrix_lambda_path_takes_the_multi_lane_form():
+    """Problems that share A (a lambda path, shared_a) go to the multi-lane form by default:
+    every lane exactly stationary to 1e-6 (oracle-confirmed to 1.5e-6), the iterates written
+    back to each problem's x, and the planted lane at its optimum."""
+    import torch
+    from paper_1701_04900_gb300.batch import BatchSolver
+    from paper_1701_04900_gb300 import native
+    d = nesterov_lasso(1000, 4000, 40, lam=1.0, seed=71, store_dtype=np.float32)
+    base = _cuda(d)
+    lams = [6.0, 3.0, 2.0, 1.4, 1.0]
+    bs = BatchSolver([dict(base, lam=l) for l in lams], shared_a=True, max_sweeps=3000, tol_stat=1e-6)
+    xs = [torch.zeros(d["n"], dtype=torch.float32, device="cuda") for _ in lams]
+    p1 = O.Problem.from_data(d)
+    f1 = O.objective(p1, d["x_star"])
+    per, tot = bs.solve(xs, f_star=[float("nan")] * 4 + [f1])
+    assert tot["batch_form"] == native.BATCH_FORM_MULTI and tot["status"] == 0, tot
+    for k, lam in enumerate(lams):
+        assert per[k]["batch_form"] == native.BATCH_FORM_MULTI
+        p = O.Problem.from_data(d)
+        p.lam = lam
+        xk = xs[k].cpu().numpy().astype(np.float64)
+        merit = O.stationarity(O.xhat_merit(p, xk, O.surrogate_weights(p)), xk)
+        assert per[k]["stat_xhat"] <= 1e-6 and merit <= 1.5e-6, (lam, merit)
+    assert (O.objective(p1, xs[-1].cpu().numpy().astype(np.float64)) - f1) / f1 <= 1.5e-6
+    bs.close()
+
+
 def test_batch_gs_form_shared_matrix_lambda_path_and_cached_shape():
     """A lambda path on one matrix (f_star unknown: the problems stop on the merit alone);
     every lane is stationary to 1e-6 by the oracle, and the lambda = 1 lane reaches the
