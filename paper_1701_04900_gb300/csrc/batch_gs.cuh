@@ -29,8 +29,9 @@
 //     r's (hi, lo) pair and every update is error-free; before that the sweeps use plain FP32
 //     FMAs (an exact refresh follows every sweep phase).
 //   * Phases of one solve: REFRESH (r = -b + sum over x_j != 0 of a_j x_j with error-free
-//     products and sums, then F with FP64 sums), SWEEP (k sweeps, k = check_every or 2 near
-//     the tolerance), MERIT (x^_j with unit step, the largest |x^_j - x_j|).  A problem stops
+//     products and sums -- plain FP32 products while the gap is above kGsFarGap -- then F with
+//     FP64 sums), SWEEP (k sweeps, k = check_every, 2 near the tolerance, kGsFarChecks
+//     check_every far from the gap), MERIT (x^_j with unit step, the largest |x^_j - x_j|).  A problem stops
 //     when its gap (if f_star is known) and its merit meet the tolerances (OK), when F is not
 //     finite (ENONFINITE), at max_sweeps, or when, with the gap met and the merit within 100
 //     tol_stat, five checks in a row do not lower the best merit by 10% (ENOTCONV: the
@@ -114,6 +115,8 @@ __host__ __device__ inline GsLayout make_gs_layout(int nw, size_t slot_bytes, in
 }
 
 constexpr int kGsRefresh = 0, kGsSweep = 1, kGsMerit = 2;
+constexpr double kGsFarGap = 1e-2;  // a relative gap above this is far from any tolerance
+constexpr int kGsFarChecks = 4;     // check intervals between checks while far
 constexpr int kGsHandoff = 2;  // status: left for the second launch (not an asyflexa_status)
 constexpr int kGsFloorChecks = 5;
 constexpr double kGsFloorBand = 100.0;  // the floor rule applies within 100 tol_stat
@@ -128,7 +131,10 @@ struct GsMisc {
     double stat_ref;  // best merit so far
     float stat_last;
     int phase, k_sweeps, status, checks, exact, flat, flat_plain, done, reset;
+    int plain_refresh;  // the next refresh may use plain FP32 products (far from the gap)
+    double gap_last;    // the relative gap at the last refresh (NaN: not known)
 };
+static_assert(sizeof(GsMisc) <= 128, "the layout reserves 128 bytes for the control state");
 
 // The coefficients of column j that the best response needs (bounds and linear term apart).
 struct GsCoef {
@@ -278,6 +284,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
             // test passed with a known f_star; without one, a merit within kGsFloorBand tol_stat,
             // or two checks in a row that did not lower the best merit by 10%), exact from then on
             misc->exact = 0;
+            misc->plain_refresh = 0;
+            misc->gap_last = NAN;
             misc->flat_plain = 0;
             misc->done = 0;
             misc->reset = 0;
@@ -286,6 +294,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
         for (;;) {
             const int phase = misc->phase, k_sweeps = misc->k_sweeps;
             const bool exact = misc->exact != 0;
+            const bool plain = misc->plain_refresh != 0 && !exact;
             // ================================================================ one phase
             if (producer) {
                 // ---- issue the phase's items into the ring (lane 0), in consumption order.
@@ -368,6 +377,24 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                         for (int t = 0; t < wb; ++t) {
                             const float xj = X[j0 + t];
                             if (xj == 0.f) continue;
+                            if (plain) {
+                                // far from the gap: plain FP32 products (the next refresh that
+                                // could pass the gap test is exact)
+                                const uint4* srcp = reinterpret_cast<const uint4*>(ring + slot * L.slot_bytes +
+                                                                                   static_cast<size_t>(t) * lda * 4);
+#pragma unroll
+                                for (int k = 0; k < UPT; ++k) {
+                                    if (k < kmine) {
+                                        float a[4];
+                                        ATraits<float>::unpack(srcp[k * T + tid], a);
+                                        const int nv = k == klast ? vlast : 4;
+#pragma unroll
+                                        for (int e = 0; e < 4; ++e)
+                                            if (e < nv) rhi[k][e] = fmaf(a[e], xj, rhi[k][e]);
+                                    }
+                                }
+                                continue;
+                            }
                             const uint4* src = reinterpret_cast<const uint4*>(ring + slot * L.slot_bytes +
                                                                               static_cast<size_t>(t) * lda * 4);
 #pragma unroll
@@ -750,8 +777,15 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                             g.k_sweeps = static_cast<int>(p.max_sweeps - g.sweeps);
                             g.phase = kGsSweep;
                         }
+                    } else if (gap_ok && g.plain_refresh && isfinite(fs)) {
+                        // a plain refresh passed the gap test: redo it exactly before trusting it
+                        g.exact = 1;
+                        g.plain_refresh = 0;
+                        g.phase = kGsRefresh;
+                        g.reset = 1;
                     } else {
                         if (gap_ok && isfinite(fs)) g.exact = 1;
+                        g.gap_last = isfinite(fs) ? (g.F - fs) / fabs(fs) : NAN;
                         if (g.sweeps > 0 && gap_ok)
                             g.phase = kGsMerit;
                         else
@@ -793,9 +827,13 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW < 8 ? 2 : 1) batch_gs_kernel
                         g.status = kGsHandoff;
                         g.done = 1;
                     } else {
-                        // near the tolerance the next check comes after 2 sweeps
+                        // near the tolerance the next check comes after 2 sweeps; far from the gap
+                        // (above 1e-2 with a known f_star) after 4 check intervals, with plain
+                        // products in the refresh
                         const bool near = phase == kGsMerit && g.stat_last <= 2.0 * p.tol_stat;
-                        long long k = near ? 2 : p.check_every;
+                        const bool far = !g.exact && g.gap_last > kGsFarGap;
+                        g.plain_refresh = far ? 1 : 0;
+                        long long k = near ? 2 : (far ? kGsFarChecks * p.check_every : p.check_every);
                         if (k > p.max_sweeps - g.sweeps) k = p.max_sweeps - g.sweeps;
                         g.k_sweeps = static_cast<int>(k);
                         g.phase = kGsSweep;
