@@ -241,8 +241,11 @@ int asyflexa_step(asyflexa_t h, void* x, int32_t n_sweeps);
  * The stopping decision and the returned stats come from the same exact check.
  * With A_master set, these sweeps run on the BF16/FP8 matrix while
  * F, the residual refreshes and the stationarity are those of the FP32 problem; when a check
- * interval lowers F by less than switch_tol * |F| the solve continues with FP32 sweeps on
- * A_master ("polish") until the same stopping rule holds.  Fills *out (may be NULL);
+ * interval lowers F by less than switch_tol * |F|, or (f_star known) F comes within
+ * max(tol_gap, u^2) of f_star relative (u the storage's unit roundoff: 2^-8 BF16, 2^-4 FP8
+ * e4m3; about how far the stored problem's optimal F lies) without the tolerances holding,
+ * the solve continues with FP32 sweeps on A_master ("polish") until the same stopping rule
+ * holds.  Fills *out (may be NULL);
  * out->block_updates counts this solve's updates.  Synchronises. */
 int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out);
 

@@ -695,6 +695,14 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
     int status = ASYFLEXA_ENOTCONV;
     double F = NAN, F_prev = NAN, rr = 0.0, br = 0.0;
     bool polish = false;
+    // With a low-precision A (unit roundoff u: 2^-8 for BF16, 2^-4 for FP8 e4m3) the objective
+    // of the stored problem's minimiser differs from the FP32 problem's by about u^2 relative:
+    // the low-precision phase ends at that gap (or tol_gap, if larger)
+    double switch_gap = h->opts.tol_gap;
+    if (h->master) {
+        const double u = h->prob.a_dtype == ASYFLEXA_BF16 ? 0x1p-8 : 0x1p-4;
+        switch_gap = std::max(switch_gap, u * u);
+    }
     // F is evaluated on an exact residual every check_every sweeps, and the exact stationarity
     // check follows once the gap test passes.  A stationarity check that fails within a factor
     // kNear of tol_stat is repeated after kNearSweeps sweeps (at most check_every times): near
@@ -734,7 +742,7 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
             if (rc) break;
         }
         F_prev = F;
-        if (known && !(gap <= h->opts.tol_gap) && !stalled) continue;
+        if (known && !(gap <= switch_gap) && !stalled) continue;
         Measures M{};
         rc = h->master ? measure(*h->master, x, &M) : measure(*h, x, &M);
         if (rc) break;
@@ -745,7 +753,9 @@ int asyflexa_solve(asyflexa_t h, void* x, asyflexa_stats* out) {
             Mf = M;
             break;
         }
-        if (stalled) {
+        // low-precision phase: once F is within switch_gap of f_star, further low-precision
+        // sweeps only approach their own fixed point, so the FP32 polish takes over
+        if (stalled || (h->master && known && gap <= switch_gap)) {
             polish = true;
             break;
         }
