@@ -1221,6 +1221,8 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
 int asyflexa_batch_destroy(asyflexa_batch_t B) {
     if (!B) return ASYFLEXA_OK;
     if (B->stream) cudaStreamSynchronize(B->stream);
+    // the multi-lane handle (and its lane-0 handle) work on the batch's stream: destroyed first
+    if (B->multi) asyflexa_multi_destroy(B->multi);
     if (B->exec) cudaGraphExecDestroy(B->exec);
     if (B->graph) cudaGraphDestroy(B->graph);
     if (B->gs_exec) cudaGraphExecDestroy(B->gs_exec);
@@ -1229,7 +1231,6 @@ int asyflexa_batch_destroy(asyflexa_batch_t B) {
     if (B->ev_in) cudaEventDestroy(B->ev_in);
     if (B->ev_out) cudaEventDestroy(B->ev_out);
     if (B->stream) cudaStreamDestroy(B->stream);
-    if (B->multi) asyflexa_multi_destroy(B->multi);
     void* ptrs[] = {B->d_bmat, B->d_xmat, B->d_inst, B->d_blk_inst, B->d_blk_local, B->d_conv, B->d_round, B->d_nactive,
                     B->counters, B->hist, B->err, B->d_gs, B->d_order, B->d_order2, B->d_queue, B->d_dd, B->d_xsave};
     for (void* p : ptrs)
