@@ -153,6 +153,13 @@ typedef struct {
                                    residual snapshot, about 1.6x the sweep time (FP32 storage only:
                                    EUNSUPPORTED otherwise, or when the register kernel does not
                                    apply).  The batched and multi-lane forms ignore it */
+    int32_t delay_ns;           /* test-only staleness widener (0 = off, the default): in the
+                                   asynchronous single-problem kernels with several CTAs, every
+                                   odd-numbered CTA sleeps this many ns (__nanosleep, at most
+                                   1000000) before each block's scatter, so that the other CTAs'
+                                   reads miss its updates for longer (Assumption D1's delays grow;
+                                   the staleness histogram shows it).  EINVAL outside [0, 1000000] */
+    int32_t reserved2;
 } asyflexa_opts;
 
 /* Results and counters.  Optimality fields are FP64 and computed from an exact

@@ -314,6 +314,7 @@ int validate_opts(const asyflexa_opts* o, std::string* why) {
         return *why = "refresh_every, check_every and max_sweeps must be >= 1", 1;
     if (o->num_ctas < 0) return *why = "num_ctas must be >= 0", 1;
     if (o->variant < 0 || o->variant > 3) return *why = "variant must be 0, 1, 2 or 3", 1;
+    if (o->delay_ns < 0 || o->delay_ns > 1000000) return *why = "delay_ns must be in [0, 1000000]", 1;
     if (!(o->tol_gap >= 0.0) || !(o->tol_stat >= 0.0)) return *why = "tolerances must be >= 0", 1;
     if (!(o->switch_tol >= 0.0)) return *why = "switch_tol must be >= 0", 1;
     if (!(o->gamma_mu >= 0.0) || !std::isfinite(o->gamma_mu)) return *why = "gamma_mu must be finite and >= 0", 1;
@@ -370,6 +371,8 @@ void asyflexa_opts_default(asyflexa_opts* o) {
     o->gamma_mu = 0.0;
     o->tau_adapt = 0;
     o->exact_grad = 0;
+    o->delay_ns = 0;
+    o->reserved2 = 0;
 }
 
 const char* asyflexa_last_error(asyflexa_t h) { return h ? h->msg.c_str() : g_thread_msg.c_str(); }

@@ -289,6 +289,7 @@ cudaError_t Launcher<TA>::sweep(asyflexa_s& h, void* x, int mode, int sweeps) {
     p.counters = h.counters;
     p.hist = h.hist;
     p.err = h.err;
+    p.delay_ns = mode == ASYFLEXA_ASYNC ? h.opts.delay_ns : 0;
     if (h.opts.gamma_mu > 0.0) {
         p.gtab = h.gtab;
         p.gtab_len = static_cast<long long>(sweeps) * h.nblocks;

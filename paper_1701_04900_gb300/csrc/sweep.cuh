@@ -108,6 +108,7 @@ struct SweepParams {
     unsigned long long* counters;  // [0] global update counter, [1] block updates, [2] blocks with Delta != 0
     unsigned long long* hist;      // 32-bucket staleness histogram
     int* err;
+    int delay_ns;                  // test-only: odd CTAs sleep this long before each scatter (0: off)
     // batched launches only
     const BatchInst* batch;        // problem table
     const int* blk_inst;           // global block -> problem
@@ -378,6 +379,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) sweep_kernel(const SweepPara
             }
 
             // ---------------- async: scatter r += A_i Delta_i
+            if (p.delay_ns > 0 && (blockIdx.x & 1u)) __nanosleep(static_cast<unsigned>(p.delay_ns));
             if (warp == 0) {
                 int base_out = 0;
                 for (int base = 0; base < wb; base += 32) {

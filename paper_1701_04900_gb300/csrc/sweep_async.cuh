@@ -605,6 +605,7 @@ __global__ void __launch_bounds__(kRegThreads, 1) sweep_async_reg_kernel(const S
             // ---- r += A_i Delta_i : one FP64 atomic per row (skipping exact zeros)
             // (the abort flag is read once per warp: the FP32 path below shuffles within the warp)
             const bool aborted = __shfl_sync(0xffffffffu, *abort_flag != 0, 0);
+            if (!BATCHED && p.delay_ns > 0 && (blockIdx.x & 1u)) __nanosleep(static_cast<unsigned>(p.delay_ns));
             if (any && !aborted) scatter_increment<V, UPT, kRegConsThreads>(inc, bv.r, bv.m, warp, lane);
             named_bar_sync(1, kRegConsThreads);  // scatter issued; rt and coef free
             if (tid == kRegConsThreads - 1) account_block(p, u_read, any, my_updates, my_active);
@@ -905,6 +906,7 @@ __global__ void __launch_bounds__(kRcThreads, 1) sweep_async_rc_kernel(const Swe
             }
             // ---- r += A_i Delta_i
             const bool aborted = __shfl_sync(0xffffffffu, *abort_flag != 0, 0);
+            if (p.delay_ns > 0 && (blockIdx.x & 1u)) __nanosleep(static_cast<unsigned>(p.delay_ns));
             if (any && !aborted) scatter_increment<V, UPT, kRcThreads>(inc, bv.r, bv.m, warp, lane);
             named_bar_sync(1, kRcThreads);  // scatter issued; rt and coef free
             if (tid == kRcThreads - 1) account_block(p, u_read, any, my_updates, my_active);

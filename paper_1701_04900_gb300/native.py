@@ -46,6 +46,7 @@ class Opts(C.Structure):
         ("seed", C.c_uint64), ("profile", C.c_int32), ("variant", C.c_int32),
         ("switch_tol", C.c_double), ("gamma_mu", C.c_double),
         ("tau_adapt", C.c_int32), ("exact_grad", C.c_int32),
+        ("delay_ns", C.c_int32), ("reserved2", C.c_int32),
     ]
 
 
@@ -184,7 +185,7 @@ def default_opts() -> Opts:
 
 def make_opts(block_w=32, mode="sync", gamma=0.9, tau=0.0, tau_rel=0.0, refresh_every=10, check_every=10,
               max_sweeps=1000, num_ctas=0, tol_gap=1e-6, tol_stat=1e-6, f_star=math.nan, profile=False, variant=0,
-              switch_tol=1e-7, gamma_mu=0.0, tau_adapt=False, exact_grad=0) -> Opts:
+              switch_tol=1e-7, gamma_mu=0.0, tau_adapt=False, exact_grad=0, delay_ns=0) -> Opts:
     """asyflexa_opts from keyword arguments (the library's defaults, then these values)."""
     o = default_opts()
     o.block_w, o.mode = int(block_w), (ASYNC if mode == "async" else SYNC)
@@ -198,6 +199,7 @@ def make_opts(block_w=32, mode="sync", gamma=0.9, tau=0.0, tau_rel=0.0, refresh_
     o.gamma_mu = float(gamma_mu)
     o.tau_adapt = 1 if tau_adapt else 0
     o.exact_grad = int(exact_grad)
+    o.delay_ns = int(delay_ns)
     return o
 
 
@@ -219,7 +221,7 @@ class Solver:
                  block_w=32, mode="sync", gamma=0.9, tau=0.0, tau_rel=0.0, refresh_every=10,
                  check_every=10, max_sweeps=1000, num_ctas=0, tol_gap=1e-6, tol_stat=1e-6,
                  f_star=math.nan, profile=False, variant=0, A_master=None, switch_tol=1e-7, lin=None,
-                 gamma_mu=0.0, tau_adapt=False, exact_grad=0, stream=None):
+                 gamma_mu=0.0, tau_adapt=False, exact_grad=0, delay_ns=0, stream=None):
         import torch
         L = lib()
         if At.dim() != 2 or not At.is_contiguous() or not At.is_cuda:
@@ -248,7 +250,7 @@ class Solver:
         o = make_opts(block_w=block_w, mode=mode, gamma=gamma, tau=tau, tau_rel=tau_rel, refresh_every=refresh_every,
                       check_every=check_every, max_sweeps=max_sweeps, num_ctas=num_ctas, tol_gap=tol_gap,
                       tol_stat=tol_stat, f_star=f_star, profile=profile, variant=variant, switch_tol=switch_tol,
-                      gamma_mu=gamma_mu, tau_adapt=tau_adapt, exact_grad=exact_grad)
+                      gamma_mu=gamma_mu, tau_adapt=tau_adapt, exact_grad=exact_grad, delay_ns=delay_ns)
         self.problem, self.opts = p, o
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream

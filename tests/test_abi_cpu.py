@@ -58,7 +58,7 @@ int main(void) {
   P(asyflexa_problem, lambda) P(asyflexa_problem, loss) P(asyflexa_problem, hi)
   P(asyflexa_opts, gamma) P(asyflexa_opts, num_ctas) P(asyflexa_opts, f_star) P(asyflexa_opts, seed)
   P(asyflexa_opts, switch_tol) P(asyflexa_opts, gamma_mu) P(asyflexa_opts, tau_adapt)
-  P(asyflexa_opts, exact_grad)
+  P(asyflexa_opts, exact_grad) P(asyflexa_opts, delay_ns)
   P(asyflexa_stats, staleness_hist) P(asyflexa_stats, kernel_launches) P(asyflexa_stats, checked)
   P(asyflexa_stats, kernel_variant) P(asyflexa_stats, dual_gap) P(asyflexa_stats, tau_extra)
   P(asyflexa_stats, batch_form) P(asyflexa_stats, ctas_per_sm) P(asyflexa_stats, handed_over)
