@@ -157,9 +157,11 @@ def test_autograd_gradient_matches_oracle_adjoint_and_finite_differences():
     Avn = val["At"][:, :300].astype(np.float64).T
     v = 2.0 * Avn.T @ (Avn @ xo - val["b"].astype(np.float64))
     dlam_o, db_o, _, S = O.lasso_adjoint_gradient(p.A, xo, v)
-    assert abs(float(lam.grad) - dlam_o) <= 2e-3 * abs(dlam_o)
+    # the forward x is an FP32 iterate at stationarity 1e-6 and the support solve runs in FP32
+    # (measured: 2.7e-5 for dL/dlam, 3.4e-5 for dL/db)
+    assert abs(float(lam.grad) - dlam_o) <= 2e-4 * abs(dlam_o)
     gb = bt.grad.double().cpu().numpy()
-    assert np.abs(gb - db_o).max() <= 2e-3 * np.abs(db_o).max()
+    assert np.abs(gb - db_o).max() <= 2e-4 * np.abs(db_o).max()
 
     def L(lam_v):
         with torch.no_grad():
