@@ -85,6 +85,15 @@ __global__ void batch_converge_kernel(ConvState* cs, BatchInst* inst, int count,
 constexpr int kCandidates[] = {16, 32, 64};
 
 // (d_j, 1/d_j) in FP32 for the Gauss-Seidel form ((0, 0) where d_j <= 0).
+// Two CUDA events destroyed with the scope (error returns included).
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 // Saves (to_save = 1) or restores the iterates of the problems order[0 .. cnt) to / from save,
 // problem k at the offset of its (d_j, 1/d_j) table: the autotuner's sweeps leave x as it was.
 __global__ void gs_copy_x_kernel(const asyflexa::GsInst* inst, const int* order, int cnt, const float2* dd_base,
@@ -580,9 +589,10 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
     };
     int rc = upload();
     if (rc) return rc;
-    cudaEvent_t e0, e1;
-    BCK(cudaEventCreate(&e0), "event");
-    BCK(cudaEventCreate(&e1), "event");
+    EventPair ev_e0;
+    BCK(cudaEventCreate(&ev_e0.a), "event");
+    BCK(cudaEventCreate(&ev_e0.b), "event");
+    cudaEvent_t e0 = ev_e0.a, e1 = ev_e0.b;
     BCK(cudaEventRecord(e0, B.stream), "event record");
     std::vector<int> all(count);
     for (int k = 0; k < count; ++k) all[k] = k;
@@ -671,8 +681,6 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
     BCK(cudaEventSynchronize(e1), "event sync");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     long long bu = 0, max_sweeps = 0;
     int nhanded = 0;
     int worst = ASYFLEXA_OK;
@@ -749,9 +757,10 @@ int rounds_solve(asyflexa_batch_s& Bref, void* const* xs, const double* f_star, 
     asyflexa_batch_s* B = &Bref;
     const long long budget = B->opts.max_sweeps;
     const int count = B->count;
-    cudaEvent_t e0, e1;
-    BCK(cudaEventCreate(&e0), "event");
-    BCK(cudaEventCreate(&e1), "event");
+    EventPair ev_e0;
+    BCK(cudaEventCreate(&ev_e0.a), "event");
+    BCK(cudaEventCreate(&ev_e0.b), "event");
+    cudaEvent_t e0 = ev_e0.a, e1 = ev_e0.b;
     BCK(cudaEventRecord(e0, B->stream), "event record");
     // reset problem states for these iterates
     for (int k = 0; k < count; ++k) {
@@ -788,9 +797,10 @@ int rounds_solve(asyflexa_batch_s& Bref, void* const* xs, const double* f_star, 
     if (B->opts.block_w == 0 && B->graph_w == 0) {
         float best = 0.f;
         int best_w = 32;
-        cudaEvent_t a0, a1;
-        BCK(cudaEventCreate(&a0), "event");
-        BCK(cudaEventCreate(&a1), "event");
+        EventPair ev_a0;
+        BCK(cudaEventCreate(&ev_a0.a), "event");
+        BCK(cudaEventCreate(&ev_a0.b), "event");
+        cudaEvent_t a0 = ev_a0.a, a1 = ev_a0.b;
         for (int w : kCandidates) {
             rc = build_blocks(*B, w);
             if (!rc) rc = upload_table(*B);
@@ -816,8 +826,6 @@ int rounds_solve(asyflexa_batch_s& Bref, void* const* xs, const double* f_star, 
             B->launches += 4;
         }
         B->graph_w = best_w;
-        cudaEventDestroy(a0);
-        cudaEventDestroy(a1);
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_w_tuned[B->shape_key] = best_w;
     }
@@ -918,8 +926,6 @@ int rounds_solve(asyflexa_batch_s& Bref, void* const* xs, const double* f_star, 
     BCK(cudaEventSynchronize(e1), "event sync");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     long long bu = 0, max_k = 0;
     int worst = ASYFLEXA_OK;
     for (int k = 0; k < count; ++k) {

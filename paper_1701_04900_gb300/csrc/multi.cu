@@ -19,6 +19,15 @@ void set_thread_error(const std::string& msg);
 
 namespace {
 
+// Two CUDA events destroyed with the scope (error returns included).
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair() {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 int mfail(const std::string& m, int code = ASYFLEXA_EINVAL) {
     asyflexa_internal::set_thread_error(m);
     return code;
@@ -360,9 +369,10 @@ int asyflexa_multi_solve(asyflexa_multi_t H, void* X, int64_t ldx, const double*
                          asyflexa_stats* total) {
     if (!H || !X) return mfail("handle or X is NULL");
     if (ldx < H->n) return mfail("ldx must be >= n");
-    cudaEvent_t e0, e1;
-    MCK(cudaEventCreate(&e0), "event");
-    MCK(cudaEventCreate(&e1), "event");
+    EventPair ev_e0;
+    MCK(cudaEventCreate(&ev_e0.a), "event");
+    MCK(cudaEventCreate(&ev_e0.b), "event");
+    cudaEvent_t e0 = ev_e0.a, e1 = ev_e0.b;
     MCK(cudaEventRecord(e0, H->stream), "event record");
     asyflexa::multi_transpose_kernel<float, float><<<H->base->sm_count * 2, 256, 0, H->stream>>>(
         static_cast<const float*>(X), ldx, H->X, 0, H->n, H->k, H->kp, 0, 1.0);
@@ -468,8 +478,6 @@ int asyflexa_multi_solve(asyflexa_multi_t H, void* X, int64_t ldx, const double*
     MCK(cudaEventSynchronize(e1), "event sync");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     const long long nblocks = (H->n + asyflexa::kMW - 1) / asyflexa::kMW;
     int worst = ASYFLEXA_OK;
     for (int l = 0; l < k; ++l) {
