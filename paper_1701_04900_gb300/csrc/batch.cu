@@ -84,7 +84,6 @@ __global__ void batch_converge_kernel(ConvState* cs, BatchInst* inst, int count,
 
 constexpr int kCandidates[] = {16, 32, 64};
 
-// (d_j, 1/d_j) in FP32 for the Gauss-Seidel form ((0, 0) where d_j <= 0).
 // Two CUDA events destroyed with the scope (error returns included).
 struct EventPair {
     cudaEvent_t a = nullptr, b = nullptr;
@@ -110,6 +109,7 @@ __global__ void gs_copy_x_kernel(const asyflexa::GsInst* inst, const int* order,
     }
 }
 
+// (d_j, 1/d_j) in FP32 for the Gauss-Seidel form ((0, 0) where d_j <= 0).
 __global__ void gs_coef_kernel(const double* dw, int64_t n, float2* dd) {
     for (int64_t j = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
          j += static_cast<int64_t>(gridDim.x) * blockDim.x) {
