@@ -474,9 +474,14 @@ def run_ours(args):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record()
-    stats = [one_step() for _ in range(args.steps)]
+    stats, step_ev = [], []
+    for _ in range(args.steps):
+        stats.append(one_step())
+        step_ev.append(torch.cuda.Event(enable_timing=True))
+        step_ev[-1].record()
     ev1.record()
     torch.cuda.synchronize()
+    step_ms = [ev0.elapsed_time(step_ev[0])] + [a.elapsed_time(b) for a, b in zip(step_ev, step_ev[1:])]
     if world > 1:
         dist.barrier()
     clocks = sampler.stop()
@@ -510,7 +515,8 @@ def run_ours(args):
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
               "data": "synthetic (Nesterov-style planted LASSO generated on the device)",
               "config": bench_config(world),
-              "time_to_gap_s": elapsed / args.steps, "sweeps_to_gap": last["sweeps"],
+              "time_to_gap_s": elapsed / args.steps, "step_ms": [round(t, 3) for t in step_ms],
+              "sweeps_to_gap": last["sweeps"],
               "rel_gap": last["rel_gap"], "stat_xhat": last["stat_xhat"], "stat_mf": last["stat_mf"],
               "kkt_viol": last["kkt_viol"], "nnz": last["nnz"], "status": last["status"],
               "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks,

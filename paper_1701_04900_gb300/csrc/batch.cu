@@ -25,6 +25,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "handle.h"
@@ -207,6 +208,7 @@ struct asyflexa_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<void*> graph_x;
+    std::vector<cudaStream_t> fin_streams;  // streams of the async finishes (created on first use)
     int graph_w = 0;
     std::vector<int> cap;  // per problem: blocks it may have in flight, max(1, m / (4 w))
     int grid = 0;          // CTAs of the next sweep launch
@@ -389,6 +391,10 @@ int enqueue_round(asyflexa_batch_s& B, void* const* xs) {
 // finished, from its current iterate, by a second Gauss-Seidel launch over such problems only:
 // they then run side by side, under a launch shape tuned for them.
 constexpr int kGsHandoffSweeps = 300;
+// At most this many problems left after a launch are finished by the async solver (all of them
+// side by side); with kAsyncFinishEarly false, only when the next launch would run to the budget.
+constexpr int kAsyncFinishMax = 16;
+constexpr bool kAsyncFinishEarly = true;
 
 // The launch shape for nw consumer warps and ring slots of at least the longest column, with room
 // for up to kGsWMax columns within slot_cap bytes: units per thread for the longest column, the
@@ -633,6 +639,7 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
     std::vector<long long> done_sw(count), done_ns(count);
     std::vector<int> extra(count, 0);               // further launches each problem ran in
     std::vector<GsChoice> shape_of(count, B.gs);   // the launch that finished it
+    std::vector<char> async_fin(count, 0);         // finished by the single-problem async solver
     for (int k = 0; k < count; ++k) {
         done_sw[k] = B.h_gs[k].sweeps;
         done_ns[k] = B.h_gs[k].ns;
@@ -651,6 +658,82 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
         const int budget2 = static_cast<int>(std::max<long long>(0, budget - done_max));
         hand *= 2;
         const int handoff2 = budget2 > 2 * hand ? hand : 0;
+        if (nrest <= kAsyncFinishMax && (handoff2 == 0 || kAsyncFinishEarly)) {
+            // The few problems left would each hold one SM while the others idle: they are
+            // finished side by side, each by the single-problem async solver on a stream of its
+            // own, with max(1, m / (4 w)) CTAs (about m / 4 columns in flight, as in the async
+            // rounds).  The async kernels have no waits between CTAs, so the solves need not be
+            // resident together.
+            BCK(cudaStreamSynchronize(B.stream), "synchronize");
+            while (static_cast<int>(B.fin_streams.size()) < nrest) {
+                cudaStream_t fs = nullptr;
+                BCK(cudaStreamCreateWithFlags(&fs, cudaStreamNonBlocking), "finish stream");
+                B.fin_streams.push_back(fs);
+            }
+            std::vector<asyflexa_opts> saved(nrest);
+            std::vector<int> saved_ctas(nrest), src(nrest, ASYFLEXA_OK);
+            std::vector<cudaStream_t> saved_stream(nrest);
+            std::vector<asyflexa_stats> sts(nrest);
+            for (int i = 0; i < nrest; ++i) {
+                const int k = rest[i];
+                asyflexa_s& hk = *B.h[k];
+                saved[i] = hk.opts;
+                saved_ctas[i] = hk.sweep_ctas;
+                saved_stream[i] = hk.stream;
+                hk.opts.max_sweeps = static_cast<int>(std::max<long long>(1, budget - done_sw[k]));
+                hk.opts.f_star = f_star ? f_star[k] : NAN;
+                hk.sweep_ctas = static_cast<int>(std::max<int64_t>(
+                    1, std::min<int64_t>({static_cast<int64_t>(hk.nblocks), static_cast<int64_t>(hk.sm_count),
+                                          hk.prob.m / (4 * static_cast<int64_t>(hk.opts.block_w))})));
+                hk.stream = B.fin_streams[i];
+                hk.r_valid = false;
+                std::memset(&sts[i], 0, sizeof sts[i]);
+            }
+            auto finish = [&](int i) {
+                const int k = rest[i];
+                if (cudaSetDevice(B.h[k]->device) != cudaSuccess) {
+                    src[i] = ASYFLEXA_ECUDA;
+                    return;
+                }
+                src[i] = asyflexa_solve(B.h[k], xs[k], &sts[i]);
+            };
+            {
+                std::vector<std::thread> th;
+                int next = 1;  // problem 0 runs on this thread; the others on threads of their own
+                try {
+                    for (; next < nrest; ++next) th.emplace_back(finish, next);
+                } catch (...) {
+                }
+                finish(0);
+                for (auto& t : th) t.join();
+                for (int i = next; i < nrest; ++i) finish(i);  // threads that could not be started
+            }
+            for (int i = 0; i < nrest; ++i) {
+                asyflexa_s& hk = *B.h[rest[i]];
+                hk.opts = saved[i];
+                hk.sweep_ctas = saved_ctas[i];
+                hk.stream = saved_stream[i];
+            }
+            for (int i = 0; i < nrest; ++i) {
+                const int k = rest[i];
+                if (src[i] < 0 && src[i] != ASYFLEXA_ENONFINITE)
+                    return bfail("problem " + std::to_string(k) + ", async finish: " + B.h[k]->msg, src[i]);
+                const asyflexa_stats& st = sts[i];
+                asyflexa::GsInst& g = B.h_gs[k];
+                g.F = st.F;
+                g.stat = st.stat_xhat;
+                g.nnz = st.nnz;
+                g.status = src[i] == ASYFLEXA_ENONFINITE ? ASYFLEXA_ENONFINITE : st.status;
+                g.checks = 1;
+                g.w_used = B.h[k]->opts.block_w;
+                done_sw[k] += st.sweeps;
+                done_ns[k] += static_cast<long long>(st.seconds * 1e9);
+                ++extra[k];
+                shape_of[k] = GsChoice{};  // not a Gauss-Seidel launch
+                async_fin[k] = 1;
+            }
+            break;
+        }
         BCK(cudaMemcpyAsync(B.d_order2, rest.data(), nrest * sizeof(int), cudaMemcpyHostToDevice, B.stream),
             "upload order");
         std::string key2 = B.shape_key + " round=" + std::to_string(round) + " of";
@@ -708,7 +791,7 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
             s.checked = g.checks > 0 ? 1 : 0;
             s.block_w = g.w_used;
             s.seconds = 1e-9 * static_cast<double>(done_ns[k]);
-            s.batch_form = ASYFLEXA_BATCH_FORM_GS;
+            s.batch_form = async_fin[k] ? ASYFLEXA_BATCH_FORM_ASYNC : ASYFLEXA_BATCH_FORM_GS;
             s.ctas_per_sm = shape_of[k].ctas_per_sm;
             s.kernel_variant = shape_of[k].nw;
             s.handed_over = extra[k];
@@ -1095,7 +1178,7 @@ int asyflexa_batch_create(asyflexa_batch_t* out, const asyflexa_problem* probs, 
     B->smem = asyflexa::make_reg_layout(static_cast<int>(B->max_mcopy), B->stages).total;
     {
         cudaError_t e = cudaFuncSetAttribute(B->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(B->smem));
+                                             static_cast<int>(B->smem_optin));
         if (e != cudaSuccess) return fail(bfail(std::string("smem attribute: ") + cudaGetErrorString(e), ASYFLEXA_ECUDA));
     }
     B->h_inst.resize(count);
@@ -1234,6 +1317,7 @@ int asyflexa_batch_destroy(asyflexa_batch_t B) {
     if (B->gs_exec) cudaGraphExecDestroy(B->gs_exec);
     if (B->gs_graph) cudaGraphDestroy(B->gs_graph);
     for (auto hk : B->h) asyflexa_destroy(hk);
+    for (cudaStream_t fs : B->fin_streams) cudaStreamDestroy(fs);
     if (B->ev_in) cudaEventDestroy(B->ev_in);
     if (B->ev_out) cudaEventDestroy(B->ev_out);
     if (B->stream) cudaStreamDestroy(B->stream);

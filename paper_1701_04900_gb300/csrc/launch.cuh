@@ -172,12 +172,12 @@ int Launcher<TA>::choose_reg(asyflexa_s& h) {
     h.reg_cpc = cpc;
     h.reg_stages = stages;
     h.reg_smem = make_reg_layout(rt_rows, stages).total;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.reg_smem));
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.smem_optin));
     if (e != cudaSuccess) return -static_cast<int>(e);
     const void* fx = reg_kernel<TA>(cpc, true);
     h.reg_exact_ok = fx != nullptr;
     if (fx) {
-        e = cudaFuncSetAttribute(fx, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.reg_smem));
+        e = cudaFuncSetAttribute(fx, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.smem_optin));
         if (e != cudaSuccess) return -static_cast<int>(e);
     }
     // the column-in-registers form: the most columns per barrier whose stages fit the ring with
@@ -193,7 +193,7 @@ int Launcher<TA>::choose_reg(asyflexa_s& h) {
     const void* fr = rc_kernel<TA>(cpc, upt, h.reg_g);
     h.reg_rc_ok = fr != nullptr;
     if (fr) {
-        e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.rc_smem));
+        e = cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(h.smem_optin));
         if (e != cudaSuccess) return -static_cast<int>(e);
     }
     return 1;
@@ -216,7 +216,7 @@ int Launcher<TA>::setup_pipe(asyflexa_s& h) {
     int bps = 64;
     for (const void* fn : fns) {
         cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             static_cast<int>(h.pipe_smem));
+                                             static_cast<int>(h.smem_optin));
         if (e != cudaSuccess) return static_cast<int>(e);
         int b = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kAuxThreads, h.pipe_smem);
@@ -229,18 +229,23 @@ int Launcher<TA>::setup_pipe(asyflexa_s& h) {
     return 0;
 }
 
+// A kernel's shared-memory limit is an attribute of the kernel function, shared by every handle
+// (and batch) in the process, while each launch asks for its own size (which alone sets the
+// occupancy).  Every such attribute is therefore set to the device's opt-in maximum: set to one
+// handle's size, it would be lowered by a handle created later for a smaller problem, and the
+// first handle's launches would then fail.
 template <typename TA>
 int Launcher<TA>::set_smem_attrs(asyflexa_s& h) {
     cudaError_t e;
     e = cudaFuncSetAttribute(sweep_kernel<TA, kJacobi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(h.sweep_smem));
+                             static_cast<int>(h.smem_optin));
     if (e != cudaSuccess) return static_cast<int>(e);
     e = cudaFuncSetAttribute(sweep_kernel<TA, kAsync>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(h.sweep_smem));
+                             static_cast<int>(h.smem_optin));
     if (e != cudaSuccess) return static_cast<int>(e);
     if (h.check_use_smem && h.check_smem > 48 * 1024) {
         e = cudaFuncSetAttribute(check_kernel<TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 static_cast<int>(h.check_smem));
+                                 static_cast<int>(h.smem_optin));
         if (e != cudaSuccess) return static_cast<int>(e);
     }
     return 0;

@@ -252,6 +252,41 @@ def test_batch_gs_form_hands_slow_problems_to_further_launches():
     bs.close()
 
 
+def test_batch_gs_form_finishes_the_last_few_problems_with_the_async_solver():
+    """With a budget of 1500 sweeps, problems still short of their tolerances after the first
+    launch's 300 sweeps would run in one further launch to the budget; there are at most four of
+    them, so each is finished by the single-problem async solver instead.  They report the async
+    form, the sweeps of both parts, and, when they stop with OK, the gap and stationarity the
+    oracle confirms at the returned x; the quick problems stay in the Gauss-Seidel form."""
+    import torch
+    from paper_1701_04900_gb300 import native
+    from paper_1701_04900_gb300.batch import BatchSolver
+    ds = [nesterov_lasso(1200, 3000, 60, lam=1.0, seed=140 + i, store_dtype=np.float32) for i in range(3)]
+    ds += [nesterov_lasso(300, 7000, 150, lam=1.0, seed=150 + i, store_dtype=np.float32) for i in range(3)]
+    f_ref = [O.objective(O.Problem.from_data(d), d["x_star"]) for d in ds]
+    bs = BatchSolver([_cuda(d) for d in ds], form="gs", max_sweeps=1500, check_every=10)
+    xs = [torch.zeros(d["n"], dtype=torch.float32, device="cuda") for d in ds]
+    per, tot = bs.solve(xs, f_star=f_ref)
+    handed = [i for i, st in enumerate(per) if st["handed_over"] > 0]
+    assert 1 <= len(handed) <= 4 and tot["handed_over"] == len(handed), [st["sweeps"] for st in per]
+    for i, st in enumerate(per):
+        assert st["status"] in (0, 1)
+        if i in handed:
+            assert st["batch_form"] == native.BATCH_FORM_ASYNC and 300 < st["sweeps"] <= 1500
+        else:
+            assert st["batch_form"] == native.BATCH_FORM_GS and st["sweeps"] <= 310
+        if st["status"] == 1:
+            continue
+        p = O.Problem.from_data(ds[i])
+        xi = xs[i].cpu().numpy().astype(np.float64)
+        F = O.objective(p, xi)
+        assert (F - f_ref[i]) / f_ref[i] <= 1.5e-6, i
+        assert abs(F - st["F"]) <= 1e-9 * F
+        assert O.stationarity(O.xhat_merit(p, xi, O.surrogate_weights(p)), xi) <= 1.5e-6, i
+    assert any(per[i]["status"] == 0 for i in handed)
+    bs.close()
+
+
 def test_batch_shared_matrix_lambda_path_takes_the_multi_lane_form():
     """Problems that share A (a lambda path, shared_a) go to the multi-lane form by default:
     every lane exactly stationary to 1e-6 (oracle-confirmed to 1.5e-6), the iterates written

@@ -763,3 +763,43 @@ def test_solve_stats_are_an_exact_check_of_the_result(known, exact_grad):
     assert O.stationarity(O.xhat_merit(p, xg, O.surrogate_weights(p)), xg) <= 1.5e-6
     if known:
         assert st["rel_gap"] <= 1e-6 and (O.objective(p, xg) - f_ref) / f_ref <= 1.5e-6
+
+
+def test_handles_of_different_sizes_share_kernel_instances():
+    """A kernel's shared-memory limit belongs to the kernel, not to a handle: a handle created
+    after another one, for fewer rows, runs the same sweep-kernel instance with a smaller shared
+    memory footprint, and must not leave the first handle unable to launch it.  Both handles
+    solve (the older one first) to the gap and stationarity tolerances, confirmed at the
+    returned x in FP64 against the planted optimum."""
+    import torch
+    from paper_1701_04900_gb300 import Solver
+    from inputs import nesterov_lasso_torch
+    n, lam = 3000, 1.0
+    gens = [nesterov_lasso_torch(m, n, 30, lam=lam, seed=21 + i, device="cuda") for i, m in enumerate((20000, 18000))]
+    f_refs, solvers = [], []
+    for g, m in zip(gens, (20000, 18000)):
+        A = g["At"][:, :m].double().T
+        r = A @ g["x_star"].double() - g["b"].double()
+        f_refs.append(0.5 * float(r @ r) + lam * float(g["x_star"].double().abs().sum()))
+    for g, m, f in zip(gens, (20000, 18000), f_refs):
+        solvers.append(Solver(g["At"], g["b"], lam, m=m, block_w=32, mode="async", gamma=0.9, max_sweeps=3000,
+                              f_star=f))
+    stats = []
+    for g, m, f, s in zip(gens, (20000, 18000), f_refs, solvers):
+        x = torch.zeros(n, dtype=torch.float32, device="cuda")
+        st = s.solve(x)
+        assert st["status"] == 0, st
+        A = g["At"][:, :m].double().T
+        xd = x.double()
+        r = A @ xd - g["b"].double()
+        F = 0.5 * float(r @ r) + lam * float(xd.abs().sum())
+        assert (F - f) / f <= 1.5e-6
+        gcol = (A.T @ r).cpu().numpy()
+        dcol = (A * A).sum(0).cpu().numpy()
+        xh = xd.cpu().numpy()
+        merit = O.best_response(xh, gcol, dcol, lam, -np.inf, np.inf) - xh
+        assert O.stationarity(merit, xh) <= 1.5e-6
+        stats.append(st)
+    assert stats[0]["kernel_variant"] == stats[1]["kernel_variant"]
+    for s in solvers:
+        s.close()
