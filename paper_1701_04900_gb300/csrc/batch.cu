@@ -689,9 +689,11 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
                 hk.r_valid = false;
                 std::memset(&sts[i], 0, sizeof sts[i]);
             }
-            auto finish = [&](int i) {
+            // (a new host thread starts on device 0: it is moved to the batch's device; the
+            // calling thread's current device is left as it is)
+            auto finish = [&](int i, bool worker) {
                 const int k = rest[i];
-                if (cudaSetDevice(B.h[k]->device) != cudaSuccess) {
+                if (worker && cudaSetDevice(B.h[k]->device) != cudaSuccess) {
                     src[i] = ASYFLEXA_ECUDA;
                     return;
                 }
@@ -701,12 +703,12 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
                 std::vector<std::thread> th;
                 int next = 1;  // problem 0 runs on this thread; the others on threads of their own
                 try {
-                    for (; next < nrest; ++next) th.emplace_back(finish, next);
+                    for (; next < nrest; ++next) th.emplace_back(finish, next, true);
                 } catch (...) {
                 }
-                finish(0);
+                finish(0, false);
                 for (auto& t : th) t.join();
-                for (int i = next; i < nrest; ++i) finish(i);  // threads that could not be started
+                for (int i = next; i < nrest; ++i) finish(i, false);  // threads that could not be started
             }
             for (int i = 0; i < nrest; ++i) {
                 asyflexa_s& hk = *B.h[rest[i]];
