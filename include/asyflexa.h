@@ -408,7 +408,7 @@ int asyflexa_adjoint(const void* A, int64_t lda, int32_t a_dtype, int64_t m, int
  * launch ends with the bulk of the batch, and the last few problems run under a shape of
  * their own.  When at most 16 problems are left after a launch, they are finished instead,
  * side by side, by the single-problem async solver (asyflexa_solve on their own handles, each
- * on a stream and a host thread of its own) with max(1, m / (4 * block_w)) CTAs each, so
+ * on a stream and a host thread of its own) with max(1, m / (2 * block_w)) CTAs each, so
  * that they do not each hold one SM while the rest idle; their stats then carry batch_form
  * ASYFLEXA_BATCH_FORM_ASYNC.
  *

@@ -661,9 +661,9 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
         if (nrest <= kAsyncFinishMax && (handoff2 == 0 || kAsyncFinishEarly)) {
             // The few problems left would each hold one SM while the others idle: they are
             // finished side by side, each by the single-problem async solver on a stream of its
-            // own, with max(1, m / (4 w)) CTAs (about m / 4 columns in flight, as in the async
-            // rounds).  The async kernels have no waits between CTAs, so the solves need not be
-            // resident together.
+            // own, with max(1, m / (2 w)) CTAs (about m / 2 columns in flight; each stops on the
+            // solver's exact check).  The async kernels have no waits between CTAs, so the solves
+            // need not be resident together.
             BCK(cudaStreamSynchronize(B.stream), "synchronize");
             while (static_cast<int>(B.fin_streams.size()) < nrest) {
                 cudaStream_t fs = nullptr;
@@ -684,7 +684,7 @@ int gs_solve(asyflexa_batch_s& B, void* const* xs, const double* f_star, asyflex
                 hk.opts.f_star = f_star ? f_star[k] : NAN;
                 hk.sweep_ctas = static_cast<int>(std::max<int64_t>(
                     1, std::min<int64_t>({static_cast<int64_t>(hk.nblocks), static_cast<int64_t>(hk.sm_count),
-                                          hk.prob.m / (4 * static_cast<int64_t>(hk.opts.block_w))})));
+                                          hk.prob.m / (2 * static_cast<int64_t>(hk.opts.block_w))})));
                 hk.stream = B.fin_streams[i];
                 hk.r_valid = false;
                 std::memset(&sts[i], 0, sizeof sts[i]);
