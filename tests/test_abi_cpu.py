@@ -119,3 +119,88 @@ def test_null_arguments_rejected_without_gpu(L):
     assert L.asyflexa_step(None, None, 1) == native.EINVAL
     assert L.asyflexa_solve(None, None, None) == native.EINVAL
     assert L.asyflexa_destroy(None) == native.OK
+
+
+def test_batch_multi_adjoint_noalloc_validation_without_gpu(L):
+    """The batched, multi-lane, adjoint and no-allocation entry points check their arguments
+    before any CUDA call: null pointers, out-of-range counts and sizes, unsupported storage and
+    non-finite parameters come back as EINVAL or EUNSUPPORTED with a message, and nothing is
+    created."""
+    from paper_1701_04900_gb300 import native
+    err = lambda: L.asyflexa_last_error(None)
+    h = C.c_void_p()
+    o = native.default_opts()
+    p = native.Problem()
+    p.m, p.n, p.lda = 64, 32, 64
+    p.a_dtype = p.x_dtype = native.F32
+    p.A = p.b = 256                       # never dereferenced: every call below fails first
+
+    # batched
+    assert L.asyflexa_batch_create(None, C.byref(p), 1, C.byref(o), 0, None) == native.EINVAL
+    assert L.asyflexa_batch_create(C.byref(h), None, 1, C.byref(o), 0, None) == native.EINVAL
+    assert h.value is None
+    assert L.asyflexa_batch_create(C.byref(h), C.byref(p), 0, C.byref(o), 0, None) == native.EINVAL
+    assert b"count" in err()
+    o.block_w = 200
+    assert L.asyflexa_batch_create(C.byref(h), C.byref(p), 1, C.byref(o), 0, None) == native.EINVAL
+    assert b"block_w" in err() and h.value is None
+    o = native.default_opts()
+    assert L.asyflexa_batch_solve(None, None, None, None, None) == native.EINVAL
+    assert L.asyflexa_batch_check(None, None, None, None) == native.EINVAL
+    assert L.asyflexa_batch_destroy(None) == native.OK
+
+    # multi-lane
+    lam = (C.c_double * 65)(*([1.0] * 65))
+    Bp = C.c_void_p(256)
+    assert L.asyflexa_multi_create(None, C.byref(p), 2, Bp, 64, lam, C.byref(o), None) == native.EINVAL
+    assert L.asyflexa_multi_create(C.byref(h), C.byref(p), 2, None, 64, lam, C.byref(o), None) == native.EINVAL
+    for k in (0, 65):
+        assert L.asyflexa_multi_create(C.byref(h), C.byref(p), k, Bp, 64, lam, C.byref(o), None) == native.EINVAL
+        assert b"k must be" in err()
+    p.a_dtype = native.BF16
+    assert L.asyflexa_multi_create(C.byref(h), C.byref(p), 2, Bp, 64, lam, C.byref(o), None) == native.EUNSUPPORTED
+    p.a_dtype = native.F32
+    p.loss = native.LOSS_NCQUAD
+    assert L.asyflexa_multi_create(C.byref(h), C.byref(p), 2, Bp, 64, lam, C.byref(o), None) == native.EUNSUPPORTED
+    p.loss = native.LOSS_LASSO
+    assert L.asyflexa_multi_create(C.byref(h), C.byref(p), 2, Bp, 63, lam, C.byref(o), None) == native.EINVAL
+    assert b"ldb" in err()
+    for bad in (-1.0, float("nan"), float("inf")):
+        lam[1] = bad
+        assert L.asyflexa_multi_create(C.byref(h), C.byref(p), 2, Bp, 64, lam, C.byref(o), None) == native.EINVAL
+        assert b"lambda" in err()
+    assert h.value is None
+    assert L.asyflexa_multi_solve(None, None, 0, None, None, None) == native.EINVAL
+    assert L.asyflexa_multi_destroy(None) == native.OK
+
+    # adjoint
+    d = C.c_double()
+    A, x, v, db = C.c_void_p(256), C.c_void_p(512), C.c_void_p(768), C.c_void_p(1024)
+    adj = lambda A_, lda, dt, m, n, tol: L.asyflexa_adjoint(A_, lda, dt, m, n, x, v, tol, None, C.byref(d), db,
+                                                             None, None, None)
+    assert adj(A, 64, native.BF16, 64, 32, 1e-6) == native.EUNSUPPORTED
+    assert adj(None, 64, native.F32, 64, 32, 1e-6) == native.EINVAL
+    assert adj(A, 64, native.F32, 0, 32, 1e-6) == native.EINVAL
+    assert adj(A, 32, native.F32, 64, 32, 1e-6) == native.EINVAL         # lda < m
+    assert adj(A, 64, native.F32, 64, 32, float("nan")) == native.EINVAL
+    assert adj(A, 66, native.F32, 66, 32, 1e-6) == native.EINVAL         # lda * 4 not a multiple of 16
+    assert adj(C.c_void_p(260), 64, native.F32, 64, 32, 1e-6) == native.EINVAL  # misaligned A
+    assert b"aligned" in err()
+
+    # no-allocation residual
+    r = C.c_void_p(1024)
+    assert L.asyflexa_residual_noalloc(None, x, r, None) == native.EINVAL
+    q = native.Problem()
+    q.m, q.n, q.lda = 64, 32, 64
+    q.a_dtype, q.x_dtype = native.F32, native.F64
+    q.A = q.b = 256
+    assert L.asyflexa_residual_noalloc(C.byref(q), x, r, None) == native.EINVAL
+    assert b"x_dtype" in err()
+    q.x_dtype = native.F32
+    q.a_dtype = native.BF16                # BF16 storage without column scales
+    assert L.asyflexa_residual_noalloc(C.byref(q), x, r, None) == native.EINVAL
+    assert b"col_scale" in err()
+    q.a_dtype = native.F32
+    q.n = 1 << 20                          # beyond the stated column limit
+    assert L.asyflexa_residual_noalloc(C.byref(q), x, r, None) == native.EINVAL
+    assert b"no-allocation limit" in err()
