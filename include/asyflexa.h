@@ -463,8 +463,10 @@ int asyflexa_batch_create(asyflexa_batch_t* hb, const asyflexa_problem* probs, i
  * block_updates and status (ENOTCONV at max_sweeps, ENONFINITE if F became non-finite) as the
  * stopping test saw them, and block_w (Gauss-Seidel form: the tuned width, or as many columns
  * as one ring slot holds if fewer); Gauss-Seidel form also: seconds (the time its CTA worked
- * on it, global timer), kernel_variant and ctas_per_sm (of the launch that finished it) and
- * handed_over; for the exact check of asyflexa_check use asyflexa_batch_check.
+ * on it, global timer, plus the time of its async finish if it had one), kernel_variant and
+ * ctas_per_sm (of the launch that finished it; 0 after an async finish), batch_form
+ * (ASYFLEXA_BATCH_FORM_ASYNC after an async finish) and handed_over; for the exact check of
+ * asyflexa_check use asyflexa_batch_check.
  * total: sweeps (the largest number of sweeps of any problem; async rounds: tuning sweeps
  * included),
  * block_updates (all problems), seconds (CUDA events around the solve), block_w, batch_form,
